@@ -1,0 +1,154 @@
+/* fpclosure.h -- C ABI of the GB300 (sm_103a) cubic Fokker-Planck moment
+ * closure library, libfpclosure.so.
+ *
+ * The closure (paper Sec. 3.4-3.7): for every cell, the particles' central
+ * velocity moments up to fifth order are gathered, the 9x9 moment-matching
+ * system of Eq. system9x9 (Table 1 and its heat-flux rows) is assembled, and
+ * a partial-pivot solve gives the drift coefficients
+ *     Y = (C11, C12, C13, C22, C23, C33, G1, G2, G3)
+ * of the cubic drift Eq. cubic_drift (C_ij = c^(1)_ij, G_i = c^(2)_i).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Array pointers are DEVICE pointers owned by the caller; the library keeps
+ *   no reference after the call returns and allocates no device memory.
+ *   Scratch space comes from a caller-provided workspace sized by
+ *   fp_workspace_bytes() (a NULL workspace is allowed when the query says 0).
+ * - Calls are asynchronous on the caller's stream (a cudaStream_t passed as
+ *   fp_stream_t; NULL = legacy default stream).  The return code reports
+ *   argument validation and launch errors only; numerical problems of a cell
+ *   are reported in its flags, never as a call error.
+ * - Velocities are structure-of-arrays: v[0..n) = x, v[n..2n) = y,
+ *   v[2n..3n) = z, sorted by cell.  cell_offsets[n_cells+1] (int64) is
+ *   non-decreasing with cell_offsets[0] = 0 and cell_offsets[n_cells] = n;
+ *   cell c owns particles [cell_offsets[c], cell_offsets[c+1]).  Offsets live
+ *   on the device and are not checked by the host.
+ * - Moment vector of a cell (FP_NMOM = 30 doubles, row-major [n_cells][30]):
+ *     0      N (particle count)
+ *     1..3   U_i = <v_i>
+ *     4      theta = <c.c>/3, c = v - U
+ *     5..10  u_ij = <c_i c_j>            ij = 11,12,13,22,23,33
+ *     11..20 u_ijk = <c_i c_j c_k>       ijk = 111,112,113,122,123,133,
+ *                                               222,223,233,333
+ *     21..26 w_ij = <|c|^2 c_i c_j>      ij as above
+ *     27..29 z_i = <|c|^4 c_i>
+ *   (<.> is the mean over the cell's N particles; the u^(p) of Sec. 3.6).
+ * - Readings of the paper used throughout: the diffusion is D = 2 theta/tau
+ *   (the noise amplitude of Sec. 3.8); eps^2 = eps2_hat / (tau theta);
+ *   a cell that cannot be closed falls back to the linear drift of
+ *   Eq. linear_drift, C = -I/tau, G = 0.
+ */
+#ifndef FPCLOSURE_H
+#define FPCLOSURE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *fp_stream_t; /* same type as cudaStream_t */
+
+#define FP_NMOM 30
+#define FP_NCOEF 9
+
+/* return codes */
+enum {
+  FP_OK = 0,
+  FP_ERR_ARG = -1,         /* invalid argument (size, pointer, enum)        */
+  FP_ERR_CUDA = -2,        /* a CUDA launch or runtime call failed           */
+  FP_ERR_WORKSPACE = -3,   /* workspace missing or smaller than required     */
+  FP_ERR_UNSUPPORTED = -4  /* valid request this build does not implement   */
+};
+
+/* particle velocity storage type */
+enum { FP_V_F32 = 0, FP_V_F64 = 1 };
+
+/* moment precision:
+ * FP_PREC_FP64          moments accumulated in FP64 from the given velocities
+ * FP_PREC_FP32_MOMENTS  moments accumulated in FP32 on velocities centred on
+ *                       the cell mean and scaled by 1/sqrt(theta), with
+ *                       compensated (two-sum) combination of partial sums;
+ *                       promoted to FP64 before assembly.
+ * The 9x9 assembly and the pivoted solve are FP64 in both modes.  With FP32
+ * moments (relative error ~1e-7) a pivot below ~1e-6 max|A| cannot be told
+ * from zero, so that mode flags a cell singular when a pivot is
+ * <= max(pivot_rtol, FP_FP32_PIVOT_FLOOR) * max|A|. */
+#define FP_FP32_PIVOT_FLOOR 1e-6
+enum { FP_PREC_FP64 = 0, FP_PREC_FP32_MOMENTS = 1 };
+
+/* per-cell flag bits */
+enum {
+  FP_FLAG_FEW = 1,        /* N < min_particles: linear-drift fallback        */
+  FP_FLAG_SINGULAR = 2,   /* theta <= 0 or a pivot <= pivot_rtol max|A|      */
+  FP_FLAG_NONFINITE = 4,  /* non-finite moment, tau or solution              */
+  FP_FLAG_RANGE = 8,      /* surrogate feature outside its training box      */
+  FP_FLAG_ENERGY = 16,    /* surrogate energy residual above tolerance       */
+  FP_FLAG_FALLBACK = 32,  /* surrogate cell recomputed by the exact closure  */
+  FP_FLAG_ALPHA = 64      /* velocity update: alpha^2 <= 0, alpha set to 1   */
+};
+
+typedef struct {
+  double eps2_hat;          /* dimensionless cubic stabiliser (Sec. 3.4)     */
+  int32_t min_particles;    /* cells with fewer particles take the fallback  */
+  double pivot_rtol;        /* singular if |pivot| <= pivot_rtol * max|A|    */
+  double surr_energy_tol;   /* surrogate: max |energy residual| accepted     */
+  double surr_range_margin; /* surrogate: feature box widened by this margin
+                               (in standard deviations)                      */
+} fp_params;
+
+/* Defaults: eps2_hat 1e-3, min_particles 4, pivot_rtol 1e-13,
+ * surr_energy_tol 0.05, surr_range_margin 0.5. */
+void fp_default_params(fp_params *p);
+
+/* Text for a return code; text of the last error of the calling thread. */
+const char *fp_status_string(int status);
+const char *fp_last_error(void);
+int fp_version(void);
+
+/* Workspace (bytes) that fp_closure_exact needs for n_cells cells when
+ * moments_out is NULL (the moments are then kept in the workspace); 0 when
+ * the caller provides moments_out.  Aligned to 256 bytes. */
+size_t fp_workspace_bytes(int64_t n_cells, int64_t n_particles, int prec, int moments_out_given);
+
+/* The exact closure (Sec. 3.6-3.7, Eq. system9x9).
+ *   v             [3][n_particles], FP_V_F32 or FP_V_F64 (v_dtype)
+ *   cell_offsets  [n_cells+1] int64
+ *   tau           [n_cells] collision time tau = 2 mu / p (Eq. tau) per cell
+ *   p             host pointer to parameters (NULL = defaults)
+ *   prec          FP_PREC_FP64 or FP_PREC_FP32_MOMENTS
+ *   moments_out   [n_cells][FP_NMOM] f64, or NULL (then ws is used)
+ *   coeffs_out    [n_cells][9] f64
+ *   flags_out     [n_cells] int32 (FP_FLAG_FEW | FP_FLAG_SINGULAR |
+ *                 FP_FLAG_NONFINITE; flagged cells hold C = -I/tau, G = 0)
+ *   ws, ws_bytes  device workspace, >= fp_workspace_bytes(...)
+ * n_cells = 0 is a no-op; n_particles = 0 with n_cells > 0 gives empty
+ * (FP_FLAG_FEW) cells. */
+int fp_closure_exact(const void *v, int v_dtype, int64_t n_particles, const int64_t *cell_offsets,
+                     int64_t n_cells, const double *tau, const fp_params *p, int prec,
+                     double *moments_out, double *coeffs_out, int32_t *flags_out, void *ws,
+                     size_t ws_bytes, fp_stream_t stream);
+
+/* The two halves of fp_closure_exact, for callers that need the moments alone
+ * (the surrogate's features, the velocity update) or hold them already.
+ *
+ * fp_moments: the per-cell moment vectors (Sec. 3.6), same arguments and
+ * precision modes as fp_closure_exact; moments_out [n_cells][FP_NMOM] f64
+ * required.  No workspace. */
+int fp_moments(const void *v, int v_dtype, int64_t n_particles, const int64_t *cell_offsets, int64_t n_cells,
+               int prec, double *moments_out, fp_stream_t stream);
+
+/* fp_closure_solve: assembly of Eq. system9x9 from given moment vectors and
+ * the FP64 pivoted solve, one thread per cell.  moments [n_cells][FP_NMOM]
+ * f64 (as fp_moments writes them), tau [n_cells]; prec = the precision the
+ * moments were gathered in (selects the singularity threshold); outputs as
+ * in fp_closure_exact.  No workspace. */
+int fp_closure_solve(const double *moments, const double *tau, int64_t n_cells, const fp_params *p, int prec,
+                     double *coeffs_out, int32_t *flags_out, fp_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FPCLOSURE_H */

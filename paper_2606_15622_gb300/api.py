@@ -1,0 +1,178 @@
+"""Thin Python binding of libfpclosure.so (C ABI in include/fpclosure.h).
+
+Argument marshalling only: every step of the closure runs in the library's
+CUDA kernels.  Tensors must be CUDA tensors; the call is enqueued on the
+current torch stream (or the one given).  There is no CPU fallback: without
+the compiled library or a GPU every entry point raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+NMOM = 30
+NCOEF = 9
+FP_OK, FP_ERR_ARG, FP_ERR_CUDA, FP_ERR_WORKSPACE, FP_ERR_UNSUPPORTED = 0, -1, -2, -3, -4
+V_F32, V_F64 = 0, 1
+PREC_FP64, PREC_FP32_MOMENTS = 0, 1
+FLAG_FEW, FLAG_SINGULAR, FLAG_NONFINITE, FLAG_RANGE, FLAG_ENERGY, FLAG_FALLBACK, FLAG_ALPHA = 1, 2, 4, 8, 16, 32, 64
+FALLBACK_FLAGS = FLAG_FEW | FLAG_SINGULAR | FLAG_NONFINITE
+FP32_PIVOT_FLOOR = 1e-6
+
+_PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32_MOMENTS, PREC_FP64: PREC_FP64, PREC_FP32_MOMENTS: PREC_FP32_MOMENTS}
+
+
+class FPError(RuntimeError):
+    pass
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("eps2_hat", ctypes.c_double), ("min_particles", ctypes.c_int32),
+                ("pivot_rtol", ctypes.c_double), ("surr_energy_tol", ctypes.c_double),
+                ("surr_range_margin", ctypes.c_double)]
+
+
+_LIB = None
+_LOCK = threading.Lock()
+_vp, _i64, _i32, _sz, _dbl, _u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t, ctypes.c_double, ctypes.c_uint64
+
+# name -> (restype, argtypes); the exported surface of include/fpclosure.h
+SIGNATURES = {
+    "fp_default_params": (None, [ctypes.POINTER(Params)]),
+    "fp_status_string": (ctypes.c_char_p, [_i32]),
+    "fp_last_error": (ctypes.c_char_p, []),
+    "fp_version": (_i32, []),
+    "fp_workspace_bytes": (_sz, [_i64, _i64, _i32, _i32]),
+    "fp_closure_exact": (_i32, [_vp, _i32, _i64, _vp, _i64, _vp, ctypes.POINTER(Params), _i32,
+                                _vp, _vp, _vp, _vp, _sz, _vp]),
+    "fp_moments": (_i32, [_vp, _i32, _i64, _vp, _i64, _i32, _vp, _vp]),
+    "fp_closure_solve": (_i32, [_vp, _vp, _i64, ctypes.POINTER(Params), _i32, _vp, _vp, _vp]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libfpclosure.so (building it in-tree first if it is stale)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            path = _build.build()
+            if not os.path.exists(path):
+                raise FPError(f"libfpclosure.so missing at {path}")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _LIB = L
+    return _LIB
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().fp_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _check(rc: int, what: str):
+    if rc != FP_OK:
+        L = lib()
+        raise FPError(f"{what}: {L.fp_status_string(rc).decode()} ({L.fp_last_error().decode()})")
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is not None and (not isinstance(t, torch.Tensor) or not t.is_cuda):
+            raise FPError("arguments must be CUDA tensors (there is no CPU path)")
+        if t is not None and not t.is_contiguous():
+            raise FPError("arguments must be contiguous")
+
+
+def _vdtype(v):
+    if v.dtype == torch.float32:
+        return V_F32
+    if v.dtype == torch.float64:
+        return V_F64
+    raise FPError(f"velocity dtype {v.dtype} (float32 or float64 expected)")
+
+
+def workspace_bytes(n_cells, n_particles, prec="fp32", moments_out_given=False) -> int:
+    return int(lib().fp_workspace_bytes(n_cells, n_particles, _PREC.get(prec, prec), int(bool(moments_out_given))))
+
+
+def fp_closure_exact(v, offsets, tau, params: Params | None = None, prec="fp32", moments_out=None,
+                     coeffs_out=None, flags_out=None, workspace=None, want_moments=True, stream=None):
+    """The exact closure.  v [3, n_p] (f32/f64), offsets [n_cells+1] int64,
+    tau [n_cells] f64 -> (moments [n_cells, 30] or None, coeffs [n_cells, 9],
+    flags [n_cells])."""
+    n_cells = offsets.numel() - 1
+    n_p = v.shape[-1] if v.dim() == 2 else v.numel() // 3
+    dev = offsets.device
+    if want_moments and moments_out is None:
+        moments_out = torch.empty((n_cells, NMOM), dtype=torch.float64, device=dev)
+    if coeffs_out is None:
+        coeffs_out = torch.empty((n_cells, NCOEF), dtype=torch.float64, device=dev)
+    if flags_out is None:
+        flags_out = torch.empty((n_cells,), dtype=torch.int32, device=dev)
+    _need_cuda(v, offsets, tau, moments_out, coeffs_out, flags_out, workspace)
+    need = workspace_bytes(n_cells, n_p, prec, moments_out is not None)
+    if need and workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    p = params if params is not None else default_params()
+    rc = lib().fp_closure_exact(_ptr(v), _vdtype(v), n_p, _ptr(offsets), n_cells, _ptr(tau), ctypes.byref(p),
+                                _PREC.get(prec, prec), _ptr(moments_out), _ptr(coeffs_out), _ptr(flags_out),
+                                _ptr(workspace), ws_bytes, _stream(stream))
+    _check(rc, "fp_closure_exact")
+    return moments_out, coeffs_out, flags_out
+
+
+def fp_moments(v, offsets, prec="fp32", moments_out=None, stream=None):
+    """Per-cell moment vectors [n_cells, 30] (f64)."""
+    n_cells = offsets.numel() - 1
+    n_p = v.shape[-1] if v.dim() == 2 else v.numel() // 3
+    if moments_out is None:
+        moments_out = torch.empty((n_cells, NMOM), dtype=torch.float64, device=offsets.device)
+    _need_cuda(v, offsets, moments_out)
+    rc = lib().fp_moments(_ptr(v), _vdtype(v), n_p, _ptr(offsets), n_cells, _PREC.get(prec, prec),
+                          _ptr(moments_out), _stream(stream))
+    _check(rc, "fp_moments")
+    return moments_out
+
+
+def fp_closure_solve(moments, tau, params: Params | None = None, prec="fp32", coeffs_out=None, flags_out=None,
+                     stream=None):
+    """Assembly + pivoted FP64 solve from moment vectors -> (coeffs, flags)."""
+    n_cells = moments.shape[0]
+    dev = moments.device
+    if coeffs_out is None:
+        coeffs_out = torch.empty((n_cells, NCOEF), dtype=torch.float64, device=dev)
+    if flags_out is None:
+        flags_out = torch.empty((n_cells,), dtype=torch.int32, device=dev)
+    _need_cuda(moments, tau, coeffs_out, flags_out)
+    p = params if params is not None else default_params()
+    rc = lib().fp_closure_solve(_ptr(moments), _ptr(tau), n_cells, ctypes.byref(p), _PREC.get(prec, prec),
+                                _ptr(coeffs_out),
+                                _ptr(flags_out), _stream(stream))
+    _check(rc, "fp_closure_solve")
+    return coeffs_out, flags_out

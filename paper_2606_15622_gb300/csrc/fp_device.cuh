@@ -1,0 +1,79 @@
+// fp_device.cuh -- device helpers shared by the closure kernels (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/fpclosure.h"
+
+namespace fpc {
+
+// moment slots (layout documented in fpclosure.h)
+constexpr int kN = 0, kU = 1, kTheta = 4, kU2 = 5, kU3 = 11, kW = 21, kZ = 27;
+constexpr int kNSum = 25;  // gathered central sums: u2 (6), u3 (10), w (6), z (3)
+
+// Error-free transformation a + b = s + e (Knuth two-sum).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Order of the central moment held in gathered sum slot q (0..24).
+__host__ __device__ constexpr int sum_order(int q) { return q < 6 ? 2 : (q < 16 ? 3 : (q < 22 ? 4 : 5)); }
+
+// Butterfly all-reduce over groups of G consecutive lanes (all 32 lanes call).
+template <int G, typename T>
+__device__ __forceinline__ T group_allreduce(T x) {
+#pragma unroll
+  for (int o = G / 2; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Reduce-scatter of 32 slots over groups of G lanes: on return lane l of the
+// group holds, in v[0 .. 32/G), the group sums of slots [l*32/G, (l+1)*32/G).
+template <int G, typename T>
+__device__ __forceinline__ void group_reduce_scatter(T (&v)[32], int lane) {
+#pragma unroll
+  for (int lvl = 0; (G >> (lvl + 1)) >= 1; ++lvl) {
+    const int o = G >> (lvl + 1);
+    const int half = 16 >> lvl;
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < half; ++j) {
+      T send = up ? v[j] : v[j + half];
+      T keep = up ? v[j + half] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+}
+
+// The same with (hi, lo) compensated pairs: hi sums by two-sum, errors and
+// lo parts accumulated in lo.
+template <int G>
+__device__ __forceinline__ void group_reduce_scatter2(float (&hi)[32], float (&lo)[32], int lane) {
+#pragma unroll
+  for (int lvl = 0; (G >> (lvl + 1)) >= 1; ++lvl) {
+    const int o = G >> (lvl + 1);
+    const int half = 16 >> lvl;
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < half; ++j) {
+      float sh = up ? hi[j] : hi[j + half];
+      float sl = up ? lo[j] : lo[j + half];
+      float kh = up ? hi[j + half] : hi[j];
+      float kl = up ? lo[j + half] : lo[j];
+      float rh = __shfl_xor_sync(0xffffffffu, sh, o);
+      float rl = __shfl_xor_sync(0xffffffffu, sl, o);
+      float s, e;
+      two_sum(kh, rh, s, e);
+      hi[j] = s;
+      lo[j] = (kl + rl) + e;
+    }
+  }
+}
+
+template <typename VT>
+__device__ __forceinline__ VT ldg_v(const VT *p) { return __ldg(p); }
+
+}  // namespace fpc
