@@ -169,6 +169,19 @@ def run_ours(args):
         torch.cuda.synchronize()
         return [a.elapsed_time(b) for a, b in evs]
 
+    if args.only:
+        # profiling mode: launch one kernel `steps` times (no timing output)
+        fns = {"gather": lambda: api.fp_moments(v32, off, prec="fp32", moments_out=mom, stream=stream),
+               "gather64": lambda: api.fp_moments(v64, off, prec="fp64", moments_out=mom, stream=stream),
+               "solve": lambda: api.fp_closure_solve(mom, tau, params=prm, prec="fp32", coeffs_out=coeffs,
+                                                     flags_out=flags, stream=stream)}
+        api.fp_moments(v32, off, prec="fp32", moments_out=mom, stream=stream)
+        for _ in range(args.steps):
+            fns[args.only]()
+        torch.cuda.synchronize()
+        print(json.dumps({"profiled": args.only, "launches": args.steps, "config": pop.name}))
+        return
+
     # ---- headline: the timed region ------------------------------------
     for _ in range(args.warmup):
         step()
@@ -339,6 +352,8 @@ def main():
     ap.add_argument("--config", default="cylinder", choices=["cylinder", "cavity", "couette"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", choices=["gather", "gather64", "solve"], default=None,
+                    help="profiling mode: launch one kernel --steps times, print no bench line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

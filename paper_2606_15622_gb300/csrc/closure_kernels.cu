@@ -486,8 +486,16 @@ static void launch_gather_t(const void *v, int v_dtype, int64_t np, const int64_
   }
 }
 
+bool launch_gather_tile(const float *v, int64_t np, const int64_t *off, int64_t n_cells, double *mom,
+                        cudaStream_t st, int sm_count);
+
 void launch_gather(const void *v, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, int prec,
                    double *mom, cudaStream_t st) {
+  // FP32 moments of FP32 velocities: shared-memory staged tiles (16-byte
+  // aligned velocity arrays); every other combination: direct loads.
+  if (prec == FP_PREC_FP32_MOMENTS && v_dtype == FP_V_F32 &&
+      launch_gather_tile((const float *)v, np, off, n_cells, mom, st, sm_count()))
+    return;
   launch_gather_t<8>(v, v_dtype, np, off, n_cells, prec, mom, st);
 }
 

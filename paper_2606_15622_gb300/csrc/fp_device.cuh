@@ -76,4 +76,44 @@ __device__ __forceinline__ void group_reduce_scatter2(float (&hi)[32], float (&l
 template <typename VT>
 __device__ __forceinline__ VT ldg_v(const VT *p) { return __ldg(p); }
 
+// Exact float -> double by integer bit manipulation (no FP64-pipe work), with
+// an optional power-of-two scale 2^exp_add folded into the exponent.
+// Normal floats and zeros convert exactly; FP32 subnormals flush to zero;
+// results outside the double range saturate to zero / infinity; inf and NaN
+// pass through.
+__device__ __forceinline__ double f2d_exact(float f, int exp_add = 0) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t sign = u & 0x80000000u;
+  const int e = (int)((u >> 23) & 0xffu);
+  const uint32_t man = u & 0x7fffffu;
+  const int ed = e + (1023 - 127) + exp_add;
+  uint32_t hi = sign | (man >> 3), lo = man << 29;
+  if (e == 0 || ed <= 0) {
+    hi = sign;
+    lo = 0u;
+  } else if (e == 255 || ed >= 2047) {
+    hi |= 0x7ff00000u;
+    if (e != 255) {
+      hi = sign | 0x7ff00000u;
+      lo = 0u;
+    }
+  } else {
+    hi |= (uint32_t)ed << 20;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// Double-float helpers (pairs of FP32 carrying ~46 significant bits).
+// (rh, rl) ~ 1/n: rh the rounded reciprocal, rl its residual.
+__device__ __forceinline__ void df_recip(float n, float &rh, float &rl) {
+  rh = __frcp_rn(n);
+  rl = fmaf(-rh, n, 1.f) * rh;
+}
+// (hi + lo) * (rh + rl) as a double-float (p, e)
+__device__ __forceinline__ void df_scale(float hi, float lo, float rh, float rl, float &p, float &e) {
+  p = hi * rh;
+  e = fmaf(hi, rh, -p);
+  e = fmaf(hi, rl, fmaf(lo, rh, e));
+}
+
 }  // namespace fpc
