@@ -5,19 +5,22 @@
 // to persistent CTAs.  Each CTA is warp-specialised:
 //   * a producer warp reads the chunk's cell offsets (one coalesced load),
 //     splits the chunk into sub-tiles of whole cells holding at most kSubP
-//     particles, and streams each sub-tile's three SoA component ranges
-//     (widened to 16-byte boundaries) into a ring of kSlots shared-memory
-//     slots with cp.async.bulk, completing on the slot's `full` mbarrier;
-//   * four consumer warps take the sub-tiles in the same order, reduce two
-//     cells per warp (16 lanes per cell) from shared memory, and release the
-//     slot on its `empty` mbarrier.
-// A cell larger than a sub-tile is reduced by one group straight from global
-// memory.  No global-memory round trip sits on a consumer's path; the
-// producer runs up to kSlots sub-tiles ahead.
+//     particles, ranks the sub-tile's cells by size, and streams the three SoA
+//     component ranges (widened to 16-byte boundaries) into a ring of kSlots
+//     shared-memory slots with cp.async.bulk, completing on the slot's `full`
+//     mbarrier;
+//   * consumer warps take the sub-tiles in the same order and reduce eight
+//     cells per warp task (four lanes per cell, the eight cells of a task
+//     consecutive in size order so their loops have similar trip counts)
+//     from shared memory, then release the slot on its `empty` mbarrier.
+// A cell larger than a sub-tile is reduced straight from global memory.  No
+// global-memory round trip sits on a consumer's path; the producer runs up
+// to kSlots sub-tiles ahead.
 //
-// Moments leave through FP32 double-float arithmetic and an integer
-// float->double conversion: the FP64 pipe (one warp instruction per ~16 SM
-// cycles on GB300) sees ~3 instructions per cell.
+// Per lane the sums are plain FP32 over blocks of BLK particles, blocks
+// folded with two-sum; lanes combine by a reduce-scatter.  Promotion to FP64
+// scales by the power of two in FP32 (exact), converts hi and lo parts and
+// adds them: one FP64-pipe instruction per moment.
 #include <cstdint>
 
 #include "fp_device.cuh"
@@ -31,7 +34,8 @@ constexpr int kCapF = kSubP + 8;             // floats per component slot (align
 constexpr int kSlots = 4;
 constexpr int kConsumerWarps = 4;
 constexpr int kTileThreads = 32 * (1 + kConsumerWarps);
-constexpr int kTileG = 16;                   // lanes per cell
+constexpr int kTileG = 4;                    // lanes per cell
+constexpr int kCellsPerTask = 32 / kTileG;   // cells per warp task
 constexpr int kSlotFloats = 3 * kCapF;
 constexpr size_t kTileSmem = (size_t)kSlots * kSlotFloats * sizeof(float);
 
@@ -42,16 +46,17 @@ struct SlotMeta {
   int big;                        // 1: the single cell cs is reduced from global memory
   int done;                       // 1: no more sub-tiles for this CTA
   int64_t offs[kChunkCells + 1];  // off[cs .. ce]
+  uint8_t order[kChunkCells];     // sub-tile cells (relative to cs), largest first
 };
 
-// One cell per 16-lane group, both groups of the warp in lockstep; px/py/pz
+// One cell per kTileG-lane group, the warp's groups in lockstep; px/py/pz
 // point at the cell's first particle (shared or global memory).
 template <bool kShared>
-__device__ __forceinline__ void reduce_cell_pair(bool valid, int n, const float *px, const float *py,
-                                                 const float *pz, int64_t c, double *__restrict__ mom, int lane) {
+__device__ __forceinline__ void reduce_cells(bool valid, int n, const float *px, const float *py, const float *pz,
+                                             int64_t c, double *__restrict__ mom, int lane) {
   constexpr int G = kTileG;
   constexpr int K = 32 / G;
-  constexpr int BLK = 8;
+  constexpr int BLK = 32;  // particles per lane summed plainly before a two-sum fold
   const int lg = lane & (G - 1);
   auto ld = [](const float *p, int i) -> float {
     if (kShared) return p[i];
@@ -65,17 +70,21 @@ __device__ __forceinline__ void reduce_cell_pair(bool valid, int n, const float 
     v0z = ld(pz, 0);
   }
   const int itmax = __reduce_max_sync(0xffffffffu, (n + G - 1) / G);
-  // pass A: offsets from the first particle
+  // pass A: offsets from the first particle (out-of-range slots read particle
+  // 0 and are zeroed, which keeps the loop free of branches)
   float sx = 0.f, sy = 0.f, sz = 0.f, sq = 0.f;
   for (int it = 0; it < itmax; ++it) {
     const int i = it * G + lg;
-    if (i < n) {
-      const float dx = ld(px, i) - v0x, dy = ld(py, i) - v0y, dz = ld(pz, i) - v0z;
-      sx += dx;
-      sy += dy;
-      sz += dz;
-      sq = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, sq)));
-    }
+    const bool in = i < n;
+    const int ii = in ? i : 0;
+    float dx = ld(px, ii) - v0x, dy = ld(py, ii) - v0y, dz = ld(pz, ii) - v0z;
+    dx = in ? dx : 0.f;
+    dy = in ? dy : 0.f;
+    dz = in ? dz : 0.f;
+    sx += dx;
+    sy += dy;
+    sz += dz;
+    sq = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, sq)));
   }
   sx = group_allreduce<G>(sx);
   sy = group_allreduce<G>(sy);
@@ -89,9 +98,13 @@ __device__ __forceinline__ void reduce_cell_pair(bool valid, int n, const float 
   if (th_est > 0.f) {
     int ex;
     frexpf(th_est, &ex);
-    ks = -(ex / 2);
+    ks = max(-20, min(20, -(ex / 2)));
   }
   const float s = ldexpf(1.f, ks);
+  const float ox = v0x + mx, oy = v0y + my, oz = v0z + mz;
+  (void)ox;
+  (void)oy;
+  (void)oz;
 
   // pass B: centred, scaled sums; FP32 blocks of BLK particles per lane folded by two-sum
   float hi[32], lo[32];
@@ -107,22 +120,23 @@ __device__ __forceinline__ void reduce_cell_pair(bool valid, int n, const float 
     const int itend = min(it0 + BLK, itmax);
     for (int it = it0; it < itend; ++it) {
       const int i = it * G + lg;
-      if (i < n) {
-        const float wx = ((ld(px, i) - v0x) - mx) * s;
-        const float wy = ((ld(py, i) - v0y) - my) * s;
-        const float wz = ((ld(pz, i) - v0z) - mz) * s;
-        const float xx = wx * wx, xy = wx * wy, xz = wx * wz, yy = wy * wy, yz = wy * wz, zz = wz * wz;
-        t[0] += xx; t[1] += xy; t[2] += xz; t[3] += yy; t[4] += yz; t[5] += zz;
-        t[6] = fmaf(xx, wx, t[6]);  t[7] = fmaf(xx, wy, t[7]);   t[8] = fmaf(xx, wz, t[8]);
-        t[9] = fmaf(xy, wy, t[9]);  t[10] = fmaf(xy, wz, t[10]); t[11] = fmaf(xz, wz, t[11]);
-        t[12] = fmaf(yy, wy, t[12]); t[13] = fmaf(yy, wz, t[13]); t[14] = fmaf(yz, wz, t[14]);
-        t[15] = fmaf(zz, wz, t[15]);
-        const float r2 = xx + yy + zz;
-        t[16] = fmaf(r2, xx, t[16]); t[17] = fmaf(r2, xy, t[17]); t[18] = fmaf(r2, xz, t[18]);
-        t[19] = fmaf(r2, yy, t[19]); t[20] = fmaf(r2, yz, t[20]); t[21] = fmaf(r2, zz, t[21]);
-        const float r4 = r2 * r2;
-        t[22] = fmaf(r4, wx, t[22]); t[23] = fmaf(r4, wy, t[23]); t[24] = fmaf(r4, wz, t[24]);
-      }
+      const bool in = i < n;
+      const int ii = in ? i : 0;
+      const float sm = in ? s : 0.f;
+      const float wx = ((ld(px, ii) - v0x) - mx) * sm;
+      const float wy = ((ld(py, ii) - v0y) - my) * sm;
+      const float wz = ((ld(pz, ii) - v0z) - mz) * sm;
+      const float xx = wx * wx, xy = wx * wy, xz = wx * wz, yy = wy * wy, yz = wy * wz, zz = wz * wz;
+      t[0] += xx; t[1] += xy; t[2] += xz; t[3] += yy; t[4] += yz; t[5] += zz;
+      t[6] = fmaf(xx, wx, t[6]);  t[7] = fmaf(xx, wy, t[7]);   t[8] = fmaf(xx, wz, t[8]);
+      t[9] = fmaf(xy, wy, t[9]);  t[10] = fmaf(xy, wz, t[10]); t[11] = fmaf(xz, wz, t[11]);
+      t[12] = fmaf(yy, wy, t[12]); t[13] = fmaf(yy, wz, t[13]); t[14] = fmaf(yz, wz, t[14]);
+      t[15] = fmaf(zz, wz, t[15]);
+      const float r2 = xx + yy + zz;
+      t[16] = fmaf(r2, xx, t[16]); t[17] = fmaf(r2, xy, t[17]); t[18] = fmaf(r2, xz, t[18]);
+      t[19] = fmaf(r2, yy, t[19]); t[20] = fmaf(r2, yz, t[20]); t[21] = fmaf(r2, zz, t[21]);
+      const float r4 = r2 * r2;
+      t[22] = fmaf(r4, wx, t[22]); t[23] = fmaf(r4, wy, t[23]); t[24] = fmaf(r4, wz, t[24]);
     }
     if (it0 == 0) {
 #pragma unroll
@@ -140,7 +154,8 @@ __device__ __forceinline__ void reduce_cell_pair(bool valid, int n, const float 
   group_reduce_scatter<G>(hi, lane);
   if (itmax > BLK) group_reduce_scatter<G>(lo, lane);  // warp-uniform branch
 
-  // promote: mean = (hi + lo) / n, then undo the 2^(ks * order) scaling
+  // promote: mean = (hi + lo) / n with the 2^(ks * order) scaling undone in
+  // FP32 (a power of two: exact), then two conversions and one FP64 add
   double val[K];
 #pragma unroll
   for (int j = 0; j < K; ++j) {
@@ -148,7 +163,8 @@ __device__ __forceinline__ void reduce_cell_pair(bool valid, int n, const float 
     const int ord = q < kNSum ? sum_order(q) : 0;
     float p, e;
     df_scale(hi[j], lo[j], rh, rl, p, e);
-    val[j] = f2d_exact(p, -ks * ord) + f2d_exact(e, -ks * ord);
+    const float sc = ldexpf(1.f, -ks * ord);
+    val[j] = (double)(p * sc) + (double)(e * sc);
   }
   const int gbase = lane & ~(G - 1);
   const double u11 = __shfl_sync(0xffffffffu, val[0 % K], gbase + 0 / K);
@@ -164,10 +180,10 @@ __device__ __forceinline__ void reduce_cell_pair(bool valid, int n, const float 
   if (lg >= 1 && lg <= 3) {
     const float v0 = lg == 1 ? v0x : (lg == 2 ? v0y : v0z);
     const float m = lg == 1 ? mx : (lg == 2 ? my : mz);
-    mo[kU + lg - 1] = f2d_exact(v0) + f2d_exact(m);
+    mo[kU + lg - 1] = (double)v0 + (double)m;
   }
   if (lg == 0) {
-    mo[kN] = n < (1 << 24) ? f2d_exact((float)n) : (double)n;
+    mo[kN] = (double)n;
     mo[kTheta] = (u11 + u22 + u33) * (1.0 / 3.0);
   }
 }
@@ -180,6 +196,38 @@ __device__ void mark_failed(int64_t n_cells, int64_t n_chunks, double *__restric
     const int64_t c1 = c0 + kChunkCells < n_cells ? c0 + kChunkCells : n_cells;
     for (int64_t c = c0 + tid; c < c1; c += kTileThreads) mom[c * FP_NMOM + kTheta] = __longlong_as_double(-1ll);
   }
+}
+
+// Order the sub-tile's cells by size, largest first (ties: lower index
+// first), with a 64-element bitonic network: lane l holds elements l and
+// l + 32; keys pack ((size + 1) << 6) | (63 - index), 0 for absent cells.
+__device__ __forceinline__ void rank_cells(int ncell, int na, int nb, uint8_t *order, int lane) {
+  uint32_t ka = lane < ncell ? ((uint32_t)(na + 1) << 6) | (uint32_t)(63 - lane) : 0u;
+  uint32_t kb = lane + 32 < ncell ? ((uint32_t)(nb + 1) << 6) | (uint32_t)(31 - lane) : 0u;
+#pragma unroll
+  for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j >= 1; j >>= 1) {
+      // element indices ea = lane, eb = lane + 32; max goes to the lower index
+      // of a pair inside blocks with (e & k) == 0, to the higher one otherwise
+      const int ea = lane, eb = lane + 32;
+      if (j == 32) {
+        const uint32_t hi = ka > kb ? ka : kb, lo = ka > kb ? kb : ka;
+        const bool up = (ea & k) == 0;  // same block for ea and eb when k = 64
+        ka = up ? hi : lo;
+        kb = up ? lo : hi;
+      } else {
+        const uint32_t pa = __shfl_xor_sync(0xffffffffu, ka, j);
+        const uint32_t pb = __shfl_xor_sync(0xffffffffu, kb, j);
+        const bool lower = (lane & j) == 0;
+        const bool upa = (ea & k) == 0, upb = (eb & k) == 0;
+        ka = (lower == upa) ? (ka > pa ? ka : pa) : (ka > pa ? pa : ka);
+        kb = (lower == upb) ? (kb > pb ? kb : pb) : (kb > pb ? pb : kb);
+      }
+    }
+  }
+  if (lane < ncell) order[lane] = (uint8_t)(63 - (ka & 63u));
+  if (lane + 32 < ncell) order[lane + 32] = (uint8_t)(63 - (kb & 63u));
 }
 
 __global__ void __launch_bounds__(kTileThreads, 2)
@@ -215,17 +263,32 @@ __global__ void __launch_bounds__(kTileThreads, 2)
       if (use > 0 && !mbar_wait_bounded(&empty_bar[s], (uint32_t)((use - 1) & 1))) ok = false;
       return s;
     };
+    // lanes hold off[c0 + lane] and off[c0 + 32 + lane] (indices clamped to
+    // c1); the next chunk's offsets are loaded while this one is streamed
+    auto load_chunk = [&](int64_t jj, int64_t &q0, int64_t &q1, int64_t &qe) {
+      if (jj >= n_chunks) return;
+      const int64_t b0 = jj * kChunkCells;
+      const int64_t b1 = b0 + kChunkCells < n_cells ? b0 + kChunkCells : n_cells;
+      q0 = off[b0 + lane < b1 ? b0 + lane : b1];
+      q1 = off[b0 + 32 + lane < b1 ? b0 + 32 + lane : b1];
+      qe = off[b1];
+    };
+    int64_t nx0 = 0, nx1 = 0, nxe = 0;
+    load_chunk(blockIdx.x, nx0, nx1, nxe);
     for (int64_t j = blockIdx.x; ok && j < n_chunks; j += gridDim.x) {
       const int64_t c0 = j * kChunkCells;
       const int64_t c1 = c0 + kChunkCells < n_cells ? c0 + kChunkCells : n_cells;
-      // this lane's two offsets: off[c0 + lane], off[c0 + 32 + lane] (clamped to c1)
       const int64_t i0 = c0 + lane, i1 = c0 + 32 + lane;
-      const int64_t o0 = off[i0 < c1 ? i0 : c1];
-      const int64_t o1 = off[i1 < c1 ? i1 : c1];
-      const int64_t oend = off[c1];
+      const int64_t o0 = nx0, o1 = nx1, oend = nxe;
+      load_chunk(j + gridDim.x, nx0, nx1, nxe);
+      // per-cell sizes of the lane's two cells (cell i0 and i1)
+      const int64_t o0n = __shfl_down_sync(0xffffffffu, o0, 1);
+      const int64_t o1f = __shfl_sync(0xffffffffu, o1, 0);
+      const int64_t o1n = __shfl_down_sync(0xffffffffu, o1, 1);
+      const int64_t e0 = lane < 31 ? o0n : o1f;           // off[i0 + 1]
+      const int64_t e1 = lane < 31 ? o1n : oend;          // off[i1 + 1]
       int64_t cs = c0;
       while (ok && cs < c1) {
-        // offset of cell cs (lanes hold off[c0..c0+63])
         const int rs = (int)(cs - c0);
         const int64_t start = rs < 32 ? __shfl_sync(0xffffffffu, o0, rs) : __shfl_sync(0xffffffffu, o1, rs - 32);
         // ce = last c in (cs, c1] with off[c] - start <= kSubP
@@ -249,10 +312,28 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         const int64_t pend = re < 32 ? __shfl_sync(0xffffffffu, o0, re)
                                      : (re < 64 ? __shfl_sync(0xffffffffu, o1, re - 32) : oend);
         SlotMeta &M = meta[s];
-        // offsets of the sub-tile's cells
         if (i0 >= cs && i0 <= ce) M.offs[i0 - cs] = o0;
         if (i1 >= cs && i1 <= ce) M.offs[i1 - cs] = o1;
         if (lane == 0 && ce == c1 && c1 - c0 == kChunkCells) M.offs[ce - cs] = oend;
+        // size ranking of the sub-tile's cells (cell cs + r held by lane r or r - 32)
+        {
+          const int ncell = (int)(ce - cs);
+          const int la = (int)(i0 - cs), lb = (int)(i1 - cs);  // this lane's cells, relative
+          // gather sizes so that lane r holds cell cs + r (and cs + r + 32)
+          const int64_t sa_abs = (i0 >= cs && i0 < ce) ? e0 - o0 : 0;
+          const int64_t sb_abs = (i1 >= cs && i1 < ce) ? e1 - o1 : 0;
+          (void)la;
+          (void)lb;
+          // cell cs + r lives at absolute index c0 + rs + r
+          const int src_a = rs + lane, src_b = rs + lane + 32;
+          const int64_t na_a = __shfl_sync(0xffffffffu, sa_abs, src_a & 31);
+          const int64_t na_b = __shfl_sync(0xffffffffu, sb_abs, src_a & 31);
+          const int64_t nb_a = __shfl_sync(0xffffffffu, sa_abs, src_b & 31);
+          const int64_t nb_b = __shfl_sync(0xffffffffu, sb_abs, src_b & 31);
+          const int na = (int)(src_a < 32 ? na_a : na_b);
+          const int nb = (int)(src_b < 32 ? nb_a : (src_b < 64 ? nb_b : 0));
+          rank_cells(ncell, na, nb, M.order, lane);
+        }
         float *buf = slot_buf + s * kSlotFloats;
         uint32_t bytes[3] = {0u, 0u, 0u};
         const float *src[3] = {nullptr, nullptr, nullptr};
@@ -314,8 +395,8 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     }
   } else {
     // ---------------- consumers ----------------
-    constexpr int GPW = 32 / kTileG;
     bool ok = true;
+    const int g = lane / kTileG;
     for (int64_t sub = 0;; ++sub) {
       const int s = (int)(sub % kSlots);
       if (!mbar_wait_bounded(&full_bar[s], (uint32_t)((sub / kSlots) & 1))) {
@@ -325,22 +406,25 @@ __global__ void __launch_bounds__(kTileThreads, 2)
       const SlotMeta &M = meta[s];
       if (M.done) break;
       const float *bx = slot_buf + s * kSlotFloats;
+      const int ncell = (int)(M.ce - M.cs);
       while (true) {
         int task = 0;
         if (lane == 0) task = atomicAdd(&task_ctr[s], 1);
         task = __shfl_sync(0xffffffffu, task, 0);
-        const int64_t cbase = M.cs + (int64_t)task * GPW;
-        if (cbase >= M.ce) break;
-        const int64_t c = cbase + lane / kTileG;
-        const bool valid = c < M.ce;
-        const int64_t a = valid ? M.offs[c - M.cs] : M.pa;
-        const int n = valid ? (int)(M.offs[c - M.cs + 1] - a) : 0;
+        const int r0 = task * kCellsPerTask;
+        if (r0 >= ncell) break;
+        const int r = r0 + g;
+        const bool valid = r < ncell;
+        const int rc = valid ? (int)M.order[r] : 0;
+        const int64_t c = M.cs + rc;
+        const int64_t a = M.offs[rc];
+        const int n = valid ? (int)(M.offs[rc + 1] - a) : 0;
         if (M.big) {
-          reduce_cell_pair<false>(valid, n, v + a, v + np + a, v + 2 * np + a, c, mom, lane);
+          reduce_cells<false>(valid, n, v + a, v + np + a, v + 2 * np + a, c, mom, lane);
         } else {
           const int64_t rel = a - M.pa;
-          reduce_cell_pair<true>(valid, n, bx + M.lead[0] + rel, bx + kCapF + M.lead[1] + rel,
-                                 bx + 2 * kCapF + M.lead[2] + rel, c, mom, lane);
+          reduce_cells<true>(valid, n, bx + M.lead[0] + rel, bx + kCapF + M.lead[1] + rel,
+                             bx + 2 * kCapF + M.lead[2] + rel, c, mom, lane);
         }
       }
       __syncwarp();

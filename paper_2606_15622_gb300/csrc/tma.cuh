@@ -61,10 +61,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
                                                   uint64_t limit_ns = 2000000000ull) {
   if (mbar_test_wait(bar, parity)) return true;
   const uint64_t t0 = global_timer_ns();
+  unsigned sleep_ns = 32;
   while (true) {
 #pragma unroll 1
-    for (int i = 0; i < 64; ++i)
+    for (int i = 0; i < 8; ++i) {
       if (mbar_test_wait(bar, parity)) return true;
+      __nanosleep(sleep_ns);  // back off: a waiting warp leaves its issue slots to others
+      if (sleep_ns < 512) sleep_ns <<= 1;
+    }
     if (global_timer_ns() - t0 > limit_ns) return false;
   }
 }
