@@ -147,6 +147,38 @@ int fp_moments(const void *v, int v_dtype, int64_t n_particles, const int64_t *c
 int fp_closure_solve(const double *moments, const double *tau, int64_t n_cells, const fp_params *p, int prec,
                      double *coeffs_out, int32_t *flags_out, fp_stream_t stream);
 
+/* fp_velocity_update: one collision step of the particle velocities with the
+ * mixed Ornstein-Uhlenbeck / Euler scheme (paper Sec. 3.9-3.10):
+ *   N_i = (C_ij + delta_ij / tau) M'_j + G_i (|M'|^2 - 3 theta)
+ *         - eps^2 (M'_i |M'|^2 - b_i)                        (Eq. update_N)
+ *   alpha^2 = 1 + tau / (3 theta) [tau (1-a)^2 <N.N> + 2 (a - a^2) <M'.N>]
+ *                                                            (Eq. update_alpha)
+ *   M^{n+1} = (M' a + (1-a) tau N + sqrt(theta (1-a^2)) xi) / alpha + U
+ *                                                            (Eq. update_vel)
+ * with M' = M - U, a = exp(-dt/tau), b_i = <c_i |c|^2> = 2 q_i / rho and the
+ * cell averages <.> over the cell's particles.
+ *   v            [3][n_particles] f32 or f64, updated IN PLACE; FP32
+ *                velocities are updated in FP32 arithmetic, FP64 in FP64
+ *   moments      [n_cells][FP_NMOM] of the same velocities (U, theta, u_ijk)
+ *   coeffs       [n_cells][9] from the closure
+ *   tau          [n_cells]; dt the time step
+ *   p            eps2_hat is read (NULL = defaults)
+ *   xi           [3][n_particles] standard normals of v's dtype, or NULL: then
+ *                xi comes from Philox4x32-10 with key (seed lo, seed hi) on
+ *                counter (particle index lo, hi, step lo, hi); the four words
+ *                w map to uniforms (floor(w / 2^8) + 1) 2^-24 and Box-Muller
+ *                in FP32 gives xi_0, xi_1 from (u0, u1) and xi_2 from (u2, u3)
+ *   alpha_out    [n_cells] f64 or NULL
+ *   flags        [n_cells] int32 IN/OUT: cells carrying FP_FLAG_FEW,
+ *                FP_FLAG_SINGULAR or FP_FLAG_NONFINITE take the exact OU step
+ *                of the linear model (N = 0, alpha = 1); alpha^2 <= 0 or
+ *                non-finite sets FP_FLAG_ALPHA and alpha = 1.
+ * No workspace. */
+int fp_velocity_update(void *v, int v_dtype, int64_t n_particles, const int64_t *cell_offsets, int64_t n_cells,
+                       const double *moments, const double *coeffs, const double *tau, double dt, const fp_params *p,
+                       const void *xi, uint64_t seed, uint64_t step, double *alpha_out, int32_t *flags,
+                       fp_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -273,7 +273,7 @@ void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], ui
 
 /* The noise variates of particle p at a given step: Philox4x32-10 with key
  * (seed_lo, seed_hi) on counter (p_lo, p_hi, step_lo, step_hi); each word w
- * gives a uniform u = (floor(w / 2^8) + 1/2) 2^-24 in (0, 1); Box-Muller maps
+ * gives a uniform u = (floor(w / 2^8) + 1) 2^-24 in (0, 1] (exact in FP32 as well); Box-Muller maps
  * (u0, u1) to xi_0 = r cos(2 pi u1), xi_1 = r sin(2 pi u1), r = sqrt(-2 ln u0),
  * and (u2, u3) to xi_2 = r' cos(2 pi u3).  Evaluated here in FP64. */
 static void particle_normals(uint64_t seed, uint64_t step, uint64_t p, double xi[3]) {
@@ -282,7 +282,7 @@ static void particle_normals(uint64_t seed, uint64_t step, uint64_t p, double xi
   uint32_t w[4];
   oracle_philox4x32_10(ctr, key, w);
   double u[4];
-  for (int i = 0; i < 4; ++i) u[i] = ((double)(w[i] >> 8) + 0.5) * (1.0 / 16777216.0);
+  for (int i = 0; i < 4; ++i) u[i] = ((double)(w[i] >> 8) + 1.0) * (1.0 / 16777216.0);
   const double two_pi = 6.283185307179586476925286766559;
   double r0 = sqrt(-2.0 * log(u[0])), r1 = sqrt(-2.0 * log(u[2]));
   xi[0] = r0 * cos(two_pi * u[1]);

@@ -53,6 +53,8 @@ SIGNATURES = {
                                 _vp, _vp, _vp, _vp, _sz, _vp]),
     "fp_moments": (_i32, [_vp, _i32, _i64, _vp, _i64, _i32, _vp, _vp]),
     "fp_closure_solve": (_i32, [_vp, _vp, _i64, ctypes.POINTER(Params), _i32, _vp, _vp, _vp]),
+    "fp_velocity_update": (_i32, [_vp, _i32, _i64, _vp, _i64, _vp, _vp, _vp, _dbl, ctypes.POINTER(Params), _vp,
+                                  _u64, _u64, _vp, _vp, _vp]),
 }
 
 
@@ -176,3 +178,22 @@ def fp_closure_solve(moments, tau, params: Params | None = None, prec="fp32", co
                                 _ptr(flags_out), _stream(stream))
     _check(rc, "fp_closure_solve")
     return coeffs_out, flags_out
+
+
+def fp_velocity_update(v, offsets, moments, coeffs, tau, flags, dt, params: Params | None = None, xi=None,
+                       seed=0, step=0, alpha_out=None, stream=None):
+    """One velocity update in place (Eqs. update_vel / update_N / update_alpha).
+    flags is read and updated; returns (v, alpha_out, flags)."""
+    n_cells = offsets.numel() - 1
+    n_p = v.shape[-1] if v.dim() == 2 else v.numel() // 3
+    _need_cuda(v, offsets, moments, coeffs, tau, flags, xi, alpha_out)
+    if xi is not None and xi.dtype != v.dtype:
+        raise FPError("xi must have the velocity dtype")
+    if flags.dtype != torch.int32:
+        raise FPError("flags must be int32")
+    p = params if params is not None else default_params()
+    rc = lib().fp_velocity_update(_ptr(v), _vdtype(v), n_p, _ptr(offsets), n_cells, _ptr(moments), _ptr(coeffs),
+                                  _ptr(tau), float(dt), ctypes.byref(p), _ptr(xi), int(seed), int(step),
+                                  _ptr(alpha_out), _ptr(flags), _stream(stream))
+    _check(rc, "fp_velocity_update")
+    return v, alpha_out, flags

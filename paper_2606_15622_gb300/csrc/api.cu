@@ -11,6 +11,9 @@ void launch_gather(const void *v, int v_dtype, int64_t np, const int64_t *off, i
                    double *mom, cudaStream_t st);
 void launch_solve(const double *mom, const double *tau, int64_t n_cells, const fp_params &p, int prec,
                   double *coeffs, int32_t *flags, cudaStream_t st);
+void launch_velocity(void *v, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, const double *mom,
+                     const double *coeffs, const double *tau, double dt, double eps2_hat, const void *xi, uint64_t seed,
+                     uint64_t step, double *alpha_out, int32_t *flags, cudaStream_t st);
 }  // namespace fpc
 
 namespace {
@@ -122,6 +125,25 @@ int fp_closure_solve(const double *moments, const double *tau, int64_t n_cells, 
   if (prm.min_particles < 1) prm.min_particles = 1;
   fpc::launch_solve(moments, tau, n_cells, prm, prec, coeffs_out, flags_out, (cudaStream_t)stream);
   return check_launch("solve");
+}
+
+int fp_velocity_update(void *v, int v_dtype, int64_t n_particles, const int64_t *cell_offsets, int64_t n_cells,
+                       const double *moments, const double *coeffs, const double *tau, double dt, const fp_params *p,
+                       const void *xi, uint64_t seed, uint64_t step, double *alpha_out, int32_t *flags,
+                       fp_stream_t stream) {
+  g_err[0] = 0;
+  if (n_cells < 0 || n_particles < 0) return fail(FP_ERR_ARG, "negative size");
+  if (n_cells == 0) return FP_OK;
+  if (v_dtype != FP_V_F32 && v_dtype != FP_V_F64) return fail(FP_ERR_ARG, "v_dtype %d", v_dtype);
+  if (!cell_offsets || !moments || !coeffs || !tau || !flags) return fail(FP_ERR_ARG, "null array pointer");
+  if (n_particles > 0 && !v) return fail(FP_ERR_ARG, "null velocity pointer");
+  if (!(dt >= 0.0)) return fail(FP_ERR_ARG, "dt must be >= 0");
+  fp_params prm;
+  fp_default_params(&prm);
+  if (p) prm = *p;
+  fpc::launch_velocity(v, v_dtype, n_particles, cell_offsets, n_cells, moments, coeffs, tau, dt, prm.eps2_hat, xi,
+                       seed, step, alpha_out, flags, (cudaStream_t)stream);
+  return check_launch("velocity");
 }
 
 }  // extern "C"

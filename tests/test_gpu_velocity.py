@@ -1,0 +1,140 @@
+"""GPU parity of fp_velocity_update (through the C ABI) against the oracle's
+update (Eqs. update_vel, update_N, update_alpha).
+
+Tolerances: FP64 velocities with given variates agree to 1e-12 relative;
+FP32 velocities are updated in FP32, so each component carries a few ulps of
+|v| plus the FP32 rounding of the cell constants: |dv| <= 4e-6 (|v| +
+sqrt(theta)).  Philox variates: the GPU maps the same 32-bit words to normals
+in FP32 (Box-Muller with CUDA's logf / sincospif, <= 2 ulp each), the oracle
+in FP64, so xi differs by <= ~1e-6 relative.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2606_15622_gb300 import api
+from paper_2606_15622_gb300 import populations as P
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _oracle_state(pop, vdtype, eps2_hat=O.DEFAULT_EPS2_HAT):
+    v = pop.v64 if vdtype == "f64" else pop.v32.astype(np.float64)
+    m = O.moments(v, pop.offsets)
+    y, fl = O.closure(m, pop.tau, eps2_hat=eps2_hat)
+    return v, m, y, fl
+
+
+def _gpu_update(pop, vdtype, m, y, fl, dt, xi=None, seed=0, step=0, eps2_hat=O.DEFAULT_EPS2_HAT):
+    v = _dev(pop.v64 if vdtype == "f64" else pop.v32)
+    x = None if xi is None else _dev(xi.astype(np.float64 if vdtype == "f64" else np.float32))
+    alpha = torch.empty(pop.n_cells, dtype=torch.float64, device="cuda")
+    flags = _dev(fl.astype(np.int32))
+    api.fp_velocity_update(v, _dev(pop.offsets), _dev(m), _dev(y), _dev(pop.tau), flags, dt,
+                           params=api.default_params(eps2_hat=eps2_hat), xi=x, seed=seed, step=step, alpha_out=alpha)
+    torch.cuda.synchronize()
+    return v.cpu().numpy().astype(np.float64), alpha.cpu().numpy(), flags.cpu().numpy()
+
+
+def _check(pop, vref, aref, fref, vg, ag, fg, vdtype, m, noise_tol=0.0):
+    np.testing.assert_array_equal(fg, fref)
+    fin = np.isfinite(vref)
+    assert np.array_equal(fin, np.isfinite(vg))
+    cell_of = np.repeat(np.arange(pop.n_cells), pop.counts)
+    scale = np.abs(vref) + np.sqrt(np.maximum(m[cell_of, 4], 0))[None, :]
+    tol = (1e-12 if vdtype == "f64" else 4e-6) + noise_tol
+    err = np.abs(vg - vref)[fin] / scale[fin]
+    assert err.max() <= tol, f"max velocity err {err.max():.3e}"
+    aok = np.isfinite(aref)
+    atol = 1e-12 if vdtype == "f64" else 2e-6
+    assert np.abs(ag[aok] - aref[aok]).max() <= atol + noise_tol
+
+
+@pytest.mark.parametrize("vdtype", ["f64", "f32"])
+@pytest.mark.parametrize("dt", [0.05, 0.7])
+def test_update_with_given_variates(cavity_pop, vdtype, dt):
+    pop = cavity_pop.subset(np.arange(0, cavity_pop.n_cells, 5))
+    v, m, y, fl = _oracle_state(pop, vdtype, eps2_hat=1e-2)
+    xi = np.random.default_rng(1).standard_normal((3, pop.n_particles))
+    if vdtype == "f32":
+        xi = xi.astype(np.float32).astype(np.float64)
+    vref, aref, fref = O.velocity_update(v, pop.offsets, m, y, pop.tau, fl, dt, eps2_hat=1e-2, xi=xi)
+    vg, ag, fg = _gpu_update(pop, vdtype, m, y, fl, dt, xi=xi, eps2_hat=1e-2)
+    _check(pop, vref, aref, fref, vg, ag, fg, vdtype, m)
+
+
+@pytest.mark.parametrize("vdtype", ["f64", "f32"])
+def test_update_with_philox_variates(couette_pop, vdtype):
+    pop = couette_pop
+    v, m, y, fl = _oracle_state(pop, vdtype)
+    vref, aref, fref = O.velocity_update(v, pop.offsets, m, y, pop.tau, fl, 0.3, seed=2024, step=17)
+    vg, ag, fg = _gpu_update(pop, vdtype, m, y, fl, 0.3, seed=2024, step=17)
+    _check(pop, vref, aref, fref, vg, ag, fg, vdtype, m, noise_tol=2e-6)
+
+
+def test_cylinder_full_size_pipeline_sampled():
+    """Full-size launch: FP64 closure then FP64 update of all 131072 cells on
+    the GPU; the oracle recomputes a seeded sample of cells from the same
+    input velocities (moments, closure and update of its own)."""
+    pop = P.cylinder()
+    v = _dev(pop.v64)
+    off, tau = _dev(pop.offsets), _dev(pop.tau)
+    mom, y, fl = api.fp_closure_exact(v, off, tau, prec="fp64")
+    alpha = torch.empty(pop.n_cells, dtype=torch.float64, device="cuda")
+    api.fp_velocity_update(v, off, mom, y, tau, fl, 0.2, seed=7, step=3, alpha_out=alpha)
+    torch.cuda.synchronize()
+    vg, ag, fg = v.cpu().numpy(), alpha.cpu().numpy(), fl.cpu().numpy()
+    rng = np.random.default_rng(5)
+    cells = np.sort(rng.choice(pop.n_cells, 1500, replace=False))
+    sub = pop.subset(cells)
+    m = O.moments(sub.v64, sub.offsets)
+    yr, flr = O.closure(m, sub.tau)
+    # the oracle's counter is the particle's global index: rebuild the
+    # sample's variates with the same counters
+    idx = np.concatenate([np.arange(pop.offsets[c], pop.offsets[c + 1]) for c in cells])
+    xi = np.concatenate([O.normals(1, 7, 3, first_index=int(i)) for i in idx], axis=1)
+    vref, aref, fref = O.velocity_update(sub.v64, sub.offsets, m, yr, sub.tau, flr, 0.2, xi=xi)
+    ok = fref == fg[cells]
+    assert ok.mean() > 0.99
+    cell_of = np.repeat(np.arange(sub.n_cells), sub.counts)
+    okp = ok[cell_of]
+    scale = np.abs(vref) + np.sqrt(np.maximum(m[cell_of, 4], 0))[None, :]
+    err = np.abs(vg[:, idx] - vref)[:, okp] / scale[:, okp]
+    assert err.max() <= 1e-6, err.max()  # FP32 Box-Muller on the GPU (noise terms)
+    assert np.abs(ag[cells][ok] - aref[ok]).max() <= 1e-9
+
+
+def test_linear_cells_alpha_flag_and_momentum():
+    pop = P.maxwellian_cells([0, 3, 40, 60, 50], theta=[1.0, 1.0, 2.0, 0.5, 1.0], tau=[1, 1, 0.5, 2.0, 1.0], seed=9)
+    v, m, y, fl = _oracle_state(pop, "f64")
+    y = y.copy()
+    y[4, 0] = np.nan  # a non-finite coefficient: alpha^2 is NaN -> FP_FLAG_ALPHA
+    xi = np.zeros((3, pop.n_particles))
+    vref, aref, fref = O.velocity_update(v, pop.offsets, m, y, pop.tau, fl, 0.4, xi=xi)
+    vg, ag, fg = _gpu_update(pop, "f64", m, y, fl, 0.4, xi=xi)
+    assert fref[1] & api.FLAG_FEW and fref[4] & api.FLAG_ALPHA
+    np.testing.assert_array_equal(fg, fref)
+    np.testing.assert_allclose(ag, aref, rtol=1e-12)
+    # without noise the cell mean velocity stays U (momentum of the drift)
+    for c in (2, 3):
+        s = slice(pop.offsets[c], pop.offsets[c + 1])
+        np.testing.assert_allclose(vg[:, s].mean(1), m[c, 1:4], atol=1e-12)
+
+
+def test_argument_errors():
+    v = torch.zeros((3, 4), dtype=torch.float32, device="cuda")
+    off = torch.tensor([0, 4], dtype=torch.int64, device="cuda")
+    mom = torch.zeros((1, 30), dtype=torch.float64, device="cuda")
+    y = torch.zeros((1, 9), dtype=torch.float64, device="cuda")
+    tau = torch.ones(1, dtype=torch.float64, device="cuda")
+    fl = torch.zeros(1, dtype=torch.int32, device="cuda")
+    with pytest.raises(api.FPError):
+        api.fp_velocity_update(v, off, mom, y, tau, fl, -1.0)
+    with pytest.raises(api.FPError):
+        api.fp_velocity_update(v, off, mom, y, tau, fl, 0.1, xi=torch.zeros((3, 4), dtype=torch.float64, device="cuda"))
