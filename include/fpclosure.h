@@ -179,6 +179,35 @@ int fp_velocity_update(void *v, int v_dtype, int64_t n_particles, const int64_t 
                        const void *xi, uint64_t seed, uint64_t step, double *alpha_out, int32_t *flags,
                        fp_stream_t stream);
 
+/* fp_closure_backward: the adjoint of fp_closure_exact (not in the paper; the
+ * closure of Eq. system9x9 differentiated as an implicit function).  With
+ * F(m, Y) = A(m) Y - r(m) = 0 and a loss gradient gY = dL/dY per cell:
+ *   lambda = A^-T gY                    (pivoted elimination of A^T, the
+ *                                        factors recomputed per cell)
+ *   grad_moments = -(dF/dm)^T lambda + grad_moments_in
+ *   grad_v[p] = (1/N) sum_k grad_moments_k (grad psi_k(c_p) - <grad psi_k>)
+ *               + grad_moments_U / N    (c_p = v_p - U, m_k = <psi_k(c)>)
+ * so the velocity gradient carries every moment gradient, including the
+ * caller's grad_moments_in (for losses that also read the moments).
+ *   v, cell_offsets, tau  as in fp_closure_exact (v only read when grad_v)
+ *   p                     eps2_hat is read (NULL = defaults)
+ *   moments, coeffs, flags  the forward outputs for the same v
+ *   grad_coeffs           [n_cells][9]
+ *   grad_moments_in       [n_cells][FP_NMOM] or NULL (= 0)
+ *   grad_moments          [n_cells][FP_NMOM] out, or NULL (then kept in ws)
+ *   grad_v                [3][n_particles] out, v's dtype, or NULL; FP32
+ *                         velocities get an FP32 particle pass, FP64 an FP64
+ *                         one; the per-cell part is FP64 in both
+ *   ws, ws_bytes          >= fp_workspace_bytes(n_cells, n_particles, prec,
+ *                         grad_moments != NULL) when grad_v is requested
+ * Cells flagged FP_FLAG_FEW | FP_FLAG_SINGULAR | FP_FLAG_NONFINITE hold the
+ * constant linear drift: their coefficient gradient contributes nothing. */
+int fp_closure_backward(const void *v, int v_dtype, int64_t n_particles, const int64_t *cell_offsets,
+                        int64_t n_cells, const double *tau, const fp_params *p, const double *moments,
+                        const double *coeffs, const int32_t *flags, const double *grad_coeffs,
+                        const double *grad_moments_in, double *grad_moments, void *grad_v, void *ws,
+                        size_t ws_bytes, fp_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

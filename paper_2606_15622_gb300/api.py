@@ -55,7 +55,36 @@ SIGNATURES = {
     "fp_closure_solve": (_i32, [_vp, _vp, _i64, ctypes.POINTER(Params), _i32, _vp, _vp, _vp]),
     "fp_velocity_update": (_i32, [_vp, _i32, _i64, _vp, _i64, _vp, _vp, _vp, _dbl, ctypes.POINTER(Params), _vp,
                                   _u64, _u64, _vp, _vp, _vp]),
+    "fp_closure_backward": (_i32, [_vp, _i32, _i64, _vp, _i64, _vp, ctypes.POINTER(Params), _vp, _vp, _vp, _vp,
+                                   _vp, _vp, _vp, _vp, _sz, _vp]),
 }
+
+
+def fp_closure_backward(v, offsets, tau, moments, coeffs, flags, grad_coeffs, grad_moments_in=None,
+                        params: Params | None = None, want_grad_moments=True, want_grad_v=True,
+                        grad_moments=None, grad_v=None, workspace=None, stream=None):
+    """Adjoint of the closure -> (grad_moments or None, grad_v or None)."""
+    n_cells = offsets.numel() - 1
+    n_p = v.shape[-1] if v.dim() == 2 else v.numel() // 3
+    dev = offsets.device
+    if want_grad_moments and grad_moments is None:
+        grad_moments = torch.empty((n_cells, NMOM), dtype=torch.float64, device=dev)
+    if want_grad_v and grad_v is None:
+        grad_v = torch.empty_like(v)
+    _need_cuda(v, offsets, tau, moments, coeffs, flags, grad_coeffs, grad_moments_in, grad_moments, grad_v, workspace)
+    if grad_v is not None and grad_v.dtype != v.dtype:
+        raise FPError("grad_v must have the velocity dtype")
+    need = workspace_bytes(n_cells, n_p, "fp64", grad_moments is not None) if grad_v is not None else 0
+    if need and workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+    p = params if params is not None else default_params()
+    rc = lib().fp_closure_backward(_ptr(v), _vdtype(v), n_p, _ptr(offsets), n_cells, _ptr(tau), ctypes.byref(p),
+                                   _ptr(moments), _ptr(coeffs), _ptr(flags), _ptr(grad_coeffs),
+                                   _ptr(grad_moments_in), _ptr(grad_moments), _ptr(grad_v), _ptr(workspace),
+                                   ws_bytes, _stream(stream))
+    _check(rc, "fp_closure_backward")
+    return grad_moments, grad_v
 
 
 def library_path() -> str:

@@ -1,0 +1,323 @@
+// adjoint.cu -- reverse mode through the exact closure (implicit function
+// of Eq. system9x9) and through the moment gather, for sm_103a.
+//
+// With F(m, Y) = A(m) Y - r(m) = 0 defining the coefficients Y(m), a loss
+// gradient gY = dL/dY pulls back to the moments as
+//     lambda = A^-T gY,       dL/dm = -(dF/dm)^T lambda,
+// and to the particle velocities through m_k = <psi_k(c)>, c = v - U:
+//     dL/dv_p = (1/N) sum_k gm_k (grad psi_k(c_p) - <grad psi_k>) + gm_U / N.
+//
+// Kernel 1 (one thread per cell, FP64): re-assembles A, eliminates A^T with
+// partial pivoting (the factors are recomputed, never stored), and
+// back-propagates -lambda through the assembly formulas by hand-written
+// reverse mode.  Kernel 2 (a group of lanes per cell): the per-particle
+// polynomial above, in the velocity's precision, one pass over the particles.
+#include <cstdint>
+
+#include "closure_math.cuh"
+#include "fp_device.cuh"
+
+namespace fpc {
+
+__global__ void __launch_bounds__(128) adjoint_cell_kernel(const double *__restrict__ mom,
+                                                           const double *__restrict__ coeffs,
+                                                           const int32_t *__restrict__ flags,
+                                                           const double *__restrict__ tau,
+                                                           const double *__restrict__ gY,
+                                                           const double *__restrict__ gm_in, int64_t n_cells,
+                                                           double eps2_hat, double *__restrict__ gm_out) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  double gm[FP_NMOM];
+#pragma unroll
+  for (int k = 0; k < FP_NMOM; ++k) gm[k] = gm_in ? gm_in[c * FP_NMOM + k] : 0.0;
+  const int fl = flags[c];
+  if (!(fl & (FP_FLAG_FEW | FP_FLAG_SINGULAR | FP_FLAG_NONFINITE))) {
+    double m[FP_NMOM];
+#pragma unroll
+    for (int k = 0; k < FP_NMOM; ++k) m[k] = mom[c * FP_NMOM + k];
+    const double tc = tau[c];
+    // lambda = A^-T gY: eliminate the transposed augmented system
+    double lam[9];
+    {
+      double a[9][10];
+      assemble(m, tc, eps2_hat, a);
+      double at[9][10];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+#pragma unroll
+        for (int j = 0; j < 9; ++j) at[i][j] = a[j][i];
+        at[i][9] = gY[c * 9 + i];
+      }
+      pivoted_solve(at, 0.0, lam);
+    }
+    double Y[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Y[q] = coeffs[c * 9 + q];
+    double C[3][3], G[3], u[3][3], w[3][3], b[3], z[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      G[i] = Y[6 + i];
+      z[i] = m[kZ + i];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        C[i][j] = Y[sym2(i, j)];
+        u[i][j] = m[kU2 + sym2(i, j)];
+        w[i][j] = m[kW + sym2(i, j)];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) b[i] = m[kU3 + sym3(i, 0, 0)] + m[kU3 + sym3(i, 1, 1)] + m[kU3 + sym3(i, 2, 2)];
+    const double th = m[kTheta];
+    const double e2 = eps2_hat / (tc * th);
+    const double itau = 1.0 / tc;
+    // adjoints of the intermediates (full-index for the symmetric tensors)
+    double ub[3][3] = {}, wb[3][3] = {}, u3b[10] = {}, zb[3] = {}, bb[3] = {};
+    double thb = 0.0, s4b = 0.0, e2b = 0.0;
+    // stress rows: F_ij = sum_k (C_ik u_kj + C_jk u_ki) + G_i b_j + G_j b_i + (2/tau) u_ij - 2 e2 w_ij
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) {
+        const double f = -lam[sym2(i, j)];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          ub[k][j] += f * C[i][k];
+          ub[k][i] += f * C[j][k];
+        }
+        bb[j] += f * G[i];
+        bb[i] += f * G[j];
+        ub[i][j] += f * 2.0 * itau;
+        wb[i][j] += f * (-2.0 * e2);
+        e2b += f * (-2.0 * w[i][j]);
+      }
+    // heat-flux rows: F_i = sum_l C_il b_l + 2 sum_kl C_kl u_ikl + G_i (s4 - 9 th^2)
+    //   + 2 sum_k G_k (w_ki - 3 th u_ki) + (4/(3 tau)) b_i - e2 (3 z_i - 3 th b_i - 2 sum_k u_ik b_k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const double f = -lam[6 + i];
+#pragma unroll
+      for (int l = 0; l < 3; ++l) bb[l] += f * C[i][l];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) u3b[sym3(i, k, l)] += f * 2.0 * C[k][l];
+      s4b += f * G[i];
+      thb += f * (-18.0 * th * G[i]);
+      double ub_sum = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        wb[k][i] += f * 2.0 * G[k];
+        ub[k][i] += f * (-6.0 * th * G[k]);
+        thb += f * (-6.0 * G[k] * u[k][i]);
+        ub[i][k] += f * (2.0 * e2 * b[k]);
+        bb[k] += f * (2.0 * e2 * u[i][k]);
+        ub_sum += u[i][k] * b[k];
+      }
+      bb[i] += f * (4.0 / 3.0) * itau;
+      zb[i] += f * (-3.0 * e2);
+      thb += f * (3.0 * e2 * b[i]);
+      bb[i] += f * (3.0 * e2 * th);
+      e2b += f * (-(3.0 * z[i] - 3.0 * th * b[i] - 2.0 * ub_sum));
+    }
+    // e2 = eps2_hat / (tau th);  b_i = sum_k u_ikk;  s4 = sum_k w_kk
+    thb += e2b * (-e2 / th);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) u3b[sym3(i, k, k)] += bb[i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) wb[k][k] += s4b;
+    // fold onto the moment slots
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) {
+        gm[kU2 + sym2(i, j)] += ub[i][j] + (i != j ? ub[j][i] : 0.0);
+        gm[kW + sym2(i, j)] += wb[i][j] + (i != j ? wb[j][i] : 0.0);
+      }
+#pragma unroll
+    for (int s = 0; s < 10; ++s) gm[kU3 + s] += u3b[s];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) gm[kZ + i] += zb[i];
+    gm[kTheta] += thb;
+  }
+#pragma unroll
+  for (int k = 0; k < FP_NMOM; ++k) gm_out[c * FP_NMOM + k] = gm[k];
+}
+
+// ---------------------------------------------------------------------------
+// particle gradient
+// ---------------------------------------------------------------------------
+constexpr int kAG = 8;  // lanes per cell
+
+template <typename T>
+__device__ __forceinline__ T shfl_g(T x, int src, int lane) {
+  return __shfl_sync(0xffffffffu, x, (lane & ~(kAG - 1)) + src);
+}
+
+// multiplicity of a symmetric third-order slot (111: 1, 112: 3, 123: 6)
+__host__ __device__ constexpr int mult3(int s) { return (s == 0 || s == 6 || s == 9) ? 1 : (s == 4 ? 6 : 3); }
+
+template <typename VT>
+__global__ void __launch_bounds__(256) adjoint_particle_kernel(const VT *__restrict__ v, int64_t np,
+                                                               const int64_t *__restrict__ off, int64_t n_cells,
+                                                               const double *__restrict__ mom,
+                                                               const double *__restrict__ gm, VT *__restrict__ gv) {
+  using T = VT;
+  constexpr int G = kAG;
+  constexpr int GPW = 32 / G;
+  const int lane = threadIdx.x & 31;
+  const int lg = lane & (G - 1);
+  const int g = lane / G;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const VT *vx = v, *vy = v + np, *vz = v + 2 * np;
+  VT *gx = gv, *gy = gv + np, *gz = gv + 2 * np;
+
+  for (int64_t base = warp * GPW; base < n_cells; base += nwarps * GPW) {
+    const int64_t c = base + g;
+    const bool valid = c < n_cells;
+    int64_t a0 = 0, e = 0;
+    if (valid) {
+      a0 = off[c];
+      e = off[c + 1];
+    }
+    const int n = (int)(e - a0);
+    // the cell's 30 moments and 30 moment gradients, converted once: lane lg
+    // holds slots lg + 8 j of the concatenation [mom | gm] (60 values)
+    T cv[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int slot = lg + 8 * j;
+      double x = 0.0;
+      if (valid && slot < 60) x = slot < 30 ? mom[c * FP_NMOM + slot] : gm[c * FP_NMOM + slot - 30];
+      cv[j] = (T)x;
+    }
+    auto M_ = [&](int k) -> T { return shfl_g(cv[k / 8], k % 8, lane); };
+    auto GM = [&](int k) -> T { return shfl_g(cv[(30 + k) / 8], (30 + k) % 8, lane); };
+    const T U0 = M_(kU), U1 = M_(kU + 1), U2 = M_(kU + 2);
+    // u-part: G_d += sum_j Mu_dj c_j with Mu_dj = gm_u(dj) (1 + delta_dj); theta adds 2/3 gm_theta c_d
+    const T gth = GM(kTheta) * T(2.0 / 3.0);
+    T Mu[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Mu[i][j] = GM(kU2 + sym2(i, j)) * (i == j ? T(2) : T(1)) + (i == j ? gth : T(0));
+    // u3-part: G_d += 3 sum_jk A_djk c_j c_k with A = gm_u3(slot) / multiplicity
+    T A3[10];
+#pragma unroll
+    for (int s = 0; s < 10; ++s) A3[s] = GM(kU3 + s) / T(mult3(s));
+    // w-part: G_d += 2 c_d (c.W c) + 2 |c|^2 (W c)_d with W = gm_w(slot) / multiplicity
+    T W[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) W[i][j] = GM(kW + sym2(i, j)) * (i == j ? T(1) : T(0.5));
+    // z-part: G_d += 4 |c|^2 c_d (gz.c) + |c|^4 gz_d
+    const T gz0 = GM(kZ), gz1 = GM(kZ + 1), gz2 = GM(kZ + 2);
+    // the cell mean of grad psi, from the moments
+    T G0[3];
+    {
+      T u[3][3], w[3][3], b[3], u3[10];
+#pragma unroll
+      for (int s = 0; s < 10; ++s) u3[s] = M_(kU3 + s);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          u[i][j] = M_(kU2 + sym2(i, j));
+          w[i][j] = M_(kW + sym2(i, j));
+        }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) b[i] = u3[sym3(i, 0, 0)] + u3[sym3(i, 1, 1)] + u3[sym3(i, 2, 2)];
+      const T s4 = w[0][0] + w[1][1] + w[2][2];
+      const T gzv[3] = {gz0, gz1, gz2};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        T acc = 0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) acc += T(3) * A3[sym3(d, j, k)] * u[j][k] + T(2) * W[j][k] * u3[sym3(d, j, k)];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) acc += T(2) * W[d][j] * b[j] + T(4) * gzv[j] * w[d][j];
+        acc += s4 * gzv[d];
+        G0[d] = acc;
+      }
+    }
+    const T inv_n = n > 0 ? T(1) / T(n) : T(0);
+    const T gU0 = GM(kU) * inv_n, gU1 = GM(kU + 1) * inv_n, gU2 = GM(kU + 2) * inv_n;
+    const int itmax = __reduce_max_sync(0xffffffffu, (n + G - 1) / G);
+    for (int it = 0; it < itmax; ++it) {
+      const int64_t p = a0 + (int64_t)it * G + lg;
+      if (p < e) {
+        const T c0 = vx[p] - U0, c1 = vy[p] - U1, c2 = vz[p] - U2;
+        const T cc[3] = {c0, c1, c2};
+        const T r2 = c0 * c0 + c1 * c1 + c2 * c2;
+        const T gzc = gz0 * c0 + gz1 * c1 + gz2 * c2;
+        T Wc[3];
+        T cWc = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          Wc[i] = W[i][0] * c0 + W[i][1] * c1 + W[i][2] * c2;
+          cWc += cc[i] * Wc[i];
+        }
+        T out[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          T gd = Mu[d][0] * c0 + Mu[d][1] * c1 + Mu[d][2] * c2;
+          T a3 = 0;
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) a3 += A3[sym3(d, j, k)] * cc[j] * cc[k];
+          gd += T(3) * a3 + T(2) * cc[d] * cWc + T(2) * r2 * Wc[d] + T(4) * r2 * cc[d] * gzc;
+          const T gzd = d == 0 ? gz0 : (d == 1 ? gz1 : gz2);
+          gd += r2 * r2 * gzd;
+          out[d] = (gd - G0[d]) * inv_n;
+        }
+        gx[p] = out[0] + gU0;
+        gy[p] = out[1] + gU1;
+        gz[p] = out[2] + gU2;
+      }
+    }
+  }
+}
+
+static int adj_sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 152;
+  }
+  return n;
+}
+
+void launch_adjoint(const void *v, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, const double *tau,
+                    double eps2_hat, const double *mom, const double *coeffs, const int32_t *flags, const double *gY,
+                    const double *gm_in, double *gm_out, void *gv, cudaStream_t st) {
+  {
+    const int threads = 128;
+    const int64_t blocks = (n_cells + threads - 1) / threads;
+    adjoint_cell_kernel<<<(unsigned)blocks, threads, 0, st>>>(mom, coeffs, flags, tau, gY, gm_in, n_cells, eps2_hat,
+                                                              gm_out);
+  }
+  if (!gv) return;
+  const int threads = 256;
+  const int64_t groups_per_block = (threads / 32) * (32 / kAG);
+  int64_t blocks = (n_cells + groups_per_block - 1) / groups_per_block;
+  const int64_t cap = (int64_t)adj_sm_count() * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  if (v_dtype == FP_V_F32)
+    adjoint_particle_kernel<float><<<(unsigned)blocks, threads, 0, st>>>((const float *)v, np, off, n_cells, mom,
+                                                                         gm_out, (float *)gv);
+  else
+    adjoint_particle_kernel<double><<<(unsigned)blocks, threads, 0, st>>>((const double *)v, np, off, n_cells, mom,
+                                                                          gm_out, (double *)gv);
+}
+
+}  // namespace fpc

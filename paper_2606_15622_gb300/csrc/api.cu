@@ -14,6 +14,9 @@ void launch_solve(const double *mom, const double *tau, int64_t n_cells, const f
 void launch_velocity(void *v, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, const double *mom,
                      const double *coeffs, const double *tau, double dt, double eps2_hat, const void *xi, uint64_t seed,
                      uint64_t step, double *alpha_out, int32_t *flags, cudaStream_t st);
+void launch_adjoint(const void *v, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, const double *tau,
+                    double eps2_hat, const double *mom, const double *coeffs, const int32_t *flags, const double *gY,
+                    const double *gm_in, double *gm_out, void *gv, cudaStream_t st);
 }  // namespace fpc
 
 namespace {
@@ -144,6 +147,36 @@ int fp_velocity_update(void *v, int v_dtype, int64_t n_particles, const int64_t 
   fpc::launch_velocity(v, v_dtype, n_particles, cell_offsets, n_cells, moments, coeffs, tau, dt, prm.eps2_hat, xi,
                        seed, step, alpha_out, flags, (cudaStream_t)stream);
   return check_launch("velocity");
+}
+
+int fp_closure_backward(const void *v, int v_dtype, int64_t n_particles, const int64_t *cell_offsets,
+                        int64_t n_cells, const double *tau, const fp_params *p, const double *moments,
+                        const double *coeffs, const int32_t *flags, const double *grad_coeffs,
+                        const double *grad_moments_in, double *grad_moments, void *grad_v, void *ws,
+                        size_t ws_bytes, fp_stream_t stream) {
+  g_err[0] = 0;
+  if (n_cells < 0 || n_particles < 0) return fail(FP_ERR_ARG, "negative size");
+  if (n_cells == 0 || (!grad_moments && !grad_v)) return FP_OK;
+  if (!tau || !moments || !coeffs || !flags || !grad_coeffs) return fail(FP_ERR_ARG, "null array pointer");
+  if (grad_v) {
+    if (v_dtype != FP_V_F32 && v_dtype != FP_V_F64) return fail(FP_ERR_ARG, "v_dtype %d", v_dtype);
+    if (!cell_offsets) return fail(FP_ERR_ARG, "null offsets");
+    if (n_particles > 0 && !v) return fail(FP_ERR_ARG, "null velocity pointer");
+  }
+  fp_params prm;
+  fp_default_params(&prm);
+  if (p) prm = *p;
+  double *gm = grad_moments;
+  if (!gm) {
+    const size_t need = fp_workspace_bytes(n_cells, n_particles, FP_PREC_FP64, 0);
+    if (!ws || ws_bytes < need)
+      return fail(FP_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", need, ws_bytes);
+    if ((uintptr_t)ws % kAlign) return fail(FP_ERR_ARG, "workspace not 256-byte aligned");
+    gm = (double *)ws;
+  }
+  fpc::launch_adjoint(v, v_dtype, n_particles, cell_offsets, n_cells, tau, prm.eps2_hat, moments, coeffs, flags,
+                      grad_coeffs, grad_moments_in, gm, grad_v, (cudaStream_t)stream);
+  return check_launch("adjoint");
 }
 
 }  // extern "C"

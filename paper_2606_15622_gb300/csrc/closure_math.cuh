@@ -1,0 +1,165 @@
+// closure_math.cuh -- per-cell FP64 assembly of the 9x9 moment-matching
+// system (Eq. system9x9, Table 1 and its heat-flux rows) and the partial-pivot
+// elimination, shared by the forward solve and the adjoint kernels.
+#pragma once
+
+#include <cstdint>
+
+#include "fp_device.cuh"
+
+namespace fpc {
+
+__host__ __device__ __forceinline__ constexpr int sym2(int i, int j) {
+  return (i < j ? i : j) == 0 ? (i > j ? i : j) : ((i < j ? i : j) == 1 ? 2 + (i > j ? i : j) : 5);
+}
+// (i,j,k) -> 0..9 in the order 111,112,113,122,123,133,222,223,233,333
+__host__ __device__ __forceinline__ constexpr int sym3s(int i, int j, int k) {  // i <= j <= k
+  return i == 0 ? (j == 0 ? k : (j == 1 ? 2 + k : 5)) : (i == 1 ? (j == 1 ? 5 + k : 8) : 9);
+}
+__host__ __device__ __forceinline__ constexpr int sym3(int i, int j, int k) {
+  return sym3s(i < j ? (i < k ? i : k) : (j < k ? j : k),
+               i + j + k - (i < j ? (i < k ? i : k) : (j < k ? j : k)) - (i > j ? (i > k ? i : k) : (j > k ? j : k)),
+               i > j ? (i > k ? i : k) : (j > k ? j : k));
+}
+static_assert(sym2(2, 1) == 4 && sym2(1, 1) == 3 && sym2(0, 2) == 2, "sym2");
+static_assert(sym3(2, 0, 1) == 4 && sym3(1, 2, 2) == 8 && sym3(2, 1, 1) == 7 && sym3(0, 2, 0) == 2, "sym3");
+
+__device__ __forceinline__ uint64_t abs_bits(double x) {
+  return (uint64_t)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ bool finite_d(double x) {
+  return (abs_bits(x) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
+
+struct SolveParams {
+  double eps2_hat;
+  double pivot_rtol;
+  int min_particles;
+};
+
+// Assemble the augmented system [A | r] (moment-matching rows for psi =
+// c_i c_j and psi = c_i |c|^2; see fpclosure.h for the readings).
+__device__ __forceinline__ void assemble(const double (&m)[FP_NMOM], double tau, double eps2_hat,
+                                         double (&a)[9][10]) {
+  double u[3][3], w[3][3], b[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      u[i][j] = m[kU2 + sym2(i, j)];
+      w[i][j] = m[kW + sym2(i, j)];
+    }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    b[i] = m[kU3 + sym3(i, 0, 0)] + m[kU3 + sym3(i, 1, 1)] + m[kU3 + sym3(i, 2, 2)];
+  const double theta = m[kTheta];
+  const double s4 = w[0][0] + w[1][1] + w[2][2];
+  const double eps2 = eps2_hat / (tau * theta);
+  const double inv_tau = 1.0 / tau;
+#pragma unroll
+  for (int r = 0; r < 9; ++r)
+#pragma unroll
+    for (int col = 0; col < 10; ++col) a[r][col] = 0.0;
+  // stress rows: sum_k (C_ik u_kj + C_jk u_ki) + G_i b_j + G_j b_i
+  //              = -(2/tau) u_ij + 2 eps^2 w_ij
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      const int row = sym2(i, j);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        a[row][sym2(i, k)] += u[k][j];
+        a[row][sym2(j, k)] += u[k][i];
+      }
+      a[row][6 + i] += b[j];
+      a[row][6 + j] += b[i];
+      a[row][9] = -2.0 * inv_tau * u[i][j] + 2.0 * eps2 * w[i][j];
+    }
+  // heat-flux rows: sum_l C_il b_l + 2 sum_kl C_kl u_ikl + G_i (s4 - 9 theta^2)
+  //                 + 2 sum_k G_k (w_ki - 3 theta u_ki)
+  //                 = -(4/(3 tau)) b_i + eps^2 (3 z_i - 3 theta b_i - 2 u_ik b_k)
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int row = 6 + i;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) a[row][sym2(i, l)] += b[l];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int l = 0; l < 3; ++l) a[row][sym2(k, l)] += 2.0 * m[kU3 + sym3(i, k, l)];
+    a[row][6 + i] += s4 - 9.0 * theta * theta;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) a[row][6 + k] += 2.0 * (w[k][i] - 3.0 * theta * u[k][i]);
+    const double ub = u[i][0] * b[0] + u[i][1] * b[1] + u[i][2] * b[2];
+    a[row][9] = -(4.0 / 3.0) * inv_tau * b[i] + eps2 * (3.0 * m[kZ + i] - 3.0 * theta * b[i] - 2.0 * ub);
+  }
+}
+
+// One elimination step for column K (a template so every index is static and
+// the matrix stays in registers).
+template <int K>
+__device__ __forceinline__ void elim_step(double (&a)[9][10], uint64_t thr, int &flag, double (&rinv)[9]) {
+  uint64_t best = abs_bits(a[K][K]);
+  int bi = K;
+#pragma unroll
+  for (int i = K + 1; i < 9; ++i) {
+    const uint64_t bb = abs_bits(a[i][K]);
+    if (bb > best) {
+      best = bb;
+      bi = i;
+    }
+  }
+  if (!(best > thr)) flag = FP_FLAG_SINGULAR;
+#pragma unroll
+  for (int i = K + 1; i < 9; ++i) {
+    const bool sw = (bi == i);
+#pragma unroll
+    for (int j = K; j < 10; ++j) {
+      const double t = a[K][j];
+      a[K][j] = sw ? a[i][j] : t;
+      a[i][j] = sw ? t : a[i][j];
+    }
+  }
+  rinv[K] = 1.0 / a[K][K];
+#pragma unroll
+  for (int i = K + 1; i < 9; ++i) {
+    const double l = a[i][K] * rinv[K];
+#pragma unroll
+    for (int j = K + 1; j < 10; ++j) a[i][j] = fma(-l, a[K][j], a[i][j]);
+  }
+}
+
+// Partial-pivot elimination and back substitution on [A | r]; returns
+// FP_FLAG_SINGULAR if a pivot is <= rtol * max|A| (y is then garbage).
+__device__ __forceinline__ int pivoted_solve(double (&a)[9][10], double rtol, double (&y)[9]) {
+  uint64_t amax = 0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+#pragma unroll
+    for (int j = 0; j < 9; ++j) amax = max(amax, abs_bits(a[i][j]));
+  const double amax_d = __longlong_as_double((long long)amax);
+  int flag = 0;
+  if (!(amax_d > 0.0) || !finite_d(amax_d)) flag = FP_FLAG_SINGULAR;
+  const uint64_t thr = abs_bits(rtol * amax_d);
+  double rinv[9];
+  elim_step<0>(a, thr, flag, rinv);
+  elim_step<1>(a, thr, flag, rinv);
+  elim_step<2>(a, thr, flag, rinv);
+  elim_step<3>(a, thr, flag, rinv);
+  elim_step<4>(a, thr, flag, rinv);
+  elim_step<5>(a, thr, flag, rinv);
+  elim_step<6>(a, thr, flag, rinv);
+  elim_step<7>(a, thr, flag, rinv);
+  elim_step<8>(a, thr, flag, rinv);
+#pragma unroll
+  for (int k = 8; k >= 0; --k) {
+    double s = a[k][9];
+#pragma unroll
+    for (int j = k + 1; j < 9; ++j) s = fma(-a[k][j], y[j], s);
+    y[k] = s * rinv[k];
+  }
+  return flag;
+}
+
+}  // namespace fpc
