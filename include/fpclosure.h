@@ -208,6 +208,103 @@ int fp_closure_backward(const void *v, int v_dtype, int64_t n_particles, const i
                         const double *grad_moments_in, double *grad_moments, void *grad_v, void *ws,
                         size_t ws_bytes, fp_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * The learned closure (the paper's neural surrogate, Sec. 4, Alg. 2): a small
+ * MLP maps a cell's normalised moments to its drift coefficients; flagged
+ * cells fall back to the exact closure.
+ *
+ * Features: the 25 moments of w = c / sqrt(theta): u_ij / theta (6),
+ * u_ijk / theta^1.5 (10), w_ij / theta^2 (6), z_i / theta^2.5 (3), in the
+ * slot order of the moment vector, standardised with (x_mu, x_sigma),
+ * rounded to BF16 and zero padded to 32.  Targets: the dimensionless
+ * coefficients t = (tau C_11, tau C_12, tau C_13, tau C_22, tau C_23,
+ * tau C_33, tau sqrt(theta) G_1..3) standardised with (y_mu, y_sigma); the
+ * cubic-FP system is invariant under c -> c / sqrt(theta), so t depends on
+ * the features alone (for the eps2_hat the network was trained with).
+ * Network: Linear(32,128) SiLU, 3 x [Linear(128,128) SiLU], Linear(128,16)
+ * (outputs 9..15 unused); BF16 weights and activations, FP32 accumulation.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  const void *W[5];             /* device, BF16 row-major [out][in]:
+                                   128x32, 128x128, 128x128, 128x128, 16x128 */
+  const float *b[5];            /* device, FP32 [128] x 4, [16]              */
+  const float *x_mu, *x_sigma;  /* device, FP32 [32] (padding: 0, 1)         */
+  const float *y_mu, *y_sigma;  /* device, FP32 [16] (padding: 0, 1)         */
+  const float *x_min, *x_max;   /* device, FP32 [32]: raw-feature box of the
+                                   training set                              */
+  int32_t in_dim, hidden, depth, out_dim; /* must be 32, 128, 4, 16          */
+  double eps2_hat;              /* eps2_hat of the training targets          */
+} fp_mlp;
+
+/* Flat FP32 parameter vector used by training: W1 | b1 | W2 | b2 | W3 | b3 |
+ * W4 | b4 | W5 | b5 (row-major W).  which = 0 for W_layer, 1 for b_layer;
+ * layer = 0..4. */
+int64_t fp_mlp_param_count(void);
+int64_t fp_mlp_param_offset(int which, int layer);
+
+/* Workspace of fp_closure_surrogate for n_cells cells. */
+size_t fp_surrogate_workspace_bytes(int64_t n_cells);
+
+/* Features of every cell: x_out [n_cells][32] BF16, and flags_out with
+ * FP_FLAG_FEW | FP_FLAG_SINGULAR | FP_FLAG_NONFINITE (the exact closure's
+ * preconditions) and FP_FLAG_RANGE when a raw feature lies outside
+ * [x_min - m x_sigma, x_max + m x_sigma], m = p->surr_range_margin. */
+int fp_surrogate_features(const fp_mlp *net, const double *moments, int64_t n_cells, const double *tau,
+                          const fp_params *p, void *x_out, int32_t *flags_out, fp_stream_t stream);
+
+/* The fused network on n rows of BF16 features x [n][32]:
+ * out [n][16] FP32 -- standardised outputs when standardized_out != 0, else
+ * y_mu + y_sigma * output.  For training, h_save ([4][n][128] BF16, the
+ * hidden activations) and z_save ([4][n][128] FP32, their pre-activations)
+ * are written when both are non-NULL.  No workspace. */
+int fp_mlp_forward(const fp_mlp *net, const void *x, int64_t n, int standardized_out, float *out, void *h_save,
+                   float *z_save, fp_stream_t stream);
+
+/* The surrogate closure: features, network, coefficients C = t / tau,
+ * G = t / (tau sqrt(theta)); a cell is recomputed by the exact FP64 closure
+ * from its moments (FP_FLAG_FALLBACK) when it fails the exact closure's
+ * preconditions, a raw feature leaves the training box (FP_FLAG_RANGE),
+ * the prediction is not finite, or the energy residual
+ * e = 1 + (sum_ij C^_ij u^_ij + sum_i G^_i b^_i - eps2_hat s4^) / 3 of the
+ * predicted drift exceeds p->surr_energy_tol (FP_FLAG_ENERGY).  prec: the
+ * precision the moments were gathered in (fallback singularity threshold).
+ *   moments [n_cells][FP_NMOM], tau [n_cells]; coeffs_out [n_cells][9],
+ *   flags_out [n_cells]; ws >= fp_surrogate_workspace_bytes(n_cells). */
+int fp_closure_surrogate(const fp_mlp *net, const double *moments, int64_t n_cells, const double *tau,
+                         const fp_params *p, int prec, double *coeffs_out, int32_t *flags_out, void *ws,
+                         size_t ws_bytes, fp_stream_t stream);
+
+/* Training loss and its gradient w.r.t. the standardised outputs, per row:
+ *   sum_a w_a (o_a - (t_a - y_mu_a) / y_sigma_a)^2
+ *   + lam_drift [tr(D u D) + 2 g.D b + |g|^2 (s4 - 9)] + lam_energy e^2
+ * with (D, g) = prediction - target in the symmetric C block and the G block,
+ * (u, b, s4) the row's normalised moments u^_ij, b^_i = u^_ikk, s4^ = w^_kk
+ * -- the first bracket is tau^2 / theta times the mean square, over the cell,
+ * of the difference of the drifts (Eq. cubic_drift) the two coefficient sets
+ * induce -- and e the energy residual above.
+ *   out [n][16] standardised network outputs; t_true [n][9] dimensionless
+ *   targets; aux [n][16] = (u^ (6), b^ (3), s4^, unused); w [9] host array;
+ *   dout [n][16] FP32 and dout_bf16 [n][16] BF16: scale * dL/dout;
+ *   loss_sum [1] FP32 += sum of the row losses. */
+int fp_surrogate_loss(const float *out, const float *t_true, const float *aux, const float *y_mu,
+                      const float *y_sigma, int64_t n, const float *w, float lam_drift, float lam_energy,
+                      float eps2_hat, float scale, float *dout, void *dout_bf16, float *loss_sum, fp_stream_t stream);
+
+/* Backward pass of fp_mlp_forward: grads (flat FP32, layout above) of
+ * sum_rows dout . out given the forward's x, h_save, z_save and dout (FP32
+ * for the last bias, BF16 for the GEMMs).  GEMMs: BF16 tensor cores, FP32
+ * accumulation.  ws >= fp_mlp_backward_workspace_bytes(n). */
+size_t fp_mlp_backward_workspace_bytes(int64_t n);
+int fp_mlp_backward(const fp_mlp *net, const void *x, const void *h_save, const float *z_save,
+                    const void *dout_bf16, const float *dout, int64_t n, float *grads, void *ws, size_t ws_bytes,
+                    fp_stream_t stream);
+
+/* One Adam step (Kingma & Ba) over n_params FP32 parameters with bias
+ * corrections for step t >= 1; shadow_bf16 (or NULL) receives the BF16 copy
+ * of the updated parameters (the forward's weights). */
+int fp_adam_step(float *params, const float *grads, float *m, float *v, int64_t n_params, float lr, float beta1,
+                 float beta2, float eps, int64_t t, void *shadow_bf16, fp_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

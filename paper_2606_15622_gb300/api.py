@@ -38,6 +38,16 @@ class Params(ctypes.Structure):
                 ("surr_range_margin", ctypes.c_double)]
 
 
+class FpMlp(ctypes.Structure):
+    """fp_mlp of fpclosure.h (device pointers)."""
+    _fields_ = [("W", ctypes.c_void_p * 5), ("b", ctypes.c_void_p * 5),
+                ("x_mu", ctypes.c_void_p), ("x_sigma", ctypes.c_void_p),
+                ("y_mu", ctypes.c_void_p), ("y_sigma", ctypes.c_void_p),
+                ("x_min", ctypes.c_void_p), ("x_max", ctypes.c_void_p),
+                ("in_dim", ctypes.c_int32), ("hidden", ctypes.c_int32), ("depth", ctypes.c_int32),
+                ("out_dim", ctypes.c_int32), ("eps2_hat", ctypes.c_double)]
+
+
 _LIB = None
 _LOCK = threading.Lock()
 _vp, _i64, _i32, _sz, _dbl, _u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t, ctypes.c_double, ctypes.c_uint64
@@ -57,6 +67,19 @@ SIGNATURES = {
                                   _u64, _u64, _vp, _vp, _vp]),
     "fp_closure_backward": (_i32, [_vp, _i32, _i64, _vp, _i64, _vp, ctypes.POINTER(Params), _vp, _vp, _vp, _vp,
                                    _vp, _vp, _vp, _vp, _sz, _vp]),
+    "fp_mlp_param_count": (_i64, []),
+    "fp_mlp_param_offset": (_i64, [_i32, _i32]),
+    "fp_surrogate_workspace_bytes": (_sz, [_i64]),
+    "fp_surrogate_features": (_i32, [ctypes.POINTER(FpMlp), _vp, _i64, _vp, ctypes.POINTER(Params), _vp, _vp, _vp]),
+    "fp_mlp_forward": (_i32, [ctypes.POINTER(FpMlp), _vp, _i64, _i32, _vp, _vp, _vp, _vp]),
+    "fp_closure_surrogate": (_i32, [ctypes.POINTER(FpMlp), _vp, _i64, _vp, ctypes.POINTER(Params), _i32, _vp, _vp,
+                                    _vp, _sz, _vp]),
+    "fp_surrogate_loss": (_i32, [_vp, _vp, _vp, _vp, _vp, _i64, _vp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                 ctypes.c_float, _vp, _vp, _vp, _vp]),
+    "fp_mlp_backward_workspace_bytes": (_sz, [_i64]),
+    "fp_mlp_backward": (_i32, [ctypes.POINTER(FpMlp), _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _sz, _vp]),
+    "fp_adam_step": (_i32, [_vp, _vp, _vp, _vp, _i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                            ctypes.c_float, _i64, _vp, _vp]),
 }
 
 

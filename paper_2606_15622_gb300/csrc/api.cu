@@ -17,7 +17,25 @@ void launch_velocity(void *v, int v_dtype, int64_t np, const int64_t *off, int64
 void launch_adjoint(const void *v, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, const double *tau,
                     double eps2_hat, const double *mom, const double *coeffs, const int32_t *flags, const double *gY,
                     const double *gm_in, double *gm_out, void *gv, cudaStream_t st);
+void launch_features(const fp_mlp &net, const double *mom, const double *tau, int64_t n, int min_particles,
+                     double margin, void *x, int32_t *flags, cudaStream_t st);
+int launch_mlp_forward(const fp_mlp &net, const void *x, int64_t n, int standardized_out, float *out, void *h_save,
+                       float *z_save, cudaStream_t st);
+void launch_surrogate_tail(const float *tpred, const double *mom, const double *tau, int64_t n, double eps2_hat,
+                           double energy_tol, const fp_params &p, int prec, double *coeffs, int32_t *flags,
+                           int32_t *list, uint32_t *count, cudaStream_t st);
+int64_t mlp_param_offset(int which, int layer);
+int64_t mlp_param_count();
+size_t mlp_backward_ws(int64_t n);
+void launch_mlp_backward(const fp_mlp &net, const void *x, const void *h_save, const float *z_save,
+                         const void *dout_bf, const float *dout, int64_t n, float *grads, void *ws, cudaStream_t st);
+void launch_loss(const float *out, const float *t_true, const float *aux, const float *y_mu, const float *y_sigma,
+                 int64_t n, const float *w, float lam_d, float lam_e, float eps2_hat, float scale, float *dout,
+                 void *dout_bf, float *loss_sum, cudaStream_t st);
+void launch_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2, float eps,
+                 float bc1, float bc2, void *shadow, cudaStream_t st);
 }  // namespace fpc
+
 
 namespace {
 thread_local char g_err[512] = "";
@@ -38,6 +56,26 @@ int check_launch(const char *what) {
 
 constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+int check_net(const fp_mlp *net) {
+  if (!net) return fail(FP_ERR_ARG, "null network");
+  if (net->in_dim != 32 || net->hidden != 128 || net->depth != 4 || net->out_dim != 16)
+    return fail(FP_ERR_UNSUPPORTED, "network shape %d-%dx%d-%d (32-128x4-16 supported)", net->in_dim, net->hidden,
+                net->depth, net->out_dim);
+  for (int l = 0; l < 5; ++l)
+    if (!net->W[l] || !net->b[l]) return fail(FP_ERR_ARG, "null weight or bias %d", l);
+  if (!net->x_mu || !net->x_sigma || !net->y_mu || !net->y_sigma || !net->x_min || !net->x_max)
+    return fail(FP_ERR_ARG, "null scaler");
+  return FP_OK;
+}
+size_t surrogate_ws_parts(int64_t n, size_t *off_t, size_t *off_list, size_t *off_count) {
+  const size_t x = align_up((size_t)n * 32 * 2);
+  const size_t t = align_up((size_t)n * 16 * 4);
+  const size_t l = align_up((size_t)n * 4);
+  *off_t = x;
+  *off_list = x + t;
+  *off_count = x + t + l;
+  return x + t + l + 256;
+}
 }  // namespace
 
 extern "C" {
@@ -177,6 +215,123 @@ int fp_closure_backward(const void *v, int v_dtype, int64_t n_particles, const i
   fpc::launch_adjoint(v, v_dtype, n_particles, cell_offsets, n_cells, tau, prm.eps2_hat, moments, coeffs, flags,
                       grad_coeffs, grad_moments_in, gm, grad_v, (cudaStream_t)stream);
   return check_launch("adjoint");
+}
+
+int64_t fp_mlp_param_count(void) { return fpc::mlp_param_count(); }
+
+int64_t fp_mlp_param_offset(int which, int layer) {
+  if (which < 0 || which > 1 || layer < 0 || layer > 4) return -1;
+  return fpc::mlp_param_offset(which, layer);
+}
+
+size_t fp_surrogate_workspace_bytes(int64_t n_cells) {
+  if (n_cells <= 0) return 0;
+  size_t a, b, c;
+  return surrogate_ws_parts(n_cells, &a, &b, &c);
+}
+
+int fp_surrogate_features(const fp_mlp *net, const double *moments, int64_t n_cells, const double *tau,
+                          const fp_params *p, void *x_out, int32_t *flags_out, fp_stream_t stream) {
+  g_err[0] = 0;
+  if (int rc = check_net(net)) return rc;
+  if (n_cells < 0) return fail(FP_ERR_ARG, "negative size");
+  if (n_cells == 0) return FP_OK;
+  if (!moments || !tau || !x_out || !flags_out) return fail(FP_ERR_ARG, "null array pointer");
+  if ((uintptr_t)x_out % 16) return fail(FP_ERR_ARG, "features not 16-byte aligned");
+  fp_params prm;
+  fp_default_params(&prm);
+  if (p) prm = *p;
+  fpc::launch_features(*net, moments, tau, n_cells, prm.min_particles, prm.surr_range_margin, x_out, flags_out,
+                       (cudaStream_t)stream);
+  return check_launch("features");
+}
+
+int fp_mlp_forward(const fp_mlp *net, const void *x, int64_t n, int standardized_out, float *out, void *h_save,
+                   float *z_save, fp_stream_t stream) {
+  g_err[0] = 0;
+  if (int rc = check_net(net)) return rc;
+  if (n < 0) return fail(FP_ERR_ARG, "negative size");
+  if (n == 0) return FP_OK;
+  if (!x || !out) return fail(FP_ERR_ARG, "null array pointer");
+  if ((uintptr_t)x % 16 || (uintptr_t)out % 8) return fail(FP_ERR_ARG, "misaligned x or out");
+  for (int l = 0; l < 5; ++l)
+    if ((uintptr_t)net->W[l] % 4) return fail(FP_ERR_ARG, "weights not 4-byte aligned");
+  if (fpc::launch_mlp_forward(*net, x, n, standardized_out, out, h_save, z_save, (cudaStream_t)stream))
+    return fail(FP_ERR_CUDA, "could not raise the shared-memory limit of the MLP kernel");
+  return check_launch("mlp_forward");
+}
+
+int fp_closure_surrogate(const fp_mlp *net, const double *moments, int64_t n_cells, const double *tau,
+                         const fp_params *p, int prec, double *coeffs_out, int32_t *flags_out, void *ws,
+                         size_t ws_bytes, fp_stream_t stream) {
+  g_err[0] = 0;
+  if (int rc = check_net(net)) return rc;
+  if (n_cells < 0) return fail(FP_ERR_ARG, "negative size");
+  if (n_cells == 0) return FP_OK;
+  if (prec != FP_PREC_FP64 && prec != FP_PREC_FP32_MOMENTS) return fail(FP_ERR_ARG, "prec %d", prec);
+  if (!moments || !tau || !coeffs_out || !flags_out) return fail(FP_ERR_ARG, "null array pointer");
+  size_t off_t, off_list, off_count;
+  const size_t need = surrogate_ws_parts(n_cells, &off_t, &off_list, &off_count);
+  if (!ws || ws_bytes < need) return fail(FP_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", need, ws_bytes);
+  if ((uintptr_t)ws % kAlign) return fail(FP_ERR_ARG, "workspace not 256-byte aligned");
+  fp_params prm;
+  fp_default_params(&prm);
+  if (p) prm = *p;
+  if (prm.min_particles < 1) prm.min_particles = 1;
+  char *w = (char *)ws;
+  cudaStream_t st = (cudaStream_t)stream;
+  fpc::launch_features(*net, moments, tau, n_cells, prm.min_particles, prm.surr_range_margin, w, flags_out, st);
+  if (int rc = check_launch("features")) return rc;
+  if (fpc::launch_mlp_forward(*net, w, n_cells, 0, (float *)(w + off_t), nullptr, nullptr, st))
+    return fail(FP_ERR_CUDA, "could not raise the shared-memory limit of the MLP kernel");
+  if (int rc = check_launch("mlp_forward")) return rc;
+  fpc::launch_surrogate_tail((const float *)(w + off_t), moments, tau, n_cells, net->eps2_hat, prm.surr_energy_tol,
+                             prm, prec, coeffs_out, flags_out, (int32_t *)(w + off_list), (uint32_t *)(w + off_count),
+                             st);
+  return check_launch("surrogate tail");
+}
+
+int fp_surrogate_loss(const float *out, const float *t_true, const float *aux, const float *y_mu,
+                      const float *y_sigma, int64_t n, const float *w, float lam_drift, float lam_energy,
+                      float eps2_hat, float scale, float *dout, void *dout_bf16, float *loss_sum,
+                      fp_stream_t stream) {
+  g_err[0] = 0;
+  if (n < 0) return fail(FP_ERR_ARG, "negative size");
+  if (n == 0) return FP_OK;
+  if (!out || !t_true || !aux || !y_mu || !y_sigma || !w || !dout || !dout_bf16 || !loss_sum)
+    return fail(FP_ERR_ARG, "null array pointer");
+  fpc::launch_loss(out, t_true, aux, y_mu, y_sigma, n, w, lam_drift, lam_energy, eps2_hat, scale, dout, dout_bf16,
+                   loss_sum, (cudaStream_t)stream);
+  return check_launch("loss");
+}
+
+size_t fp_mlp_backward_workspace_bytes(int64_t n) { return n > 0 ? fpc::mlp_backward_ws(n) : 0; }
+
+int fp_mlp_backward(const fp_mlp *net, const void *x, const void *h_save, const float *z_save,
+                    const void *dout_bf16, const float *dout, int64_t n, float *grads, void *ws, size_t ws_bytes,
+                    fp_stream_t stream) {
+  g_err[0] = 0;
+  if (int rc = check_net(net)) return rc;
+  if (n < 0) return fail(FP_ERR_ARG, "negative size");
+  if (n == 0) return FP_OK;
+  if (!x || !h_save || !z_save || !dout_bf16 || !dout || !grads) return fail(FP_ERR_ARG, "null array pointer");
+  const size_t need = fpc::mlp_backward_ws(n);
+  if (!ws || ws_bytes < need) return fail(FP_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", need, ws_bytes);
+  if ((uintptr_t)ws % kAlign) return fail(FP_ERR_ARG, "workspace not 256-byte aligned");
+  fpc::launch_mlp_backward(*net, x, h_save, z_save, dout_bf16, dout, n, grads, ws, (cudaStream_t)stream);
+  return check_launch("mlp_backward");
+}
+
+int fp_adam_step(float *params, const float *grads, float *m, float *v, int64_t n_params, float lr, float beta1,
+                 float beta2, float eps, int64_t t, void *shadow_bf16, fp_stream_t stream) {
+  g_err[0] = 0;
+  if (n_params < 0 || t < 1) return fail(FP_ERR_ARG, "n_params < 0 or t < 1");
+  if (n_params == 0) return FP_OK;
+  if (!params || !grads || !m || !v) return fail(FP_ERR_ARG, "null array pointer");
+  const float bc1 = (float)(1.0 - pow((double)beta1, (double)t));
+  const float bc2 = (float)(1.0 - pow((double)beta2, (double)t));
+  fpc::launch_adam(params, grads, m, v, n_params, lr, beta1, beta2, eps, bc1, bc2, shadow_bf16, (cudaStream_t)stream);
+  return check_launch("adam");
 }
 
 }  // extern "C"

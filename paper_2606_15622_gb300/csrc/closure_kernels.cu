@@ -261,37 +261,8 @@ __global__ void __launch_bounds__(128) solve_kernel(const double *__restrict__ m
                                                     int32_t *__restrict__ flags) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_cells) return;
-  double m[FP_NMOM];
-  const double *mc = mom + c * FP_NMOM;
-#pragma unroll
-  for (int k = 0; k < FP_NMOM; ++k) m[k] = mc[k];
-  const double tc = tau[c];
-  int fl = 0;
-  bool fin = finite_d(tc) && tc > 0.0;
-#pragma unroll
-  for (int k = 0; k < FP_NMOM; ++k) fin = fin && finite_d(m[k]);
-  if (!fin) fl |= FP_FLAG_NONFINITE;
-  if (m[kN] < (double)prm.min_particles) fl |= FP_FLAG_FEW;
-  if (!(m[kTheta] > 0.0)) fl |= FP_FLAG_SINGULAR;
   double y[9];
-  if (!fl) {
-    double a[9][10];
-    assemble(m, tc, prm.eps2_hat, a);
-    fl |= pivoted_solve(a, prm.pivot_rtol, y);
-    if (!fl) {
-#pragma unroll
-      for (int q = 0; q < 9; ++q)
-        if (!finite_d(y[q])) fl |= FP_FLAG_NONFINITE;
-    }
-  }
-  if (fl) {
-    const double c0 = (finite_d(tc) && tc > 0.0) ? -1.0 / tc : 0.0;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) y[q] = 0.0;
-    y[0] = c0;
-    y[3] = c0;
-    y[5] = c0;
-  }
+  const int fl = closure_cell(mom + c * FP_NMOM, tau[c], prm, y);
   double *yc = coeffs + c * 9;
 #pragma unroll
   for (int q = 0; q < 9; ++q) yc[q] = y[q];

@@ -162,4 +162,40 @@ __device__ __forceinline__ int pivoted_solve(double (&a)[9][10], double rtol, do
   return flag;
 }
 
+
+// The closure of one cell from its moment vector: flags, and Y (the linear
+// drift C = -I/tau, G = 0 for flagged cells).
+__device__ __forceinline__ int closure_cell(const double *__restrict__ mc, double tc, const SolveParams &prm,
+                                            double (&y)[9]) {
+  double m[FP_NMOM];
+#pragma unroll
+  for (int k = 0; k < FP_NMOM; ++k) m[k] = mc[k];
+  int fl = 0;
+  bool fin = finite_d(tc) && tc > 0.0;
+#pragma unroll
+  for (int k = 0; k < FP_NMOM; ++k) fin = fin && finite_d(m[k]);
+  if (!fin) fl |= FP_FLAG_NONFINITE;
+  if (m[kN] < (double)prm.min_particles) fl |= FP_FLAG_FEW;
+  if (!(m[kTheta] > 0.0)) fl |= FP_FLAG_SINGULAR;
+  if (!fl) {
+    double a[9][10];
+    assemble(m, tc, prm.eps2_hat, a);
+    fl |= pivoted_solve(a, prm.pivot_rtol, y);
+    if (!fl) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q)
+        if (!finite_d(y[q])) fl |= FP_FLAG_NONFINITE;
+    }
+  }
+  if (fl) {
+    const double c0 = (finite_d(tc) && tc > 0.0) ? -1.0 / tc : 0.0;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) y[q] = 0.0;
+    y[0] = c0;
+    y[3] = c0;
+    y[5] = c0;
+  }
+  return fl;
+}
+
 }  // namespace fpc

@@ -1,0 +1,381 @@
+// mlp.cu -- the learned closure: features, the fused BF16 tensor-core MLP,
+// the surrogate epilogue with its range / energy checks, and the exact
+// per-cell fallback (sm_103a).
+//
+// Features: the 25 moments of w = c / sqrt(theta) (u/theta, u3/theta^1.5,
+// w/theta^2, z/theta^2.5), standardised, BF16, zero padded to 32.  The
+// network maps them to the standardised dimensionless coefficients
+// (tau C, tau sqrt(theta) G); the cubic-FP system of Eq. system9x9 is
+// invariant under c -> c/sqrt(theta), so those depend on the features alone.
+//
+// Fused forward: one CTA of 8 warps holds all five weight matrices in shared
+// memory (~120 KB, loaded once) and streams 128-row tiles; each warp owns 16
+// rows for the whole network, so a layer's activations go from the FP32
+// accumulators through bias + SiLU to BF16 in the warp's own rows of the
+// activation tile and feed the next layer with no block barrier.  The MMAs
+// are mma.sync m16n8k16 (BF16 x BF16 -> FP32).
+#include <cstdint>
+#include <cuda_bf16.h>
+
+#include "closure_math.cuh"
+#include "fp_device.cuh"
+#include "mlp_common.cuh"
+
+namespace fpc {
+
+struct MlpDev {
+  const __nv_bfloat16 *W[5];
+  const float *b[5];
+  const float *x_mu, *x_sigma, *y_mu, *y_sigma, *x_min, *x_max;
+};
+
+constexpr int kWS1 = kIn + 8;    // smem row stride (bf16) of W1
+constexpr int kWSH = kHid + 8;   // smem row stride of W2..W5 and of the activation tile
+constexpr int kRows = 128;       // rows per CTA tile
+constexpr int kMlpWarps = 8;
+constexpr int kMlpThreads = 32 * kMlpWarps;
+constexpr size_t kMlpSmem =
+    (size_t)(kHid * kWS1 + 3 * kHid * kWSH + kOut * kWSH + kRows * kWSH) * sizeof(__nv_bfloat16) +
+    (size_t)(4 * kHid + kOut) * sizeof(float);
+
+// ---------------------------------------------------------------------------
+// features
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cell_features(const double *__restrict__ m, float (&f)[kNFeat]) {
+  const float th = (float)m[kTheta];
+  const float i1 = 1.f / th;
+  const float ih = rsqrtf(th);
+  const float i15 = i1 * ih, i2 = i1 * i1, i25 = i2 * ih;
+#pragma unroll
+  for (int a = 0; a < 6; ++a) f[a] = (float)m[kU2 + a] * i1;
+#pragma unroll
+  for (int a = 0; a < 10; ++a) f[6 + a] = (float)m[kU3 + a] * i15;
+#pragma unroll
+  for (int a = 0; a < 6; ++a) f[16 + a] = (float)m[kW + a] * i2;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) f[22 + a] = (float)m[kZ + a] * i25;
+}
+
+__global__ void __launch_bounds__(256) features_kernel(MlpDev net, const double *__restrict__ mom,
+                                                       const double *__restrict__ tau, int64_t n, int min_particles,
+                                                       float margin, __nv_bfloat16 *__restrict__ x,
+                                                       int32_t *__restrict__ flags) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const double *m = mom + c * FP_NMOM;
+  int fl = 0;
+  bool fin = finite_d(tau[c]) && tau[c] > 0.0;
+#pragma unroll
+  for (int k = 0; k < FP_NMOM; ++k) fin = fin && finite_d(m[k]);
+  if (!fin) fl |= FP_FLAG_NONFINITE;
+  if (m[kN] < (double)min_particles) fl |= FP_FLAG_FEW;
+  if (!(m[kTheta] > 0.0)) fl |= FP_FLAG_SINGULAR;
+  float f[kNFeat];
+  cell_features(m, f);
+  uint32_t packed[kIn / 2];
+#pragma unroll
+  for (int k = 0; k < kIn; k += 2) {
+    float xs[2] = {0.f, 0.f};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = k + h;
+      if (q < kNFeat) {
+        const float sg = net.x_sigma[q];
+        const float lo = net.x_min[q] - margin * sg, hi = net.x_max[q] + margin * sg;
+        if (!(f[q] >= lo && f[q] <= hi)) fl |= FP_FLAG_RANGE;
+        xs[h] = (f[q] - net.x_mu[q]) / sg;
+      }
+    }
+    packed[k / 2] = pack_bf16(xs[0], xs[1]);
+  }
+  uint4 *dst = reinterpret_cast<uint4 *>(x + c * kIn);
+#pragma unroll
+  for (int q = 0; q < kIn / 8; ++q)
+    dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
+  flags[c] = fl;
+}
+
+// ---------------------------------------------------------------------------
+// fused forward
+// ---------------------------------------------------------------------------
+// One layer for the warp's 16 rows: acc[NT][4] = act[rows][0:K] . W^T
+template <int K, int NT, int WS>
+__device__ __forceinline__ void warp_layer(const __nv_bfloat16 *__restrict__ act, const __nv_bfloat16 *__restrict__ W,
+                                           float (&acc)[NT][4], int r0, int lane) {
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    const uint32_t a0 = *reinterpret_cast<const uint32_t *>(act + (r0 + g) * kWSH + k0 + 2 * t);
+    const uint32_t a1 = *reinterpret_cast<const uint32_t *>(act + (r0 + g + 8) * kWSH + k0 + 2 * t);
+    const uint32_t a2 = *reinterpret_cast<const uint32_t *>(act + (r0 + g) * kWSH + k0 + 8 + 2 * t);
+    const uint32_t a3 = *reinterpret_cast<const uint32_t *>(act + (r0 + g + 8) * kWSH + k0 + 8 + 2 * t);
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      const __nv_bfloat16 *wr = W + (nt * 8 + g) * WS + k0 + 2 * t;
+      const uint32_t b0 = *reinterpret_cast<const uint32_t *>(wr);
+      const uint32_t b1 = *reinterpret_cast<const uint32_t *>(wr + 8);
+      mma_bf16(acc[nt], a0, a1, a2, a3, b0, b1);
+    }
+  }
+}
+
+template <bool kSave>
+__global__ void __launch_bounds__(kMlpThreads, 1)
+    mlp_forward_kernel(MlpDev net, const __nv_bfloat16 *__restrict__ x, int64_t n, int standardized_out,
+                       float *__restrict__ out, __nv_bfloat16 *__restrict__ h_save, float *__restrict__ z_save) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __nv_bfloat16 *W1 = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
+  __nv_bfloat16 *WH = W1 + kHid * kWS1;          // W2, W3, W4
+  __nv_bfloat16 *W5 = WH + 3 * kHid * kWSH;
+  __nv_bfloat16 *act = W5 + kOut * kWSH;
+  float *bias = reinterpret_cast<float *>(act + kRows * kWSH);  // b1..b4 [4][128], b5 [16]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  // weights and biases into shared memory (once per CTA)
+  for (int i = tid; i < kHid * kIn / 2; i += kMlpThreads) {
+    const int r = (2 * i) / kIn, cidx = (2 * i) % kIn;
+    *reinterpret_cast<uint32_t *>(W1 + r * kWS1 + cidx) = *reinterpret_cast<const uint32_t *>(net.W[0] + 2 * i);
+  }
+  for (int l = 0; l < 3; ++l)
+    for (int i = tid; i < kHid * kHid / 2; i += kMlpThreads) {
+      const int r = (2 * i) / kHid, cidx = (2 * i) % kHid;
+      *reinterpret_cast<uint32_t *>(WH + l * kHid * kWSH + r * kWSH + cidx) =
+          *reinterpret_cast<const uint32_t *>(net.W[1 + l] + 2 * i);
+    }
+  for (int i = tid; i < kOut * kHid / 2; i += kMlpThreads) {
+    const int r = (2 * i) / kHid, cidx = (2 * i) % kHid;
+    *reinterpret_cast<uint32_t *>(W5 + r * kWSH + cidx) = *reinterpret_cast<const uint32_t *>(net.W[4] + 2 * i);
+  }
+  for (int i = tid; i < 4 * kHid + kOut; i += kMlpThreads) bias[i] = i < 4 * kHid ? net.b[i / kHid][i % kHid] : net.b[4][i - 4 * kHid];
+  __syncthreads();
+
+  const int g = lane >> 2, t = lane & 3;
+  const int r0 = warp * 16;
+  const int64_t n_tiles = (n + kRows - 1) / kRows;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t row0 = tile * kRows + r0;  // first global row of this warp
+    // input rows -> act[:, 0:32]; 16 rows x 64 B = 64 x 16 B, two per lane
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int e = lane + 32 * q;  // 0..63
+      const int rr = e >> 2, part = e & 3;
+      uint4 val = make_uint4(0u, 0u, 0u, 0u);
+      if (row0 + rr < n) val = *reinterpret_cast<const uint4 *>(x + (row0 + rr) * kIn + part * 8);
+      *reinterpret_cast<uint4 *>(act + (r0 + rr) * kWSH + part * 8) = val;
+    }
+    __syncwarp();
+    // hidden layers
+#pragma unroll 1
+    for (int l = 0; l < 4; ++l) {
+      float acc[kHid / 8][4];
+      if (l == 0)
+        warp_layer<kIn, kHid / 8, kWS1>(act, W1, acc, r0, lane);
+      else
+        warp_layer<kHid, kHid / 8, kWSH>(act, WH + (l - 1) * kHid * kWSH, acc, r0, lane);
+      __syncwarp();
+      const float *bl = bias + l * kHid;
+#pragma unroll
+      for (int nt = 0; nt < kHid / 8; ++nt) {
+        const int col = nt * 8 + 2 * t;
+        const float z0 = acc[nt][0] + bl[col], z1 = acc[nt][1] + bl[col + 1];
+        const float z2 = acc[nt][2] + bl[col], z3 = acc[nt][3] + bl[col + 1];
+        const uint32_t h01 = pack_bf16(silu(z0), silu(z1)), h23 = pack_bf16(silu(z2), silu(z3));
+        *reinterpret_cast<uint32_t *>(act + (r0 + g) * kWSH + col) = h01;
+        *reinterpret_cast<uint32_t *>(act + (r0 + g + 8) * kWSH + col) = h23;
+        if (kSave) {
+          const int64_t ra = row0 + g, rb = row0 + g + 8;
+          const size_t plane = (size_t)n * kHid * l;
+          if (ra < n) {
+            *reinterpret_cast<float2 *>(z_save + plane + ra * kHid + col) = make_float2(z0, z1);
+            *reinterpret_cast<uint32_t *>(h_save + plane + ra * kHid + col) = h01;
+          }
+          if (rb < n) {
+            *reinterpret_cast<float2 *>(z_save + plane + rb * kHid + col) = make_float2(z2, z3);
+            *reinterpret_cast<uint32_t *>(h_save + plane + rb * kHid + col) = h23;
+          }
+        }
+      }
+      __syncwarp();
+    }
+    // output layer (16 columns, 9 used)
+    float acc[kOut / 8][4];
+    warp_layer<kHid, kOut / 8, kWSH>(act, W5, acc, r0, lane);
+    const float *b5 = bias + 4 * kHid;
+#pragma unroll
+    for (int nt = 0; nt < kOut / 8; ++nt) {
+      const int col = nt * 8 + 2 * t;
+      float o[4] = {acc[nt][0] + b5[col], acc[nt][1] + b5[col + 1], acc[nt][2] + b5[col], acc[nt][3] + b5[col + 1]};
+      if (!standardized_out) {
+        const float m0 = net.y_mu[col], m1 = net.y_mu[col + 1], s0 = net.y_sigma[col], s1 = net.y_sigma[col + 1];
+        o[0] = fmaf(o[0], s0, m0);
+        o[1] = fmaf(o[1], s1, m1);
+        o[2] = fmaf(o[2], s0, m0);
+        o[3] = fmaf(o[3], s1, m1);
+      }
+      const int64_t ra = row0 + g, rb = row0 + g + 8;
+      if (ra < n) *reinterpret_cast<float2 *>(out + ra * kOut + col) = make_float2(o[0], o[1]);
+      if (rb < n) *reinterpret_cast<float2 *>(out + rb * kOut + col) = make_float2(o[2], o[3]);
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// surrogate epilogue: dimensionless targets -> C, G; energy check
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) surrogate_epilogue_kernel(const float *__restrict__ tpred,
+                                                                 const double *__restrict__ mom,
+                                                                 const double *__restrict__ tau, int64_t n,
+                                                                 float eps2_hat, float energy_tol,
+                                                                 double *__restrict__ coeffs,
+                                                                 int32_t *__restrict__ flags) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  int fl = flags[c];
+  if (fl & (FP_FLAG_FEW | FP_FLAG_SINGULAR | FP_FLAG_NONFINITE)) return;  // the exact fallback decides
+  float tp[kNOut];
+  bool fin = true;
+#pragma unroll
+  for (int a = 0; a < kNOut; ++a) {
+    tp[a] = tpred[c * kOut + a];
+    fin = fin && isfinite(tp[a]);
+  }
+  float f[kNFeat];
+  cell_features(mom + c * FP_NMOM, f);
+  // e = 1 + (sum_ij C_hat_ij u_hat_ij + sum_i G_hat_i b_hat_i - eps2_hat s4_hat) / 3
+  const float cu = tp[0] * f[0] + 2.f * tp[1] * f[1] + 2.f * tp[2] * f[2] + tp[3] * f[3] + 2.f * tp[4] * f[4] +
+                   tp[5] * f[5];
+  const float b0 = f[6 + 0] + f[6 + 3] + f[6 + 5], b1 = f[6 + 1] + f[6 + 6] + f[6 + 8],
+              b2 = f[6 + 2] + f[6 + 7] + f[6 + 9];
+  const float s4 = f[16] + f[19] + f[21];
+  const float e = 1.f + (cu + tp[6] * b0 + tp[7] * b1 + tp[8] * b2 - eps2_hat * s4) * (1.f / 3.f);
+  if (!fin) fl |= FP_FLAG_NONFINITE;
+  if (!(fabsf(e) <= energy_tol)) fl |= FP_FLAG_ENERGY;
+  const double itc = 1.0 / tau[c];
+  const double ig = itc / sqrt(mom[c * FP_NMOM + kTheta]);
+  double *y = coeffs + c * 9;
+#pragma unroll
+  for (int a = 0; a < 6; ++a) y[a] = (double)tp[a] * itc;
+#pragma unroll
+  for (int a = 6; a < 9; ++a) y[a] = (double)tp[a] * ig;
+  flags[c] = fl;
+}
+
+// ---------------------------------------------------------------------------
+// fallback: compact the flagged cells, solve them exactly
+// ---------------------------------------------------------------------------
+constexpr int kFallbackMask = FP_FLAG_FEW | FP_FLAG_SINGULAR | FP_FLAG_NONFINITE | FP_FLAG_RANGE | FP_FLAG_ENERGY;
+
+__global__ void __launch_bounds__(256) compact_kernel(const int32_t *__restrict__ flags, int64_t n,
+                                                      int32_t *__restrict__ list, uint32_t *__restrict__ count) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool pick = c < n && (flags[c] & kFallbackMask);
+  const unsigned m = __ballot_sync(0xffffffffu, pick);
+  if (!m) return;
+  const int lane = threadIdx.x & 31;
+  uint32_t base = 0;
+  if (lane == 0) base = atomicAdd(count, (uint32_t)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (pick) list[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)c;
+}
+
+__global__ void __launch_bounds__(128) fallback_kernel(const int32_t *__restrict__ list,
+                                                       const uint32_t *__restrict__ count,
+                                                       const double *__restrict__ mom, const double *__restrict__ tau,
+                                                       SolveParams prm, double *__restrict__ coeffs,
+                                                       int32_t *__restrict__ flags) {
+  const uint32_t cnt = *count;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    const int64_t c = list[i];
+    double y[9];
+    const int fe = closure_cell(mom + c * FP_NMOM, tau[c], prm, y);
+    double *yc = coeffs + c * 9;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) yc[q] = y[q];
+    flags[c] = fe | (flags[c] & (FP_FLAG_RANGE | FP_FLAG_ENERGY)) | FP_FLAG_FALLBACK;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static int mlp_sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 152;
+  }
+  return n;
+}
+
+static int g_mlp_attr_done[64][2];
+
+MlpDev make_mlp_dev(const fp_mlp &m) {
+  MlpDev d;
+  for (int l = 0; l < 5; ++l) {
+    d.W[l] = reinterpret_cast<const __nv_bfloat16 *>(m.W[l]);
+    d.b[l] = m.b[l];
+  }
+  d.x_mu = m.x_mu;
+  d.x_sigma = m.x_sigma;
+  d.y_mu = m.y_mu;
+  d.y_sigma = m.y_sigma;
+  d.x_min = m.x_min;
+  d.x_max = m.x_max;
+  return d;
+}
+
+void launch_features(const fp_mlp &net, const double *mom, const double *tau, int64_t n, int min_particles,
+                     double margin, void *x, int32_t *flags, cudaStream_t st) {
+  const int64_t blocks = (n + 255) / 256;
+  features_kernel<<<(unsigned)blocks, 256, 0, st>>>(make_mlp_dev(net), mom, tau, n, min_particles, (float)margin,
+                                                     reinterpret_cast<__nv_bfloat16 *>(x), flags);
+}
+
+int launch_mlp_forward(const fp_mlp &net, const void *x, int64_t n, int standardized_out, float *out, void *h_save,
+                       float *z_save, cudaStream_t st) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int save = (h_save != nullptr && z_save != nullptr) ? 1 : 0;
+  if (dev >= 0 && dev < 64 && !g_mlp_attr_done[dev][save]) {
+    cudaError_t e = save ? cudaFuncSetAttribute(mlp_forward_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)kMlpSmem)
+                         : cudaFuncSetAttribute(mlp_forward_kernel<false>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMlpSmem);
+    if (e != cudaSuccess) return -1;
+    g_mlp_attr_done[dev][save] = 1;
+  }
+  const int64_t n_tiles = (n + kRows - 1) / kRows;
+  int64_t grid = mlp_sm_count();
+  if (grid > n_tiles) grid = n_tiles;
+  if (grid < 1) grid = 1;
+  const MlpDev d = make_mlp_dev(net);
+  const __nv_bfloat16 *xb = reinterpret_cast<const __nv_bfloat16 *>(x);
+  if (save)
+    mlp_forward_kernel<true><<<(unsigned)grid, kMlpThreads, kMlpSmem, st>>>(
+        d, xb, n, standardized_out, out, reinterpret_cast<__nv_bfloat16 *>(h_save), z_save);
+  else
+    mlp_forward_kernel<false><<<(unsigned)grid, kMlpThreads, kMlpSmem, st>>>(d, xb, n, standardized_out, out,
+                                                                             nullptr, nullptr);
+  return 0;
+}
+
+void launch_surrogate_tail(const float *tpred, const double *mom, const double *tau, int64_t n, double eps2_hat,
+                           double energy_tol, const fp_params &p, int prec, double *coeffs, int32_t *flags,
+                           int32_t *list, uint32_t *count, cudaStream_t st) {
+  const int64_t blocks = (n + 255) / 256;
+  surrogate_epilogue_kernel<<<(unsigned)blocks, 256, 0, st>>>(tpred, mom, tau, n, (float)eps2_hat,
+                                                               (float)energy_tol, coeffs, flags);
+  cudaMemsetAsync(count, 0, sizeof(uint32_t), st);
+  compact_kernel<<<(unsigned)blocks, 256, 0, st>>>(flags, n, list, count);
+  double rtol = p.pivot_rtol;
+  if (prec == FP_PREC_FP32_MOMENTS && rtol < FP_FP32_PIVOT_FLOOR) rtol = FP_FP32_PIVOT_FLOOR;
+  SolveParams prm{p.eps2_hat, rtol, p.min_particles};
+  fallback_kernel<<<(unsigned)(mlp_sm_count() * 4), 128, 0, st>>>(list, count, mom, tau, prm, coeffs, flags);
+}
+
+}  // namespace fpc

@@ -1,0 +1,35 @@
+// mlp_common.cuh -- shapes and helpers of the surrogate network
+// (32 -> 128 -> 128 -> 128 -> 128 -> 16, SiLU, BF16 operands, FP32
+// accumulation) shared by the inference and training kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_bf16.h>
+
+namespace fpc {
+
+constexpr int kIn = 32, kHid = 128, kOut = 16, kDepth = 4, kNFeat = 25, kNOut = 9;
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x = lo (low half)
+  return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.f + __expf(-z)); }
+
+__device__ __forceinline__ float silu_grad(float z) {
+  const float s = __fdividef(1.f, 1.f + __expf(-z));
+  return s * (1.f + z * (1.f - s));
+}
+
+// D = A * B + C for one m16n8k16 tile (BF16 x BF16 -> FP32)
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+}  // namespace fpc

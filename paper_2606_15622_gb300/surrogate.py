@@ -1,0 +1,333 @@
+"""The learned closure: network container, training on exact-closure data,
+and the surrogate call (paper Sec. 4: phases 1-3; Alg. 2).
+
+Every numerical step of training and inference runs in libfpclosure's
+kernels (features, fused BF16 MLP forward, loss + gradient, BF16 backward
+GEMMs, Adam, exact fallback); torch provides device memory, the data
+shuffling and the scaler statistics of the training set.
+
+Weight file (little-endian): magic b"FPCW", u32 version, u32 dims (32, 128,
+4, 16), f64 eps2_hat, u64 training seed, then FP32 arrays: the flat
+parameters (fp_mlp_param_count), x_mu, x_sigma, x_min, x_max [32],
+y_mu, y_sigma [16].
+"""
+
+from __future__ import annotations
+
+import ctypes
+import io
+import os
+import struct
+import time
+
+import numpy as np
+import torch
+
+from . import api
+
+IN, HID, OUT, DEPTH, NFEAT, NOUT = 32, 128, 16, 4, 25, 9
+MAGIC = b"FPCW"
+VERSION = 1
+
+
+FpMlp = api.FpMlp
+
+
+def _lib():
+    return api.lib()
+
+
+def param_count() -> int:
+    return int(_lib().fp_mlp_param_count())
+
+
+def param_offset(which: int, layer: int) -> int:
+    return int(_lib().fp_mlp_param_offset(which, layer))
+
+
+def _p(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Surrogate:
+    """Parameters (FP32 master + BF16 shadow), scalers and the fp_mlp view."""
+
+    def __init__(self, device="cuda", eps2_hat=1e-3, seed=0):
+        self.device = torch.device(device)
+        self.eps2_hat = float(eps2_hat)
+        self.seed = int(seed)
+        n = param_count()
+        self.params = torch.zeros(n, dtype=torch.float32, device=self.device)
+        self.shadow = torch.zeros(n, dtype=torch.bfloat16, device=self.device)
+        self.x_mu = torch.zeros(IN, dtype=torch.float32, device=self.device)
+        self.x_sigma = torch.ones(IN, dtype=torch.float32, device=self.device)
+        self.x_min = torch.full((IN,), -3e38, dtype=torch.float32, device=self.device)
+        self.x_max = torch.full((IN,), 3e38, dtype=torch.float32, device=self.device)
+        self.y_mu = torch.zeros(OUT, dtype=torch.float32, device=self.device)
+        self.y_sigma = torch.ones(OUT, dtype=torch.float32, device=self.device)
+        self._net = None
+
+    # ---- parameters ----------------------------------------------------
+    def layer_views(self):
+        dims = [(HID, IN), (HID, HID), (HID, HID), (HID, HID), (OUT, HID)]
+        W = [self.params[param_offset(0, l):param_offset(0, l) + o * i].view(o, i) for l, (o, i) in enumerate(dims)]
+        b = [self.params[param_offset(1, l):param_offset(1, l) + o] for l, (o, _) in enumerate(dims)]
+        return W, b
+
+    def init_params(self, seed=None):
+        """He-style init (uniform scaled 1/sqrt(fan_in)); padded inputs and
+        outputs are zero."""
+        g = torch.Generator(device="cpu").manual_seed(self.seed if seed is None else seed)
+        W, b = self.layer_views()
+        for l, w in enumerate(W):
+            fan_in = w.shape[1] if l > 0 else NFEAT
+            w.copy_((torch.rand(w.shape, generator=g) * 2 - 1) * np.sqrt(3.0 / fan_in))
+            b[l].zero_()
+        W[0][:, NFEAT:] = 0
+        W[4][NOUT:, :] = 0
+        self.sync_shadow()
+
+    def set_params(self, Ws, bs):
+        W, b = self.layer_views()
+        for l in range(5):
+            W[l].copy_(torch.as_tensor(np.asarray(Ws[l]), dtype=torch.float32))
+            b[l].copy_(torch.as_tensor(np.asarray(bs[l]), dtype=torch.float32))
+        self.sync_shadow()
+
+    def sync_shadow(self):
+        self.shadow.copy_(self.params.to(torch.bfloat16))
+        self._net = None
+
+    def net(self) -> FpMlp:
+        if self._net is None:
+            m = FpMlp()
+            for l in range(5):
+                m.W[l] = self.shadow.data_ptr() + 2 * param_offset(0, l)
+                m.b[l] = self.params.data_ptr() + 4 * param_offset(1, l)
+            m.x_mu, m.x_sigma = self.x_mu.data_ptr(), self.x_sigma.data_ptr()
+            m.y_mu, m.y_sigma = self.y_mu.data_ptr(), self.y_sigma.data_ptr()
+            m.x_min, m.x_max = self.x_min.data_ptr(), self.x_max.data_ptr()
+            m.in_dim, m.hidden, m.depth, m.out_dim = IN, HID, DEPTH, OUT
+            m.eps2_hat = self.eps2_hat
+            self._net = m
+        return self._net
+
+    # ---- kernels -------------------------------------------------------
+    def features(self, moments, tau, params=None, x_out=None, flags_out=None, stream=None):
+        n = moments.shape[0]
+        x = x_out if x_out is not None else torch.empty((n, IN), dtype=torch.bfloat16, device=self.device)
+        fl = flags_out if flags_out is not None else torch.empty(n, dtype=torch.int32, device=self.device)
+        p = params if params is not None else api.default_params(eps2_hat=self.eps2_hat)
+        rc = _lib().fp_surrogate_features(ctypes.byref(self.net()), _p(moments), n, _p(tau), ctypes.byref(p),
+                                          _p(x), _p(fl), api._stream(stream))
+        api._check(rc, "fp_surrogate_features")
+        return x, fl
+
+    def forward(self, x, standardized=True, save=False, out=None, stream=None):
+        n = x.shape[0]
+        o = out if out is not None else torch.empty((n, OUT), dtype=torch.float32, device=self.device)
+        h = z = None
+        if save:
+            h = torch.empty((DEPTH, n, HID), dtype=torch.bfloat16, device=self.device)
+            z = torch.empty((DEPTH, n, HID), dtype=torch.float32, device=self.device)
+        rc = _lib().fp_mlp_forward(ctypes.byref(self.net()), _p(x), n, int(bool(standardized)), _p(o), _p(h), _p(z),
+                                   api._stream(stream))
+        api._check(rc, "fp_mlp_forward")
+        return (o, h, z) if save else o
+
+    def closure(self, moments, tau, params=None, prec="fp64", coeffs_out=None, flags_out=None, workspace=None,
+                stream=None):
+        """The surrogate closure with exact fallback -> (coeffs, flags)."""
+        n = moments.shape[0]
+        y = coeffs_out if coeffs_out is not None else torch.empty((n, 9), dtype=torch.float64, device=self.device)
+        fl = flags_out if flags_out is not None else torch.empty(n, dtype=torch.int32, device=self.device)
+        need = int(_lib().fp_surrogate_workspace_bytes(n))
+        ws = workspace if workspace is not None else torch.empty(need, dtype=torch.uint8, device=self.device)
+        p = params if params is not None else api.default_params(eps2_hat=self.eps2_hat)
+        rc = _lib().fp_closure_surrogate(ctypes.byref(self.net()), _p(moments), n, _p(tau), ctypes.byref(p),
+                                         api._PREC.get(prec, prec), _p(y), _p(fl), _p(ws), ws.numel(),
+                                         api._stream(stream))
+        api._check(rc, "fp_closure_surrogate")
+        return y, fl
+
+    # ---- persistence ---------------------------------------------------
+    def save(self, path):
+        buf = io.BytesIO()
+        buf.write(MAGIC)
+        buf.write(struct.pack("<IIIIIdQ", VERSION, IN, HID, DEPTH, OUT, self.eps2_hat, self.seed))
+        for t in (self.params, self.x_mu, self.x_sigma, self.x_min, self.x_max, self.y_mu, self.y_sigma):
+            buf.write(t.detach().cpu().numpy().astype("<f4").tobytes())
+        tmp = path + ".tmp"
+        with open(tmp, "wb") as f:
+            f.write(buf.getvalue())
+        os.replace(tmp, path)
+
+    @classmethod
+    def load(cls, path, device="cuda"):
+        raw = open(path, "rb").read()
+        if raw[:4] != MAGIC:
+            raise api.FPError(f"{path}: not a weight file")
+        ver, i, h, d, o, eps2_hat, seed = struct.unpack("<IIIIIdQ", raw[4:4 + 36])
+        if ver != VERSION or (i, h, d, o) != (IN, HID, DEPTH, OUT):
+            raise api.FPError(f"{path}: unsupported version/shape")
+        s = cls(device=device, eps2_hat=eps2_hat, seed=seed)
+        arr = np.frombuffer(raw[40:], dtype="<f4")
+        n = param_count()
+        parts = [n, IN, IN, IN, IN, OUT, OUT]
+        if arr.size != sum(parts):
+            raise api.FPError(f"{path}: truncated")
+        pos = 0
+        for t, k in zip((s.params, s.x_mu, s.x_sigma, s.x_min, s.x_max, s.y_mu, s.y_sigma), parts):
+            t.copy_(torch.from_numpy(arr[pos:pos + k].copy()))
+            pos += k
+        s.sync_shadow()
+        return s
+
+
+# ---------------------------------------------------------------------------
+# training data and training
+# ---------------------------------------------------------------------------
+def raw_features_t(mom):
+    """[n, 25] normalised moments (u/theta, u3/theta^1.5, w/theta^2, z/theta^2.5)."""
+    th = mom[:, 4:5]
+    return torch.cat([mom[:, 5:11] / th, mom[:, 11:21] / th ** 1.5, mom[:, 21:27] / th ** 2,
+                      mom[:, 27:30] / th ** 2.5], dim=1)
+
+
+def dimensionless(coeffs, mom, tau):
+    th = mom[:, 4]
+    return torch.cat([coeffs[:, :6] * tau[:, None], coeffs[:, 6:] * (tau * th.sqrt())[:, None]], dim=1)
+
+
+def aux_from_features(f):
+    """(u_hat (6), b_hat (3), s4_hat, 0 x 6) per row, FP32 [n, 16]."""
+    b = torch.stack([f[:, 6] + f[:, 9] + f[:, 11], f[:, 7] + f[:, 12] + f[:, 14], f[:, 8] + f[:, 13] + f[:, 15]],
+                    dim=1)
+    s4 = (f[:, 16] + f[:, 19] + f[:, 21])[:, None]
+    out = torch.zeros((f.shape[0], 16), dtype=torch.float32, device=f.device)
+    out[:, :6] = f[:, :6]
+    out[:, 6:9] = b
+    out[:, 9:10] = s4
+    return out
+
+
+class TrainingSet:
+    """Cells labelled by the exact FP64 GPU closure: raw features, targets,
+    aux moments; cells the exact closure flags, and coefficients beyond
+    1e6 in magnitude (dimensionless), are dropped."""
+
+    def __init__(self, pop, eps2_hat=1e-3, device="cuda", chunk=262144):
+        dev = torch.device(device)
+        prm = api.default_params(eps2_hat=eps2_hat)
+        feats, targs = [], []
+        n_cells = pop.n_cells
+        for c0 in range(0, n_cells, chunk):
+            c1 = min(n_cells, c0 + chunk)
+            a, b = int(pop.offsets[c0]), int(pop.offsets[c1])
+            v = torch.from_numpy(np.ascontiguousarray(pop.v64[:, a:b])).to(dev)
+            off = torch.from_numpy(pop.offsets[c0:c1 + 1] - a).to(dev)
+            tau = torch.from_numpy(pop.tau[c0:c1]).to(dev)
+            mom, y, fl = api.fp_closure_exact(v, off, tau, params=prm, prec="fp64")
+            t = dimensionless(y, mom, tau)
+            f = raw_features_t(mom)
+            keep = (fl == 0) & torch.isfinite(t).all(1) & (t.abs() <= 1e6).all(1) & torch.isfinite(f).all(1)
+            feats.append(f[keep].float())
+            targs.append(t[keep].float())
+        self.f = torch.cat(feats)
+        self.t = torch.cat(targs)
+        self.aux = aux_from_features(self.f)
+        self.eps2_hat = eps2_hat
+
+    def __len__(self):
+        return self.f.shape[0]
+
+
+def fit_scalers(s: Surrogate, ts: TrainingSet):
+    f, t = ts.f.double(), ts.t.double()
+    mu = f.mean(0)
+    sd = f.std(0).clamp_min(1e-6)
+    s.x_mu[:NFEAT] = mu.float()
+    s.x_sigma[:NFEAT] = sd.float()
+    s.x_min[:NFEAT] = f.min(0).values.float()
+    s.x_max[:NFEAT] = f.max(0).values.float()
+    s.x_mu[NFEAT:] = 0
+    s.x_sigma[NFEAT:] = 1
+    s.x_min[NFEAT:] = -1
+    s.x_max[NFEAT:] = 1
+    s.y_mu[:NOUT] = t.mean(0).float()
+    s.y_sigma[:NOUT] = t.std(0).clamp_min(1e-6).float()
+    s.y_mu[NOUT:] = 0
+    s.y_sigma[NOUT:] = 1
+    s._net = None
+
+
+def standardized_inputs(s: Surrogate, f):
+    """BF16 standardised features [n, 32] (the layout the forward reads)."""
+    x = torch.zeros((f.shape[0], IN), dtype=torch.float32, device=f.device)
+    x[:, :NFEAT] = (f - s.x_mu[:NFEAT]) / s.x_sigma[:NFEAT]
+    return x.to(torch.bfloat16)
+
+
+class Trainer:
+    """Adam on the loss of fp_surrogate_loss, every step in the library's
+    kernels; returns the per-epoch mean losses."""
+
+    def __init__(self, s: Surrogate, batch=8192, lr=1e-3, w_gamma=2.0, lam_drift=0.1, lam_energy=1.0):
+        self.s = s
+        self.batch = batch
+        self.lr = lr
+        self.w = np.array([1.0] * 6 + [w_gamma] * 3, dtype=np.float32)  # Gamma block weighted up (q-weighting)
+        self.lam_drift = lam_drift
+        self.lam_energy = lam_energy
+        n = param_count()
+        dev = s.device
+        self.grads = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.m = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.v = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.t = 0
+        B = batch
+        self.dout = torch.empty((B, OUT), dtype=torch.float32, device=dev)
+        self.dout_bf = torch.empty((B, OUT), dtype=torch.bfloat16, device=dev)
+        self.loss_acc = torch.zeros(1, dtype=torch.float32, device=dev)
+        self.ws = torch.empty(int(_lib().fp_mlp_backward_workspace_bytes(B)), dtype=torch.uint8, device=dev)
+
+    def step(self, x, t, aux, scale):
+        s = self.s
+        L = _lib()
+        n = x.shape[0]
+        out, h, z = s.forward(x, standardized=True, save=True)
+        wbuf = (ctypes.c_float * 9)(*self.w.tolist())
+        rc = L.fp_surrogate_loss(_p(out), _p(t), _p(aux), _p(s.y_mu), _p(s.y_sigma), n, wbuf, self.lam_drift,
+                                 self.lam_energy, s.eps2_hat, scale, _p(self.dout), _p(self.dout_bf),
+                                 _p(self.loss_acc), api._stream(None))
+        api._check(rc, "fp_surrogate_loss")
+        rc = L.fp_mlp_backward(ctypes.byref(s.net()), _p(x), _p(h), _p(z), _p(self.dout_bf), _p(self.dout), n,
+                               _p(self.grads), _p(self.ws), self.ws.numel(), api._stream(None))
+        api._check(rc, "fp_mlp_backward")
+        self.t += 1
+        rc = L.fp_adam_step(_p(s.params), _p(self.grads), _p(self.m), _p(self.v), s.params.numel(), self.lr, 0.9,
+                            0.999, 1e-8, self.t, _p(s.shadow), api._stream(None))
+        api._check(rc, "fp_adam_step")
+
+    def fit(self, ts: TrainingSet, epochs=10, seed=0, log=None, lr_decay=0.85):
+        s = self.s
+        x_all = standardized_inputs(s, ts.f)
+        n = len(ts)
+        gen = torch.Generator(device="cpu").manual_seed(seed)
+        hist = []
+        for ep in range(epochs):
+            perm = torch.randperm(n, generator=gen).to(s.device)
+            self.loss_acc.zero_()
+            t0 = time.time()
+            nb = 0
+            for b0 in range(0, n - self.batch + 1, self.batch):
+                idx = perm[b0:b0 + self.batch]
+                self.step(x_all[idx].contiguous(), ts.t[idx].contiguous(), ts.aux[idx].contiguous(), 1.0 / self.batch)
+                nb += 1
+            torch.cuda.synchronize()
+            mean_loss = float(self.loss_acc.item()) / max(1, nb * self.batch)
+            hist.append(mean_loss)
+            if log:
+                log(f"epoch {ep}: loss {mean_loss:.5f} ({time.time() - t0:.1f} s, {nb} steps)")
+            self.lr *= lr_decay
+        return hist

@@ -1,0 +1,203 @@
+"""GPU learned closure (features, fused BF16 MLP, loss, backward, Adam,
+surrogate with exact fallback) against the numpy reference oracle/mlp.py.
+
+Tolerances: the GPU and the reference round the same BF16 inputs, weights
+and activations; they differ by FP32 accumulation order, which moves a few
+activations by one BF16 ulp (2^-8 relative) and propagates -- outputs agree
+to 2e-2 of their largest magnitude and 3e-3 on average; gradients (BF16
+dZ operands) to 3e-2 relative per layer.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from oracle import mlp as M
+from paper_2606_15622_gb300 import api, surrogate as S
+from paper_2606_15622_gb300 import populations as P
+
+pytestmark = pytest.mark.gpu
+
+
+def _surrogate_with_random_params(seed=5):
+    s = S.Surrogate(eps2_hat=1e-3, seed=seed)
+    prm = M.init_params(seed)
+    s.set_params(prm["W"], prm["b"])
+    return s, prm
+
+
+def _inputs(n, seed):
+    x = np.random.default_rng(seed).standard_normal((n, M.IN)).astype(np.float32)
+    x[:, M.NFEAT:] = 0
+    return M.bf16_round(x)
+
+
+@pytest.mark.parametrize("n", [1, 127, 1000, 4099])
+def test_forward_matches_reference(n):
+    s, prm = _surrogate_with_random_params()
+    x = _inputs(n, n)
+    xd = torch.from_numpy(x).cuda().to(torch.bfloat16)
+    out = s.forward(xd, standardized=True).cpu().numpy()
+    ref = M.forward(prm, x.astype(np.float64), bf16=True)
+    err = np.abs(out - ref)
+    assert err.max() <= 2e-2 * np.abs(ref).max()
+    assert err.mean() <= 3e-3 * np.abs(ref).mean()
+
+
+def test_forward_saves_activations_and_unstandardizes():
+    s, prm = _surrogate_with_random_params()
+    s.y_mu[:9] = torch.linspace(-1, 1, 9, device="cuda")
+    s.y_sigma[:9] = torch.linspace(0.5, 2, 9, device="cuda")
+    s._net = None
+    x = torch.from_numpy(_inputs(300, 1)).cuda().to(torch.bfloat16)
+    o_std, h, z = s.forward(x, standardized=True, save=True)
+    o_raw = s.forward(x, standardized=False)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose((o_std * s.y_sigma + s.y_mu).cpu().numpy()[:, :9], o_raw.cpu().numpy()[:, :9],
+                               rtol=1e-6, atol=1e-6)
+    # saved activations are SiLU of the saved pre-activations, rounded to BF16
+    np.testing.assert_allclose(h.float().cpu().numpy(), M.bf16_round(M.silu(z.cpu().numpy())), rtol=1e-2, atol=1e-3)
+
+
+def _loss_args(n, seed):
+    rng = np.random.default_rng(seed)
+    pop = P.cavity(seed=seed, nx=32, ny=32)
+    m = O.moments(pop.v64, pop.offsets)[:n]
+    y, fl = O.closure(m, pop.tau[:n])
+    t_true = M.targets(y, m, pop.tau[:n])
+    out = rng.standard_normal((n, M.OUT)) * 0.5
+    y_mu = np.zeros(16)
+    y_sigma = np.ones(16)
+    y_mu[:9] = t_true.mean(0)
+    y_sigma[:9] = t_true.std(0) + 1e-3
+    f = M.raw_features(m)
+    aux = np.zeros((n, 16))
+    aux[:, :6] = f[:, :6]
+    aux[:, 6] = f[:, 6] + f[:, 9] + f[:, 11]
+    aux[:, 7] = f[:, 7] + f[:, 12] + f[:, 14]
+    aux[:, 8] = f[:, 8] + f[:, 13] + f[:, 15]
+    aux[:, 9] = f[:, 16] + f[:, 19] + f[:, 21]
+    return out, t_true, aux, y_mu, y_sigma, m
+
+
+def test_loss_gradient_matches_reference_finite_differences():
+    n = 64
+    out, t_true, aux, y_mu, y_sigma, m = _loss_args(n, 3)
+    w = np.array([1.0] * 6 + [2.0] * 3, dtype=np.float32)
+    lam_d, lam_e, eps2 = 0.1, 1.0, 1e-3
+    dev = lambda a, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
+    dout = torch.empty((n, 16), dtype=torch.float32, device="cuda")
+    doutb = torch.empty((n, 16), dtype=torch.bfloat16, device="cuda")
+    ls = torch.zeros(1, dtype=torch.float32, device="cuda")
+    import ctypes
+    L = api.lib()
+    keep = [dev(out), dev(t_true), dev(aux), dev(y_mu), dev(y_sigma)]  # alive until the kernel has run
+    rc = L.fp_surrogate_loss(*[api._ptr(t) for t in keep], n, (ctypes.c_float * 9)(*w.tolist()), lam_d, lam_e,
+                             eps2, 1.0, api._ptr(dout), api._ptr(doutb), api._ptr(ls), api._stream(None))
+    assert rc == 0
+    torch.cuda.synchronize()
+    ref_loss = M.loss(out, t_true, m, y_mu[:9], y_sigma[:9], eps2, w, lam_d, lam_e)
+    assert abs(float(ls.item()) / n - ref_loss) <= 1e-4 * abs(ref_loss)
+    g = dout.cpu().numpy()
+    h = 1e-5
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        r, a = rng.integers(n), rng.integers(9)
+        op, om = out.copy(), out.copy()
+        op[r, a] += h
+        om[r, a] -= h
+        fd = (M.loss(op, t_true, m, y_mu[:9], y_sigma[:9], eps2, w, lam_d, lam_e)
+              - M.loss(om, t_true, m, y_mu[:9], y_sigma[:9], eps2, w, lam_d, lam_e)) / (2 * h) * n
+        assert abs(g[r, a] - fd) <= 2e-3 * max(1.0, abs(fd)), (r, a, g[r, a], fd)
+    assert np.all(g[:, 9:] == 0)
+
+
+def test_backward_matches_reference():
+    n = 2048
+    s, prm = _surrogate_with_random_params(7)
+    x = _inputs(n, 11)
+    xd = torch.from_numpy(x).cuda().to(torch.bfloat16)
+    out, h, z = s.forward(xd, standardized=True, save=True)
+    dout = np.random.default_rng(2).standard_normal((n, 16)).astype(np.float32) / n
+    dout[:, 9:] = 0
+    dd = torch.from_numpy(dout).cuda()
+    grads = torch.zeros(S.param_count(), dtype=torch.float32, device="cuda")
+    ws = torch.empty(int(api.lib().fp_mlp_backward_workspace_bytes(n)), dtype=torch.uint8, device="cuda")
+    import ctypes
+    dd_bf = dd.to(torch.bfloat16)
+    rc = api.lib().fp_mlp_backward(ctypes.byref(s.net()), api._ptr(xd), api._ptr(h), api._ptr(z),
+                                   api._ptr(dd_bf), api._ptr(dd), n, api._ptr(grads), api._ptr(ws),
+                                   ws.numel(), api._stream(None))
+    assert rc == 0
+    torch.cuda.synchronize()
+    # reference: FP64 reverse mode on the BF16-rounded forward
+    pb = {"W": [M.bf16_round(w).astype(np.float64) for w in prm["W"]], "b": prm["b"]}
+    _, cache = M.forward(pb, x.astype(np.float64), bf16=True, keep=True)
+    dW, db, _ = M.backward(pb, cache, M.bf16_round(dout).astype(np.float64))
+    g = grads.cpu().numpy()
+    for l in range(5):
+        gw = g[S.param_offset(0, l):S.param_offset(0, l) + dW[l].size].reshape(dW[l].shape)
+        gb = g[S.param_offset(1, l):S.param_offset(1, l) + db[l].size]
+        assert np.linalg.norm(gw - dW[l]) <= 3e-2 * np.linalg.norm(dW[l]), l
+        assert np.linalg.norm(gb - db[l]) <= 3e-2 * np.linalg.norm(db[l]) + 1e-12, l
+
+
+def test_adam_matches_reference():
+    n = 5000
+    rng = np.random.default_rng(1)
+    p, g = rng.standard_normal(n).astype(np.float32), rng.standard_normal(n).astype(np.float32)
+    m, v = np.zeros(n, np.float32), np.zeros(n, np.float32)
+    P_, G_, M_, V_ = (torch.from_numpy(a.copy()).cuda() for a in (p, g, m, v))
+    sh = torch.empty(n, dtype=torch.bfloat16, device="cuda")
+    pr, mr, vr = p.astype(np.float64), m.astype(np.float64), v.astype(np.float64)
+    for t in (1, 2, 3):
+        rc = api.lib().fp_adam_step(api._ptr(P_), api._ptr(G_), api._ptr(M_), api._ptr(V_), n, 1e-2, 0.9, 0.999,
+                                    1e-8, t, api._ptr(sh), api._stream(None))
+        assert rc == 0
+        pr, mr, vr = M.adam_step(pr, g.astype(np.float64), mr, vr, t, lr=1e-2)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(P_.cpu().numpy(), pr, rtol=1e-5, atol=1e-6)
+    assert torch.equal(sh, P_.to(torch.bfloat16))
+
+
+def test_surrogate_fallback_is_exact_for_flagged_cells(cavity_pop):
+    """An untrained network fails the energy check on essentially every cell;
+    those cells must come back with the exact FP64 closure."""
+    s, _ = _surrogate_with_random_params(3)
+    pop = cavity_pop.subset(np.arange(0, cavity_pop.n_cells, 9))
+    mom = torch.from_numpy(O.moments(pop.v64, pop.offsets)).cuda()
+    tau = torch.from_numpy(pop.tau).cuda()
+    y, fl = s.closure(mom, tau)
+    torch.cuda.synchronize()
+    y, fl = y.cpu().numpy(), fl.cpu().numpy()
+    yr, flr = O.closure(mom.cpu().numpy(), pop.tau)
+    fb = (fl & api.FLAG_FALLBACK) != 0
+    assert fb.mean() > 0.95
+    err = np.linalg.norm(y[fb] - yr[fb], axis=1) / np.linalg.norm(yr[fb], axis=1)
+    assert err.max() <= 1e-10
+    assert np.all((fl[fb] & api.FALLBACK_FLAGS) == flr[fb])
+
+
+def test_training_reduces_error_below_linear_closure():
+    """Train on 60k cells for a few epochs with the library's kernels: the
+    loss falls and the trained network's coefficients (on held-out cells,
+    before any fallback) beat the linear-drift closure by a wide margin."""
+    train = P.training_cells(60000, seed=101)
+    ts = S.TrainingSet(train, eps2_hat=1e-3)
+    s = S.Surrogate(eps2_hat=1e-3, seed=9)
+    s.init_params()
+    S.fit_scalers(s, ts)
+    tr = S.Trainer(s, batch=4096, lr=2e-3)
+    hist = tr.fit(ts, epochs=6, seed=1)
+    assert hist[-1] < 0.5 * hist[0]
+    test = P.training_cells(4000, seed=202)
+    tt = S.TrainingSet(test, eps2_hat=1e-3)
+    x = S.standardized_inputs(s, tt.f)
+    pred = s.forward(x, standardized=False)[:, :9]
+    torch.cuda.synchronize()
+    err_net = ((pred - tt.t).norm(dim=1) / tt.t.norm(dim=1)).median().item()
+    lin = torch.zeros_like(tt.t)
+    lin[:, [0, 3, 5]] = -1.0
+    err_lin = ((lin - tt.t).norm(dim=1) / tt.t.norm(dim=1)).median().item()
+    assert err_net < 0.5 * err_lin, (err_net, err_lin)
