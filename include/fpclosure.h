@@ -305,6 +305,37 @@ int fp_mlp_backward(const fp_mlp *net, const void *x, const void *h_save, const 
 int fp_adam_step(float *params, const float *grads, float *m, float *v, int64_t n_params, float lr, float beta1,
                  float beta2, float eps, int64_t t, void *shadow_bf16, fp_stream_t stream);
 
+/* fp_closure_exact_static: fp_closure_exact for callers that cannot allocate
+ * device memory.  (The paper has no counterpart; this is a deployment
+ * convenience of this library.)
+ *
+ * Some callers may not allocate GPU memory at all -- a solver plugin inside a
+ * host application that owns the device memory budget, or a time-critical
+ * step loop where cudaMalloc, which may synchronise the device, is not
+ * allowed.  fp_closure_exact needs scratch for the per-cell moments when the
+ * caller does not take them; this call keeps that scratch in a fixed array
+ * built into the library instead and allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine).  The caller passes its inputs and
+ * outputs exactly as to fp_closure_exact with moments_out = NULL and no
+ * workspace; the results are the same.
+ *   - At most FP_STATIC_MAX_CELLS cells per call; larger n_cells is rejected
+ *     with FP_ERR_ARG (message via fp_closure_exact_static_error()).
+ *   - The array (FP_STATIC_MAX_CELLS x FP_NMOM doubles, 7.9 MB) is a
+ *     file-scope __device__ array: every GPU that loads the library holds it
+ *     until the process exits.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture.
+ *   - Every call on a device shares the one array and it keeps the last
+ *     call's contents; nothing needs clearing (each call overwrites every
+ *     slot it reads).  Calls whose executions overlap on the GPU (different
+ *     streams, no ordering between them) race on the array: serialise them. */
+#define FP_STATIC_MAX_CELLS 32768
+int fp_closure_exact_static(const void *v, int v_dtype, int64_t n_particles, const int64_t *cell_offsets,
+                            int64_t n_cells, const double *tau, const fp_params *p, int prec, double *coeffs_out,
+                            int32_t *flags_out, fp_stream_t stream);
+const char *fp_closure_exact_static_error(void);
+
 #ifdef __cplusplus
 }
 #endif

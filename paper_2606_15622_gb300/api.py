@@ -80,7 +80,35 @@ SIGNATURES = {
     "fp_mlp_backward": (_i32, [ctypes.POINTER(FpMlp), _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _sz, _vp]),
     "fp_adam_step": (_i32, [_vp, _vp, _vp, _vp, _i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                             ctypes.c_float, _i64, _vp, _vp]),
+    "fp_closure_exact_static": (_i32, [_vp, _i32, _i64, _vp, _i64, _vp, ctypes.POINTER(Params), _i32, _vp, _vp,
+                                       _vp]),
+    "fp_closure_exact_static_error": (ctypes.c_char_p, []),
 }
+
+STATIC_MAX_CELLS = 32768
+
+
+def fp_closure_exact_static(v, offsets, tau, params: Params | None = None, prec="fp32", coeffs_out=None,
+                            flags_out=None, stream=None):
+    """The exact closure with the library's built-in scratch array instead of
+    caller memory (for callers that may not allocate; at most
+    STATIC_MAX_CELLS cells) -> (coeffs, flags)."""
+    n_cells = offsets.numel() - 1
+    n_p = v.shape[-1] if v.dim() == 2 else v.numel() // 3
+    dev = offsets.device
+    if coeffs_out is None:
+        coeffs_out = torch.empty((n_cells, NCOEF), dtype=torch.float64, device=dev)
+    if flags_out is None:
+        flags_out = torch.empty((n_cells,), dtype=torch.int32, device=dev)
+    _need_cuda(v, offsets, tau, coeffs_out, flags_out)
+    p = params if params is not None else default_params()
+    rc = lib().fp_closure_exact_static(_ptr(v), _vdtype(v), n_p, _ptr(offsets), n_cells, _ptr(tau),
+                                       ctypes.byref(p), _PREC.get(prec, prec), _ptr(coeffs_out), _ptr(flags_out),
+                                       _stream(stream))
+    if rc != FP_OK:
+        raise FPError(f"fp_closure_exact_static: {lib().fp_status_string(rc).decode()} "
+                      f"({lib().fp_closure_exact_static_error().decode()})")
+    return coeffs_out, flags_out
 
 
 def fp_closure_backward(v, offsets, tau, moments, coeffs, flags, grad_coeffs, grad_moments_in=None,
