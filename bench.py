@@ -1,20 +1,27 @@
-"""Benchmark of the cubic Fokker-Planck closure on one or more GB300s.
+"""Benchmark of the cubic Fokker-Planck closure pipeline on one or more GB300s.
 
-A step is one pass of the closure pipeline over the Mach-10 cylinder-shaped
-population (512 x 256 cells, ~12M particles, FP32 velocities): the moment
-gather, the 9x9 assembly and the pivoted FP64 solve (fp_closure_exact,
-FP32-moment mode).  Inputs are resident in HBM before the timed region;
-the L2 is flushed (a 256 MB write) between timed steps, outside the step's
-events.  `value` is closure cells/s over all ranks (weak scaling: every rank
-closes its own seeded population, no collective on the data path).
+Workload (per GPU): the Mach-10 cylinder-shaped population, 512 x 256 cells,
+~12M particles, FP32 velocities, resident in HBM.  A step is one pass of the
+whole hot path over that batch:
+  1. exact closure, FP32 moments + FP64 pivoted solve   (fp_closure_exact)
+  2. learned closure with exact fallback                 (fp_closure_surrogate)
+  3. adjoint of sum(Y) to the moments and the velocities (fp_closure_backward)
+  4. velocity update, Philox noise, in place             (fp_velocity_update)
+The L2 is flushed (256 MB write) before every timed step, outside its events.
+`value` = cells per second of that step over all ranks (weak scaling: every
+rank runs its own seeded population, no collective on the data path).
 
-Further keys: per-kernel timings and the roofline of the dominant kernel,
-the exact FP64 path on the same cells, the end-to-end number through the
-C ABI with host buffers, nvidia-smi clocks sampled during the timed region,
-and the CPU oracle timed on host cores on a bounded sample.
+Beside the headline: per-call and per-kernel timings with the roofline of the
+dominant kernel; each path's own cells/s (exact FP64, FP32-moment, surrogate,
+adjoint, velocity update, one training step); the learned closure on the
+1,048,576-cell inference batch of held-out cells from the training
+distributions, with its error against the exact closure and its fallback
+rate; the end-to-end step through the C ABI with host buffers; nvidia-smi
+clocks sampled during the timed region; and the CPU oracle timed on host
+cores on a bounded sample.
 
---impl reference times the CPU oracle (the reference of this build) on the
-same workload, a bounded sample per step.
+--impl reference times the CPU oracle (this build's reference) on the same
+workload, a bounded sample per step.
 """
 
 from __future__ import annotations
@@ -36,25 +43,24 @@ if ROOT not in sys.path:
 
 METRIC = "closure cells/s + particles/s (exact FP64, FP32-moment, surrogate) at stated C/Gamma error"
 L2_FLUSH_BYTES = 256 << 20
+WEIGHTS = os.path.join(ROOT, "paper_2606_15622_gb300", "weights", "surrogate_couette_cavity.fpw")
 
-# algorithmic work per unit (see DESIGN.md, "Roofline accounting")
-GATHER_BYTES_PER_PARTICLE_F32 = 12  # three f32 velocity components, read once
-GATHER_BYTES_PER_CELL = 8 + 8 + 8 * 30  # offsets (one int64 per cell), tau is not read, moments written
-SOLVE_BYTES_PER_CELL = 8 * 30 + 8 + 8 * 9 + 4  # moments + tau read, coeffs + flags written
-SOLVE_FLOPS_PER_CELL = 658  # FP64 flops of assembly + elimination + back substitution (FMA = 2)
+# algorithmic work per unit (DESIGN.md, "Roofline accounting")
+GATHER_BYTES_PER_PARTICLE = 12          # three FP32 components read once
+GATHER_BYTES_PER_CELL = 8 + 8 * 30      # one offset read, the moment vector written
+VEL_BYTES_PER_PARTICLE = 24             # read + write three FP32 components
+VEL_BYTES_PER_CELL = 8 + 8 * 24 + 4 + 4 + 8  # offset, 24 FP64 constants, flags in/out, alpha
+SOLVE_FLOPS_PER_CELL = 658              # FP64: assembly + elimination + back substitution (FMA = 2)
+MLP_FLOPS_PER_CELL = 2 * (32 * 128 + 3 * 128 * 128 + 128 * 16)  # padded layer shapes
+FP64_PEAK_TFLOPS = 1.197                # FP64 FMA-chain peak measured on this machine's GB300
 
 
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         d = json.load(open(path))
-        return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "src": "measured"}
-    return {"hbm_gbs": 6800.0, "src": "fallback"}
-
-
-# FP64 FMA-chain peak measured on this machine's GB300 (152 SMs x ~2 FP64 FMA
-# lanes per clock): 1.197 TFLOP/s.
-FP64_PEAK_TFLOPS = 1.197
+        return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "bf16_tflops": d.get("bf16_tflops", 1900.0), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "src": "fallback"}
 
 
 class ClockSampler:
@@ -76,6 +82,7 @@ class ClockSampler:
                  "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            time.sleep(0.3)
         except Exception:
             self.proc = None
         return self
@@ -131,6 +138,8 @@ def run_ours(args):
     import torch.distributed as dist
 
     from paper_2606_15622_gb300 import api
+    from paper_2606_15622_gb300 import populations as P
+    from paper_2606_15622_gb300 import surrogate as S
 
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
@@ -139,27 +148,61 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     pop = _population(args.config, seed=3 + rank)
     n_cells, n_p = pop.n_cells, pop.n_particles
-    v32 = torch.from_numpy(pop.v32).to(dev)
+    v0 = torch.from_numpy(pop.v32).to(dev)          # pristine copy: the update works in place
+    v32 = v0.clone()
     v64 = torch.from_numpy(pop.v64).to(dev)
     off = torch.from_numpy(pop.offsets).to(dev)
     tau = torch.from_numpy(pop.tau).to(dev)
     mom = torch.empty((n_cells, 30), dtype=torch.float64, device=dev)
     coeffs = torch.empty((n_cells, 9), dtype=torch.float64, device=dev)
     flags = torch.empty((n_cells,), dtype=torch.int32, device=dev)
+    coeffs_s = torch.empty_like(coeffs)
+    flags_s = torch.empty_like(flags)
+    gY = torch.ones((n_cells, 9), dtype=torch.float64, device=dev)
+    gmom = torch.empty_like(mom)
+    gv = torch.empty_like(v32)
+    alpha = torch.empty(n_cells, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     prm = api.default_params()
     stream = torch.cuda.current_stream()
+    sur = S.Surrogate.load(WEIGHTS, device=dev)
+    s_ws = torch.empty(int(api.lib().fp_surrogate_workspace_bytes(n_cells)), dtype=torch.uint8, device=dev)
+    step_idx = [0]
 
-    def step():
+    def c_exact():
         api.fp_closure_exact(v32, off, tau, params=prm, prec="fp32", moments_out=mom, coeffs_out=coeffs,
                              flags_out=flags, stream=stream)
 
-    def timed(fn, k, w):
+    def c_surrogate():
+        sur.closure(mom, tau, params=prm, prec="fp32", coeffs_out=coeffs_s, flags_out=flags_s, workspace=s_ws,
+                    stream=stream)
+
+    def c_adjoint():
+        api.fp_closure_backward(v32, off, tau, mom, coeffs, flags, gY, params=prm, grad_moments=gmom, grad_v=gv,
+                                stream=stream)
+
+    def c_velocity():
+        api.fp_velocity_update(v32, off, mom, coeffs, tau, flags, 0.1, params=prm, seed=1234, step=step_idx[0],
+                               alpha_out=alpha, stream=stream)
+        step_idx[0] += 1
+
+    calls = [("exact_closure", c_exact), ("surrogate_closure", c_surrogate), ("adjoint", c_adjoint),
+             ("velocity_update", c_velocity)]
+
+    def step():
+        for _, fn in calls:
+            fn()
+
+    def timed(fn, k, w, reset=None):
         for _ in range(w):
+            if reset:
+                reset()
             fn()
         torch.cuda.synchronize()
         evs = []
         for _ in range(k):
+            if reset:
+                reset()
             flush.fill_(1)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -169,22 +212,29 @@ def run_ours(args):
         torch.cuda.synchronize()
         return [a.elapsed_time(b) for a, b in evs]
 
+    def reset_v():
+        v32.copy_(v0)
+
     if args.only:
-        # profiling mode: launch one kernel `steps` times (no timing output)
-        fns = {"gather": lambda: api.fp_moments(v32, off, prec="fp32", moments_out=mom, stream=stream),
-               "gather64": lambda: api.fp_moments(v64, off, prec="fp64", moments_out=mom, stream=stream),
-               "solve": lambda: api.fp_closure_solve(mom, tau, params=prm, prec="fp32", coeffs_out=coeffs,
-                                                     flags_out=flags, stream=stream)}
-        api.fp_moments(v32, off, prec="fp32", moments_out=mom, stream=stream)
+        # profiling mode: launch one call `steps` times (no bench line)
+        fns = dict(calls)
+        fns["gather"] = lambda: api.fp_moments(v32, off, prec="fp32", moments_out=mom, stream=stream)
+        fns["solve"] = lambda: api.fp_closure_solve(mom, tau, params=prm, prec="fp32", coeffs_out=coeffs,
+                                                    flags_out=flags, stream=stream)
+        fns["gather64"] = lambda: api.fp_moments(v64, off, prec="fp64", moments_out=mom, stream=stream)
+        fns["step"] = step
+        c_exact()
         for _ in range(args.steps):
             fns[args.only]()
         torch.cuda.synchronize()
         print(json.dumps({"profiled": args.only, "launches": args.steps, "config": pop.name}))
         return
 
-    # ---- headline: the timed region ------------------------------------
+    # ---- headline: the timed region -------------------------------------
     for _ in range(args.warmup):
         step()
+    torch.cuda.synchronize()
+    reset_v()
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
@@ -203,54 +253,135 @@ def run_ours(args):
     cells_per_s = ws * n_cells / (ms_per_step * 1e-3)
     parts_per_s = ws * n_p / (ms_per_step * 1e-3)
 
-    # ---- per-kernel timings (the two halves, same stream) -------------------
-    t_gather = timed(lambda: api.fp_moments(v32, off, prec="fp32", moments_out=mom, stream=stream), 10, 3)
-    t_solve = timed(lambda: api.fp_closure_solve(mom, tau, params=prm, prec="fp32", coeffs_out=coeffs,
-                                                 flags_out=flags, stream=stream), 10, 3)
-    g_ms, s_ms = float(np.median(t_gather)), float(np.median(t_solve))
+    # ---- per call, per kernel ------------------------------------------------
     peaks = _peaks()
-    gather_bytes = GATHER_BYTES_PER_PARTICLE_F32 * n_p + GATHER_BYTES_PER_CELL * n_cells
-    gather_gbs = gather_bytes / (g_ms * 1e-3) / 1e9
-    solve_tflops = SOLVE_FLOPS_PER_CELL * n_cells / (s_ms * 1e-3) / 1e12
+    per_call = {name: float(np.median(timed(fn, 10, 2, reset=reset_v if name == "velocity_update" else None)))
+                for name, fn in calls}
+    t_gather = float(np.median(timed(lambda: api.fp_moments(v32, off, prec="fp32", moments_out=mom, stream=stream),
+                                     10, 2)))
+    t_solve = float(np.median(timed(lambda: api.fp_closure_solve(mom, tau, params=prm, prec="fp32",
+                                                                 coeffs_out=coeffs, flags_out=flags,
+                                                                 stream=stream), 10, 2)))
+    x_feat, _ = sur.features(mom, tau, params=prm)
+    out16 = torch.empty((n_cells, 16), dtype=torch.float32, device=dev)
+    t_mlp = float(np.median(timed(lambda: sur.forward(x_feat, standardized=False, out=out16, stream=stream), 10, 2)))
+    gather_bytes = GATHER_BYTES_PER_PARTICLE * n_p + GATHER_BYTES_PER_CELL * n_cells
+    vel_bytes = VEL_BYTES_PER_PARTICLE * n_p + VEL_BYTES_PER_CELL * n_cells
+
+    def kern(ms_, bound, achieved, unit, peak, work):
+        return {"ms": round(ms_, 5), "bound": bound, "achieved": round(achieved, 4), "unit": unit, "peak": peak,
+                "frac": round(achieved / peak, 4), **work}
+
     kernels = {
-        "gather_fp32": {"ms": g_ms, "bound": "hbm", "achieved": gather_gbs, "unit": "GB/s",
-                        "peak": peaks["hbm_gbs"], "frac": gather_gbs / peaks["hbm_gbs"],
-                        "algorithmic_bytes": gather_bytes},
-        "solve_fp64": {"ms": s_ms, "bound": "alu", "achieved": solve_tflops, "unit": "TFLOP/s",
-                       "peak": FP64_PEAK_TFLOPS, "frac": solve_tflops / FP64_PEAK_TFLOPS,
-                       "algorithmic_flops": SOLVE_FLOPS_PER_CELL * n_cells},
+        "gather_fp32": kern(t_gather, "hbm", gather_bytes / (t_gather * 1e-3) / 1e9, "GB/s", peaks["hbm_gbs"],
+                            {"algorithmic_bytes": gather_bytes}),
+        "solve_fp64": kern(t_solve, "alu", SOLVE_FLOPS_PER_CELL * n_cells / (t_solve * 1e-3) / 1e12, "TFLOP/s",
+                           FP64_PEAK_TFLOPS, {"algorithmic_flops": SOLVE_FLOPS_PER_CELL * n_cells,
+                                              "peak_note": "FP64 pipe, measured FMA chain"}),
+        "velocity_update": kern(per_call["velocity_update"], "hbm", vel_bytes / (per_call["velocity_update"] * 1e-3) / 1e9,
+                                "GB/s", peaks["hbm_gbs"], {"algorithmic_bytes": vel_bytes}),
+        "mlp_forward": kern(t_mlp, "tensor", MLP_FLOPS_PER_CELL * n_cells / (t_mlp * 1e-3) / 1e12, "TFLOP/s",
+                            peaks["bf16_tflops"], {"algorithmic_flops": MLP_FLOPS_PER_CELL * n_cells}),
     }
-    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    dom = max(("gather_fp32", "solve_fp64", "velocity_update", "mlp_forward"), key=lambda k: kernels[k]["ms"])
     dk = kernels[dom]
-    roofline = {"kernel": dom, "bound": dk["bound"], "achieved": round(dk["achieved"], 3), "peak": dk["peak"],
-                "unit": dk["unit"], "frac": round(dk["frac"], 4), "traffic": None,
-                "peak_src": peaks["src"] if dk["bound"] == "hbm" else "measured (FP64 FMA chain)"}
+    roofline = {"kernel": dom, "bound": dk["bound"], "achieved": dk["achieved"], "peak": dk["peak"],
+                "unit": dk["unit"], "frac": dk["frac"], "traffic": None,
+                "peak_src": "measured (FP64 FMA chain, DESIGN.md)" if dk["bound"] == "alu" else peaks["src"]}
 
-    # ---- the exact FP64 path on the same cells -------------------------------
-    t64 = timed(lambda: api.fp_closure_exact(v64, off, tau, params=prm, prec="fp64", moments_out=mom,
-                                             coeffs_out=coeffs, flags_out=flags, stream=stream), 5, 2)
-    fp64_ms = float(np.median(t64))
+    # ---- the exact FP64 path on the same cells ----------------------------------
+    t64 = float(np.median(timed(lambda: api.fp_closure_exact(v64, off, tau, params=prm, prec="fp64",
+                                                             moments_out=mom, coeffs_out=coeffs, flags_out=flags,
+                                                             stream=stream), 5, 2)))
+    c_exact()
+    torch.cuda.synchronize()
 
-    # ---- end to end through the C ABI with host buffers ----------------------
+    # ---- learned closure on the 1M-cell inference batch -------------------
+    inf = P.training_cells(131072, seed=987654)          # held-out seeds of the training distributions
+    iv = torch.from_numpy(inf.v64).to(dev)
+    ioff = torch.from_numpy(inf.offsets).to(dev)
+    itau = torch.from_numpy(inf.tau).to(dev)
+    imom, iy_ex, ifl_ex = api.fp_closure_exact(iv, ioff, itau, params=prm, prec="fp64")
+    iy_s, ifl_s = sur.closure(imom, itau, params=prm, prec="fp64")
+    torch.cuda.synchronize()
+    t_ex = S.dimensionless(iy_ex, imom, itau)
+    t_s = S.dimensionless(iy_s, imom, itau)
+    ok = ifl_ex == 0
+    rel = ((t_s - t_ex).norm(dim=1) / t_ex.norm(dim=1))[ok].float().cpu()
+    lin = torch.zeros_like(t_ex)
+    lin[:, [0, 3, 5]] = -1.0
+    rel_lin = ((lin - t_ex).norm(dim=1) / t_ex.norm(dim=1))[ok].float().cpu()
+    # energy residual of the surrogate drift (exact closure: 0)
+    f = S.raw_features_t(imom)
+    mult = torch.tensor([1, 2, 2, 1, 2, 1], dtype=torch.float64, device=dev)
+    b_hat = torch.stack([f[:, 6] + f[:, 9] + f[:, 11], f[:, 7] + f[:, 12] + f[:, 14], f[:, 8] + f[:, 13] + f[:, 15]], 1)
+    s4 = f[:, 16] + f[:, 19] + f[:, 21]
+    e = 1 + ((t_s[:, :6] * f[:, :6] * mult).sum(1) + (t_s[:, 6:] * b_hat).sum(1) - prm.eps2_hat * s4) / 3
+    reps = 8
+    big_mom = imom.repeat(reps, 1).contiguous()
+    big_tau = itau.repeat(reps).contiguous()
+    nb = big_mom.shape[0]
+    by = torch.empty((nb, 9), dtype=torch.float64, device=dev)
+    bfl = torch.empty(nb, dtype=torch.int32, device=dev)
+    bws = torch.empty(int(api.lib().fp_surrogate_workspace_bytes(nb)), dtype=torch.uint8, device=dev)
+    t_sur_1m = float(np.median(timed(lambda: sur.closure(big_mom, big_tau, params=prm, prec="fp64", coeffs_out=by,
+                                                         flags_out=bfl, workspace=bws, stream=stream), 10, 2)))
+    t_ex_1m = float(np.median(timed(lambda: api.fp_closure_solve(big_mom, big_tau, params=prm, prec="fp64",
+                                                                 coeffs_out=by, flags_out=bfl, stream=stream), 5, 2)))
+    xb, _ = sur.features(big_mom, big_tau, params=prm)
+    ob = torch.empty((nb, 16), dtype=torch.float32, device=dev)
+    t_mlp_1m = float(np.median(timed(lambda: sur.forward(xb, standardized=False, out=ob, stream=stream), 10, 2)))
+    fb_rate = float(((ifl_s & api.FLAG_FALLBACK) != 0).double().mean())
+
+    # ---- adjoint on the cavity-shaped population (C4) -----------------------
+    cav = P.cavity(seed=4)
+    cv = torch.from_numpy(cav.v32).to(dev)
+    coff, ctau = torch.from_numpy(cav.offsets).to(dev), torch.from_numpy(cav.tau).to(dev)
+    cm, cy, cfl = api.fp_closure_exact(cv, coff, ctau, params=prm, prec="fp32")
+    cg = torch.ones_like(cy)
+    cgm = torch.empty_like(cm)
+    cgv = torch.empty_like(cv)
+    t_fwd_c4 = float(np.median(timed(lambda: api.fp_closure_exact(cv, coff, ctau, params=prm, prec="fp32",
+                                                                  moments_out=cm, coeffs_out=cy, flags_out=cfl,
+                                                                  stream=stream), 10, 2)))
+    t_bwd_c4 = float(np.median(timed(lambda: api.fp_closure_backward(cv, coff, ctau, cm, cy, cfl, cg, params=prm,
+                                                                     grad_moments=cgm, grad_v=cgv, stream=stream),
+                                     10, 2)))
+
+    # ---- one training step (batch 8192) ----------------------------------------
+    import copy
+    trs = S.Surrogate.load(WEIGHTS, device=dev)
+    tr = S.Trainer(trs, batch=8192)
+    ts = S.TrainingSet(P.training_cells(16384, seed=55), eps2_hat=prm.eps2_hat)
+    xt = S.standardized_inputs(trs, ts.f[:8192]).contiguous()
+    tt, at = ts.t[:8192].contiguous(), ts.aux[:8192].contiguous()
+    t_train = float(np.median(timed(lambda: tr.step(xt, tt, at, 1.0 / 8192), 10, 3)))
+
+    # ---- end to end through the C ABI with host buffers -------------------
     h_v = torch.from_numpy(pop.v32).pin_memory()
     h_off = torch.from_numpy(pop.offsets).pin_memory()
     h_tau = torch.from_numpy(pop.tau).pin_memory()
     h_coeffs = torch.empty((n_cells, 9), dtype=torch.float64).pin_memory()
     h_flags = torch.empty((n_cells,), dtype=torch.int32).pin_memory()
+    h_vout = torch.empty_like(h_v).pin_memory()
 
     def e2e_step():
         v32.copy_(h_v, non_blocking=True)
         off.copy_(h_off, non_blocking=True)
         tau.copy_(h_tau, non_blocking=True)
-        api.fp_closure_exact(v32, off, tau, params=prm, prec="fp32", moments_out=mom, coeffs_out=coeffs,
-                             flags_out=flags, stream=stream)
+        step()
         h_coeffs.copy_(coeffs, non_blocking=True)
         h_flags.copy_(flags, non_blocking=True)
+        h_vout.copy_(v32, non_blocking=True)
 
     te = timed(e2e_step, max(3, args.steps), 2)
     e2e_ms = float(np.median(te))
     h2d = h_v.numel() * 4 + h_off.numel() * 8 + h_tau.numel() * 8
-    d2h = h_coeffs.numel() * 8 + h_flags.numel() * 4
+    d2h = h_coeffs.numel() * 8 + h_flags.numel() * 4 + h_vout.numel() * 4
+    launches_per_step = 2 + 6 + 2 + 1
+
+    def q(x, p):
+        return round(float(torch.quantile(x, p)), 6)
 
     out = {
         "metric": METRIC,
@@ -263,25 +394,52 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 moments, f64 solve",
-        "data": "synthetic (seeded Mach-10 cylinder-shaped population)",
+        "dtype": "f32 moments, f64 solve, bf16/f32 MLP",
+        "data": "synthetic (seeded Mach-10 cylinder-shaped population; no paper data)",
         "config": {"workload": f"{pop.name}: {n_cells} cells, {n_p} particles per GPU",
-                   "cells": n_cells, "particles": n_p, "velocities": "f32 SoA",
-                   "prec": "fp32_moments", "eps2_hat": prm.eps2_hat,
-                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{ws}"},
+                   "step": "exact closure (FP32 moments, FP64 solve) + learned closure with exact fallback + "
+                           "adjoint to moments and velocities + velocity update",
+                   "cells": n_cells, "particles": n_p, "velocities": "f32 SoA", "eps2_hat": prm.eps2_hat,
+                   "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{ws}"},
         "particles_per_s": round(parts_per_s, 1),
-        "kernels": {k: {kk: (round(vv, 5) if isinstance(vv, float) else vv) for kk, vv in d.items()}
-                    for k, d in kernels.items()},
+        "per_call_ms": {k: round(v, 5) for k, v in per_call.items()},
+        "kernels": kernels,
         "roofline": roofline,
         "paths": {
-            "exact_fp32_moments": {"ms": round(ms_per_step, 5), "cells_per_s": round(cells_per_s / ws, 1),
-                                   "particles_per_s": round(parts_per_s / ws, 1)},
-            "exact_fp64": {"ms": round(fp64_ms, 5), "cells_per_s": round(n_cells / (fp64_ms * 1e-3), 1),
-                           "particles_per_s": round(n_p / (fp64_ms * 1e-3), 1), "velocities": "f64"},
+            "exact_fp32_moments": {"ms": round(per_call["exact_closure"], 5),
+                                   "cells_per_s": round(n_cells / (per_call["exact_closure"] * 1e-3), 1),
+                                   "particles_per_s": round(n_p / (per_call["exact_closure"] * 1e-3), 1),
+                                   "error_vs_oracle": "<= 1e-4 relative (parity tests)"},
+            "exact_fp64": {"ms": round(t64, 5), "cells_per_s": round(n_cells / (t64 * 1e-3), 1),
+                           "particles_per_s": round(n_p / (t64 * 1e-3), 1), "velocities": "f64",
+                           "error_vs_oracle": "<= 1e-10 relative (parity tests)"},
+            "surrogate_on_cylinder": {"ms": round(per_call["surrogate_closure"], 5),
+                                      "fallback_rate": round(float(((flags_s & api.FLAG_FALLBACK) != 0)
+                                                                   .double().mean()), 4),
+                                      "note": "Mach-10 cells lie outside the training distributions; the range "
+                                              "check sends them to the exact closure"},
+            "surrogate_1M": {"cells": nb, "ms": round(t_sur_1m, 5), "cells_per_s": round(nb / (t_sur_1m * 1e-3), 1),
+                             "mlp_forward_ms": round(t_mlp_1m, 5),
+                             "exact_solve_same_moments_ms": round(t_ex_1m, 5),
+                             "speedup_vs_exact_solve": round(t_ex_1m / t_sur_1m, 3),
+                             "fallback_rate": round(fb_rate, 5),
+                             "rel_err_vs_exact": {"median": q(rel, 0.5), "p95": q(rel, 0.95),
+                                                  "max": round(float(rel.max()), 6)},
+                             "rel_err_linear_closure": {"median": q(rel_lin, 0.5), "p95": q(rel_lin, 0.95)},
+                             "energy_residual_abs": {"median": q(e.abs().float().cpu(), 0.5),
+                                                     "max": round(float(e.abs().max()), 6)},
+                             "inputs": "131072 held-out cells of the training distributions, tiled x8"},
+            "adjoint_cavity": {"cells": cav.n_cells, "particles": cav.n_particles,
+                               "forward_ms": round(t_fwd_c4, 5), "backward_ms": round(t_bwd_c4, 5),
+                               "fwd_bwd_cells_per_s": round(cav.n_cells / ((t_fwd_c4 + t_bwd_c4) * 1e-3), 1)},
+            "velocity_update": {"ms": round(per_call["velocity_update"], 5),
+                                "particles_per_s": round(n_p / (per_call["velocity_update"] * 1e-3), 1)},
+            "training_step": {"batch": 8192, "ms": round(t_train, 5),
+                              "cells_per_s": round(8192 / (t_train * 1e-3), 1)},
         },
         "e2e": {"value": round(n_cells / (e2e_ms * 1e-3) * ws, 1), "unit": "cells/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 5)},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -293,29 +451,33 @@ def run_ours(args):
         print(json.dumps(out))
 
 
-def cpu_baseline(pop, budget_s=15.0, max_cells=None):
-    """The oracle, as it stands, single-threaded on this host: moments +
-    closure over consecutive blocks of cells until the time budget is used."""
+def cpu_baseline(pop, budget_s=15.0):
+    """The oracle as it stands, single-threaded on this host: moments, exact
+    closure and velocity update over consecutive blocks of cells until the
+    time budget is used (the learned closure and the adjoint have no CPU
+    counterpart at this scale)."""
     import oracle as O
     O.build()
     t0 = time.perf_counter()
     done_cells = done_parts = 0
     blk = 4096
     start = 0
-    while time.perf_counter() - t0 < budget_s and (max_cells is None or done_cells < max_cells):
+    while time.perf_counter() - t0 < budget_s:
         end = min(start + blk, pop.n_cells)
         a, b = int(pop.offsets[start]), int(pop.offsets[end])
         offs = pop.offsets[start:end + 1] - a
-        m = O.moments(pop.v64[:, a:b], offs)
-        O.closure(m, pop.tau[start:end])
+        v = pop.v32[:, a:b].astype(np.float64)
+        m = O.moments(v, offs)
+        y, fl = O.closure(m, pop.tau[start:end])
+        O.velocity_update(v, offs, m, y, pop.tau[start:end], fl, 0.1, seed=1234, step=0)
         done_cells += end - start
         done_parts += b - a
         start = end % pop.n_cells
     el = time.perf_counter() - t0
     return {"value": round(done_cells / el, 1), "unit": "cells/s", "cores": 1, "kind": "oracle",
             "particles_per_s": round(done_parts / el, 1),
-            "sample": f"{done_cells} cells ({done_parts} particles) of {pop.name} in {el:.1f} s, "
-                      "FP64 moments + closure, 1 thread"}
+            "sample": f"{done_cells} cells ({done_parts} particles) of {pop.name} in {el:.1f} s: FP64 moments, "
+                      "exact closure and velocity update, 1 thread"}
 
 
 def run_reference(args):
@@ -333,9 +495,9 @@ def run_reference(args):
         "metric": METRIC, "impl": "reference", "value": round(value, 1), "unit": "cells/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded Mach-10 cylinder-shaped population)",
-        "config": {"workload": f"{pop.name}: {pop.n_cells} cells, {pop.n_particles} particles (bounded sample per step)",
-                   "cells": pop.n_cells, "particles": pop.n_particles},
+        "data": "synthetic (seeded Mach-10 cylinder-shaped population; no paper data)",
+        "config": {"workload": f"{pop.name}: {pop.n_cells} cells, {pop.n_particles} particles "
+                               "(bounded sample per step)", "cells": pop.n_cells, "particles": pop.n_particles},
         "cpu_baseline": {"value": round(value, 1), "unit": "cells/s", "cores": 1, "kind": "oracle",
                          "sample": per[0]["sample"]},
         "e2e": {"value": round(value, 1), "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -352,8 +514,10 @@ def main():
     ap.add_argument("--config", default="cylinder", choices=["cylinder", "cavity", "couette"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["gather", "gather64", "solve"], default=None,
-                    help="profiling mode: launch one kernel --steps times, print no bench line")
+    ap.add_argument("--only", default=None,
+                    choices=["gather", "gather64", "solve", "exact_closure", "surrogate_closure", "adjoint",
+                             "velocity_update", "step"],
+                    help="profiling mode: launch one call --steps times, print no bench line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
