@@ -10,8 +10,9 @@
 // Kernel 1 (one thread per cell, FP64): re-assembles A, eliminates A^T with
 // partial pivoting (the factors are recomputed, never stored), and
 // back-propagates -lambda through the assembly formulas by hand-written
-// reverse mode.  Kernel 2 (a group of lanes per cell): the per-particle
-// polynomial above, in the velocity's precision, one pass over the particles.
+// reverse mode.  Kernel 2 (four consecutive cells per warp, their particles
+// walked flat by all lanes): the per-particle polynomial above, in the
+// velocity's precision, one pass over the particles.
 #include <cstdint>
 
 #include "closure_math.cuh"
@@ -149,7 +150,13 @@ __global__ void __launch_bounds__(128) adjoint_cell_kernel(const double *__restr
 // ---------------------------------------------------------------------------
 // particle gradient
 // ---------------------------------------------------------------------------
-constexpr int kAG = 8;  // lanes per cell
+constexpr int kAG = 8;              // lanes per cell while building constants
+constexpr int kACells = 32 / kAG;   // consecutive cells per warp task
+constexpr int kAWarps = 8;          // warps per block
+constexpr int kAConst = 36;         // table entries per cell
+
+// table slots: U, Mu (sym), A3 (10), W (sym), gz, <grad psi>, gm_U / N, 1 / N
+enum { AU = 0, AMU = 3, AA3 = 9, AW = 19, AGZ = 25, AG0 = 28, AGU = 31, AINVN = 34 };
 
 template <typename T>
 __device__ __forceinline__ T shfl_g(T x, int src, int lane) {
@@ -159,30 +166,35 @@ __device__ __forceinline__ T shfl_g(T x, int src, int lane) {
 // multiplicity of a symmetric third-order slot (111: 1, 112: 3, 123: 6)
 __host__ __device__ constexpr int mult3(int s) { return (s == 0 || s == 6 || s == 9) ? 1 : (s == 4 ? 6 : 3); }
 
+// A warp takes four consecutive cells; an 8-lane group folds its cell's
+// moments and moment gradients into the 35 coefficients of the per-particle
+// polynomial (shared-memory table), then all 32 lanes walk the four cells'
+// contiguous particle range.
 template <typename VT>
-__global__ void __launch_bounds__(256) adjoint_particle_kernel(const VT *__restrict__ v, int64_t np,
-                                                               const int64_t *__restrict__ off, int64_t n_cells,
-                                                               const double *__restrict__ mom,
-                                                               const double *__restrict__ gm, VT *__restrict__ gv) {
+__global__ void __launch_bounds__(32 * kAWarps) adjoint_particle_kernel(const VT *__restrict__ v, int64_t np,
+                                                                        const int64_t *__restrict__ off,
+                                                                        int64_t n_cells,
+                                                                        const double *__restrict__ mom,
+                                                                        const double *__restrict__ gm,
+                                                                        VT *__restrict__ gv) {
   using T = VT;
   constexpr int G = kAG;
-  constexpr int GPW = 32 / G;
+  __shared__ __align__(16) T table[kAWarps][kACells][kAConst];
   const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
   const int lg = lane & (G - 1);
   const int g = lane / G;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const VT *vx = v, *vy = v + np, *vz = v + 2 * np;
   VT *gx = gv, *gy = gv + np, *gz = gv + 2 * np;
+  T(*tab)[kAConst] = table[wib];
 
-  for (int64_t base = warp * GPW; base < n_cells; base += nwarps * GPW) {
+  for (int64_t base = warp * kACells; base < n_cells; base += nwarps * kACells) {
     const int64_t c = base + g;
     const bool valid = c < n_cells;
-    int64_t a0 = 0, e = 0;
-    if (valid) {
-      a0 = off[c];
-      e = off[c + 1];
-    }
+    const int64_t a0 = off[valid ? c : n_cells];
+    const int64_t e = valid ? off[c + 1] : a0;
     const int n = (int)(e - a0);
     // the cell's 30 moments and 30 moment gradients, converted once: lane lg
     // holds slots lg + 8 j of the concatenation [mom | gm] (60 values)
@@ -194,94 +206,125 @@ __global__ void __launch_bounds__(256) adjoint_particle_kernel(const VT *__restr
       if (valid && slot < 60) x = slot < 30 ? mom[c * FP_NMOM + slot] : gm[c * FP_NMOM + slot - 30];
       cv[j] = (T)x;
     }
-    auto M_ = [&](int k) -> T { return shfl_g(cv[k / 8], k % 8, lane); };
-    auto GM = [&](int k) -> T { return shfl_g(cv[(30 + k) / 8], (30 + k) % 8, lane); };
-    const T U0 = M_(kU), U1 = M_(kU + 1), U2 = M_(kU + 2);
-    // u-part: G_d += sum_j Mu_dj c_j with Mu_dj = gm_u(dj) (1 + delta_dj); theta adds 2/3 gm_theta c_d
-    const T gth = GM(kTheta) * T(2.0 / 3.0);
-    T Mu[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) Mu[i][j] = GM(kU2 + sym2(i, j)) * (i == j ? T(2) : T(1)) + (i == j ? gth : T(0));
-    // u3-part: G_d += 3 sum_jk A_djk c_j c_k with A = gm_u3(slot) / multiplicity
-    T A3[10];
-#pragma unroll
-    for (int s = 0; s < 10; ++s) A3[s] = GM(kU3 + s) / T(mult3(s));
-    // w-part: G_d += 2 c_d (c.W c) + 2 |c|^2 (W c)_d with W = gm_w(slot) / multiplicity
-    T W[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) W[i][j] = GM(kW + sym2(i, j)) * (i == j ? T(1) : T(0.5));
-    // z-part: G_d += 4 |c|^2 c_d (gz.c) + |c|^4 gz_d
-    const T gz0 = GM(kZ), gz1 = GM(kZ + 1), gz2 = GM(kZ + 2);
-    // the cell mean of grad psi, from the moments
-    T G0[3];
     {
-      T u[3][3], w[3][3], b[3], u3[10];
+      auto M_ = [&](int k) -> T { return shfl_g(cv[k / 8], k % 8, lane); };
+      auto GM = [&](int k) -> T { return shfl_g(cv[(30 + k) / 8], (30 + k) % 8, lane); };
+      // u-part: G_d += sum_j Mu_dj c_j with Mu_dj = gm_u(dj) (1 + delta_dj); theta adds 2/3 gm_theta c_d
+      const T gth = GM(kTheta) * T(2.0 / 3.0);
+      T Mu[6];
 #pragma unroll
-      for (int s = 0; s < 10; ++s) u3[s] = M_(kU3 + s);
+      for (int s = 0; s < 6; ++s) {
+        const bool diag = s == 0 || s == 3 || s == 5;
+        Mu[s] = GM(kU2 + s) * (diag ? T(2) : T(1)) + (diag ? gth : T(0));
+      }
+      // u3-part: G_d += 3 sum_jk A_djk c_j c_k with A = gm_u3(slot) / multiplicity
+      T A3[10];
+#pragma unroll
+      for (int s = 0; s < 10; ++s) A3[s] = GM(kU3 + s) / T(mult3(s));
+      // w-part: G_d += 2 c_d (c.W c) + 2 |c|^2 (W c)_d with W = gm_w(slot) / multiplicity
+      T W[3][3];
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          u[i][j] = M_(kU2 + sym2(i, j));
-          w[i][j] = M_(kW + sym2(i, j));
-        }
+        for (int j = 0; j < 3; ++j) W[i][j] = GM(kW + sym2(i, j)) * (i == j ? T(1) : T(0.5));
+      // z-part: G_d += 4 |c|^2 c_d (gz.c) + |c|^4 gz_d
+      const T gzv[3] = {GM(kZ), GM(kZ + 1), GM(kZ + 2)};
+      // the cell mean of grad psi, from the moments
+      T G0[3];
+      {
+        T u[3][3], w[3][3], b[3], u3[10];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) b[i] = u3[sym3(i, 0, 0)] + u3[sym3(i, 1, 1)] + u3[sym3(i, 2, 2)];
-      const T s4 = w[0][0] + w[1][1] + w[2][2];
-      const T gzv[3] = {gz0, gz1, gz2};
+        for (int s = 0; s < 10; ++s) u3[s] = M_(kU3 + s);
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        T acc = 0;
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
+          for (int j = 0; j < 3; ++j) {
+            u[i][j] = M_(kU2 + sym2(i, j));
+            w[i][j] = M_(kW + sym2(i, j));
+          }
 #pragma unroll
-          for (int k = 0; k < 3; ++k) acc += T(3) * A3[sym3(d, j, k)] * u[j][k] + T(2) * W[j][k] * u3[sym3(d, j, k)];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) acc += T(2) * W[d][j] * b[j] + T(4) * gzv[j] * w[d][j];
-        acc += s4 * gzv[d];
-        G0[d] = acc;
-      }
-    }
-    const T inv_n = n > 0 ? T(1) / T(n) : T(0);
-    const T gU0 = GM(kU) * inv_n, gU1 = GM(kU + 1) * inv_n, gU2 = GM(kU + 2) * inv_n;
-    const int itmax = __reduce_max_sync(0xffffffffu, (n + G - 1) / G);
-    for (int it = 0; it < itmax; ++it) {
-      const int64_t p = a0 + (int64_t)it * G + lg;
-      if (p < e) {
-        const T c0 = vx[p] - U0, c1 = vy[p] - U1, c2 = vz[p] - U2;
-        const T cc[3] = {c0, c1, c2};
-        const T r2 = c0 * c0 + c1 * c1 + c2 * c2;
-        const T gzc = gz0 * c0 + gz1 * c1 + gz2 * c2;
-        T Wc[3];
-        T cWc = 0;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          Wc[i] = W[i][0] * c0 + W[i][1] * c1 + W[i][2] * c2;
-          cWc += cc[i] * Wc[i];
-        }
-        T out[3];
+        for (int i = 0; i < 3; ++i) b[i] = u3[sym3(i, 0, 0)] + u3[sym3(i, 1, 1)] + u3[sym3(i, 2, 2)];
+        const T s4 = w[0][0] + w[1][1] + w[2][2];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          T gd = Mu[d][0] * c0 + Mu[d][1] * c1 + Mu[d][2] * c2;
-          T a3 = 0;
+          T acc = 0;
 #pragma unroll
           for (int j = 0; j < 3; ++j)
 #pragma unroll
-            for (int k = 0; k < 3; ++k) a3 += A3[sym3(d, j, k)] * cc[j] * cc[k];
-          gd += T(3) * a3 + T(2) * cc[d] * cWc + T(2) * r2 * Wc[d] + T(4) * r2 * cc[d] * gzc;
-          const T gzd = d == 0 ? gz0 : (d == 1 ? gz1 : gz2);
-          gd += r2 * r2 * gzd;
-          out[d] = (gd - G0[d]) * inv_n;
+            for (int k = 0; k < 3; ++k)
+              acc += T(3) * A3[sym3(d, j, k)] * u[j][k] + T(2) * W[j][k] * u3[sym3(d, j, k)];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) acc += T(2) * W[d][j] * b[j] + T(4) * gzv[j] * w[d][j];
+          acc += s4 * gzv[d];
+          G0[d] = acc;
         }
-        gx[p] = out[0] + gU0;
-        gy[p] = out[1] + gU1;
-        gz[p] = out[2] + gU2;
+      }
+      const T inv_n = n > 0 ? T(1) / T(n) : T(0);
+      const T U0 = M_(kU), U1 = M_(kU + 1), U2 = M_(kU + 2);
+      const T gU0 = GM(kU) * inv_n, gU1 = GM(kU + 1) * inv_n, gU2 = GM(kU + 2) * inv_n;
+      if (lg == 0) {
+        T *r = tab[g];
+        r[AU] = U0;
+        r[AU + 1] = U1;
+        r[AU + 2] = U2;
+#pragma unroll
+        for (int s = 0; s < 6; ++s) r[AMU + s] = Mu[s];
+#pragma unroll
+        for (int s = 0; s < 10; ++s) r[AA3 + s] = A3[s];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = i; j < 3; ++j) r[AW + sym2(i, j)] = W[i][j];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          r[AGZ + d] = gzv[d];
+          r[AG0 + d] = G0[d];
+        }
+        r[AGU] = gU0;
+        r[AGU + 1] = gU1;
+        r[AGU + 2] = gU2;
+        r[AINVN] = inv_n;
+        r[AINVN + 1] = T(0);
       }
     }
+    const int64_t o0 = __shfl_sync(0xffffffffu, a0, 0);
+    const int64_t o1 = __shfl_sync(0xffffffffu, a0, 8);
+    const int64_t o2 = __shfl_sync(0xffffffffu, a0, 16);
+    const int64_t o3 = __shfl_sync(0xffffffffu, a0, 24);
+    const int64_t o4 = __shfl_sync(0xffffffffu, e, 24);
+    __syncwarp();
+    for (int64_t p = o0 + lane; p < o4; p += 32) {
+      const int cl = (p >= o1) + (p >= o2) + (p >= o3);
+      T K[kAConst];
+      load_row(tab[cl], K);
+      const T cc[3] = {vx[p] - K[AU], vy[p] - K[AU + 1], vz[p] - K[AU + 2]};
+      const T r2 = cc[0] * cc[0] + cc[1] * cc[1] + cc[2] * cc[2];
+      const T gzc = K[AGZ] * cc[0] + K[AGZ + 1] * cc[1] + K[AGZ + 2] * cc[2];
+      T Wc[3];
+      T cWc = 0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        Wc[i] = K[AW + sym2(i, 0)] * cc[0] + K[AW + sym2(i, 1)] * cc[1] + K[AW + sym2(i, 2)] * cc[2];
+        cWc += cc[i] * Wc[i];
+      }
+      T out[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        T gd = K[AMU + sym2(d, 0)] * cc[0] + K[AMU + sym2(d, 1)] * cc[1] + K[AMU + sym2(d, 2)] * cc[2];
+        T a3 = 0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) a3 += K[AA3 + sym3(d, j, k)] * cc[j] * cc[k];
+        gd += T(3) * a3 + T(2) * cc[d] * cWc + T(2) * r2 * Wc[d] + T(4) * r2 * cc[d] * gzc;
+        gd += r2 * r2 * K[AGZ + d];
+        out[d] = (gd - K[AG0 + d]) * K[AINVN] + K[AGU + d];
+      }
+      gx[p] = out[0];
+      gy[p] = out[1];
+      gz[p] = out[2];
+    }
+    __syncwarp();
   }
 }
 
@@ -306,9 +349,9 @@ void launch_adjoint(const void *v, int v_dtype, int64_t np, const int64_t *off, 
                                                               gm_out);
   }
   if (!gv) return;
-  const int threads = 256;
-  const int64_t groups_per_block = (threads / 32) * (32 / kAG);
-  int64_t blocks = (n_cells + groups_per_block - 1) / groups_per_block;
+  const int threads = 32 * kAWarps;
+  const int64_t cells_per_block = kAWarps * kACells;
+  int64_t blocks = (n_cells + cells_per_block - 1) / cells_per_block;
   const int64_t cap = (int64_t)adj_sm_count() * 8;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;

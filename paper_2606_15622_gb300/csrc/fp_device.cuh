@@ -116,4 +116,31 @@ __device__ __forceinline__ void df_scale(float hi, float lo, float rh, float rl,
   e = fmaf(hi, rl, fmaf(lo, rh, e));
 }
 
+// Copy a per-cell constant row (NC entries, 16-byte aligned, NC a multiple of
+// four) from shared memory into registers with 16-byte loads.
+template <int NC>
+__device__ __forceinline__ void load_row(const float *__restrict__ row, float (&K)[NC]) {
+  static_assert(NC % 4 == 0, "row length");
+  const float4 *r4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+  for (int q = 0; q < NC / 4; ++q) {
+    const float4 x = r4[q];
+    K[4 * q] = x.x;
+    K[4 * q + 1] = x.y;
+    K[4 * q + 2] = x.z;
+    K[4 * q + 3] = x.w;
+  }
+}
+template <int NC>
+__device__ __forceinline__ void load_row(const double *__restrict__ row, double (&K)[NC]) {
+  static_assert(NC % 2 == 0, "row length");
+  const double2 *r2 = reinterpret_cast<const double2 *>(row);
+#pragma unroll
+  for (int q = 0; q < NC / 2; ++q) {
+    const double2 x = r2[q];
+    K[2 * q] = x.x;
+    K[2 * q + 1] = x.y;
+  }
+}
+
 }  // namespace fpc
