@@ -173,9 +173,12 @@ def run_ours(args):
         api.fp_closure_exact(v32, off, tau, params=prm, prec="fp32", moments_out=mom, coeffs_out=coeffs,
                              flags_out=flags, stream=stream)
 
-    def c_surrogate():
+    side = torch.cuda.Stream(device=dev)
+    ev_mom, ev_sur = torch.cuda.Event(), torch.cuda.Event()
+
+    def c_surrogate(on=None):
         sur.closure(mom, tau, params=prm, prec="fp32", coeffs_out=coeffs_s, flags_out=flags_s, workspace=s_ws,
-                    stream=stream)
+                    stream=on if on is not None else stream)
 
     def c_adjoint():
         api.fp_closure_backward(v32, off, tau, mom, coeffs, flags, gY, params=prm, grad_moments=gmom, grad_v=gv,
@@ -190,8 +193,17 @@ def run_ours(args):
              ("velocity_update", c_velocity)]
 
     def step():
-        for _, fn in calls:
-            fn()
+        # the learned closure needs only the moments: it runs on a second
+        # stream beside the adjoint (FP64-bound) and the velocity update, and
+        # joins before the step ends (the next step's gather rewrites them)
+        c_exact()
+        ev_mom.record(stream)
+        side.wait_event(ev_mom)
+        c_surrogate(on=side)
+        c_adjoint()
+        c_velocity()
+        ev_sur.record(side)
+        stream.wait_event(ev_sur)
 
     def timed(fn, k, w, reset=None):
         for _ in range(w):
@@ -400,7 +412,8 @@ def run_ours(args):
                    "step": "exact closure (FP32 moments, FP64 solve) + learned closure with exact fallback + "
                            "adjoint to moments and velocities + velocity update",
                    "cells": n_cells, "particles": n_p, "velocities": "f32 SoA", "eps2_hat": prm.eps2_hat,
-                   "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{ws}"},
+                   "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{ws}",
+                   "streams": "learned closure on a second stream, concurrent with adjoint + velocity update"},
         "particles_per_s": round(parts_per_s, 1),
         "per_call_ms": {k: round(v, 5) for k, v in per_call.items()},
         "kernels": kernels,

@@ -171,7 +171,7 @@ __host__ __device__ constexpr int mult3(int s) { return (s == 0 || s == 6 || s =
 // polynomial (shared-memory table), then all 32 lanes walk the four cells'
 // contiguous particle range.
 template <typename VT>
-__global__ void __launch_bounds__(32 * kAWarps) adjoint_particle_kernel(const VT *__restrict__ v, int64_t np,
+__global__ void __launch_bounds__(32 * kAWarps, sizeof(VT) == 4 ? 3 : 1) adjoint_particle_kernel(const VT *__restrict__ v, int64_t np,
                                                                         const int64_t *__restrict__ off,
                                                                         int64_t n_cells,
                                                                         const double *__restrict__ mom,
@@ -288,16 +288,19 @@ __global__ void __launch_bounds__(32 * kAWarps) adjoint_particle_kernel(const VT
       }
     }
     const int64_t o0 = __shfl_sync(0xffffffffu, a0, 0);
-    const int64_t o1 = __shfl_sync(0xffffffffu, a0, 8);
-    const int64_t o2 = __shfl_sync(0xffffffffu, a0, 16);
-    const int64_t o3 = __shfl_sync(0xffffffffu, a0, 24);
-    const int64_t o4 = __shfl_sync(0xffffffffu, e, 24);
+    const int i1 = (int)(__shfl_sync(0xffffffffu, a0, 8) - o0);
+    const int i2 = (int)(__shfl_sync(0xffffffffu, a0, 16) - o0);
+    const int i3 = (int)(__shfl_sync(0xffffffffu, a0, 24) - o0);
+    const int i4 = (int)(__shfl_sync(0xffffffffu, e, 24) - o0);
+    const VT *px = vx + o0, *py = vy + o0, *pz = vz + o0;
+    VT *qx = gx + o0, *qy = gy + o0, *qz = gz + o0;
     __syncwarp();
-    for (int64_t p = o0 + lane; p < o4; p += 32) {
-      const int cl = (p >= o1) + (p >= o2) + (p >= o3);
+#pragma unroll 2
+    for (int q = lane; q < i4; q += 32) {
+      const int cl = (q >= i1) + (q >= i2) + (q >= i3);
       T K[kAConst];
       load_row(tab[cl], K);
-      const T cc[3] = {vx[p] - K[AU], vy[p] - K[AU + 1], vz[p] - K[AU + 2]};
+      const T cc[3] = {px[q] - K[AU], py[q] - K[AU + 1], pz[q] - K[AU + 2]};
       const T r2 = cc[0] * cc[0] + cc[1] * cc[1] + cc[2] * cc[2];
       const T gzc = K[AGZ] * cc[0] + K[AGZ + 1] * cc[1] + K[AGZ + 2] * cc[2];
       T Wc[3];
@@ -320,9 +323,9 @@ __global__ void __launch_bounds__(32 * kAWarps) adjoint_particle_kernel(const VT
         gd += r2 * r2 * K[AGZ + d];
         out[d] = (gd - K[AG0 + d]) * K[AINVN] + K[AGU + d];
       }
-      gx[p] = out[0];
-      gy[p] = out[1];
-      gz[p] = out[2];
+      qx[q] = out[0];
+      qy[q] = out[1];
+      qz[q] = out[2];
     }
     __syncwarp();
   }

@@ -39,9 +39,9 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1
       k0 += 0x9E3779B9u;
       k1 += 0xBB67AE85u;
     }
-    const uint32_t hi0 = __umulhi(0xD2511F53u, x.x), lo0 = 0xD2511F53u * x.x;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, x.z), lo1 = 0xCD9E8D57u * x.z;
-    x = make_uint4(hi1 ^ x.y ^ k0, lo1, hi0 ^ x.w ^ k1, lo0);
+    // one 32x32 -> 64-bit multiply gives both halves of each product
+    const uint64_t p0 = (uint64_t)0xD2511F53u * x.x, p1 = (uint64_t)0xCD9E8D57u * x.z;
+    x = make_uint4((uint32_t)(p1 >> 32) ^ x.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ x.w ^ k1, (uint32_t)p0);
   }
   return x;
 }
@@ -155,23 +155,26 @@ __global__ void __launch_bounds__(32 * kVWarps) velocity_kernel(VT *__restrict__
         for (int q = 0; q < kVConst; ++q) tab[g][q] = vals[q];
       }
     }
-    // the warp's contiguous particle range and the inner boundaries
+    // the warp's contiguous particle range and the inner boundaries,
+    // relative to its first particle
     const int64_t o0 = __shfl_sync(0xffffffffu, a0, 0);
-    const int64_t o1 = __shfl_sync(0xffffffffu, a0, 8);
-    const int64_t o2 = __shfl_sync(0xffffffffu, a0, 16);
-    const int64_t o3 = __shfl_sync(0xffffffffu, a0, 24);
-    const int64_t o4 = __shfl_sync(0xffffffffu, e, 24);
+    const int i1 = (int)(__shfl_sync(0xffffffffu, a0, 8) - o0);
+    const int i2 = (int)(__shfl_sync(0xffffffffu, a0, 16) - o0);
+    const int i3 = (int)(__shfl_sync(0xffffffffu, a0, 24) - o0);
+    const int i4 = (int)(__shfl_sync(0xffffffffu, e, 24) - o0);
+    VT *px = vx + o0, *py = vy + o0, *pz = vz + o0;
     __syncwarp();
     // ---- pass 1: <N.N>, <M'.N> per cell ----
     const unsigned nonlin = __ballot_sync(0xffffffffu, !linear && n > 0 && lg == 0);
     T s_nn[kVCells] = {}, s_mn[kVCells] = {};
     if (nonlin) {
-      for (int64_t p = o0 + lane; p < o4; p += 32) {
-        const int cl = (p >= o1) + (p >= o2) + (p >= o3);
+#pragma unroll 2
+      for (int q = lane; q < i4; q += 32) {
+        const int cl = (q >= i1) + (q >= i2) + (q >= i3);
         T K[kVConst];
         load_row(tab[cl], K);
         if (K[VLIN] == T(0)) {
-          const T m0 = vx[p] - K[VU0], m1 = vy[p] - K[VU1], m2 = vz[p] - K[VU2];
+          const T m0 = px[q] - K[VU0], m1 = py[q] - K[VU1], m2 = pz[q] - K[VU2];
           T n0, n1, n2;
           drift(K, m0, m1, m2, n0, n1, n2);
           const T nn = n0 * n0 + n1 * n1 + n2 * n2, mn = m0 * n0 + m1 * n1 + m2 * n2;
@@ -221,13 +224,15 @@ __global__ void __launch_bounds__(32 * kVWarps) velocity_kernel(VT *__restrict__
     }
     __syncwarp();
     // ---- pass 2: the update ----
-    for (int64_t p = o0 + lane; p < o4; p += 32) {
-      const int cl = (p >= o1) + (p >= o2) + (p >= o3);
+#pragma unroll 2
+    for (int q = lane; q < i4; q += 32) {
+      const int cl = (q >= i1) + (q >= i2) + (q >= i3);
       T K[kVConst];
       load_row(tab[cl], K);
-      const T m0 = vx[p] - K[VU0], m1 = vy[p] - K[VU1], m2 = vz[p] - K[VU2];
+      const T m0 = px[q] - K[VU0], m1 = py[q] - K[VU1], m2 = pz[q] - K[VU2];
       T n0 = 0, n1 = 0, n2 = 0;
       if (K[VLIN] == T(0)) drift(K, m0, m1, m2, n0, n1, n2);
+      const int64_t p = o0 + q;
       T x0, x1, x2;
       if (xi) {
         x0 = xi[p];
@@ -241,9 +246,9 @@ __global__ void __launch_bounds__(32 * kVWarps) velocity_kernel(VT *__restrict__
         x2 = f2;
       }
       const T a = K[VA], df = K[VDRIFT], nz = K[VNOISE], ia = K[VIA];
-      vx[p] = (m0 * a + df * n0 + nz * x0) * ia + K[VU0];
-      vy[p] = (m1 * a + df * n1 + nz * x1) * ia + K[VU1];
-      vz[p] = (m2 * a + df * n2 + nz * x2) * ia + K[VU2];
+      px[q] = (m0 * a + df * n0 + nz * x0) * ia + K[VU0];
+      py[q] = (m1 * a + df * n1 + nz * x1) * ia + K[VU1];
+      pz[q] = (m2 * a + df * n2 + nz * x2) * ia + K[VU2];
     }
     __syncwarp();
   }
