@@ -26,6 +26,7 @@ constexpr int kVG = 8;              // lanes per cell while building constants
 constexpr int kVCells = 32 / kVG;   // consecutive cells per warp task
 constexpr int kVWarps = 8;          // warps per block
 constexpr int kVConst = 24;         // table entries per cell
+constexpr int kVBatch = 4;          // particles per lane per round
 
 // table slots
 enum { VU0 = 0, VU1, VU2, VTH, VB0, VB1, VB2, VC00, VC01, VC02, VC11, VC12, VC22, VG0, VG1, VG2, VEPS, VA, VDRIFT,
@@ -168,20 +169,32 @@ __global__ void __launch_bounds__(32 * kVWarps) velocity_kernel(VT *__restrict__
     const unsigned nonlin = __ballot_sync(0xffffffffu, !linear && n > 0 && lg == 0);
     T s_nn[kVCells] = {}, s_mn[kVCells] = {};
     if (nonlin) {
-#pragma unroll 2
-      for (int q = lane; q < i4; q += 32) {
-        const int cl = (q >= i1) + (q >= i2) + (q >= i3);
-        T K[kVConst];
-        load_row(tab[cl], K);
-        if (K[VLIN] == T(0)) {
-          const T m0 = px[q] - K[VU0], m1 = py[q] - K[VU1], m2 = pz[q] - K[VU2];
-          T n0, n1, n2;
-          drift(K, m0, m1, m2, n0, n1, n2);
-          const T nn = n0 * n0 + n1 * n1 + n2 * n2, mn = m0 * n0 + m1 * n1 + m2 * n2;
+      // kVBatch particles per lane per round, all loads issued first
+      for (int q0 = lane; q0 < i4; q0 += 32 * kVBatch) {
+        T mx[kVBatch], my[kVBatch], mz[kVBatch];
 #pragma unroll
-          for (int j = 0; j < kVCells; ++j) {
-            s_nn[j] += cl == j ? nn : T(0);
-            s_mn[j] += cl == j ? mn : T(0);
+        for (int u = 0; u < kVBatch; ++u) {
+          const int q = min(q0 + 32 * u, i4 - 1);
+          mx[u] = px[q];
+          my[u] = py[q];
+          mz[u] = pz[q];
+        }
+#pragma unroll
+        for (int u = 0; u < kVBatch; ++u) {
+          const int q = q0 + 32 * u;
+          const int cl = (q >= i1) + (q >= i2) + (q >= i3);
+          T K[kVConst];
+          load_row(tab[cl], K);
+          if (q < i4 && K[VLIN] == T(0)) {
+            const T m0 = mx[u] - K[VU0], m1 = my[u] - K[VU1], m2 = mz[u] - K[VU2];
+            T n0, n1, n2;
+            drift(K, m0, m1, m2, n0, n1, n2);
+            const T nn = n0 * n0 + n1 * n1 + n2 * n2, mn = m0 * n0 + m1 * n1 + m2 * n2;
+#pragma unroll
+            for (int j = 0; j < kVCells; ++j) {
+              s_nn[j] += cl == j ? nn : T(0);
+              s_mn[j] += cl == j ? mn : T(0);
+            }
           }
         }
       }
@@ -223,32 +236,47 @@ __global__ void __launch_bounds__(32 * kVWarps) velocity_kernel(VT *__restrict__
       }
     }
     __syncwarp();
-    // ---- pass 2: the update ----
-#pragma unroll 2
-    for (int q = lane; q < i4; q += 32) {
-      const int cl = (q >= i1) + (q >= i2) + (q >= i3);
-      T K[kVConst];
-      load_row(tab[cl], K);
-      const T m0 = px[q] - K[VU0], m1 = py[q] - K[VU1], m2 = pz[q] - K[VU2];
-      T n0 = 0, n1 = 0, n2 = 0;
-      if (K[VLIN] == T(0)) drift(K, m0, m1, m2, n0, n1, n2);
-      const int64_t p = o0 + q;
-      T x0, x1, x2;
-      if (xi) {
-        x0 = xi[p];
-        x1 = xi[np + p];
-        x2 = xi[2 * np + p];
-      } else {
-        float f0, f1, f2;
-        philox_normals(prm.seed, prm.step, (uint64_t)p, f0, f1, f2);
-        x0 = f0;
-        x1 = f1;
-        x2 = f2;
+    // ---- pass 2: the update (kVBatch particles per lane per round; the
+    //      loads go first, since the stores to the three components may
+    //      alias later loads as far as the compiler can tell) ----
+    for (int q0 = lane; q0 < i4; q0 += 32 * kVBatch) {
+      T mx[kVBatch], my[kVBatch], mz[kVBatch];
+#pragma unroll
+      for (int u = 0; u < kVBatch; ++u) {
+        const int q = min(q0 + 32 * u, i4 - 1);
+        mx[u] = px[q];
+        my[u] = py[q];
+        mz[u] = pz[q];
       }
-      const T a = K[VA], df = K[VDRIFT], nz = K[VNOISE], ia = K[VIA];
-      px[q] = (m0 * a + df * n0 + nz * x0) * ia + K[VU0];
-      py[q] = (m1 * a + df * n1 + nz * x1) * ia + K[VU1];
-      pz[q] = (m2 * a + df * n2 + nz * x2) * ia + K[VU2];
+#pragma unroll
+      for (int u = 0; u < kVBatch; ++u) {
+        const int q = q0 + 32 * u;
+        if (q < i4) {
+          const int cl = (q >= i1) + (q >= i2) + (q >= i3);
+          T K[kVConst];
+          load_row(tab[cl], K);
+          const T m0 = mx[u] - K[VU0], m1 = my[u] - K[VU1], m2 = mz[u] - K[VU2];
+          T n0 = 0, n1 = 0, n2 = 0;
+          if (K[VLIN] == T(0)) drift(K, m0, m1, m2, n0, n1, n2);
+          const int64_t p = o0 + q;
+          T x0, x1, x2;
+          if (xi) {
+            x0 = xi[p];
+            x1 = xi[np + p];
+            x2 = xi[2 * np + p];
+          } else {
+            float f0, f1, f2;
+            philox_normals(prm.seed, prm.step, (uint64_t)p, f0, f1, f2);
+            x0 = f0;
+            x1 = f1;
+            x2 = f2;
+          }
+          const T a = K[VA], df = K[VDRIFT], nz = K[VNOISE], ia = K[VIA];
+          px[q] = (m0 * a + df * n0 + nz * x0) * ia + K[VU0];
+          py[q] = (m1 * a + df * n1 + nz * x1) * ia + K[VU1];
+          pz[q] = (m2 * a + df * n2 + nz * x2) * ia + K[VU2];
+        }
+      }
     }
     __syncwarp();
   }
