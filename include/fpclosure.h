@@ -157,8 +157,12 @@ int fp_closure_solve(const double *moments, const double *tau, int64_t n_cells, 
  *                                                            (Eq. update_vel)
  * with M' = M - U, a = exp(-dt/tau), b_i = <c_i |c|^2> = 2 q_i / rho and the
  * cell averages <.> over the cell's particles.
- *   v            [3][n_particles] f32 or f64, updated IN PLACE; FP32
+ *   v            [3][n_particles] f32 or f64, the velocities M^n; FP32
  *                velocities are updated in FP32 arithmetic, FP64 in FP64
+ *   v_out        [3][n_particles] of v's dtype receiving M^{n+1}, or NULL (or
+ *                v itself) to update v in place; a distinct v_out must not
+ *                overlap v.  Writing out of place lets a caller keep M^n for
+ *                a concurrent reader (e.g. the adjoint's particle pass)
  *   moments      [n_cells][FP_NMOM] of the same velocities (U, theta, u_ijk)
  *   coeffs       [n_cells][9] from the closure
  *   tau          [n_cells]; dt the time step
@@ -174,10 +178,10 @@ int fp_closure_solve(const double *moments, const double *tau, int64_t n_cells, 
  *                of the linear model (N = 0, alpha = 1); alpha^2 <= 0 or
  *                non-finite sets FP_FLAG_ALPHA and alpha = 1.
  * No workspace. */
-int fp_velocity_update(void *v, int v_dtype, int64_t n_particles, const int64_t *cell_offsets, int64_t n_cells,
-                       const double *moments, const double *coeffs, const double *tau, double dt, const fp_params *p,
-                       const void *xi, uint64_t seed, uint64_t step, double *alpha_out, int32_t *flags,
-                       fp_stream_t stream);
+int fp_velocity_update(void *v, void *v_out, int v_dtype, int64_t n_particles, const int64_t *cell_offsets,
+                       int64_t n_cells, const double *moments, const double *coeffs, const double *tau, double dt,
+                       const fp_params *p, const void *xi, uint64_t seed, uint64_t step, double *alpha_out,
+                       int32_t *flags, fp_stream_t stream);
 
 /* fp_closure_backward: the adjoint of fp_closure_exact (not in the paper; the
  * closure of Eq. system9x9 differentiated as an implicit function).  With

@@ -63,8 +63,8 @@ SIGNATURES = {
                                 _vp, _vp, _vp, _vp, _sz, _vp]),
     "fp_moments": (_i32, [_vp, _i32, _i64, _vp, _i64, _i32, _vp, _vp]),
     "fp_closure_solve": (_i32, [_vp, _vp, _i64, ctypes.POINTER(Params), _i32, _vp, _vp, _vp]),
-    "fp_velocity_update": (_i32, [_vp, _i32, _i64, _vp, _i64, _vp, _vp, _vp, _dbl, ctypes.POINTER(Params), _vp,
-                                  _u64, _u64, _vp, _vp, _vp]),
+    "fp_velocity_update": (_i32, [_vp, _vp, _i32, _i64, _vp, _i64, _vp, _vp, _vp, _dbl, ctypes.POINTER(Params),
+                                  _vp, _u64, _u64, _vp, _vp, _vp]),
     "fp_closure_backward": (_i32, [_vp, _i32, _i64, _vp, _i64, _vp, ctypes.POINTER(Params), _vp, _vp, _vp, _vp,
                                    _vp, _vp, _vp, _vp, _sz, _vp]),
     "fp_mlp_param_count": (_i64, []),
@@ -261,19 +261,22 @@ def fp_closure_solve(moments, tau, params: Params | None = None, prec="fp32", co
 
 
 def fp_velocity_update(v, offsets, moments, coeffs, tau, flags, dt, params: Params | None = None, xi=None,
-                       seed=0, step=0, alpha_out=None, stream=None):
-    """One velocity update in place (Eqs. update_vel / update_N / update_alpha).
-    flags is read and updated; returns (v, alpha_out, flags)."""
+                       seed=0, step=0, alpha_out=None, stream=None, v_out=None):
+    """One velocity update (Eqs. update_vel / update_N / update_alpha), in
+    place or into v_out (same shape and dtype, not overlapping v).  flags is
+    read and updated; returns (updated velocities, alpha_out, flags)."""
     n_cells = offsets.numel() - 1
     n_p = v.shape[-1] if v.dim() == 2 else v.numel() // 3
-    _need_cuda(v, offsets, moments, coeffs, tau, flags, xi, alpha_out)
+    _need_cuda(v, offsets, moments, coeffs, tau, flags, xi, alpha_out, v_out)
+    if v_out is not None and (v_out.dtype != v.dtype or v_out.numel() != v.numel() or not v_out.is_contiguous()):
+        raise FPError("v_out must be a contiguous array of v's shape and dtype")
     if xi is not None and xi.dtype != v.dtype:
         raise FPError("xi must have the velocity dtype")
     if flags.dtype != torch.int32:
         raise FPError("flags must be int32")
     p = params if params is not None else default_params()
-    rc = lib().fp_velocity_update(_ptr(v), _vdtype(v), n_p, _ptr(offsets), n_cells, _ptr(moments), _ptr(coeffs),
-                                  _ptr(tau), float(dt), ctypes.byref(p), _ptr(xi), int(seed), int(step),
+    rc = lib().fp_velocity_update(_ptr(v), _ptr(v_out), _vdtype(v), n_p, _ptr(offsets), n_cells, _ptr(moments),
+                                  _ptr(coeffs), _ptr(tau), float(dt), ctypes.byref(p), _ptr(xi), int(seed), int(step),
                                   _ptr(alpha_out), _ptr(flags), _stream(stream))
     _check(rc, "fp_velocity_update")
-    return v, alpha_out, flags
+    return (v if v_out is None else v_out), alpha_out, flags

@@ -20,15 +20,11 @@
 
 namespace fpc {
 
-__global__ void __launch_bounds__(128) adjoint_cell_kernel(const double *__restrict__ mom,
-                                                           const double *__restrict__ coeffs,
-                                                           const int32_t *__restrict__ flags,
-                                                           const double *__restrict__ tau,
-                                                           const double *__restrict__ gY,
-                                                           const double *__restrict__ gm_in, int64_t n_cells,
-                                                           double eps2_hat, double *__restrict__ gm_out) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n_cells) return;
+__device__ __forceinline__ void adjoint_cell(int64_t c, const double *__restrict__ mom,
+                                             const double *__restrict__ coeffs, const int32_t *__restrict__ flags,
+                                             const double *__restrict__ tau, const double *__restrict__ gY,
+                                             const double *__restrict__ gm_in, double eps2_hat,
+                                             double *__restrict__ gm_out) {
   double gm[FP_NMOM];
 #pragma unroll
   for (int k = 0; k < FP_NMOM; ++k) gm[k] = gm_in ? gm_in[c * FP_NMOM + k] : 0.0;
@@ -145,6 +141,20 @@ __global__ void __launch_bounds__(128) adjoint_cell_kernel(const double *__restr
   }
 #pragma unroll
   for (int k = 0; k < FP_NMOM; ++k) gm_out[c * FP_NMOM + k] = gm[k];
+}
+
+// One thread per cell, grid-stride, one 128-thread block per SM (FP64-bound:
+// see solve_kernel).
+__global__ void __launch_bounds__(128, 1) adjoint_cell_kernel(const double *__restrict__ mom,
+                                                              const double *__restrict__ coeffs,
+                                                              const int32_t *__restrict__ flags,
+                                                              const double *__restrict__ tau,
+                                                              const double *__restrict__ gY,
+                                                              const double *__restrict__ gm_in, int64_t n_cells,
+                                                              double eps2_hat, double *__restrict__ gm_out) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells;
+       c += (int64_t)gridDim.x * blockDim.x)
+    adjoint_cell(c, mom, coeffs, flags, tau, gY, gm_in, eps2_hat, gm_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -347,7 +357,8 @@ void launch_adjoint(const void *v, int v_dtype, int64_t np, const int64_t *off, 
                     const double *gm_in, double *gm_out, void *gv, cudaStream_t st) {
   {
     const int threads = 128;
-    const int64_t blocks = (n_cells + threads - 1) / threads;
+    int64_t blocks = (n_cells + threads - 1) / threads;
+    if (blocks > adj_sm_count()) blocks = adj_sm_count();
     adjoint_cell_kernel<<<(unsigned)blocks, threads, 0, st>>>(mom, coeffs, flags, tau, gY, gm_in, n_cells, eps2_hat,
                                                               gm_out);
   }

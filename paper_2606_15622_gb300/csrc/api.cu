@@ -11,9 +11,9 @@ void launch_gather(const void *v, int v_dtype, int64_t np, const int64_t *off, i
                    double *mom, cudaStream_t st);
 void launch_solve(const double *mom, const double *tau, int64_t n_cells, const fp_params &p, int prec,
                   double *coeffs, int32_t *flags, cudaStream_t st);
-void launch_velocity(void *v, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, const double *mom,
-                     const double *coeffs, const double *tau, double dt, double eps2_hat, const void *xi, uint64_t seed,
-                     uint64_t step, double *alpha_out, int32_t *flags, cudaStream_t st);
+void launch_velocity(const void *v, void *v_out, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells,
+                     const double *mom, const double *coeffs, const double *tau, double dt, double eps2_hat,
+                     const void *xi, uint64_t seed, uint64_t step, double *alpha_out, int32_t *flags, cudaStream_t st);
 void launch_adjoint(const void *v, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, const double *tau,
                     double eps2_hat, const double *mom, const double *coeffs, const int32_t *flags, const double *gY,
                     const double *gm_in, double *gm_out, void *gv, cudaStream_t st);
@@ -168,10 +168,10 @@ int fp_closure_solve(const double *moments, const double *tau, int64_t n_cells, 
   return check_launch("solve");
 }
 
-int fp_velocity_update(void *v, int v_dtype, int64_t n_particles, const int64_t *cell_offsets, int64_t n_cells,
-                       const double *moments, const double *coeffs, const double *tau, double dt, const fp_params *p,
-                       const void *xi, uint64_t seed, uint64_t step, double *alpha_out, int32_t *flags,
-                       fp_stream_t stream) {
+int fp_velocity_update(void *v, void *v_out, int v_dtype, int64_t n_particles, const int64_t *cell_offsets,
+                       int64_t n_cells, const double *moments, const double *coeffs, const double *tau, double dt,
+                       const fp_params *p, const void *xi, uint64_t seed, uint64_t step, double *alpha_out,
+                       int32_t *flags, fp_stream_t stream) {
   g_err[0] = 0;
   if (n_cells < 0 || n_particles < 0) return fail(FP_ERR_ARG, "negative size");
   if (n_cells == 0) return FP_OK;
@@ -179,11 +179,16 @@ int fp_velocity_update(void *v, int v_dtype, int64_t n_particles, const int64_t 
   if (!cell_offsets || !moments || !coeffs || !tau || !flags) return fail(FP_ERR_ARG, "null array pointer");
   if (n_particles > 0 && !v) return fail(FP_ERR_ARG, "null velocity pointer");
   if (!(dt >= 0.0)) return fail(FP_ERR_ARG, "dt must be >= 0");
+  if (v_out && v_out != v && n_particles > 0) {
+    const size_t bytes = (size_t)3 * (size_t)n_particles * (v_dtype == FP_V_F32 ? 4 : 8);
+    const char *a = (const char *)v, *b = (const char *)v_out;
+    if (a < b + bytes && b < a + bytes) return fail(FP_ERR_ARG, "v_out overlaps v without being v");
+  }
   fp_params prm;
   fp_default_params(&prm);
   if (p) prm = *p;
-  fpc::launch_velocity(v, v_dtype, n_particles, cell_offsets, n_cells, moments, coeffs, tau, dt, prm.eps2_hat, xi,
-                       seed, step, alpha_out, flags, (cudaStream_t)stream);
+  fpc::launch_velocity(v, v_out ? v_out : v, v_dtype, n_particles, cell_offsets, n_cells, moments, coeffs, tau, dt,
+                       prm.eps2_hat, xi, seed, step, alpha_out, flags, (cudaStream_t)stream);
   return check_launch("velocity");
 }
 

@@ -256,17 +256,22 @@ __global__ void __launch_bounds__(256) gather_fp64_kernel(const VT *__restrict__
 // ---------------------------------------------------------------------------
 // assembly + solve (closure_math.cuh)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) solve_kernel(const double *__restrict__ mom, const double *__restrict__ tau,
-                                                    int64_t n_cells, SolveParams prm, double *__restrict__ coeffs,
-                                                    int32_t *__restrict__ flags) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n_cells) return;
-  double y[9];
-  const int fl = closure_cell(mom + c * FP_NMOM, tau[c], prm, y);
-  double *yc = coeffs + c * 9;
+// One thread per cell, grid-stride: the launch uses one 128-thread block per
+// SM.  A single warp per SM sub-partition keeps its FP64 unit busy (each FP64
+// warp instruction occupies it for many cycles), and the half of the register
+// file left free lets kernels of other streams run beside it.
+__global__ void __launch_bounds__(128, 1) solve_kernel(const double *__restrict__ mom, const double *__restrict__ tau,
+                                                       int64_t n_cells, SolveParams prm, double *__restrict__ coeffs,
+                                                       int32_t *__restrict__ flags) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    double y[9];
+    const int fl = closure_cell(mom + c * FP_NMOM, tau[c], prm, y);
+    double *yc = coeffs + c * 9;
 #pragma unroll
-  for (int q = 0; q < 9; ++q) yc[q] = y[q];
-  flags[c] = fl;
+    for (int q = 0; q < 9; ++q) yc[q] = y[q];
+    flags[c] = fl;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -324,7 +329,8 @@ void launch_solve(const double *mom, const double *tau, int64_t n_cells, const f
   if (prec == FP_PREC_FP32_MOMENTS && rtol < FP_FP32_PIVOT_FLOOR) rtol = FP_FP32_PIVOT_FLOOR;
   SolveParams prm{p.eps2_hat, rtol, p.min_particles};
   const int threads = 128;
-  const int64_t blocks = (n_cells + threads - 1) / threads;
+  int64_t blocks = (n_cells + threads - 1) / threads;
+  if (blocks > sm_count()) blocks = sm_count();
   solve_kernel<<<(unsigned)blocks, threads, 0, st>>>(mom, tau, n_cells, prm, coeffs, flags);
 }
 

@@ -8,7 +8,7 @@
 //   pass 1  <N.N> and <M'.N> per cell (four accumulator pairs per lane, one
 //           warp reduction) -> alpha;
 //   pass 2  M^{n+1} = (M' a + (1-a) tau N + sqrt(theta (1-a^2)) xi) / alpha + U,
-//           written in place.
+//           written in place or to a separate output array.
 // The per-cell constants (U, theta, b, C + I/tau, G, eps^2, a, (1-a) tau, the
 // noise amplitude, 1/alpha) are built once per cell by an 8-lane group from
 // the FP64 moments and coefficients -- one FP64 conversion per constant --
@@ -80,8 +80,10 @@ __device__ __forceinline__ void drift(const T *K, T m0, T m1, T m2, T &n0, T &n1
   n2 = K[VC02] * m0 + K[VC12] * m1 + K[VC22] * m2 + K[VG2] * q - e * (m2 * m2s - K[VB2]);
 }
 
+// v and vout may be the same array (in-place update): every particle is read
+// before it is written, by the same lane.
 template <typename VT>
-__global__ void __launch_bounds__(32 * kVWarps) velocity_kernel(VT *__restrict__ v, int64_t np,
+__global__ void __launch_bounds__(32 * kVWarps) velocity_kernel(const VT *v, VT *vout, int64_t np,
                                                                 const int64_t *__restrict__ off, int64_t n_cells,
                                                                 const double *__restrict__ mom,
                                                                 const double *__restrict__ coeffs,
@@ -97,7 +99,8 @@ __global__ void __launch_bounds__(32 * kVWarps) velocity_kernel(VT *__restrict__
   const int g = lane / kVG;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  VT *vx = v, *vy = v + np, *vz = v + 2 * np;
+  const VT *vx = v, *vy = v + np, *vz = v + 2 * np;
+  VT *wx = vout, *wy = vout + np, *wz = vout + 2 * np;
   T(*tab)[kVConst] = table[wib];
 
   for (int64_t base = warp * kVCells; base < n_cells; base += nwarps * kVCells) {
@@ -163,7 +166,8 @@ __global__ void __launch_bounds__(32 * kVWarps) velocity_kernel(VT *__restrict__
     const int i2 = (int)(__shfl_sync(0xffffffffu, a0, 16) - o0);
     const int i3 = (int)(__shfl_sync(0xffffffffu, a0, 24) - o0);
     const int i4 = (int)(__shfl_sync(0xffffffffu, e, 24) - o0);
-    VT *px = vx + o0, *py = vy + o0, *pz = vz + o0;
+    const VT *px = vx + o0, *py = vy + o0, *pz = vz + o0;
+    VT *ox = wx + o0, *oy = wy + o0, *oz = wz + o0;
     __syncwarp();
     // ---- pass 1: <N.N>, <M'.N> per cell ----
     const unsigned nonlin = __ballot_sync(0xffffffffu, !linear && n > 0 && lg == 0);
@@ -237,8 +241,8 @@ __global__ void __launch_bounds__(32 * kVWarps) velocity_kernel(VT *__restrict__
     }
     __syncwarp();
     // ---- pass 2: the update (kVBatch particles per lane per round; the
-    //      loads go first, since the stores to the three components may
-    //      alias later loads as far as the compiler can tell) ----
+    //      loads go first, since the stores may alias later loads as far
+    //      as the compiler can tell) ----
     for (int q0 = lane; q0 < i4; q0 += 32 * kVBatch) {
       T mx[kVBatch], my[kVBatch], mz[kVBatch];
 #pragma unroll
@@ -272,9 +276,9 @@ __global__ void __launch_bounds__(32 * kVWarps) velocity_kernel(VT *__restrict__
             x2 = f2;
           }
           const T a = K[VA], df = K[VDRIFT], nz = K[VNOISE], ia = K[VIA];
-          px[q] = (m0 * a + df * n0 + nz * x0) * ia + K[VU0];
-          py[q] = (m1 * a + df * n1 + nz * x1) * ia + K[VU1];
-          pz[q] = (m2 * a + df * n2 + nz * x2) * ia + K[VU2];
+          ox[q] = (m0 * a + df * n0 + nz * x0) * ia + K[VU0];
+          oy[q] = (m1 * a + df * n1 + nz * x1) * ia + K[VU1];
+          oz[q] = (m2 * a + df * n2 + nz * x2) * ia + K[VU2];
         }
       }
     }
@@ -293,7 +297,7 @@ static int vel_sm_count() {
   return n;
 }
 
-void launch_velocity(void *v, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, const double *mom,
+void launch_velocity(const void *v, void *v_out, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, const double *mom,
                      const double *coeffs, const double *tau, double dt, double eps2_hat, const void *xi, uint64_t seed,
                      uint64_t step, double *alpha_out, int32_t *flags, cudaStream_t st) {
   VelParams prm{dt, eps2_hat, seed, step};
@@ -304,11 +308,13 @@ void launch_velocity(void *v, int v_dtype, int64_t np, const int64_t *off, int64
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   if (v_dtype == FP_V_F32)
-    velocity_kernel<float><<<(unsigned)blocks, threads, 0, st>>>((float *)v, np, off, n_cells, mom, coeffs, tau, prm,
-                                                                 (const float *)xi, alpha_out, flags);
+    velocity_kernel<float><<<(unsigned)blocks, threads, 0, st>>>((const float *)v, (float *)v_out, np, off, n_cells,
+                                                                 mom, coeffs, tau, prm, (const float *)xi, alpha_out,
+                                                                 flags);
   else
-    velocity_kernel<double><<<(unsigned)blocks, threads, 0, st>>>((double *)v, np, off, n_cells, mom, coeffs, tau,
-                                                                  prm, (const double *)xi, alpha_out, flags);
+    velocity_kernel<double><<<(unsigned)blocks, threads, 0, st>>>((const double *)v, (double *)v_out, np, off,
+                                                                  n_cells, mom, coeffs, tau, prm, (const double *)xi,
+                                                                  alpha_out, flags);
 }
 
 }  // namespace fpc

@@ -138,3 +138,28 @@ def test_argument_errors():
         api.fp_velocity_update(v, off, mom, y, tau, fl, -1.0)
     with pytest.raises(api.FPError):
         api.fp_velocity_update(v, off, mom, y, tau, fl, 0.1, xi=torch.zeros((3, 4), dtype=torch.float64, device="cuda"))
+    big = torch.zeros(15, dtype=torch.float32, device="cuda")
+    with pytest.raises(api.FPError):  # v_out overlapping v without being v
+        api.fp_velocity_update(big[:12].view(3, 4), off, mom, y, tau, fl, 0.1, v_out=big[3:].view(3, 4))
+
+
+@pytest.mark.parametrize("vdtype", ["f64", "f32"])
+def test_out_of_place_matches_in_place(cavity_pop, vdtype):
+    """Writing M^{n+1} to a separate array gives the in-place result bit for
+    bit and leaves M^n untouched."""
+    pop = cavity_pop.subset(np.arange(0, cavity_pop.n_cells, 3))
+    _, m, y, fl = _oracle_state(pop, vdtype)
+    v0 = _dev(pop.v64 if vdtype == "f64" else pop.v32)
+    off, mom, yd, tau = _dev(pop.offsets), _dev(m), _dev(y), _dev(pop.tau)
+    v_in = v0.clone()
+    f_in = _dev(fl.astype(np.int32))
+    a_in = torch.empty(pop.n_cells, dtype=torch.float64, device="cuda")
+    api.fp_velocity_update(v_in, off, mom, yd, tau, f_in, 0.3, seed=11, step=2, alpha_out=a_in)
+    v_src, v_dst = v0.clone(), torch.full_like(v0, float("nan"))
+    f_out = _dev(fl.astype(np.int32))
+    a_out = torch.empty(pop.n_cells, dtype=torch.float64, device="cuda")
+    api.fp_velocity_update(v_src, off, mom, yd, tau, f_out, 0.3, seed=11, step=2, alpha_out=a_out, v_out=v_dst)
+    torch.cuda.synchronize()
+    assert torch.equal(v_dst, v_in)
+    assert torch.equal(v_src, v0)
+    assert torch.equal(f_out, f_in) and torch.equal(a_out, a_in)
