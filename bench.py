@@ -262,6 +262,9 @@ def run_ours(args):
         fns["gather64"] = lambda: api.fp_moments(v64, off, prec="fp64", moments_out=mom, stream=stream)
         fns["step"] = step
         c_exact()
+        xf, _ = sur.features(mom, tau, params=prm)
+        of = torch.empty((n_cells, 16), dtype=torch.float32, device=dev)
+        fns["mlp"] = lambda: sur.forward(xf, standardized=False, out=of, stream=stream)
         for _ in range(args.steps):
             fns[args.only]()
         torch.cuda.synchronize()
@@ -554,7 +557,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default=None,
                     choices=["gather", "gather64", "solve", "exact_closure", "surrogate_closure", "adjoint",
-                             "velocity_update", "step"],
+                             "velocity_update", "step", "mlp"],
                     help="profiling mode: launch one call --steps times, print no bench line")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -229,8 +229,9 @@ int fp_closure_backward(const void *v, int v_dtype, int64_t n_particles, const i
  * (outputs 9..15 unused); BF16 weights and activations, FP32 accumulation.
  * ------------------------------------------------------------------------- */
 typedef struct {
-  const void *W[5];             /* device, BF16 row-major [out][in]:
-                                   128x32, 128x128, 128x128, 128x128, 16x128 */
+  const void *W[5];             /* device, BF16 row-major [out][in], each
+                                   16-byte aligned: 128x32, 128x128,
+                                   128x128, 128x128, 16x128                  */
   const float *b[5];            /* device, FP32 [128] x 4, [16]              */
   const float *x_mu, *x_sigma;  /* device, FP32 [32] (padding: 0, 1)         */
   const float *y_mu, *y_sigma;  /* device, FP32 [16] (padding: 0, 1)         */

@@ -61,8 +61,10 @@ int check_net(const fp_mlp *net) {
   if (net->in_dim != 32 || net->hidden != 128 || net->depth != 4 || net->out_dim != 16)
     return fail(FP_ERR_UNSUPPORTED, "network shape %d-%dx%d-%d (32-128x4-16 supported)", net->in_dim, net->hidden,
                 net->depth, net->out_dim);
-  for (int l = 0; l < 5; ++l)
+  for (int l = 0; l < 5; ++l) {
     if (!net->W[l] || !net->b[l]) return fail(FP_ERR_ARG, "null weight or bias %d", l);
+    if ((uintptr_t)net->W[l] % 16) return fail(FP_ERR_ARG, "weight %d not 16-byte aligned", l);
+  }
   if (!net->x_mu || !net->x_sigma || !net->y_mu || !net->y_sigma || !net->x_min || !net->x_max)
     return fail(FP_ERR_ARG, "null scaler");
   return FP_OK;
@@ -259,8 +261,6 @@ int fp_mlp_forward(const fp_mlp *net, const void *x, int64_t n, int standardized
   if (n == 0) return FP_OK;
   if (!x || !out) return fail(FP_ERR_ARG, "null array pointer");
   if ((uintptr_t)x % 16 || (uintptr_t)out % 8) return fail(FP_ERR_ARG, "misaligned x or out");
-  for (int l = 0; l < 5; ++l)
-    if ((uintptr_t)net->W[l] % 4) return fail(FP_ERR_ARG, "weights not 4-byte aligned");
   if (fpc::launch_mlp_forward(*net, x, n, standardized_out, out, h_save, z_save, (cudaStream_t)stream))
     return fail(FP_ERR_CUDA, "could not raise the shared-memory limit of the MLP kernel");
   return check_launch("mlp_forward");

@@ -8,12 +8,14 @@
 // (tau C, tau sqrt(theta) G); the cubic-FP system of Eq. system9x9 is
 // invariant under c -> c/sqrt(theta), so those depend on the features alone.
 //
-// Fused forward: one CTA of 8 warps holds all five weight matrices in shared
+// Fused forward for training (the inference pass is the tcgen05 kernel of
+// mlp_tc.cu): one CTA of 8 warps holds all five weight matrices in shared
 // memory (~120 KB, loaded once) and streams 128-row tiles; each warp owns 16
 // rows for the whole network, so a layer's activations go from the FP32
 // accumulators through bias + SiLU to BF16 in the warp's own rows of the
-// activation tile and feed the next layer with no block barrier.  The MMAs
-// are mma.sync m16n8k16 (BF16 x BF16 -> FP32).
+// activation tile -- and, with the pre-activations, out to the buffers the
+// backward pass reads -- and feed the next layer with no block barrier.  The
+// MMAs are mma.sync m16n8k16 (BF16 x BF16 -> FP32).
 #include <cstdint>
 #include <cuda_bf16.h>
 
@@ -22,12 +24,6 @@
 #include "mlp_common.cuh"
 
 namespace fpc {
-
-struct MlpDev {
-  const __nv_bfloat16 *W[5];
-  const float *b[5];
-  const float *x_mu, *x_sigma, *y_mu, *y_sigma, *x_min, *x_max;
-};
 
 constexpr int kWS1 = kIn + 8;    // smem row stride (bf16) of W1
 constexpr int kWSH = kHid + 8;   // smem row stride of W2..W5 and of the activation tile
@@ -312,7 +308,10 @@ static int mlp_sm_count() {
   return n;
 }
 
-static int g_mlp_attr_done[64][2];
+static int g_mlp_attr_done[64];
+
+int launch_mlp_forward_tc(const MlpDev &net, const __nv_bfloat16 *x, int64_t n, int standardized_out, float *out,
+                          cudaStream_t st);
 
 MlpDev make_mlp_dev(const fp_mlp &m) {
   MlpDev d;
@@ -338,29 +337,25 @@ void launch_features(const fp_mlp &net, const double *mom, const double *tau, in
 
 int launch_mlp_forward(const fp_mlp &net, const void *x, int64_t n, int standardized_out, float *out, void *h_save,
                        float *z_save, cudaStream_t st) {
+  const MlpDev d = make_mlp_dev(net);
+  const __nv_bfloat16 *xb = reinterpret_cast<const __nv_bfloat16 *>(x);
+  // inference: the tcgen05 kernel; training (activations saved for the
+  // backward pass): the mma.sync kernel, whose warps own their rows end to end
+  if (h_save == nullptr || z_save == nullptr) return launch_mlp_forward_tc(d, xb, n, standardized_out, out, st);
   int dev = 0;
   cudaGetDevice(&dev);
-  const int save = (h_save != nullptr && z_save != nullptr) ? 1 : 0;
-  if (dev >= 0 && dev < 64 && !g_mlp_attr_done[dev][save]) {
-    cudaError_t e = save ? cudaFuncSetAttribute(mlp_forward_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)kMlpSmem)
-                         : cudaFuncSetAttribute(mlp_forward_kernel<false>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMlpSmem);
-    if (e != cudaSuccess) return -1;
-    g_mlp_attr_done[dev][save] = 1;
+  if (dev >= 0 && dev < 64 && !g_mlp_attr_done[dev]) {
+    if (cudaFuncSetAttribute(mlp_forward_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMlpSmem) !=
+        cudaSuccess)
+      return -1;
+    g_mlp_attr_done[dev] = 1;
   }
   const int64_t n_tiles = (n + kRows - 1) / kRows;
   int64_t grid = mlp_sm_count();
   if (grid > n_tiles) grid = n_tiles;
   if (grid < 1) grid = 1;
-  const MlpDev d = make_mlp_dev(net);
-  const __nv_bfloat16 *xb = reinterpret_cast<const __nv_bfloat16 *>(x);
-  if (save)
-    mlp_forward_kernel<true><<<(unsigned)grid, kMlpThreads, kMlpSmem, st>>>(
-        d, xb, n, standardized_out, out, reinterpret_cast<__nv_bfloat16 *>(h_save), z_save);
-  else
-    mlp_forward_kernel<false><<<(unsigned)grid, kMlpThreads, kMlpSmem, st>>>(d, xb, n, standardized_out, out,
-                                                                             nullptr, nullptr);
+  mlp_forward_kernel<true><<<(unsigned)grid, kMlpThreads, kMlpSmem, st>>>(
+      d, xb, n, standardized_out, out, reinterpret_cast<__nv_bfloat16 *>(h_save), z_save);
   return 0;
 }
 

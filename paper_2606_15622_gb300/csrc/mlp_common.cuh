@@ -10,6 +10,13 @@ namespace fpc {
 
 constexpr int kIn = 32, kHid = 128, kOut = 16, kDepth = 4, kNFeat = 25, kNOut = 9;
 
+// device pointers of the network (weights W[l] are [out][in] row-major)
+struct MlpDev {
+  const __nv_bfloat16 *W[5];
+  const float *b[5];
+  const float *x_mu, *x_sigma, *y_mu, *y_sigma, *x_min, *x_max;
+};
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x = lo (low half)
   return *reinterpret_cast<const uint32_t *>(&v);

@@ -1,0 +1,378 @@
+// mlp_tc.cu -- inference forward pass of the learned closure's network
+// (32 -> 4 x [128, SiLU] -> 16, BF16 operands, FP32 accumulation) on the
+// fifth-generation tensor cores of sm_103a.
+//
+// One persistent CTA per SM keeps all five weight matrices in shared memory.
+// Its two groups of eight warps each stream their own 128-row tiles; two
+// threads (warps w and w + 4 of the group, which share TMEM lanes 32 (w % 4)
+// ..) own each row and split every 32 columns.  Per tile and layer:
+//   - the layer's accumulators D[l] (128 x 128 FP32, tensor memory) are read
+//     32 columns at a time with tcgen05.ld; bias, SiLU (through tanh) and
+//     BF16 rounding turn them into 32 columns of the next layer's A operand
+//     in shared memory;
+//   - after each 32-column chunk the group's leader issues the next layer's
+//     tcgen05.mma instructions over those 32 K-columns (M = 128, K = 16 each,
+//     N = 128, or 16 for the output layer) into the other accumulator buffer
+//     D[l + 1], so the tensor cores work while the epilogue continues, and
+//     commits the layer to the group's mbarrier after the last chunk;
+//   - the input tile of the next tile is staged in its own buffer as soon as
+//     the first layer's MMAs have consumed the current one.
+// The output layer adds its bias, undoes the target standardisation if asked
+// and stores 16 FP32 per row.
+// Operands use the canonical K-major layout without swizzle: 8-row x 16-byte
+// "core matrices", adjacent along K at 128 bytes (leading byte offset) and
+// along M/N at K * 16 bytes (stride byte offset); enumerating (8-row group,
+// K-chunk, row) makes that layout linear, so the staging copies (cp.async,
+// all in flight at once) write contiguous shared memory.
+// Only the group's leader waits on the mbarrier, with a bound, and passes its
+// verdict to the group through shared memory at the next group barrier; a
+// wait that runs out writes NaN outputs for the group's tile (the surrogate
+// epilogue then sends those cells to the exact closure), and the CTA frees
+// its tensor memory before returning.
+#include <cstdint>
+#include <cuda_bf16.h>
+
+#include "fp_device.cuh"
+#include "mlp_common.cuh"
+#include "tma.cuh"
+
+namespace fpc {
+
+namespace {
+
+constexpr int kTcRows = 128;                 // rows per tile = TMEM lanes
+constexpr int kTcGroups = 2;                 // tiles in flight per CTA
+constexpr int kTcGroupThreads = 256;         // two threads per row: 16 of every 32 columns each
+constexpr int kTcThreads = kTcGroupThreads * kTcGroups;
+constexpr uint32_t kTmemCols = 512;          // two 128-column accumulators per group
+
+// shared-memory carve-up (bytes from a 1024-byte aligned base)
+constexpr uint32_t kOffW1 = 0;                                 // [128][32]  8 KB
+constexpr uint32_t kOffWH = kOffW1 + kHid * kIn * 2;           // 3 x [128][128]
+constexpr uint32_t kOffW5 = kOffWH + 3 * kHid * kHid * 2;      // [16][128]
+constexpr uint32_t kOffA = kOffW5 + kOut * kHid * 2;           // 2 x [128][128] activations
+constexpr uint32_t kOffX = kOffA + kTcGroups * kTcRows * kHid * 2;  // 2 x [128][32] input tiles
+constexpr uint32_t kOffBias = kOffX + kTcGroups * kTcRows * kIn * 2;
+constexpr uint32_t kNBias = 4 * kHid + 3 * kOut;               // b1..b4 / 2, b5, y_mu, y_sigma
+constexpr uint32_t kOffBar = kOffBias + kNBias * 4;            // 2 mbarriers
+constexpr uint32_t kOffTmemSlot = kOffBar + 8 * kTcGroups;
+constexpr uint32_t kTcSmemUsed = kOffTmemSlot + 16;  // TMEM address + two verdicts
+constexpr size_t kTcSmem = kTcSmemUsed + 1024;                 // room to align the base
+static_assert(kOffBar % 8 == 0, "mbarrier alignment");
+static_assert(kTcSmem <= 227 * 1024, "shared memory");
+
+// byte offset of the 16-byte chunk (row r, k-chunk c) of a K-major operand
+// with K columns, in the no-swizzle core-matrix layout
+__device__ __forceinline__ uint32_t cm_off(int r, int c, int K) {
+  return (uint32_t)((r >> 3) * (K * 16) + c * 128 + (r & 7) * 16);
+}
+
+// shared-memory matrix descriptor (no swizzle): start address, leading byte
+// offset (K direction), stride byte offset (M/N direction), descriptor
+// version 1 at bit 46
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: D = FP32 (bit 4), A = B = BF16
+// (bits 7, 10), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.  The load is
+// asynchronous: tc_wait16 completes it and names the registers as operands,
+// so the compiler cannot read them before the wait.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tc_wait16(uint32_t (&r)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15])
+               :
+               : "memory");
+}
+
+__device__ __forceinline__ void group_sync(int g) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kTcGroupThreads) : "memory");
+}
+
+// Spin on the group's mbarrier (MMAs finish within microseconds, so no
+// sleeping back-off at first); false after ~2 s.
+__device__ __forceinline__ bool mma_wait(uint64_t *bar, uint32_t parity) {
+#pragma unroll 1
+  for (int i = 0; i < 4096; ++i)
+    if (mbar_test_wait(bar, parity)) return true;
+  return mbar_wait_bounded(bar, parity);
+}
+
+// SiLU(z) = z sigma(z) with sigma(z) = (1 + tanh(z / 2)) / 2: one hardware
+// tanh (relative error about 2^-11, below the 2^-9 of the BF16 rounding
+// that follows) instead of an exponential and a reciprocal.  Called with
+// the accumulator a and the halved bias hb: z / 2 = a / 2 + hb.
+__device__ __forceinline__ float silu_tanh(float a, float hb) {
+  const float hz = fmaf(a, 0.5f, hb);
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(hz));
+  return fmaf(hz, t, hz);
+}
+
+// bias + SiLU of 16 accumulators (columns 16 h16 .. 16 h16 + 15) -> two
+// 16-byte chunks of BF16 in the next layer's A operand (row `row`)
+__device__ __forceinline__ void epilogue16(const uint32_t (&r)[16], const float *__restrict__ hb, unsigned char *A,
+                                           int row, int h16) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const float4 b0 = *reinterpret_cast<const float4 *>(hb + h16 * 16 + q * 8);
+    const float4 b1 = *reinterpret_cast<const float4 *>(hb + h16 * 16 + q * 8 + 4);
+    const float bq[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+    uint32_t pk[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      pk[e] = pack_bf16(silu_tanh(__uint_as_float(r[q * 8 + 2 * e]), bq[2 * e]),
+                        silu_tanh(__uint_as_float(r[q * 8 + 2 * e + 1]), bq[2 * e + 1]));
+    *reinterpret_cast<uint4 *>(A + cm_off(row, h16 * 2 + q, kHid)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+  }
+}
+
+// Asynchronous copy of rows [0, N) of a row-major [N][K] BF16 matrix into the
+// core-matrix layout (cp.async, 16 bytes per copy, all in flight at once);
+// chunk i = (8-row group, K-chunk, row in group) lands at byte 16 i.  Rows
+// at or beyond `valid` are zero-filled (source size 0).  Complete with
+// cp_async_wait().
+__device__ __forceinline__ void stage_rows_async(unsigned char *dst, const __nv_bfloat16 *__restrict__ src, int N,
+                                                 int K, int64_t valid, int t0, int nt) {
+  const int chunks = N * K / 8;
+  for (int i = t0; i < chunks; i += nt) {
+    const int rg = i / K, c = (i >> 3) % (K / 8), r = rg * 8 + (i & 7);
+    const bool ok = r < valid;
+    const __nv_bfloat16 *g = ok ? src + (int64_t)r * K + c * 8 : src;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst + 16 * i)), "l"(g),
+                 "r"(ok ? 16 : 0)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+}  // namespace
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    mlp_forward_tc_kernel(MlpDev net, const __nv_bfloat16 *__restrict__ x, int64_t n, int standardized_out,
+                          float *__restrict__ out) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  float *bias = reinterpret_cast<float *>(sm + kOffBias);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kOffBar);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + kOffTmemSlot);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = warp >> 3;                      // group
+  const int half = (warp >> 2) & 1;             // which 16 of every 32 columns
+  const int row = (warp & 3) * 32 + lane;       // = TMEM lane (warps may use lanes 32 (warp % 4) ..)
+
+  // ---- one-time setup: weights, biases, barriers, tensor memory ----
+  stage_rows_async(sm + kOffW1, net.W[0], kHid, kIn, kHid, tid, kTcThreads);
+  for (int l = 0; l < 3; ++l)
+    stage_rows_async(sm + kOffWH + l * kHid * kHid * 2, net.W[1 + l], kHid, kHid, kHid, tid, kTcThreads);
+  stage_rows_async(sm + kOffW5, net.W[4], kOut, kHid, kOut, tid, kTcThreads);
+  for (int i = tid; i < (int)kNBias; i += blockDim.x) {
+    float b;
+    if (i < 4 * kHid)
+      b = 0.5f * net.b[i / kHid][i % kHid];  // hidden biases halved (see silu_tanh)
+    else if (i < 4 * kHid + kOut)
+      b = net.b[4][i - 4 * kHid];
+    else if (i < 4 * kHid + 2 * kOut)
+      b = net.y_mu[i - 4 * kHid - kOut];
+    else
+      b = net.y_sigma[i - 4 * kHid - 2 * kOut];
+    bias[i] = b;
+  }
+  if (tid == 0) {
+    for (int q = 0; q < kTcGroups; ++q) mbar_init(&bar[q], 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  cp_async_wait();
+  fence_proxy_async_smem();  // weights written through the generic proxy, read by the MMA
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot + (uint32_t)(g * 2 * kHid);  // the group's two accumulators
+  const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;   // this warp's TMEM lanes
+
+  unsigned char *A = sm + kOffA + g * (kTcRows * kHid * 2);
+  unsigned char *X = sm + kOffX + g * (kTcRows * kIn * 2);
+  const uint32_t a_addr = smem_u32(A), x_addr = smem_u32(X);
+  const uint32_t w1_addr = smem_u32(sm + kOffW1), wh_addr = smem_u32(sm + kOffWH), w5_addr = smem_u32(sm + kOffW5);
+  const int gt = tid & (kTcGroupThreads - 1);  // thread index within the group
+  const bool leader = gt == 0;
+  volatile uint32_t *group_ok = tmem_slot + 1 + g;  // the leader's verdict on the last wait
+  uint32_t phase = 0;
+  bool failed = false;
+  const int64_t n_tiles = (n + kTcRows - 1) / kTcRows;
+  const int64_t tile_step = (int64_t)gridDim.x * kTcGroups;
+  int64_t tile = (int64_t)blockIdx.x * kTcGroups + g;
+  if (tile < n_tiles)
+    stage_rows_async(X, x + tile * kTcRows * kIn, kTcRows, kIn, n - tile * kTcRows, gt, kTcGroupThreads);
+
+  // the leader waits for the group's last commit; the group learns the verdict
+  auto wait_layer = [&]() -> bool {
+    if (leader) *group_ok = mma_wait(&bar[g], phase) ? 1u : 0u;
+    phase ^= 1u;
+    group_sync(g);
+    tc_fence_after();
+    return *group_ok != 0u;
+  };
+
+  for (; tile < n_tiles && !failed; tile += tile_step) {
+    const int64_t row0 = tile * kTcRows;
+    // layer 1: D[0] = X W1^T
+    cp_async_wait();  // this thread's part of the input tile has landed
+    fence_proxy_async_smem();
+    tc_fence_before();
+    group_sync(g);
+    if (leader) {
+      tc_fence_after();
+      for (int s = 0; s < kIn / 16; ++s)
+        tc_mma(tmem, smem_desc(x_addr + 256 * s, 128, kIn * 16), smem_desc(w1_addr + 256 * s, 128, kIn * 16),
+               idesc_bf16(kTcRows, kHid), s > 0 ? 1u : 0u);
+      tc_commit(&bar[g]);
+    }
+    // hidden layers l = 0..3: epilogue of D[l & 1], MMAs of layer l + 1
+#pragma unroll 1
+    for (int l = 0; l < 4; ++l) {
+      if (!wait_layer()) {
+        failed = true;
+        break;
+      }
+      if (l == 0 && tile + tile_step < n_tiles)  // X is free: stage the next input tile
+        stage_rows_async(X, x + (tile + tile_step) * kTcRows * kIn, kTcRows, kIn, n - (tile + tile_step) * kTcRows,
+                         gt, kTcGroupThreads);
+      const uint32_t d_in = tmem + (uint32_t)((l & 1) * kHid), d_out = tmem + (uint32_t)(((l + 1) & 1) * kHid);
+      const int n_next = l == 3 ? kOut : kHid;
+      const uint32_t w_next = l == 3 ? w5_addr : wh_addr + (uint32_t)(l * kHid * kHid * 2);
+      const float *hb = bias + l * kHid;
+      // TMEM loads run one chunk ahead of the arithmetic (two register sets)
+      uint32_t ra[16], rb[16];
+      tc_ld16(d_in + lane_off + (uint32_t)(half * 16), ra);
+      tc_wait16(ra);
+#pragma unroll
+      for (int c32 = 0; c32 < kHid / 32; ++c32) {
+        uint32_t(&cur)[16] = (c32 & 1) ? rb : ra;
+        uint32_t(&nxt)[16] = (c32 & 1) ? ra : rb;
+        if (c32 + 1 < kHid / 32) tc_ld16(d_in + lane_off + (uint32_t)((c32 + 1) * 32 + half * 16), nxt);
+        epilogue16(cur, hb, A, row, c32 * 2 + half);
+        if (c32 & 1) {
+          // these 64 columns are the next layer's K-steps 2 c32 - 2 .. 2 c32 + 1
+          fence_proxy_async_smem();
+          tc_fence_before();
+          group_sync(g);
+          if (leader) {
+            tc_fence_after();
+            for (int s = 2 * c32 - 2; s < 2 * c32 + 2; ++s)
+              tc_mma(d_out, smem_desc(a_addr + 256 * s, 128, kHid * 16),
+                     smem_desc(w_next + 256 * s, 128, kHid * 16), idesc_bf16(kTcRows, n_next), s > 0 ? 1u : 0u);
+            if (c32 == kHid / 32 - 1) tc_commit(&bar[g]);
+          }
+        }
+        if (c32 + 1 < kHid / 32) tc_wait16(nxt);
+      }
+    }
+    // output layer: D[0] columns 0..15
+    if (!failed && !wait_layer()) failed = true;
+    if (!failed && half == 0) {
+      uint32_t r16[16];
+      tc_ld16(tmem + lane_off, r16);
+      tc_wait16(r16);
+      float v[16];
+      const float *b5 = bias + 4 * kHid, *ymu = b5 + kOut, *ysg = ymu + kOut;
+#pragma unroll
+      for (int j = 0; j < kOut; ++j) {
+        v[j] = __uint_as_float(r16[j]) + b5[j];
+        if (!standardized_out) v[j] = fmaf(v[j], ysg[j], ymu[j]);
+      }
+      if (row0 + row < n) {
+        float2 *o = reinterpret_cast<float2 *>(out + (row0 + row) * kOut);
+#pragma unroll
+        for (int q = 0; q < kOut / 2; ++q) o[q] = make_float2(v[2 * q], v[2 * q + 1]);
+      }
+    } else if (failed && half == 0 && row0 + row < n) {
+      float2 *o = reinterpret_cast<float2 *>(out + (row0 + row) * kOut);
+      const float nan = __int_as_float(0x7fc00000);
+#pragma unroll
+      for (int q = 0; q < kOut / 2; ++q) o[q] = make_float2(nan, nan);
+    }
+  }
+  // ---- teardown: every tcgen05 operation of this CTA has completed ----
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tmem_slot), "r"(kTmemCols)
+                 : "memory");
+}
+
+static int g_tc_attr_done[64];
+
+static int tc_sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 152;
+  }
+  return n;
+}
+
+// Returns -1 if the shared-memory limit could not be raised.
+int launch_mlp_forward_tc(const MlpDev &net, const __nv_bfloat16 *x, int64_t n, int standardized_out, float *out,
+                          cudaStream_t st) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !g_tc_attr_done[dev]) {
+    if (cudaFuncSetAttribute(mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem) !=
+        cudaSuccess)
+      return -1;
+    g_tc_attr_done[dev] = 1;
+  }
+  const int64_t n_tiles = (n + kTcRows - 1) / kTcRows;
+  int64_t grid = (n_tiles + kTcGroups - 1) / kTcGroups;
+  if (grid > tc_sm_count()) grid = tc_sm_count();
+  if (grid < 1) grid = 1;
+  mlp_forward_tc_kernel<<<(unsigned)grid, kTcThreads, kTcSmem, st>>>(net, x, n, standardized_out, out);
+  return 0;
+}
+
+}  // namespace fpc

@@ -45,6 +45,24 @@ def test_forward_matches_reference(n):
     assert err.mean() <= 3e-3 * np.abs(ref).mean()
 
 
+@pytest.mark.parametrize("n", [1, 128, 129, 255, 256, 40000])
+def test_tensor_core_inference_matches_training_forward(n):
+    """The inference pass (tcgen05, accumulators in tensor memory) and the
+    training pass (mma.sync) round at the same points; they differ only by
+    FP32 accumulation order.  Sizes cover one row, exact and ragged 128-row
+    tiles, both groups of a CTA and many tiles per CTA."""
+    s, prm = _surrogate_with_random_params(seed=8)
+    x = torch.from_numpy(_inputs(n, 100 + n)).cuda().to(torch.bfloat16)
+    o_tc = s.forward(x, standardized=True)
+    o_mma = s.forward(x, standardized=True, save=True)[0]
+    torch.cuda.synchronize()
+    a, b = o_tc.cpu().numpy(), o_mma.cpu().numpy()
+    assert np.isfinite(a).all()
+    err = np.abs(a - b)
+    assert err.max() <= 2e-2 * np.abs(b).max()
+    assert err.mean() <= 3e-3 * np.abs(b).mean()
+
+
 def test_forward_saves_activations_and_unstandardizes():
     s, prm = _surrogate_with_random_params()
     s.y_mu[:9] = torch.linspace(-1, 1, 9, device="cuda")
@@ -52,9 +70,14 @@ def test_forward_saves_activations_and_unstandardizes():
     s._net = None
     x = torch.from_numpy(_inputs(300, 1)).cuda().to(torch.bfloat16)
     o_std, h, z = s.forward(x, standardized=True, save=True)
+    o_raw_t = s.forward(x, standardized=False, save=True)[0]
+    o_inf = s.forward(x, standardized=True)
     o_raw = s.forward(x, standardized=False)
     torch.cuda.synchronize()
-    np.testing.assert_allclose((o_std * s.y_sigma + s.y_mu).cpu().numpy()[:, :9], o_raw.cpu().numpy()[:, :9],
+    # each kernel undoes the standardisation of its own output exactly
+    np.testing.assert_allclose((o_std * s.y_sigma + s.y_mu).cpu().numpy()[:, :9], o_raw_t.cpu().numpy()[:, :9],
+                               rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose((o_inf * s.y_sigma + s.y_mu).cpu().numpy()[:, :9], o_raw.cpu().numpy()[:, :9],
                                rtol=1e-6, atol=1e-6)
     # saved activations are SiLU of the saved pre-activations, rounded to BF16
     np.testing.assert_allclose(h.float().cpu().numpy(), M.bf16_round(M.silu(z.cpu().numpy())), rtol=1e-2, atol=1e-3)
