@@ -341,6 +341,68 @@ int fp_closure_exact_static(const void *v, int v_dtype, int64_t n_particles, con
                             int32_t *flags_out, fp_stream_t stream);
 const char *fp_closure_exact_static_error(void);
 
+/* ------------------------------------------------------------------------
+ * Host-resident step (a runtime layer; the paper has no counterpart).
+ *
+ * fp_step_host runs one step of the hot path -- the exact closure (gather +
+ * solve), optionally the learned closure and the adjoint, and the velocity
+ * update -- for velocities held in HOST memory, and returns the coefficients,
+ * flags and updated velocities to host memory.  The cells are split into
+ * n_chunks contiguous chunks; each chunk's host -> device copies, compute and
+ * device -> host copies run on separate streams of the pipeline, so the
+ * copies of one chunk overlap the compute of its neighbours.  The results
+ * equal those of the separate calls on the whole population (the Philox
+ * counter of a particle is its global index).  Host buffers must be
+ * page-locked for the copies to overlap.  Device buffers are caller-owned and
+ * full size; the call allocates nothing.  The call is ordered after work
+ * already queued on `stream`, and `stream` waits for all of its work; it
+ * returns once everything is queued.
+ * ------------------------------------------------------------------------ */
+typedef struct fp_pipeline fp_pipeline;  /* streams and events of the pipeline */
+
+/* Creates the pipeline's streams (one at the highest priority) and events.
+ * FP_ERR_CUDA if they cannot be created; *out is NULL then. */
+int fp_pipeline_create(fp_pipeline **out);
+/* Waits for the pipeline's streams and releases them. NULL is ignored. */
+void fp_pipeline_destroy(fp_pipeline *pl);
+
+typedef struct {
+  /* host */
+  const void *h_v;          /* [3][n_particles] velocities M^n (v_dtype)        */
+  void *h_v_out;            /* [3][n_particles] receives M^{n+1}                */
+  const int64_t *h_offsets; /* [n_cells + 1], 0 .. n_particles                  */
+  const double *h_tau;      /* [n_cells]                                        */
+  double *h_coeffs;         /* [n_cells][9] receives the exact closure          */
+  int32_t *h_flags;         /* [n_cells] receives the flags after the update    */
+  /* device, full size */
+  void *d_v, *d_v_out;      /* [3][n_particles] each; distinct                  */
+  int64_t *d_offsets;       /* [n_cells + 1]                                    */
+  double *d_tau;            /* [n_cells]                                        */
+  double *d_moments;        /* [n_cells][FP_NMOM]                               */
+  double *d_coeffs;         /* [n_cells][9]                                     */
+  int32_t *d_flags;         /* [n_cells] closure flags                          */
+  int32_t *d_flags_v;       /* [n_cells] the update's flags (closure flags plus
+                               FP_FLAG_ALPHA), copied to h_flags                */
+  /* learned closure with exact fallback: skipped if net is NULL */
+  const fp_mlp *net;
+  double *d_coeffs_s;       /* [n_cells][9]                                     */
+  int32_t *d_flags_s;       /* [n_cells]                                        */
+  void *d_surrogate_ws;     /* fp_surrogate_workspace_bytes(n_cells) bytes      */
+  size_t surrogate_ws_bytes;
+  /* adjoint: skipped if d_grad_coeffs is NULL */
+  const double *d_grad_coeffs; /* [n_cells][9] dL/dY                            */
+  double *d_grad_moments;      /* [n_cells][FP_NMOM] receives dL/dm             */
+  void *d_grad_v;              /* [3][n_particles] receives dL/dv, or NULL      */
+} fp_step_io;
+
+/* n_chunks in [1, 64] (clamped to n_cells); dt, seed, step as for
+ * fp_velocity_update (Philox noise), p and prec as for fp_closure_exact.
+ * FP_ERR_ARG for null buffers, d_v_out == d_v, offsets not running from 0 to
+ * n_particles; otherwise the first error of a chunk's call. */
+int fp_step_host(fp_pipeline *pl, const fp_step_io *io, int v_dtype, int64_t n_particles, int64_t n_cells,
+                 const fp_params *p, int prec, double dt, uint64_t seed, uint64_t step, int n_chunks,
+                 fp_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

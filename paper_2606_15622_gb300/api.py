@@ -52,8 +52,24 @@ _LIB = None
 _LOCK = threading.Lock()
 _vp, _i64, _i32, _sz, _dbl, _u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t, ctypes.c_double, ctypes.c_uint64
 
+
+class StepIO(ctypes.Structure):
+    """fp_step_io of fpclosure.h (host and device pointers)."""
+    _fields_ = [("h_v", _vp), ("h_v_out", _vp), ("h_offsets", _vp), ("h_tau", _vp), ("h_coeffs", _vp),
+                ("h_flags", _vp),
+                ("d_v", _vp), ("d_v_out", _vp), ("d_offsets", _vp), ("d_tau", _vp), ("d_moments", _vp),
+                ("d_coeffs", _vp), ("d_flags", _vp), ("d_flags_v", _vp),
+                ("net", ctypes.POINTER(FpMlp)), ("d_coeffs_s", _vp), ("d_flags_s", _vp), ("d_surrogate_ws", _vp),
+                ("surrogate_ws_bytes", _sz),
+                ("d_grad_coeffs", _vp), ("d_grad_moments", _vp), ("d_grad_v", _vp)]
+
+
 # name -> (restype, argtypes); the exported surface of include/fpclosure.h
 SIGNATURES = {
+    "fp_pipeline_create": (_i32, [ctypes.POINTER(_vp)]),
+    "fp_pipeline_destroy": (None, [_vp]),
+    "fp_step_host": (_i32, [_vp, ctypes.POINTER(StepIO), _i32, _i64, _i64, ctypes.POINTER(Params), _i32, _dbl,
+                            _u64, _u64, _i32, _vp]),
     "fp_default_params": (None, [ctypes.POINTER(Params)]),
     "fp_status_string": (ctypes.c_char_p, [_i32]),
     "fp_last_error": (ctypes.c_char_p, []),
@@ -136,6 +152,87 @@ def fp_closure_backward(v, offsets, tau, moments, coeffs, flags, grad_coeffs, gr
                                    ws_bytes, _stream(stream))
     _check(rc, "fp_closure_backward")
     return grad_moments, grad_v
+
+
+class HostStep:
+    """One step of the hot path on velocities in host memory (fp_step_host):
+    exact closure, optionally the learned closure and the adjoint, and the
+    velocity update, with the host <-> device copies of each chunk of cells
+    overlapped with the compute of the others.  Owns the full-size device
+    buffers and the pipeline's streams; host tensors should be pinned.
+
+        hs = HostStep(n_cells, n_particles, surrogate=s, adjoint=True)
+        hs(h_v, h_offsets, h_tau, h_v_out, h_coeffs, h_flags, dt=0.1, seed=1, step=n)
+    """
+
+    def __init__(self, n_cells, n_particles, dtype=torch.float32, surrogate=None, adjoint=False, device=None):
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.n_cells, self.n_particles, self.dtype, self.device = n_cells, n_particles, dtype, dev
+        f64 = dict(dtype=torch.float64, device=dev)
+        self.d_v = torch.empty((3, n_particles), dtype=dtype, device=dev)
+        self.d_v_out = torch.empty_like(self.d_v)
+        self.d_offsets = torch.empty(n_cells + 1, dtype=torch.int64, device=dev)
+        self.d_tau = torch.empty(n_cells, **f64)
+        self.moments = torch.empty((n_cells, NMOM), **f64)
+        self.coeffs = torch.empty((n_cells, NCOEF), **f64)
+        self.flags = torch.empty(n_cells, dtype=torch.int32, device=dev)
+        self.flags_v = torch.empty_like(self.flags)
+        self.surrogate = surrogate
+        if surrogate is not None:
+            self.coeffs_s = torch.empty_like(self.coeffs)
+            self.flags_s = torch.empty_like(self.flags)
+            self.surrogate_ws = torch.empty(int(lib().fp_surrogate_workspace_bytes(n_cells)), dtype=torch.uint8,
+                                            device=dev)
+        self.adjoint = adjoint
+        if adjoint:
+            self.grad_coeffs = torch.ones((n_cells, NCOEF), **f64)
+            self.grad_moments = torch.empty_like(self.moments)
+            self.grad_v = torch.empty_like(self.d_v)
+        h = _vp()
+        _check(lib().fp_pipeline_create(ctypes.byref(h)), "fp_pipeline_create")
+        self._pl = h
+
+    def __call__(self, h_v, h_offsets, h_tau, h_v_out, h_coeffs, h_flags, dt, params: Params | None = None,
+                 prec="fp32", seed=0, step=0, n_chunks=8, stream=None):
+        for t in (h_v, h_offsets, h_tau, h_v_out, h_coeffs, h_flags):
+            if t.is_cuda or not t.is_contiguous():
+                raise FPError("fp_step_host takes contiguous host tensors")
+        if h_v.dtype != self.dtype or h_v_out.dtype != self.dtype:
+            raise FPError("host velocities must have the pipeline's dtype")
+        io = StepIO()
+        io.h_v, io.h_v_out = h_v.data_ptr(), h_v_out.data_ptr()
+        io.h_offsets, io.h_tau = h_offsets.data_ptr(), h_tau.data_ptr()
+        io.h_coeffs, io.h_flags = h_coeffs.data_ptr(), h_flags.data_ptr()
+        io.d_v, io.d_v_out = self.d_v.data_ptr(), self.d_v_out.data_ptr()
+        io.d_offsets, io.d_tau = self.d_offsets.data_ptr(), self.d_tau.data_ptr()
+        io.d_moments, io.d_coeffs = self.moments.data_ptr(), self.coeffs.data_ptr()
+        io.d_flags, io.d_flags_v = self.flags.data_ptr(), self.flags_v.data_ptr()
+        net = None
+        if self.surrogate is not None:
+            net = self.surrogate.net()
+            io.net = ctypes.pointer(net)
+            io.d_coeffs_s, io.d_flags_s = self.coeffs_s.data_ptr(), self.flags_s.data_ptr()
+            io.d_surrogate_ws, io.surrogate_ws_bytes = self.surrogate_ws.data_ptr(), self.surrogate_ws.numel()
+        if self.adjoint:
+            io.d_grad_coeffs, io.d_grad_moments = self.grad_coeffs.data_ptr(), self.grad_moments.data_ptr()
+            io.d_grad_v = self.grad_v.data_ptr()
+        p = params if params is not None else default_params()
+        rc = lib().fp_step_host(self._pl, ctypes.byref(io), _vdtype(self.d_v), self.n_particles, self.n_cells,
+                                ctypes.byref(p), _PREC.get(prec, prec), float(dt), int(seed), int(step),
+                                int(n_chunks), _stream(stream))
+        _check(rc, "fp_step_host")
+        return h_v_out, h_coeffs, h_flags
+
+    def close(self):
+        if getattr(self, "_pl", None):
+            lib().fp_pipeline_destroy(self._pl)
+            self._pl = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def library_path() -> str:

@@ -80,6 +80,11 @@ size_t surrogate_ws_parts(int64_t n, size_t *off_t, size_t *off_list, size_t *of
 }
 }  // namespace
 
+namespace fpc {
+// error reporting for the other translation units of the C ABI
+int report(int code, const char *msg) { return fail(code, "%s", msg); }
+}  // namespace fpc
+
 extern "C" {
 
 void fp_default_params(fp_params *p) {
