@@ -163,6 +163,7 @@ def run_ours(args):
     flags_s = torch.empty_like(flags)
     gY = torch.ones((n_cells, 9), dtype=torch.float64, device=dev)
     gmom = torch.empty_like(mom)
+    lu = torch.empty(api.lu_doubles(n_cells), dtype=torch.float64, device=dev)  # factors kept for the adjoint
     gv = torch.empty_like(v0)
     alpha = torch.empty(n_cells, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -178,15 +179,19 @@ def run_ours(args):
     s_ws = torch.empty(int(api.lib().fp_surrogate_workspace_bytes(n_cells)), dtype=torch.uint8, device=dev)
     step_idx = [0]
 
-    def c_exact():
-        api.fp_closure_exact(vb[cur[0]], off, tau, params=prm, prec="fp32", moments_out=mom, coeffs_out=coeffs,
-                             flags_out=flags, stream=stream)
-
     def c_moments():
         api.fp_moments(vb[cur[0]], off, prec="fp32", moments_out=mom, stream=stream)
 
     def c_solve():
-        api.fp_closure_solve(mom, tau, params=prm, prec="fp32", coeffs_out=coeffs, flags_out=flags, stream=stream)
+        # keeps its factors for the adjoint (fp_closure_backward(lu=...))
+        api.fp_closure_solve(mom, tau, params=prm, prec="fp32", coeffs_out=coeffs, flags_out=flags, stream=stream,
+                             lu_out=lu)
+
+    def c_exact():
+        # the exact closure as the step runs it: gather, then the solve that
+        # also keeps its factors for the adjoint
+        c_moments()
+        c_solve()
 
     def c_surrogate(on=None):
         sur.closure(mom, tau, params=prm, prec="fp32", coeffs_out=coeffs_s, flags_out=flags_s, workspace=s_ws,
@@ -194,7 +199,7 @@ def run_ours(args):
 
     def c_adjoint():
         api.fp_closure_backward(vb[cur[0]], off, tau, mom, coeffs, flags, gY, params=prm, grad_moments=gmom,
-                                grad_v=gv, stream=stream)
+                                grad_v=gv, stream=stream, lu=lu)
 
     def c_velocity(on=None):
         # M^n -> M^{n+1} out of place: the adjoint still reads M^n meanwhile

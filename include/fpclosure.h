@@ -51,6 +51,8 @@ extern "C" {
 typedef struct CUstream_st *fp_stream_t; /* same type as cudaStream_t */
 
 #define FP_NMOM 30
+#define FP_LU_STRIDE 82  /* entries per cell of stored factors (fp_closure_solve) */
+#define FP_LU_DOUBLES(n) ((((n) + 31) / 32) * 32 * FP_LU_STRIDE) /* buffer size, doubles */
 #define FP_NCOEF 9
 
 /* return codes */
@@ -143,9 +145,16 @@ int fp_moments(const void *v, int v_dtype, int64_t n_particles, const int64_t *c
  * the FP64 pivoted solve, one thread per cell.  moments [n_cells][FP_NMOM]
  * f64 (as fp_moments writes them), tau [n_cells]; prec = the precision the
  * moments were gathered in (selects the singularity threshold); outputs as
- * in fp_closure_exact.  No workspace. */
+ * in fp_closure_exact.  lu_out: FP_LU_DOUBLES(n_cells) f64 or NULL; if
+ * given, every unflagged cell's factors P A = L U of the elimination are
+ * stored there for fp_closure_backward: FP_LU_STRIDE entries per cell (the
+ * row-major 9 x 9 with L below the diagonal, the reciprocal pivots on it and
+ * U above it, then the row swaps, 4 bits per step, in the bits of a double),
+ * tiled by 32 cells so a warp's accesses coalesce: entry k of cell c (counted
+ * from the call's first cell) at lu_out[(c / 32) * 32 * FP_LU_STRIDE + 32 k +
+ * c % 32].  Entries of flagged cells are left as they were.  No workspace. */
 int fp_closure_solve(const double *moments, const double *tau, int64_t n_cells, const fp_params *p, int prec,
-                     double *coeffs_out, int32_t *flags_out, fp_stream_t stream);
+                     double *coeffs_out, int32_t *flags_out, double *lu_out, fp_stream_t stream);
 
 /* fp_velocity_update: one collision step of the particle velocities with the
  * mixed Ornstein-Uhlenbeck / Euler scheme (paper Sec. 3.9-3.10):
@@ -186,8 +195,9 @@ int fp_velocity_update(void *v, void *v_out, int v_dtype, int64_t n_particles, c
 /* fp_closure_backward: the adjoint of fp_closure_exact (not in the paper; the
  * closure of Eq. system9x9 differentiated as an implicit function).  With
  * F(m, Y) = A(m) Y - r(m) = 0 and a loss gradient gY = dL/dY per cell:
- *   lambda = A^-T gY                    (pivoted elimination of A^T, the
- *                                        factors recomputed per cell)
+ *   lambda = A^-T gY                    (two triangular solves with the
+ *                                        forward's factors when lu is given,
+ *                                        else a pivoted elimination of A^T)
  *   grad_moments = -(dF/dm)^T lambda + grad_moments_in
  *   grad_v[p] = (1/N) sum_k grad_moments_k (grad psi_k(c_p) - <grad psi_k>)
  *               + grad_moments_U / N    (c_p = v_p - U, m_k = <psi_k(c)>)
@@ -196,6 +206,9 @@ int fp_velocity_update(void *v, void *v_out, int v_dtype, int64_t n_particles, c
  *   v, cell_offsets, tau  as in fp_closure_exact (v only read when grad_v)
  *   p                     eps2_hat is read (NULL = defaults)
  *   moments, coeffs, flags  the forward outputs for the same v
+ *   lu                    FP_LU_DOUBLES(n_cells) from fp_closure_solve for
+ *                         the same moments and first cell, or NULL
+ *                         (recomputed)
  *   grad_coeffs           [n_cells][9]
  *   grad_moments_in       [n_cells][FP_NMOM] or NULL (= 0)
  *   grad_moments          [n_cells][FP_NMOM] out, or NULL (then kept in ws)
@@ -208,7 +221,7 @@ int fp_velocity_update(void *v, void *v_out, int v_dtype, int64_t n_particles, c
  * constant linear drift: their coefficient gradient contributes nothing. */
 int fp_closure_backward(const void *v, int v_dtype, int64_t n_particles, const int64_t *cell_offsets,
                         int64_t n_cells, const double *tau, const fp_params *p, const double *moments,
-                        const double *coeffs, const int32_t *flags, const double *grad_coeffs,
+                        const double *coeffs, const int32_t *flags, const double *lu, const double *grad_coeffs,
                         const double *grad_moments_in, double *grad_moments, void *grad_v, void *ws,
                         size_t ws_bytes, fp_stream_t stream);
 
@@ -390,6 +403,9 @@ typedef struct {
   void *d_surrogate_ws;     /* fp_surrogate_workspace_bytes(n_cells) bytes      */
   size_t surrogate_ws_bytes;
   /* adjoint: skipped if d_grad_coeffs is NULL */
+  double *d_lu;                /* FP_LU_DOUBLES(n_cells): factors kept by the
+                                  solve for the adjoint, or NULL (recomputed);
+                                  chunks start on multiples of 32 cells      */
   const double *d_grad_coeffs; /* [n_cells][9] dL/dY                            */
   double *d_grad_moments;      /* [n_cells][FP_NMOM] receives dL/dm             */
   void *d_grad_v;              /* [3][n_particles] receives dL/dv, or NULL      */

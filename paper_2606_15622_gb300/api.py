@@ -18,6 +18,12 @@ from . import build as _build
 
 NMOM = 30
 NCOEF = 9
+LU_STRIDE = 82
+
+
+def lu_doubles(n_cells: int) -> int:
+    """Size (float64 entries) of the factor buffer of fp_closure_solve."""
+    return (n_cells + 31) // 32 * 32 * LU_STRIDE
 FP_OK, FP_ERR_ARG, FP_ERR_CUDA, FP_ERR_WORKSPACE, FP_ERR_UNSUPPORTED = 0, -1, -2, -3, -4
 V_F32, V_F64 = 0, 1
 PREC_FP64, PREC_FP32_MOMENTS = 0, 1
@@ -61,7 +67,7 @@ class StepIO(ctypes.Structure):
                 ("d_coeffs", _vp), ("d_flags", _vp), ("d_flags_v", _vp),
                 ("net", ctypes.POINTER(FpMlp)), ("d_coeffs_s", _vp), ("d_flags_s", _vp), ("d_surrogate_ws", _vp),
                 ("surrogate_ws_bytes", _sz),
-                ("d_grad_coeffs", _vp), ("d_grad_moments", _vp), ("d_grad_v", _vp)]
+                ("d_lu", _vp), ("d_grad_coeffs", _vp), ("d_grad_moments", _vp), ("d_grad_v", _vp)]
 
 
 # name -> (restype, argtypes); the exported surface of include/fpclosure.h
@@ -78,11 +84,11 @@ SIGNATURES = {
     "fp_closure_exact": (_i32, [_vp, _i32, _i64, _vp, _i64, _vp, ctypes.POINTER(Params), _i32,
                                 _vp, _vp, _vp, _vp, _sz, _vp]),
     "fp_moments": (_i32, [_vp, _i32, _i64, _vp, _i64, _i32, _vp, _vp]),
-    "fp_closure_solve": (_i32, [_vp, _vp, _i64, ctypes.POINTER(Params), _i32, _vp, _vp, _vp]),
+    "fp_closure_solve": (_i32, [_vp, _vp, _i64, ctypes.POINTER(Params), _i32, _vp, _vp, _vp, _vp]),
     "fp_velocity_update": (_i32, [_vp, _vp, _i32, _i64, _vp, _i64, _vp, _vp, _vp, _dbl, ctypes.POINTER(Params),
                                   _vp, _u64, _u64, _vp, _vp, _vp]),
     "fp_closure_backward": (_i32, [_vp, _i32, _i64, _vp, _i64, _vp, ctypes.POINTER(Params), _vp, _vp, _vp, _vp,
-                                   _vp, _vp, _vp, _vp, _sz, _vp]),
+                                   _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "fp_mlp_param_count": (_i64, []),
     "fp_mlp_param_offset": (_i64, [_i32, _i32]),
     "fp_surrogate_workspace_bytes": (_sz, [_i64]),
@@ -129,8 +135,9 @@ def fp_closure_exact_static(v, offsets, tau, params: Params | None = None, prec=
 
 def fp_closure_backward(v, offsets, tau, moments, coeffs, flags, grad_coeffs, grad_moments_in=None,
                         params: Params | None = None, want_grad_moments=True, want_grad_v=True,
-                        grad_moments=None, grad_v=None, workspace=None, stream=None):
-    """Adjoint of the closure -> (grad_moments or None, grad_v or None)."""
+                        grad_moments=None, grad_v=None, workspace=None, stream=None, lu=None):
+    """Adjoint of the closure -> (grad_moments or None, grad_v or None).
+    lu: the factors fp_closure_solve kept for the same moments (optional)."""
     n_cells = offsets.numel() - 1
     n_p = v.shape[-1] if v.dim() == 2 else v.numel() // 3
     dev = offsets.device
@@ -138,7 +145,10 @@ def fp_closure_backward(v, offsets, tau, moments, coeffs, flags, grad_coeffs, gr
         grad_moments = torch.empty((n_cells, NMOM), dtype=torch.float64, device=dev)
     if want_grad_v and grad_v is None:
         grad_v = torch.empty_like(v)
-    _need_cuda(v, offsets, tau, moments, coeffs, flags, grad_coeffs, grad_moments_in, grad_moments, grad_v, workspace)
+    _need_cuda(v, offsets, tau, moments, coeffs, flags, grad_coeffs, grad_moments_in, grad_moments, grad_v, workspace,
+               lu)
+    if lu is not None and (lu.dtype != torch.float64 or lu.numel() < lu_doubles(n_cells)):
+        raise FPError(f"lu must be float64 with lu_doubles(n_cells) = {lu_doubles(n_cells)} entries")
     if grad_v is not None and grad_v.dtype != v.dtype:
         raise FPError("grad_v must have the velocity dtype")
     need = workspace_bytes(n_cells, n_p, "fp64", grad_moments is not None) if grad_v is not None else 0
@@ -147,7 +157,7 @@ def fp_closure_backward(v, offsets, tau, moments, coeffs, flags, grad_coeffs, gr
     ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
     p = params if params is not None else default_params()
     rc = lib().fp_closure_backward(_ptr(v), _vdtype(v), n_p, _ptr(offsets), n_cells, _ptr(tau), ctypes.byref(p),
-                                   _ptr(moments), _ptr(coeffs), _ptr(flags), _ptr(grad_coeffs),
+                                   _ptr(moments), _ptr(coeffs), _ptr(flags), _ptr(lu), _ptr(grad_coeffs),
                                    _ptr(grad_moments_in), _ptr(grad_moments), _ptr(grad_v), _ptr(workspace),
                                    ws_bytes, _stream(stream))
     _check(rc, "fp_closure_backward")
@@ -185,6 +195,7 @@ class HostStep:
                                             device=dev)
         self.adjoint = adjoint
         if adjoint:
+            self.lu = torch.empty(lu_doubles(n_cells), **f64)
             self.grad_coeffs = torch.ones((n_cells, NCOEF), **f64)
             self.grad_moments = torch.empty_like(self.moments)
             self.grad_v = torch.empty_like(self.d_v)
@@ -214,6 +225,7 @@ class HostStep:
             io.d_coeffs_s, io.d_flags_s = self.coeffs_s.data_ptr(), self.flags_s.data_ptr()
             io.d_surrogate_ws, io.surrogate_ws_bytes = self.surrogate_ws.data_ptr(), self.surrogate_ws.numel()
         if self.adjoint:
+            io.d_lu = self.lu.data_ptr()
             io.d_grad_coeffs, io.d_grad_moments = self.grad_coeffs.data_ptr(), self.grad_moments.data_ptr()
             io.d_grad_v = self.grad_v.data_ptr()
         p = params if params is not None else default_params()
@@ -340,19 +352,22 @@ def fp_moments(v, offsets, prec="fp32", moments_out=None, stream=None):
 
 
 def fp_closure_solve(moments, tau, params: Params | None = None, prec="fp32", coeffs_out=None, flags_out=None,
-                     stream=None):
-    """Assembly + pivoted FP64 solve from moment vectors -> (coeffs, flags)."""
+                     stream=None, lu_out=None):
+    """Assembly + pivoted FP64 solve from moment vectors -> (coeffs, flags).
+    lu_out: [n_cells, LU_STRIDE] float64 receiving the factors the adjoint
+    can reuse (fp_closure_backward(lu=...))."""
     n_cells = moments.shape[0]
     dev = moments.device
     if coeffs_out is None:
         coeffs_out = torch.empty((n_cells, NCOEF), dtype=torch.float64, device=dev)
     if flags_out is None:
         flags_out = torch.empty((n_cells,), dtype=torch.int32, device=dev)
-    _need_cuda(moments, tau, coeffs_out, flags_out)
+    _need_cuda(moments, tau, coeffs_out, flags_out, lu_out)
+    if lu_out is not None and (lu_out.dtype != torch.float64 or lu_out.numel() < lu_doubles(n_cells)):
+        raise FPError(f"lu_out must be float64 with lu_doubles(n_cells) = {lu_doubles(n_cells)} entries")
     p = params if params is not None else default_params()
     rc = lib().fp_closure_solve(_ptr(moments), _ptr(tau), n_cells, ctypes.byref(p), _PREC.get(prec, prec),
-                                _ptr(coeffs_out),
-                                _ptr(flags_out), _stream(stream))
+                                _ptr(coeffs_out), _ptr(flags_out), _ptr(lu_out), _stream(stream))
     _check(rc, "fp_closure_solve")
     return coeffs_out, flags_out
 

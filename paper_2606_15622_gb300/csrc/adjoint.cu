@@ -7,10 +7,10 @@
 // and to the particle velocities through m_k = <psi_k(c)>, c = v - U:
 //     dL/dv_p = (1/N) sum_k gm_k (grad psi_k(c_p) - <grad psi_k>) + gm_U / N.
 //
-// Kernel 1 (one thread per cell, FP64): re-assembles A, eliminates A^T with
-// partial pivoting (the factors are recomputed, never stored), and
-// back-propagates -lambda through the assembly formulas by hand-written
-// reverse mode.  Kernel 2 (four consecutive cells per warp, their particles
+// Kernel 1 (one thread per cell, FP64): lambda from the forward solve's
+// stored factors (two triangular solves) or, without them, by re-assembling
+// A and eliminating A^T with partial pivoting; then -lambda is propagated
+// back through the assembly formulas by hand-written reverse mode.  Kernel 2 (four consecutive cells per warp, their particles
 // walked flat by all lanes): the per-particle polynomial above, in the
 // velocity's precision, one pass over the particles.
 #include <cstdint>
@@ -20,11 +20,12 @@
 
 namespace fpc {
 
+template <bool kLU>
 __device__ __forceinline__ void adjoint_cell(int64_t c, const double *__restrict__ mom,
                                              const double *__restrict__ coeffs, const int32_t *__restrict__ flags,
-                                             const double *__restrict__ tau, const double *__restrict__ gY,
-                                             const double *__restrict__ gm_in, double eps2_hat,
-                                             double *__restrict__ gm_out) {
+                                             const double *__restrict__ lu, const double *__restrict__ tau,
+                                             const double *__restrict__ gY, const double *__restrict__ gm_in,
+                                             double eps2_hat, double *__restrict__ gm_out) {
   double gm[FP_NMOM];
 #pragma unroll
   for (int k = 0; k < FP_NMOM; ++k) gm[k] = gm_in ? gm_in[c * FP_NMOM + k] : 0.0;
@@ -34,9 +35,15 @@ __device__ __forceinline__ void adjoint_cell(int64_t c, const double *__restrict
 #pragma unroll
     for (int k = 0; k < FP_NMOM; ++k) m[k] = mom[c * FP_NMOM + k];
     const double tc = tau[c];
-    // lambda = A^-T gY: eliminate the transposed augmented system
+    // lambda = A^-T gY: with the forward's factors two triangular solves,
+    // else eliminate the transposed augmented system
     double lam[9];
-    {
+    if (kLU) {
+      double g[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) g[i] = gY[c * 9 + i];
+      lu_solve_transposed(lu + lu_base(c), g, lam);
+    } else {
       double a[9][10];
       assemble(m, tc, eps2_hat, a);
       double at[9][10];
@@ -145,16 +152,18 @@ __device__ __forceinline__ void adjoint_cell(int64_t c, const double *__restrict
 
 // One thread per cell, grid-stride, one 128-thread block per SM (FP64-bound:
 // see solve_kernel).
+template <bool kLU>
 __global__ void __launch_bounds__(128, 1) adjoint_cell_kernel(const double *__restrict__ mom,
                                                               const double *__restrict__ coeffs,
                                                               const int32_t *__restrict__ flags,
+                                                              const double *__restrict__ lu,
                                                               const double *__restrict__ tau,
                                                               const double *__restrict__ gY,
                                                               const double *__restrict__ gm_in, int64_t n_cells,
                                                               double eps2_hat, double *__restrict__ gm_out) {
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells;
        c += (int64_t)gridDim.x * blockDim.x)
-    adjoint_cell(c, mom, coeffs, flags, tau, gY, gm_in, eps2_hat, gm_out);
+    adjoint_cell<kLU>(c, mom, coeffs, flags, lu, tau, gY, gm_in, eps2_hat, gm_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -353,14 +362,18 @@ static int adj_sm_count() {
 }
 
 void launch_adjoint(const void *v, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, const double *tau,
-                    double eps2_hat, const double *mom, const double *coeffs, const int32_t *flags, const double *gY,
-                    const double *gm_in, double *gm_out, void *gv, cudaStream_t st) {
+                    double eps2_hat, const double *mom, const double *coeffs, const int32_t *flags, const double *lu,
+                    const double *gY, const double *gm_in, double *gm_out, void *gv, cudaStream_t st) {
   {
     const int threads = 128;
     int64_t blocks = (n_cells + threads - 1) / threads;
     if (blocks > adj_sm_count()) blocks = adj_sm_count();
-    adjoint_cell_kernel<<<(unsigned)blocks, threads, 0, st>>>(mom, coeffs, flags, tau, gY, gm_in, n_cells, eps2_hat,
-                                                              gm_out);
+    if (lu)
+      adjoint_cell_kernel<true><<<(unsigned)blocks, threads, 0, st>>>(mom, coeffs, flags, lu, tau, gY, gm_in,
+                                                                      n_cells, eps2_hat, gm_out);
+    else
+      adjoint_cell_kernel<false><<<(unsigned)blocks, threads, 0, st>>>(mom, coeffs, flags, nullptr, tau, gY, gm_in,
+                                                                       n_cells, eps2_hat, gm_out);
   }
   if (!gv) return;
   const int threads = 32 * kAWarps;

@@ -10,13 +10,13 @@ namespace fpc {
 void launch_gather(const void *v, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, int prec,
                    double *mom, cudaStream_t st);
 void launch_solve(const double *mom, const double *tau, int64_t n_cells, const fp_params &p, int prec,
-                  double *coeffs, int32_t *flags, cudaStream_t st);
+                  double *coeffs, int32_t *flags, double *lu, cudaStream_t st);
 void launch_velocity(const void *v, void *v_out, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells,
                      const double *mom, const double *coeffs, const double *tau, double dt, double eps2_hat,
                      const void *xi, uint64_t seed, uint64_t step, double *alpha_out, int32_t *flags, cudaStream_t st);
 void launch_adjoint(const void *v, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, const double *tau,
-                    double eps2_hat, const double *mom, const double *coeffs, const int32_t *flags, const double *gY,
-                    const double *gm_in, double *gm_out, void *gv, cudaStream_t st);
+                    double eps2_hat, const double *mom, const double *coeffs, const int32_t *flags, const double *lu,
+                    const double *gY, const double *gm_in, double *gm_out, void *gv, cudaStream_t st);
 void launch_features(const fp_mlp &net, const double *mom, const double *tau, int64_t n, int min_particles,
                      double margin, void *x, int32_t *flags, cudaStream_t st);
 int launch_mlp_forward(const fp_mlp &net, const void *x, int64_t n, int standardized_out, float *out, void *h_save,
@@ -143,7 +143,7 @@ int fp_closure_exact(const void *v, int v_dtype, int64_t n_particles, const int6
   cudaStream_t st = (cudaStream_t)stream;
   fpc::launch_gather(v, v_dtype, n_particles, cell_offsets, n_cells, prec, mom, st);
   if (int rc = check_launch("gather")) return rc;
-  fpc::launch_solve(mom, tau, n_cells, prm, prec, coeffs_out, flags_out, st);
+  fpc::launch_solve(mom, tau, n_cells, prm, prec, coeffs_out, flags_out, nullptr, st);
   return check_launch("solve");
 }
 
@@ -161,7 +161,7 @@ int fp_moments(const void *v, int v_dtype, int64_t n_particles, const int64_t *c
 }
 
 int fp_closure_solve(const double *moments, const double *tau, int64_t n_cells, const fp_params *p, int prec,
-                     double *coeffs_out, int32_t *flags_out, fp_stream_t stream) {
+                     double *coeffs_out, int32_t *flags_out, double *lu_out, fp_stream_t stream) {
   g_err[0] = 0;
   if (n_cells < 0) return fail(FP_ERR_ARG, "negative size");
   if (n_cells == 0) return FP_OK;
@@ -171,7 +171,7 @@ int fp_closure_solve(const double *moments, const double *tau, int64_t n_cells, 
   fp_default_params(&prm);
   if (p) prm = *p;
   if (prm.min_particles < 1) prm.min_particles = 1;
-  fpc::launch_solve(moments, tau, n_cells, prm, prec, coeffs_out, flags_out, (cudaStream_t)stream);
+  fpc::launch_solve(moments, tau, n_cells, prm, prec, coeffs_out, flags_out, lu_out, (cudaStream_t)stream);
   return check_launch("solve");
 }
 
@@ -201,7 +201,7 @@ int fp_velocity_update(void *v, void *v_out, int v_dtype, int64_t n_particles, c
 
 int fp_closure_backward(const void *v, int v_dtype, int64_t n_particles, const int64_t *cell_offsets,
                         int64_t n_cells, const double *tau, const fp_params *p, const double *moments,
-                        const double *coeffs, const int32_t *flags, const double *grad_coeffs,
+                        const double *coeffs, const int32_t *flags, const double *lu, const double *grad_coeffs,
                         const double *grad_moments_in, double *grad_moments, void *grad_v, void *ws,
                         size_t ws_bytes, fp_stream_t stream) {
   g_err[0] = 0;
@@ -224,7 +224,7 @@ int fp_closure_backward(const void *v, int v_dtype, int64_t n_particles, const i
     if ((uintptr_t)ws % kAlign) return fail(FP_ERR_ARG, "workspace not 256-byte aligned");
     gm = (double *)ws;
   }
-  fpc::launch_adjoint(v, v_dtype, n_particles, cell_offsets, n_cells, tau, prm.eps2_hat, moments, coeffs, flags,
+  fpc::launch_adjoint(v, v_dtype, n_particles, cell_offsets, n_cells, tau, prm.eps2_hat, moments, coeffs, flags, lu,
                       grad_coeffs, grad_moments_in, gm, grad_v, (cudaStream_t)stream);
   return check_launch("adjoint");
 }

@@ -259,14 +259,16 @@ __global__ void __launch_bounds__(256) gather_fp64_kernel(const VT *__restrict__
 // One thread per cell, grid-stride: the launch uses one 128-thread block per
 // SM.  A single warp per SM sub-partition keeps its FP64 unit busy (each FP64
 // warp instruction occupies it for many cycles), and the half of the register
-// file left free lets kernels of other streams run beside it.
+// file left free lets kernels of other streams run beside it.  With kLU the
+// factors of P A = L U of every unflagged cell go to lu for the adjoint.
+template <bool kLU>
 __global__ void __launch_bounds__(128, 1) solve_kernel(const double *__restrict__ mom, const double *__restrict__ tau,
                                                        int64_t n_cells, SolveParams prm, double *__restrict__ coeffs,
-                                                       int32_t *__restrict__ flags) {
+                                                       int32_t *__restrict__ flags, double *__restrict__ lu) {
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells;
        c += (int64_t)gridDim.x * blockDim.x) {
     double y[9];
-    const int fl = closure_cell(mom + c * FP_NMOM, tau[c], prm, y);
+    const int fl = closure_cell<kLU>(mom + c * FP_NMOM, tau[c], prm, y, kLU ? lu + lu_base(c) : nullptr);
     double *yc = coeffs + c * 9;
 #pragma unroll
     for (int q = 0; q < 9; ++q) yc[q] = y[q];
@@ -324,14 +326,17 @@ void launch_gather(const void *v, int v_dtype, int64_t np, const int64_t *off, i
 }
 
 void launch_solve(const double *mom, const double *tau, int64_t n_cells, const fp_params &p, int prec,
-                  double *coeffs, int32_t *flags, cudaStream_t st) {
+                  double *coeffs, int32_t *flags, double *lu, cudaStream_t st) {
   double rtol = p.pivot_rtol;
   if (prec == FP_PREC_FP32_MOMENTS && rtol < FP_FP32_PIVOT_FLOOR) rtol = FP_FP32_PIVOT_FLOOR;
   SolveParams prm{p.eps2_hat, rtol, p.min_particles};
   const int threads = 128;
   int64_t blocks = (n_cells + threads - 1) / threads;
   if (blocks > sm_count()) blocks = sm_count();
-  solve_kernel<<<(unsigned)blocks, threads, 0, st>>>(mom, tau, n_cells, prm, coeffs, flags);
+  if (lu)
+    solve_kernel<true><<<(unsigned)blocks, threads, 0, st>>>(mom, tau, n_cells, prm, coeffs, flags, lu);
+  else
+    solve_kernel<false><<<(unsigned)blocks, threads, 0, st>>>(mom, tau, n_cells, prm, coeffs, flags, nullptr);
 }
 
 }  // namespace fpc

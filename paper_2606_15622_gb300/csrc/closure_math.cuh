@@ -97,9 +97,13 @@ __device__ __forceinline__ void assemble(const double (&m)[FP_NMOM], double tau,
 }
 
 // One elimination step for column K (a template so every index is static and
-// the matrix stays in registers).
-template <int K>
-__device__ __forceinline__ void elim_step(double (&a)[9][10], uint64_t thr, int &flag, double (&rinv)[9]) {
+// the matrix stays in registers).  With kLU the whole rows are swapped and
+// the multipliers are kept below the diagonal, so that afterwards P A = L U
+// with L unit lower triangular in a[i][j < i], U in a[i][j >= i], and the
+// row swapped with row K at step K in bits 4K..4K+3 of perm.
+template <int K, bool kLU>
+__device__ __forceinline__ void elim_step(double (&a)[9][10], uint64_t thr, int &flag, double (&rinv)[9],
+                                          uint64_t &perm) {
   uint64_t best = abs_bits(a[K][K]);
   int bi = K;
 #pragma unroll
@@ -111,11 +115,12 @@ __device__ __forceinline__ void elim_step(double (&a)[9][10], uint64_t thr, int 
     }
   }
   if (!(best > thr)) flag = FP_FLAG_SINGULAR;
+  if (kLU) perm |= (uint64_t)bi << (4 * K);
 #pragma unroll
   for (int i = K + 1; i < 9; ++i) {
     const bool sw = (bi == i);
 #pragma unroll
-    for (int j = K; j < 10; ++j) {
+    for (int j = kLU ? 0 : K; j < 10; ++j) {
       const double t = a[K][j];
       a[K][j] = sw ? a[i][j] : t;
       a[i][j] = sw ? t : a[i][j];
@@ -125,6 +130,7 @@ __device__ __forceinline__ void elim_step(double (&a)[9][10], uint64_t thr, int 
 #pragma unroll
   for (int i = K + 1; i < 9; ++i) {
     const double l = a[i][K] * rinv[K];
+    if (kLU) a[i][K] = l;
 #pragma unroll
     for (int j = K + 1; j < 10; ++j) a[i][j] = fma(-l, a[K][j], a[i][j]);
   }
@@ -132,7 +138,11 @@ __device__ __forceinline__ void elim_step(double (&a)[9][10], uint64_t thr, int 
 
 // Partial-pivot elimination and back substitution on [A | r]; returns
 // FP_FLAG_SINGULAR if a pivot is <= rtol * max|A| (y is then garbage).
-__device__ __forceinline__ int pivoted_solve(double (&a)[9][10], double rtol, double (&y)[9]) {
+// With kLU the factors stay in a (see elim_step), rinv holds the reciprocal
+// pivots and perm the row swaps.
+template <bool kLU = false>
+__device__ __forceinline__ int pivoted_solve(double (&a)[9][10], double rtol, double (&y)[9], double (&rinv)[9],
+                                             uint64_t &perm) {
   uint64_t amax = 0;
 #pragma unroll
   for (int i = 0; i < 9; ++i)
@@ -142,16 +152,16 @@ __device__ __forceinline__ int pivoted_solve(double (&a)[9][10], double rtol, do
   int flag = 0;
   if (!(amax_d > 0.0) || !finite_d(amax_d)) flag = FP_FLAG_SINGULAR;
   const uint64_t thr = abs_bits(rtol * amax_d);
-  double rinv[9];
-  elim_step<0>(a, thr, flag, rinv);
-  elim_step<1>(a, thr, flag, rinv);
-  elim_step<2>(a, thr, flag, rinv);
-  elim_step<3>(a, thr, flag, rinv);
-  elim_step<4>(a, thr, flag, rinv);
-  elim_step<5>(a, thr, flag, rinv);
-  elim_step<6>(a, thr, flag, rinv);
-  elim_step<7>(a, thr, flag, rinv);
-  elim_step<8>(a, thr, flag, rinv);
+  perm = 0;
+  elim_step<0, kLU>(a, thr, flag, rinv, perm);
+  elim_step<1, kLU>(a, thr, flag, rinv, perm);
+  elim_step<2, kLU>(a, thr, flag, rinv, perm);
+  elim_step<3, kLU>(a, thr, flag, rinv, perm);
+  elim_step<4, kLU>(a, thr, flag, rinv, perm);
+  elim_step<5, kLU>(a, thr, flag, rinv, perm);
+  elim_step<6, kLU>(a, thr, flag, rinv, perm);
+  elim_step<7, kLU>(a, thr, flag, rinv, perm);
+  elim_step<8, kLU>(a, thr, flag, rinv, perm);
 #pragma unroll
   for (int k = 8; k >= 0; --k) {
     double s = a[k][9];
@@ -161,12 +171,63 @@ __device__ __forceinline__ int pivoted_solve(double (&a)[9][10], double rtol, do
   }
   return flag;
 }
+__device__ __forceinline__ int pivoted_solve(double (&a)[9][10], double rtol, double (&y)[9]) {
+  double rinv[9];
+  uint64_t perm;
+  return pivoted_solve<false>(a, rtol, y, rinv, perm);
+}
 
+// Stored factors: FP_LU_STRIDE doubles per cell -- L below / reciprocal
+// pivots on / U above the diagonal (row-major 9 x 9), then the packed swaps
+// as the bits of a double -- tiled by 32 cells: entry k of cell c lives at
+// lu[(c / 32) * 32 * FP_LU_STRIDE + 32 k + c % 32], so the 32 cells of a warp
+// write and read each entry as one contiguous 256-byte line.
+__device__ __forceinline__ int64_t lu_base(int64_t c) { return (c >> 5) * 32 * FP_LU_STRIDE + (c & 31); }
+
+// Solve A^T x = g with the stored factors of P A = L U: U^T z = g (forward),
+// L^T w = z (backward), x = P^T w (the swaps undone in reverse order).
+// lu points at the cell's first entry (lu_base); entries are 32 apart.
+__device__ __forceinline__ void lu_solve_transposed(const double *__restrict__ lu, const double (&g)[9],
+                                                    double (&x)[9]) {
+  double z[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    double s = g[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) s = fma(-lu[32 * (k * 9 + i)], z[k], s);  // U^T[i][k] = U[k][i]
+    z[i] = s * lu[32 * (i * 9 + i)];
+  }
+#pragma unroll
+  for (int i = 8; i >= 0; --i) {
+    double s = z[i];
+#pragma unroll
+    for (int k = i + 1; k < 9; ++k) s = fma(-lu[32 * (k * 9 + i)], x[k], s);  // L^T[i][k] = L[k][i]
+    x[i] = s;
+  }
+  const uint64_t perm = (uint64_t)__double_as_longlong(lu[32 * 81]);
+#pragma unroll
+  for (int K = 8; K >= 0; --K) {
+    const int bi = (int)((perm >> (4 * K)) & 15u);
+    // swap x[K] and x[bi] (bi >= K) with selects: registers stay static
+    double xk = x[K];
+#pragma unroll
+    for (int i = K + 1; i < 9; ++i) {
+      const bool sw = bi == i;
+      const double t = x[i];
+      x[i] = sw ? xk : t;
+      xk = sw ? t : xk;
+    }
+    x[K] = xk;
+  }
+}
 
 // The closure of one cell from its moment vector: flags, and Y (the linear
-// drift C = -I/tau, G = 0 for flagged cells).
+// drift C = -I/tau, G = 0 for flagged cells).  With lu != nullptr the factors
+// of an unflagged cell are written there (the cell's first entry, see
+// lu_base; entries 32 apart).
+template <bool kLU = false>
 __device__ __forceinline__ int closure_cell(const double *__restrict__ mc, double tc, const SolveParams &prm,
-                                            double (&y)[9]) {
+                                            double (&y)[9], double *__restrict__ lu = nullptr) {
   double m[FP_NMOM];
 #pragma unroll
   for (int k = 0; k < FP_NMOM; ++k) m[k] = mc[k];
@@ -178,13 +239,21 @@ __device__ __forceinline__ int closure_cell(const double *__restrict__ mc, doubl
   if (m[kN] < (double)prm.min_particles) fl |= FP_FLAG_FEW;
   if (!(m[kTheta] > 0.0)) fl |= FP_FLAG_SINGULAR;
   if (!fl) {
-    double a[9][10];
+    double a[9][10], rinv[9];
+    uint64_t perm;
     assemble(m, tc, prm.eps2_hat, a);
-    fl |= pivoted_solve(a, prm.pivot_rtol, y);
+    fl |= pivoted_solve<kLU>(a, prm.pivot_rtol, y, rinv, perm);
     if (!fl) {
 #pragma unroll
       for (int q = 0; q < 9; ++q)
         if (!finite_d(y[q])) fl |= FP_FLAG_NONFINITE;
+    }
+    if (kLU && !fl) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i)
+#pragma unroll
+        for (int j = 0; j < 9; ++j) lu[32 * (i * 9 + j)] = i == j ? rinv[i] : a[i][j];
+      lu[32 * 81] = __longlong_as_double((long long)perm);
     }
   }
   if (fl) {

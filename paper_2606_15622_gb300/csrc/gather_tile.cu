@@ -34,7 +34,7 @@ constexpr int kCapF = kSubP + 8;             // floats per component slot (align
 constexpr int kSlots = 4;
 constexpr int kConsumerWarps = 4;
 constexpr int kTileThreads = 32 * (1 + kConsumerWarps);
-constexpr int kTileG = 4;                    // lanes per cell
+constexpr int kTileG = 8;                    // lanes per cell (measured best of 4, 8, 16, 32)
 constexpr int kCellsPerTask = 32 / kTileG;   // cells per warp task
 constexpr int kSlotFloats = 3 * kCapF;
 constexpr size_t kTileSmem = (size_t)kSlots * kSlotFloats * sizeof(float);

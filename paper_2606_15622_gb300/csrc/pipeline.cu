@@ -5,7 +5,8 @@
 // chunk is the closure problem of its own cells).  For every chunk, on five
 // streams ordered by events:
 //   copy-in  (H2D)   velocities of the chunk's particles, offsets, tau
-//   main     (high priority) gather -> solve -> [adjoint]
+//   main     (high priority) gather -> solve (keeping its factors for the
+//            adjoint when asked) -> [adjoint]
 //   learned  [surrogate closure]                    after the solve
 //   update   flags copy, velocity update M^n -> M^{n+1}  after the solve
 //   copy-out (D2H)   coefficients, flags, updated velocities
@@ -132,7 +133,11 @@ int fp_step_host(fp_pipeline *pl, const fp_step_io *io, int v_dtype, int64_t n_p
   char *dv = (char *)io->d_v, *dvo = (char *)io->d_v_out;
   int rc = FP_OK;
   for (int k = 0; k < n_chunks && rc == FP_OK; ++k) {
-    const int64_t c0 = n_cells * k / n_chunks, c1 = n_cells * (k + 1) / n_chunks, nc = c1 - c0;
+    // chunk boundaries on multiples of 32 cells (the tiles of stored factors)
+    const int64_t c0 = k == 0 ? 0 : (n_cells * k / n_chunks) & ~(int64_t)31;
+    const int64_t c1 = k == n_chunks - 1 ? n_cells : (n_cells * (k + 1) / n_chunks) & ~(int64_t)31;
+    const int64_t nc = c1 - c0;
+    if (nc <= 0) continue;
     const int64_t p0 = io->h_offsets[c0], p1 = io->h_offsets[c1];
     if (p0 < 0 || p1 < p0 || p1 > n_particles) {
       rc = fpc::report(FP_ERR_ARG, "fp_step_host: offsets are not non-decreasing");
@@ -152,8 +157,9 @@ int fp_step_host(fp_pipeline *pl, const fp_step_io *io, int v_dtype, int64_t n_p
     cudaStreamWaitEvent(pl->main, pl->ev_h2d[k], 0);
     double *mom = io->d_moments + c0 * FP_NMOM;
     if ((rc = fp_moments(io->d_v, v_dtype, n_particles, io->d_offsets + c0, nc, prec, mom, pl->main))) break;
+    double *lu = io->d_lu ? io->d_lu + (c0 / 32) * 32 * FP_LU_STRIDE : nullptr;
     if ((rc = fp_closure_solve(mom, io->d_tau + c0, nc, p, prec, io->d_coeffs + c0 * 9, io->d_flags + c0,
-                               pl->main)))
+                               io->d_grad_coeffs ? lu : nullptr, pl->main)))
       break;
     cudaEventRecord(pl->ev_solve[k], pl->main);
     // ---- learned closure, velocity update, adjoint side by side ----
@@ -173,7 +179,7 @@ int fp_step_host(fp_pipeline *pl, const fp_step_io *io, int v_dtype, int64_t n_p
     cudaEventRecord(pl->ev_vel[k], pl->vel);
     if (io->d_grad_coeffs) {
       if ((rc = fp_closure_backward(io->d_v, v_dtype, n_particles, io->d_offsets + c0, nc, io->d_tau + c0, p, mom,
-                                    io->d_coeffs + c0 * 9, io->d_flags + c0, io->d_grad_coeffs + c0 * 9, nullptr,
+                                    io->d_coeffs + c0 * 9, io->d_flags + c0, lu, io->d_grad_coeffs + c0 * 9, nullptr,
                                     io->d_grad_moments + c0 * FP_NMOM, io->d_grad_v, nullptr, 0, pl->main)))
         break;
     }

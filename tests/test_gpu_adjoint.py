@@ -129,3 +129,67 @@ def test_autograd_function_and_flagged_cells(small_cells):
     gm2, _ = api.fp_closure_backward(v.detach(), off, tau, mom.detach(), y.detach(), fl2, gY, want_grad_v=False)
     assert torch.all(gm2[:5] == 0)
     assert not flagged[:5].all()
+
+
+def _lu_row(lu, c):
+    """The FP_LU_STRIDE entries of cell c (tiles of 32 cells, entries 32 apart)."""
+    base = (c // 32) * 32 * api.LU_STRIDE + c % 32
+    return lu[base + 32 * np.arange(api.LU_STRIDE)]
+
+
+def _unpack_lu(row):
+    """(P, L, U) with P A = L U from one cell's stored entries."""
+    M = row[:81].reshape(9, 9)
+    L = np.tril(M, -1) + np.eye(9)
+    U = np.triu(M, 1) + np.diag(1.0 / np.diag(M))  # the diagonal holds 1 / pivot
+    perm = int(np.frombuffer(row[81:82].tobytes(), dtype=np.uint64)[0])
+    P = np.eye(9)
+    for k in range(9):  # the swaps of the elimination, in order
+        b = (perm >> (4 * k)) & 15
+        P[[k, b]] = P[[b, k]]
+    return P, L, U
+
+
+def test_stored_factors_reproduce_the_oracle_matrix(cavity_pop):
+    """The factors fp_closure_solve keeps satisfy P A = L U for the oracle's
+    assembled A (relative to max |A|), with |L| <= 1 (partial pivoting)."""
+    pop = cavity_pop.subset(np.arange(0, cavity_pop.n_cells, 97))
+    v, off, tau, mom, y, fl = _forward(pop)
+    lu = torch.full((api.lu_doubles(pop.n_cells),), np.nan, dtype=torch.float64, device="cuda")
+    y2, fl2 = api.fp_closure_solve(mom, tau, prec="fp64", lu_out=lu)
+    torch.cuda.synchronize()
+    assert torch.equal(y2, y) and torch.equal(fl2, fl)
+    m, lu = mom.cpu().numpy(), lu.cpu().numpy()
+    checked = 0
+    for c in np.flatnonzero(fl.cpu().numpy() == 0):
+        A, _ = O.assemble(m[c], pop.tau[c])
+        Pm, L, U = _unpack_lu(_lu_row(lu, c))
+        assert np.abs(np.tril(L, -1)).max() <= 1.0
+        assert np.abs(Pm @ A - L @ U).max() <= 1e-13 * np.abs(A).max() * 9
+        checked += 1
+    assert checked > 100
+
+
+@pytest.mark.parametrize("vdtype", ["f64", "f32"])
+def test_backward_with_stored_factors_matches_recomputation(cavity_pop, vdtype):
+    pop = cavity_pop.subset(np.arange(0, cavity_pop.n_cells, 7))
+    prec = "fp64" if vdtype == "f64" else "fp32"
+    v, off, tau, mom, y, fl = _forward(pop, prec, vdtype)
+    lu = torch.empty(api.lu_doubles(pop.n_cells), dtype=torch.float64, device="cuda")
+    api.fp_closure_solve(mom, tau, prec=prec, lu_out=lu)
+    g = _dev(np.random.default_rng(12).standard_normal((pop.n_cells, 9)))
+    gm0, gv0 = api.fp_closure_backward(v, off, tau, mom, y, fl, g)
+    gm1, gv1 = api.fp_closure_backward(v, off, tau, mom, y, fl, g, lu=lu)
+    torch.cuda.synchronize()
+    _, _, cond, _ = O.closure(mom.cpu().numpy(), pop.tau, want_cond=True)
+    ok = torch.from_numpy((cond < 1e6) & (fl.cpu().numpy() == 0)).cuda()
+    assert ok.float().mean() > 0.9
+    rel = (gm1 - gm0).norm(dim=1) / gm0.norm(dim=1).clamp_min(1e-300)
+    assert rel[ok].max().item() < 1e-9
+    # flagged cells carry only grad_moments_in (zero here) in both
+    assert torch.equal(gm1[fl != 0], gm0[fl != 0])
+    cell_of = torch.repeat_interleave(torch.arange(pop.n_cells, device="cuda"), _dev(pop.counts))
+    okp = ok[cell_of]
+    scale = gv0.abs().max()
+    tol = 1e-9 if vdtype == "f64" else 1e-4
+    assert ((gv1 - gv0).abs()[:, okp].max() / scale).item() < tol

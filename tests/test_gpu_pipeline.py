@@ -28,12 +28,14 @@ def _reference(pop, v, prec, sur, dt, seed, step):
     dev = v.device
     off, tau = torch.from_numpy(pop.offsets).to(dev), torch.from_numpy(pop.tau).to(dev)
     mom, y, fl = api.fp_closure_exact(v, off, tau, prec=prec)
+    lu = torch.empty(api.lu_doubles(pop.n_cells), dtype=torch.float64, device=dev)
+    api.fp_closure_solve(mom, tau, prec=prec, lu_out=lu)  # the factors the pipeline's adjoint reuses
     fl_v = fl.clone()
     v_out = torch.empty_like(v)
     api.fp_velocity_update(v, off, mom, y, tau, fl_v, dt, seed=seed, step=step, v_out=v_out)
     ys, fls = sur.closure(mom, tau, prec=prec)
     gY = torch.ones_like(y)
-    gm, gv = api.fp_closure_backward(v, off, tau, mom, y, fl, gY)
+    gm, gv = api.fp_closure_backward(v, off, tau, mom, y, fl, gY, lu=lu)
     torch.cuda.synchronize()
     return dict(coeffs=y, flags=fl_v, v_out=v_out, coeffs_s=ys, flags_s=fls, grad_m=gm, grad_v=gv)
 
