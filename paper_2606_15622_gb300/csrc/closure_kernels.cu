@@ -256,13 +256,13 @@ __global__ void __launch_bounds__(256) gather_fp64_kernel(const VT *__restrict__
 // ---------------------------------------------------------------------------
 // assembly + solve (closure_math.cuh)
 // ---------------------------------------------------------------------------
-// One thread per cell, grid-stride: the launch uses one 128-thread block per
-// SM.  A single warp per SM sub-partition keeps its FP64 unit busy (each FP64
-// warp instruction occupies it for many cycles), and the half of the register
-// file left free lets kernels of other streams run beside it.  With kLU the
-// factors of P A = L U of every unflagged cell go to lu for the adjoint.
+// One thread per cell, grid-stride over two resident 128-thread blocks per SM
+// (254 registers a thread: the whole register file); two warps per SM
+// sub-partition keep its FP64 unit busy through each other's dependency
+// stalls.  With kLU the factors of P A = L U of every unflagged cell go to lu
+// for the adjoint.
 template <bool kLU>
-__global__ void __launch_bounds__(128, 1) solve_kernel(const double *__restrict__ mom, const double *__restrict__ tau,
+__global__ void __launch_bounds__(128, 2) solve_kernel(const double *__restrict__ mom, const double *__restrict__ tau,
                                                        int64_t n_cells, SolveParams prm, double *__restrict__ coeffs,
                                                        int32_t *__restrict__ flags, double *__restrict__ lu) {
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells;
@@ -332,7 +332,7 @@ void launch_solve(const double *mom, const double *tau, int64_t n_cells, const f
   SolveParams prm{p.eps2_hat, rtol, p.min_particles};
   const int threads = 128;
   int64_t blocks = (n_cells + threads - 1) / threads;
-  if (blocks > sm_count()) blocks = sm_count();
+  if (blocks > 2 * sm_count()) blocks = 2 * sm_count();
   if (lu)
     solve_kernel<true><<<(unsigned)blocks, threads, 0, st>>>(mom, tau, n_cells, prm, coeffs, flags, lu);
   else
