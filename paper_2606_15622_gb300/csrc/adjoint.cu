@@ -172,10 +172,15 @@ __global__ void __launch_bounds__(128, 1) adjoint_cell_kernel(const double *__re
 constexpr int kAG = 8;              // lanes per cell while building constants
 constexpr int kACells = 32 / kAG;   // consecutive cells per warp task
 constexpr int kAWarps = 8;          // warps per block
-constexpr int kAConst = 36;         // table entries per cell
+constexpr int kAConst = 44;         // table entries per cell
 
-// table slots: U, Mu (sym), A3 (10), W (sym), gz, <grad psi>, gm_U / N, 1 / N
-enum { AU = 0, AMU = 3, AA3 = 9, AW = 19, AGZ = 25, AG0 = 28, AGU = 31, AINVN = 34 };
+// Per-cell table of the particle polynomial, every coefficient already
+// multiplied by 1/N and by its constant factor:
+//   dL/dv_d = Mu'_d.c + sum_{j<=k} A3'_{d,jk} c_j c_k
+//             + c_d (c.W'c + |c|^2 gz'.c) + |c|^2 (W'c)_d + |c|^4 gz''_d + B_d
+// with Mu' = Mu/N, A3'_{d,jk} = 3 m_jk A_{djk}/N (m = 1 on, 2 off the
+// diagonal), W' = 2W/N, gz' = 4gz/N, gz'' = gz/N, B = (gm_U - <grad psi>)/N.
+enum { AU = 0, AMU = 3, AA3 = 9, AW = 27, AGZ4 = 33, AGZ1 = 36, AB = 39 };
 
 template <typename T>
 __device__ __forceinline__ T shfl_g(T x, int src, int lane) {
@@ -287,23 +292,27 @@ __global__ void __launch_bounds__(32 * kAWarps, sizeof(VT) == 4 ? 3 : 1) adjoint
         r[AU + 1] = U1;
         r[AU + 2] = U2;
 #pragma unroll
-        for (int s = 0; s < 6; ++s) r[AMU + s] = Mu[s];
+        for (int s = 0; s < 6; ++s) r[AMU + s] = Mu[s] * inv_n;
 #pragma unroll
-        for (int s = 0; s < 10; ++s) r[AA3 + s] = A3[s];
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = j; k < 3; ++k)
+              r[AA3 + 6 * d + sym2(j, k)] = A3[sym3(d, j, k)] * (j == k ? T(3) : T(6)) * inv_n;
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
-          for (int j = i; j < 3; ++j) r[AW + sym2(i, j)] = W[i][j];
+          for (int j = i; j < 3; ++j) r[AW + sym2(i, j)] = T(2) * W[i][j] * inv_n;
+        const T gUv[3] = {gU0, gU1, gU2};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          r[AGZ + d] = gzv[d];
-          r[AG0 + d] = G0[d];
+          r[AGZ4 + d] = T(4) * gzv[d] * inv_n;
+          r[AGZ1 + d] = gzv[d] * inv_n;
+          r[AB + d] = gUv[d] - G0[d] * inv_n;
         }
-        r[AGU] = gU0;
-        r[AGU + 1] = gU1;
-        r[AGU + 2] = gU2;
-        r[AINVN] = inv_n;
-        r[AINVN + 1] = T(0);
+        r[AB + 3] = T(0);
+        r[AB + 4] = T(0);
       }
     }
     const int64_t o0 = __shfl_sync(0xffffffffu, a0, 0);
@@ -320,27 +329,23 @@ __global__ void __launch_bounds__(32 * kAWarps, sizeof(VT) == 4 ? 3 : 1) adjoint
       T K[kAConst];
       load_row(tab[cl], K);
       const T cc[3] = {px[q] - K[AU], py[q] - K[AU + 1], pz[q] - K[AU + 2]};
-      const T r2 = cc[0] * cc[0] + cc[1] * cc[1] + cc[2] * cc[2];
-      const T gzc = K[AGZ] * cc[0] + K[AGZ + 1] * cc[1] + K[AGZ + 2] * cc[2];
+      // the six products c_j c_k (j <= k), in sym2 order
+      const T pr[6] = {cc[0] * cc[0], cc[0] * cc[1], cc[0] * cc[2], cc[1] * cc[1], cc[1] * cc[2], cc[2] * cc[2]};
+      const T r2 = pr[0] + pr[3] + pr[5];
+      const T r4 = r2 * r2;
       T Wc[3];
-      T cWc = 0;
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
+      for (int i = 0; i < 3; ++i)
         Wc[i] = K[AW + sym2(i, 0)] * cc[0] + K[AW + sym2(i, 1)] * cc[1] + K[AW + sym2(i, 2)] * cc[2];
-        cWc += cc[i] * Wc[i];
-      }
+      const T t = cc[0] * Wc[0] + cc[1] * Wc[1] + cc[2] * Wc[2] +
+                  r2 * (K[AGZ4] * cc[0] + K[AGZ4 + 1] * cc[1] + K[AGZ4 + 2] * cc[2]);
       T out[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         T gd = K[AMU + sym2(d, 0)] * cc[0] + K[AMU + sym2(d, 1)] * cc[1] + K[AMU + sym2(d, 2)] * cc[2];
-        T a3 = 0;
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-          for (int k = 0; k < 3; ++k) a3 += K[AA3 + sym3(d, j, k)] * cc[j] * cc[k];
-        gd += T(3) * a3 + T(2) * cc[d] * cWc + T(2) * r2 * Wc[d] + T(4) * r2 * cc[d] * gzc;
-        gd += r2 * r2 * K[AGZ + d];
-        out[d] = (gd - K[AG0 + d]) * K[AINVN] + K[AGU + d];
+        for (int s = 0; s < 6; ++s) gd += K[AA3 + 6 * d + s] * pr[s];
+        out[d] = gd + cc[d] * t + r2 * Wc[d] + r4 * K[AGZ1 + d] + K[AB + d];
       }
       qx[q] = out[0];
       qy[q] = out[1];
