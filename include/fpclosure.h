@@ -137,9 +137,12 @@ int fp_closure_exact(const void *v, int v_dtype, int64_t n_particles, const int6
  *
  * fp_moments: the per-cell moment vectors (Sec. 3.6), same arguments and
  * precision modes as fp_closure_exact; moments_out [n_cells][FP_NMOM] f64
- * required.  No workspace. */
+ * required; m6_out [n_cells] f64 or NULL receives <|c|^6>, the sixth central
+ * moment of the peculiar speed, which lets fp_velocity_update evaluate the
+ * cell averages of Eq. update_alpha from moments (one particle pass).  No
+ * workspace. */
 int fp_moments(const void *v, int v_dtype, int64_t n_particles, const int64_t *cell_offsets, int64_t n_cells,
-               int prec, double *moments_out, fp_stream_t stream);
+               int prec, double *moments_out, double *m6_out, fp_stream_t stream);
 
 /* fp_closure_solve: assembly of Eq. system9x9 from given moment vectors and
  * the FP64 pivoted solve, one thread per cell.  moments [n_cells][FP_NMOM]
@@ -173,6 +176,12 @@ int fp_closure_solve(const double *moments, const double *tau, int64_t n_cells, 
  *                overlap v.  Writing out of place lets a caller keep M^n for
  *                a concurrent reader (e.g. the adjoint's particle pass)
  *   moments      [n_cells][FP_NMOM] of the same velocities (U, theta, u_ijk)
+ *   m6           [n_cells] <|c|^6> of the same velocities (fp_moments), or
+ *                NULL.  Given, <N.N> and <M'.N> are evaluated from the moments
+ *                in closed form (N is a cubic in M' = c, so <N.N> needs
+ *                moments up to the sixth) and the particles are read once;
+ *                NULL, they are summed over the particles in a first pass.
+ *                Both are the same cell averages up to rounding.
  *   coeffs       [n_cells][9] from the closure
  *   tau          [n_cells]; dt the time step
  *   p            eps2_hat is read (NULL = defaults)
@@ -188,9 +197,9 @@ int fp_closure_solve(const double *moments, const double *tau, int64_t n_cells, 
  *                non-finite sets FP_FLAG_ALPHA and alpha = 1.
  * No workspace. */
 int fp_velocity_update(void *v, void *v_out, int v_dtype, int64_t n_particles, const int64_t *cell_offsets,
-                       int64_t n_cells, const double *moments, const double *coeffs, const double *tau, double dt,
-                       const fp_params *p, const void *xi, uint64_t seed, uint64_t step, double *alpha_out,
-                       int32_t *flags, fp_stream_t stream);
+                       int64_t n_cells, const double *moments, const double *m6, const double *coeffs,
+                       const double *tau, double dt, const fp_params *p, const void *xi, uint64_t seed,
+                       uint64_t step, double *alpha_out, int32_t *flags, fp_stream_t stream);
 
 /* fp_closure_backward: the adjoint of fp_closure_exact (not in the paper; the
  * closure of Eq. system9x9 differentiated as an implicit function).  With
@@ -392,6 +401,7 @@ typedef struct {
   int64_t *d_offsets;       /* [n_cells + 1]                                    */
   double *d_tau;            /* [n_cells]                                        */
   double *d_moments;        /* [n_cells][FP_NMOM]                               */
+  double *d_m6;             /* [n_cells] <|c|^6> for a one-pass update, or NULL */
   double *d_coeffs;         /* [n_cells][9]                                     */
   int32_t *d_flags;         /* [n_cells] closure flags                          */
   int32_t *d_flags_v;       /* [n_cells] the update's flags (closure flags plus

@@ -96,6 +96,22 @@ def moments(v, offsets):
     return out
 
 
+def speed_moment6(v, offsets):
+    """<|c|^6> per cell, c = v - U (the cell mean): the sixth central moment
+    of the peculiar speed, which the cell average <N.N> of Eq. update_alpha
+    contains once N (Eq. update_N, cubic in c) is expanded.  Plain definition:
+    mean over the cell's particles of (c.c)^3, in FP64 (empty cells: 0)."""
+    v = _f64(v)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    out = np.zeros(offsets.size - 1)
+    for k in range(offsets.size - 1):
+        a, b = offsets[k], offsets[k + 1]
+        if b > a:
+            c = v[:, a:b] - v[:, a:b].mean(axis=1, keepdims=True)
+            out[k] = np.mean(np.sum(c * c, axis=0) ** 3)
+    return out
+
+
 def assemble(m, tau, eps2_hat=DEFAULT_EPS2_HAT):
     """The 9x9 matrix and right-hand side of one cell."""
     m = _f64(m)

@@ -64,6 +64,7 @@ class StepIO(ctypes.Structure):
     _fields_ = [("h_v", _vp), ("h_v_out", _vp), ("h_offsets", _vp), ("h_tau", _vp), ("h_coeffs", _vp),
                 ("h_flags", _vp),
                 ("d_v", _vp), ("d_v_out", _vp), ("d_offsets", _vp), ("d_tau", _vp), ("d_moments", _vp),
+                ("d_m6", _vp),
                 ("d_coeffs", _vp), ("d_flags", _vp), ("d_flags_v", _vp),
                 ("net", ctypes.POINTER(FpMlp)), ("d_coeffs_s", _vp), ("d_flags_s", _vp), ("d_surrogate_ws", _vp),
                 ("surrogate_ws_bytes", _sz),
@@ -83,10 +84,10 @@ SIGNATURES = {
     "fp_workspace_bytes": (_sz, [_i64, _i64, _i32, _i32]),
     "fp_closure_exact": (_i32, [_vp, _i32, _i64, _vp, _i64, _vp, ctypes.POINTER(Params), _i32,
                                 _vp, _vp, _vp, _vp, _sz, _vp]),
-    "fp_moments": (_i32, [_vp, _i32, _i64, _vp, _i64, _i32, _vp, _vp]),
+    "fp_moments": (_i32, [_vp, _i32, _i64, _vp, _i64, _i32, _vp, _vp, _vp]),
     "fp_closure_solve": (_i32, [_vp, _vp, _i64, ctypes.POINTER(Params), _i32, _vp, _vp, _vp, _vp]),
-    "fp_velocity_update": (_i32, [_vp, _vp, _i32, _i64, _vp, _i64, _vp, _vp, _vp, _dbl, ctypes.POINTER(Params),
-                                  _vp, _u64, _u64, _vp, _vp, _vp]),
+    "fp_velocity_update": (_i32, [_vp, _vp, _i32, _i64, _vp, _i64, _vp, _vp, _vp, _vp, _dbl,
+                                  ctypes.POINTER(Params), _vp, _u64, _u64, _vp, _vp, _vp]),
     "fp_closure_backward": (_i32, [_vp, _i32, _i64, _vp, _i64, _vp, ctypes.POINTER(Params), _vp, _vp, _vp, _vp,
                                    _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "fp_mlp_param_count": (_i64, []),
@@ -184,6 +185,7 @@ class HostStep:
         self.d_offsets = torch.empty(n_cells + 1, dtype=torch.int64, device=dev)
         self.d_tau = torch.empty(n_cells, **f64)
         self.moments = torch.empty((n_cells, NMOM), **f64)
+        self.m6 = torch.empty(n_cells, **f64)
         self.coeffs = torch.empty((n_cells, NCOEF), **f64)
         self.flags = torch.empty(n_cells, dtype=torch.int32, device=dev)
         self.flags_v = torch.empty_like(self.flags)
@@ -217,6 +219,7 @@ class HostStep:
         io.d_v, io.d_v_out = self.d_v.data_ptr(), self.d_v_out.data_ptr()
         io.d_offsets, io.d_tau = self.d_offsets.data_ptr(), self.d_tau.data_ptr()
         io.d_moments, io.d_coeffs = self.moments.data_ptr(), self.coeffs.data_ptr()
+        io.d_m6 = self.m6.data_ptr()
         io.d_flags, io.d_flags_v = self.flags.data_ptr(), self.flags_v.data_ptr()
         net = None
         if self.surrogate is not None:
@@ -338,15 +341,18 @@ def fp_closure_exact(v, offsets, tau, params: Params | None = None, prec="fp32",
     return moments_out, coeffs_out, flags_out
 
 
-def fp_moments(v, offsets, prec="fp32", moments_out=None, stream=None):
-    """Per-cell moment vectors [n_cells, 30] (f64)."""
+def fp_moments(v, offsets, prec="fp32", moments_out=None, stream=None, m6_out=None):
+    """Per-cell moment vectors [n_cells, 30] (f64); m6_out (float64
+    [n_cells], optional) receives <|c|^6> for a one-pass velocity update."""
     n_cells = offsets.numel() - 1
     n_p = v.shape[-1] if v.dim() == 2 else v.numel() // 3
     if moments_out is None:
         moments_out = torch.empty((n_cells, NMOM), dtype=torch.float64, device=offsets.device)
-    _need_cuda(v, offsets, moments_out)
+    _need_cuda(v, offsets, moments_out, m6_out)
+    if m6_out is not None and (m6_out.dtype != torch.float64 or m6_out.numel() < n_cells):
+        raise FPError("m6_out must be float64 with one entry per cell")
     rc = lib().fp_moments(_ptr(v), _vdtype(v), n_p, _ptr(offsets), n_cells, _PREC.get(prec, prec),
-                          _ptr(moments_out), _stream(stream))
+                          _ptr(moments_out), _ptr(m6_out), _stream(stream))
     _check(rc, "fp_moments")
     return moments_out
 
@@ -354,8 +360,8 @@ def fp_moments(v, offsets, prec="fp32", moments_out=None, stream=None):
 def fp_closure_solve(moments, tau, params: Params | None = None, prec="fp32", coeffs_out=None, flags_out=None,
                      stream=None, lu_out=None):
     """Assembly + pivoted FP64 solve from moment vectors -> (coeffs, flags).
-    lu_out: [n_cells, LU_STRIDE] float64 receiving the factors the adjoint
-    can reuse (fp_closure_backward(lu=...))."""
+    lu_out: float64 of lu_doubles(n_cells) entries receiving the factors
+    the adjoint can reuse (fp_closure_backward(lu=...)), tiled by 32 cells."""
     n_cells = moments.shape[0]
     dev = moments.device
     if coeffs_out is None:
@@ -373,13 +379,15 @@ def fp_closure_solve(moments, tau, params: Params | None = None, prec="fp32", co
 
 
 def fp_velocity_update(v, offsets, moments, coeffs, tau, flags, dt, params: Params | None = None, xi=None,
-                       seed=0, step=0, alpha_out=None, stream=None, v_out=None):
+                       seed=0, step=0, alpha_out=None, stream=None, v_out=None, m6=None):
     """One velocity update (Eqs. update_vel / update_N / update_alpha), in
     place or into v_out (same shape and dtype, not overlapping v).  flags is
-    read and updated; returns (updated velocities, alpha_out, flags)."""
+    read and updated; returns (updated velocities, alpha_out, flags).  With
+    m6 (fp_moments' m6_out of the same velocities) the particles are read
+    once."""
     n_cells = offsets.numel() - 1
     n_p = v.shape[-1] if v.dim() == 2 else v.numel() // 3
-    _need_cuda(v, offsets, moments, coeffs, tau, flags, xi, alpha_out, v_out)
+    _need_cuda(v, offsets, moments, coeffs, tau, flags, xi, alpha_out, v_out, m6)
     if v_out is not None and (v_out.dtype != v.dtype or v_out.numel() != v.numel() or not v_out.is_contiguous()):
         raise FPError("v_out must be a contiguous array of v's shape and dtype")
     if xi is not None and xi.dtype != v.dtype:
@@ -388,6 +396,7 @@ def fp_velocity_update(v, offsets, moments, coeffs, tau, flags, dt, params: Para
         raise FPError("flags must be int32")
     p = params if params is not None else default_params()
     rc = lib().fp_velocity_update(_ptr(v), _ptr(v_out), _vdtype(v), n_p, _ptr(offsets), n_cells, _ptr(moments),
+                                  _ptr(m6),
                                   _ptr(coeffs), _ptr(tau), float(dt), ctypes.byref(p), _ptr(xi), int(seed), int(step),
                                   _ptr(alpha_out), _ptr(flags), _stream(stream))
     _check(rc, "fp_velocity_update")

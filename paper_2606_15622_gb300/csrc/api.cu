@@ -8,12 +8,13 @@
 
 namespace fpc {
 void launch_gather(const void *v, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, int prec,
-                   double *mom, cudaStream_t st);
+                   double *mom, double *m6, cudaStream_t st);
 void launch_solve(const double *mom, const double *tau, int64_t n_cells, const fp_params &p, int prec,
                   double *coeffs, int32_t *flags, double *lu, cudaStream_t st);
 void launch_velocity(const void *v, void *v_out, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells,
-                     const double *mom, const double *coeffs, const double *tau, double dt, double eps2_hat,
-                     const void *xi, uint64_t seed, uint64_t step, double *alpha_out, int32_t *flags, cudaStream_t st);
+                     const double *mom, const double *m6, const double *coeffs, const double *tau, double dt,
+                     double eps2_hat, const void *xi, uint64_t seed, uint64_t step, double *alpha_out,
+                     int32_t *flags, cudaStream_t st);
 void launch_adjoint(const void *v, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, const double *tau,
                     double eps2_hat, const double *mom, const double *coeffs, const int32_t *flags, const double *lu,
                     const double *gY, const double *gm_in, double *gm_out, void *gv, cudaStream_t st);
@@ -141,14 +142,14 @@ int fp_closure_exact(const void *v, int v_dtype, int64_t n_particles, const int6
     mom = (double *)ws;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  fpc::launch_gather(v, v_dtype, n_particles, cell_offsets, n_cells, prec, mom, st);
+  fpc::launch_gather(v, v_dtype, n_particles, cell_offsets, n_cells, prec, mom, nullptr, st);
   if (int rc = check_launch("gather")) return rc;
   fpc::launch_solve(mom, tau, n_cells, prm, prec, coeffs_out, flags_out, nullptr, st);
   return check_launch("solve");
 }
 
 int fp_moments(const void *v, int v_dtype, int64_t n_particles, const int64_t *cell_offsets, int64_t n_cells,
-               int prec, double *moments_out, fp_stream_t stream) {
+               int prec, double *moments_out, double *m6_out, fp_stream_t stream) {
   g_err[0] = 0;
   if (n_cells < 0 || n_particles < 0) return fail(FP_ERR_ARG, "negative size");
   if (n_cells == 0) return FP_OK;
@@ -156,7 +157,8 @@ int fp_moments(const void *v, int v_dtype, int64_t n_particles, const int64_t *c
   if (prec != FP_PREC_FP64 && prec != FP_PREC_FP32_MOMENTS) return fail(FP_ERR_ARG, "prec %d", prec);
   if (!cell_offsets || !moments_out) return fail(FP_ERR_ARG, "null array pointer");
   if (n_particles > 0 && !v) return fail(FP_ERR_ARG, "null velocity pointer");
-  fpc::launch_gather(v, v_dtype, n_particles, cell_offsets, n_cells, prec, moments_out, (cudaStream_t)stream);
+  fpc::launch_gather(v, v_dtype, n_particles, cell_offsets, n_cells, prec, moments_out, m6_out,
+                     (cudaStream_t)stream);
   return check_launch("gather");
 }
 
@@ -176,9 +178,9 @@ int fp_closure_solve(const double *moments, const double *tau, int64_t n_cells, 
 }
 
 int fp_velocity_update(void *v, void *v_out, int v_dtype, int64_t n_particles, const int64_t *cell_offsets,
-                       int64_t n_cells, const double *moments, const double *coeffs, const double *tau, double dt,
-                       const fp_params *p, const void *xi, uint64_t seed, uint64_t step, double *alpha_out,
-                       int32_t *flags, fp_stream_t stream) {
+                       int64_t n_cells, const double *moments, const double *m6, const double *coeffs,
+                       const double *tau, double dt, const fp_params *p, const void *xi, uint64_t seed,
+                       uint64_t step, double *alpha_out, int32_t *flags, fp_stream_t stream) {
   g_err[0] = 0;
   if (n_cells < 0 || n_particles < 0) return fail(FP_ERR_ARG, "negative size");
   if (n_cells == 0) return FP_OK;
@@ -194,8 +196,8 @@ int fp_velocity_update(void *v, void *v_out, int v_dtype, int64_t n_particles, c
   fp_params prm;
   fp_default_params(&prm);
   if (p) prm = *p;
-  fpc::launch_velocity(v, v_out ? v_out : v, v_dtype, n_particles, cell_offsets, n_cells, moments, coeffs, tau, dt,
-                       prm.eps2_hat, xi, seed, step, alpha_out, flags, (cudaStream_t)stream);
+  fpc::launch_velocity(v, v_out ? v_out : v, v_dtype, n_particles, cell_offsets, n_cells, moments, m6, coeffs, tau,
+                       dt, prm.eps2_hat, xi, seed, step, alpha_out, flags, (cudaStream_t)stream);
   return check_launch("velocity");
 }
 

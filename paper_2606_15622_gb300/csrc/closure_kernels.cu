@@ -5,7 +5,8 @@
 // cells.  Each group makes two passes over its cell's particles (contiguous,
 // coalesced loads of the SoA arrays):
 //   pass A  mean offset m and spread from the first particle v0;
-//   pass B  the 25 central sums (u_ij, u_ijk, |c|^2 c_i c_j, |c|^4 c_i).
+//   pass B  the 25 central sums (u_ij, u_ijk, |c|^2 c_i c_j, |c|^4 c_i) and
+//           <|c|^6> (which the velocity update's <N.N> needs).
 // FP32 mode centres on v0 + m and scales by a power of two s ~ 1/sqrt(theta)
 // (exact scaling), accumulates short blocks in FP32 and folds the blocks with
 // two-sum; the group reduction is a compensated reduce-scatter.  FP64 mode
@@ -29,7 +30,7 @@ namespace fpc {
 // ---------------------------------------------------------------------------
 // gather
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void accumulate25(float (&t)[25], float wx, float wy, float wz) {
+__device__ __forceinline__ void accumulate26(float (&t)[kNSum], float wx, float wy, float wz) {
   const float xx = wx * wx, xy = wx * wy, xz = wx * wz, yy = wy * wy, yz = wy * wz, zz = wz * wz;
   t[0] += xx; t[1] += xy; t[2] += xz; t[3] += yy; t[4] += yz; t[5] += zz;
   t[6] = fmaf(xx, wx, t[6]);  t[7] = fmaf(xx, wy, t[7]);   t[8] = fmaf(xx, wz, t[8]);
@@ -41,9 +42,10 @@ __device__ __forceinline__ void accumulate25(float (&t)[25], float wx, float wy,
   t[19] = fmaf(r2, yy, t[19]); t[20] = fmaf(r2, yz, t[20]); t[21] = fmaf(r2, zz, t[21]);
   const float r4 = r2 * r2;
   t[22] = fmaf(r4, wx, t[22]); t[23] = fmaf(r4, wy, t[23]); t[24] = fmaf(r4, wz, t[24]);
+  t[25] = fmaf(r4, r2, t[25]);
 }
 
-__device__ __forceinline__ void accumulate25d(double (&t)[32], double cx, double cy, double cz) {
+__device__ __forceinline__ void accumulate26d(double (&t)[32], double cx, double cy, double cz) {
   const double xx = cx * cx, xy = cx * cy, xz = cx * cz, yy = cy * cy, yz = cy * cz, zz = cz * cz;
   t[0] += xx; t[1] += xy; t[2] += xz; t[3] += yy; t[4] += yz; t[5] += zz;
   t[6] = fma(xx, cx, t[6]);  t[7] = fma(xx, cy, t[7]);   t[8] = fma(xx, cz, t[8]);
@@ -55,17 +57,20 @@ __device__ __forceinline__ void accumulate25d(double (&t)[32], double cx, double
   t[19] = fma(r2, yy, t[19]); t[20] = fma(r2, yz, t[20]); t[21] = fma(r2, zz, t[21]);
   const double r4 = r2 * r2;
   t[22] = fma(r4, cx, t[22]); t[23] = fma(r4, cy, t[23]); t[24] = fma(r4, cz, t[24]);
+  t[25] = fma(r4, r2, t[25]);
 }
 
 template <typename VT>
 __device__ __forceinline__ float as_f32(VT x) { return (float)x; }
 
-// Lane-held slots -> moments[5 + q]; lane lg of the group owns slots
-// [lg*K, lg*K + K).  theta needs u11, u22, u33 (slots 0, 3, 5): fetched from
-// their owners by shuffles executed by every lane.
+// Lane-held slots -> moments[5 + q] (q < 25) and m6[c] (q = 25, if m6 is
+// given); lane lg of the group owns slots [lg*K, lg*K + K).  theta needs u11,
+// u22, u33 (slots 0, 3, 5): fetched from their owners by shuffles executed by
+// every lane.
 template <int G>
 __device__ __forceinline__ void store_moments(double (&val)[32 / G], bool valid, int lane, int64_t c, int n,
-                                              double U0, double U1, double U2, double *__restrict__ mom) {
+                                              double U0, double U1, double U2, double *__restrict__ mom,
+                                              double *__restrict__ m6) {
   constexpr int K = 32 / G;
   const int lg = lane & (G - 1);
   const int gbase = lane & ~(G - 1);
@@ -77,7 +82,8 @@ __device__ __forceinline__ void store_moments(double (&val)[32 / G], bool valid,
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     const int q = lg * K + j;
-    if (q < kNSum) mo[kU2 + q] = val[j];
+    if (q < kNMomSum) mo[kU2 + q] = val[j];
+    if (q == kM6Sum && m6) m6[c] = val[j];
   }
   if (lg == 0) {
     mo[kN] = (double)n;
@@ -91,7 +97,7 @@ __device__ __forceinline__ void store_moments(double (&val)[32 / G], bool valid,
 template <typename VT, int G>
 __global__ void __launch_bounds__(256) gather_fp32_kernel(const VT *__restrict__ v, int64_t np,
                                                           const int64_t *__restrict__ off, int64_t n_cells,
-                                                          double *__restrict__ mom) {
+                                                          double *__restrict__ mom, double *__restrict__ m6) {
   constexpr int GPW = 32 / G;
   constexpr int K = 32 / G;
   constexpr int BLK = 8;  // particles per lane accumulated plainly before a two-sum fold
@@ -157,9 +163,9 @@ __global__ void __launch_bounds__(256) gather_fp32_kernel(const VT *__restrict__
       lo[q] = 0.f;
     }
     for (int it0 = 0; it0 < itmax; it0 += BLK) {
-      float t[25];
+      float t[kNSum];
 #pragma unroll
-      for (int q = 0; q < 25; ++q) t[q] = 0.f;
+      for (int q = 0; q < kNSum; ++q) t[q] = 0.f;
       const int itend = min(it0 + BLK, itmax);
       for (int it = it0; it < itend; ++it) {
         const int64_t p = a + (int64_t)it * G + lg;
@@ -167,15 +173,15 @@ __global__ void __launch_bounds__(256) gather_fp32_kernel(const VT *__restrict__
           const float wx = ((as_f32(ldg_v(vx + p)) - v0x) - mx) * s;
           const float wy = ((as_f32(ldg_v(vy + p)) - v0y) - my) * s;
           const float wz = ((as_f32(ldg_v(vz + p)) - v0z) - mz) * s;
-          accumulate25(t, wx, wy, wz);
+          accumulate26(t, wx, wy, wz);
         }
       }
       if (it0 == 0) {
 #pragma unroll
-        for (int q = 0; q < 25; ++q) hi[q] = t[q];
+        for (int q = 0; q < kNSum; ++q) hi[q] = t[q];
       } else {
 #pragma unroll
-        for (int q = 0; q < 25; ++q) {
+        for (int q = 0; q < kNSum; ++q) {
           float sum, err;
           two_sum(hi[q], t[q], sum, err);
           hi[q] = sum;
@@ -196,14 +202,14 @@ __global__ void __launch_bounds__(256) gather_fp32_kernel(const VT *__restrict__
       val[j] = ((double)hi[j] + (double)lo[j]) * fac;
     }
     const double U0 = (double)v0x + (double)mx, U1 = (double)v0y + (double)my, U2 = (double)v0z + (double)mz;
-    store_moments<G>(val, valid, lane, c, n, U0, U1, U2, mom);
+    store_moments<G>(val, valid, lane, c, n, U0, U1, U2, mom, m6);
   }
 }
 
 template <typename VT, int G>
 __global__ void __launch_bounds__(256) gather_fp64_kernel(const VT *__restrict__ v, int64_t np,
                                                           const int64_t *__restrict__ off, int64_t n_cells,
-                                                          double *__restrict__ mom) {
+                                                          double *__restrict__ mom, double *__restrict__ m6) {
   constexpr int GPW = 32 / G;
   constexpr int K = 32 / G;
   const int lane = threadIdx.x & 31;
@@ -243,13 +249,13 @@ __global__ void __launch_bounds__(256) gather_fp64_kernel(const VT *__restrict__
     for (int it = 0; it < itmax; ++it) {
       const int64_t p = a + (int64_t)it * G + lg;
       if (p < e)
-        accumulate25d(t, (double)ldg_v(vx + p) - Ux, (double)ldg_v(vy + p) - Uy, (double)ldg_v(vz + p) - Uz);
+        accumulate26d(t, (double)ldg_v(vx + p) - Ux, (double)ldg_v(vy + p) - Uy, (double)ldg_v(vz + p) - Uz);
     }
     group_reduce_scatter<G>(t, lane);
     double val[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) val[j] = t[j] * inv_nd;
-    store_moments<G>(val, valid, lane, c, n, Ux, Uy, Uz, mom);
+    store_moments<G>(val, valid, lane, c, n, Ux, Uy, Uz, mom, m6);
   }
 }
 
@@ -292,7 +298,7 @@ static int sm_count() {
 
 template <int G>
 static void launch_gather_t(const void *v, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, int prec,
-                            double *mom, cudaStream_t st) {
+                            double *mom, double *m6, cudaStream_t st) {
   const int threads = 256;
   const int64_t groups_per_block = (threads / 32) * (32 / G);
   int64_t blocks = (n_cells + groups_per_block - 1) / groups_per_block;
@@ -301,28 +307,30 @@ static void launch_gather_t(const void *v, int v_dtype, int64_t np, const int64_
   if (blocks < 1) blocks = 1;
   if (prec == FP_PREC_FP32_MOMENTS) {
     if (v_dtype == FP_V_F32)
-      gather_fp32_kernel<float, G><<<(unsigned)blocks, threads, 0, st>>>((const float *)v, np, off, n_cells, mom);
+      gather_fp32_kernel<float, G><<<(unsigned)blocks, threads, 0, st>>>((const float *)v, np, off, n_cells, mom, m6);
     else
-      gather_fp32_kernel<double, G><<<(unsigned)blocks, threads, 0, st>>>((const double *)v, np, off, n_cells, mom);
+      gather_fp32_kernel<double, G><<<(unsigned)blocks, threads, 0, st>>>((const double *)v, np, off, n_cells, mom,
+                                                                          m6);
   } else {
     if (v_dtype == FP_V_F32)
-      gather_fp64_kernel<float, G><<<(unsigned)blocks, threads, 0, st>>>((const float *)v, np, off, n_cells, mom);
+      gather_fp64_kernel<float, G><<<(unsigned)blocks, threads, 0, st>>>((const float *)v, np, off, n_cells, mom, m6);
     else
-      gather_fp64_kernel<double, G><<<(unsigned)blocks, threads, 0, st>>>((const double *)v, np, off, n_cells, mom);
+      gather_fp64_kernel<double, G><<<(unsigned)blocks, threads, 0, st>>>((const double *)v, np, off, n_cells, mom,
+                                                                          m6);
   }
 }
 
-bool launch_gather_tile(const float *v, int64_t np, const int64_t *off, int64_t n_cells, double *mom,
+bool launch_gather_tile(const float *v, int64_t np, const int64_t *off, int64_t n_cells, double *mom, double *m6,
                         cudaStream_t st, int sm_count);
 
 void launch_gather(const void *v, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, int prec,
-                   double *mom, cudaStream_t st) {
+                   double *mom, double *m6, cudaStream_t st) {
   // FP32 moments of FP32 velocities: shared-memory staged tiles (16-byte
   // aligned velocity arrays); every other combination: direct loads.
   if (prec == FP_PREC_FP32_MOMENTS && v_dtype == FP_V_F32 &&
-      launch_gather_tile((const float *)v, np, off, n_cells, mom, st, sm_count()))
+      launch_gather_tile((const float *)v, np, off, n_cells, mom, m6, st, sm_count()))
     return;
-  launch_gather_t<8>(v, v_dtype, np, off, n_cells, prec, mom, st);
+  launch_gather_t<8>(v, v_dtype, np, off, n_cells, prec, mom, m6, st);
 }
 
 void launch_solve(const double *mom, const double *tau, int64_t n_cells, const fp_params &p, int prec,

@@ -10,7 +10,9 @@ namespace fpc {
 
 // moment slots (layout documented in fpclosure.h)
 constexpr int kN = 0, kU = 1, kTheta = 4, kU2 = 5, kU3 = 11, kW = 21, kZ = 27;
-constexpr int kNSum = 25;  // gathered central sums: u2 (6), u3 (10), w (6), z (3)
+constexpr int kNSum = 26;   // gathered central sums: u2 (6), u3 (10), w (6), z (3), <|c|^6> (1)
+constexpr int kNMomSum = 25;  // of those, the ones stored in the moment vector (from slot kU2)
+constexpr int kM6Sum = 25;    // the sum slot of <|c|^6> (its own optional output array)
 
 // Error-free transformation a + b = s + e (Knuth two-sum).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
@@ -19,8 +21,10 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
-// Order of the central moment held in gathered sum slot q (0..24).
-__host__ __device__ constexpr int sum_order(int q) { return q < 6 ? 2 : (q < 16 ? 3 : (q < 22 ? 4 : 5)); }
+// Order of the central moment held in gathered sum slot q (0..25).
+__host__ __device__ constexpr int sum_order(int q) {
+  return q < 6 ? 2 : (q < 16 ? 3 : (q < 22 ? 4 : (q < 25 ? 5 : 6)));
+}
 
 // Butterfly all-reduce over groups of G consecutive lanes (all 32 lanes call).
 template <int G, typename T>

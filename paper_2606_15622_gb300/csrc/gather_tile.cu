@@ -53,7 +53,8 @@ struct SlotMeta {
 // point at the cell's first particle (shared or global memory).
 template <bool kShared>
 __device__ __forceinline__ void reduce_cells(bool valid, int n, const float *px, const float *py, const float *pz,
-                                             int64_t c, double *__restrict__ mom, int lane) {
+                                             int64_t c, double *__restrict__ mom, double *__restrict__ m6,
+                                             int lane) {
   constexpr int G = kTileG;
   constexpr int K = 32 / G;
   constexpr int BLK = 32;  // particles per lane summed plainly before a two-sum fold
@@ -114,9 +115,9 @@ __device__ __forceinline__ void reduce_cells(bool valid, int n, const float *px,
     lo[q] = 0.f;
   }
   for (int it0 = 0; it0 < itmax; it0 += BLK) {
-    float t[25];
+    float t[kNSum];
 #pragma unroll
-    for (int q = 0; q < 25; ++q) t[q] = 0.f;
+    for (int q = 0; q < kNSum; ++q) t[q] = 0.f;
     const int itend = min(it0 + BLK, itmax);
     for (int it = it0; it < itend; ++it) {
       const int i = it * G + lg;
@@ -137,13 +138,14 @@ __device__ __forceinline__ void reduce_cells(bool valid, int n, const float *px,
       t[19] = fmaf(r2, yy, t[19]); t[20] = fmaf(r2, yz, t[20]); t[21] = fmaf(r2, zz, t[21]);
       const float r4 = r2 * r2;
       t[22] = fmaf(r4, wx, t[22]); t[23] = fmaf(r4, wy, t[23]); t[24] = fmaf(r4, wz, t[24]);
+      t[25] = fmaf(r4, r2, t[25]);
     }
     if (it0 == 0) {
 #pragma unroll
-      for (int q = 0; q < 25; ++q) hi[q] = t[q];
+      for (int q = 0; q < kNSum; ++q) hi[q] = t[q];
     } else {
 #pragma unroll
-      for (int q = 0; q < 25; ++q) {
+      for (int q = 0; q < kNSum; ++q) {
         float sum, err;
         two_sum(hi[q], t[q], sum, err);
         hi[q] = sum;
@@ -175,7 +177,8 @@ __device__ __forceinline__ void reduce_cells(bool valid, int n, const float *px,
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     const int q = lg * K + j;
-    if (q < kNSum) mo[kU2 + q] = val[j];
+    if (q < kNMomSum) mo[kU2 + q] = val[j];
+    if (q == kM6Sum && m6) m6[c] = val[j];
   }
   if (lg >= 1 && lg <= 3) {
     const float v0 = lg == 1 ? v0x : (lg == 2 ? v0y : v0z);
@@ -232,7 +235,7 @@ __device__ __forceinline__ void rank_cells(int ncell, int na, int nb, uint8_t *o
 
 __global__ void __launch_bounds__(kTileThreads, 2)
     gather_tile_kernel(const float *__restrict__ v, int64_t np, const int64_t *__restrict__ off, int64_t n_cells,
-                       double *__restrict__ mom, int64_t n_chunks) {
+                       double *__restrict__ mom, double *__restrict__ m6, int64_t n_chunks) {
   extern __shared__ __align__(128) float slot_buf[];
   __shared__ __align__(8) uint64_t full_bar[kSlots], empty_bar[kSlots];
   __shared__ SlotMeta meta[kSlots];
@@ -420,11 +423,11 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         const int64_t a = M.offs[rc];
         const int n = valid ? (int)(M.offs[rc + 1] - a) : 0;
         if (M.big) {
-          reduce_cells<false>(valid, n, v + a, v + np + a, v + 2 * np + a, c, mom, lane);
+          reduce_cells<false>(valid, n, v + a, v + np + a, v + 2 * np + a, c, mom, m6, lane);
         } else {
           const int64_t rel = a - M.pa;
           reduce_cells<true>(valid, n, bx + M.lead[0] + rel, bx + kCapF + M.lead[1] + rel,
-                             bx + 2 * kCapF + M.lead[2] + rel, c, mom, lane);
+                             bx + 2 * kCapF + M.lead[2] + rel, c, mom, m6, lane);
         }
       }
       __syncwarp();
@@ -438,7 +441,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
 
 static int g_tile_attr_done[64];
 
-bool launch_gather_tile(const float *v, int64_t np, const int64_t *off, int64_t n_cells, double *mom,
+bool launch_gather_tile(const float *v, int64_t np, const int64_t *off, int64_t n_cells, double *mom, double *m6,
                         cudaStream_t st, int sm_count) {
   if (((uintptr_t)v & 15) != 0) return false;
   int dev = 0;
@@ -453,7 +456,7 @@ bool launch_gather_tile(const float *v, int64_t np, const int64_t *off, int64_t 
   int64_t grid = (int64_t)sm_count * 2;
   if (grid > n_chunks) grid = n_chunks;
   if (grid < 1) grid = 1;
-  gather_tile_kernel<<<(unsigned)grid, kTileThreads, kTileSmem, st>>>(v, np, off, n_cells, mom, n_chunks);
+  gather_tile_kernel<<<(unsigned)grid, kTileThreads, kTileSmem, st>>>(v, np, off, n_cells, mom, m6, n_chunks);
   return true;
 }
 

@@ -23,7 +23,7 @@
 
 namespace fpc {
 void launch_gather(const void *v, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, int prec,
-                   double *mom, cudaStream_t st);
+                   double *mom, double *m6, cudaStream_t st);
 void launch_solve(const double *mom, const double *tau, int64_t n_cells, const fp_params &p, int prec,
                   double *coeffs, int32_t *flags, double *lu, cudaStream_t st);
 }  // namespace fpc
@@ -90,7 +90,7 @@ int fp_closure_exact_static(const void *v, int v_dtype, int64_t n_particles, con
   const cudaStream_t st = (cudaStream_t)stream;
   // the gather writes every slot of cells [0, n_cells) before the solve
   // reads them, so the scratch needs no clearing between calls
-  fpc::launch_gather(v, v_dtype, n_particles, cell_offsets, n_cells, prec, scratch, st);
+  fpc::launch_gather(v, v_dtype, n_particles, cell_offsets, n_cells, prec, scratch, nullptr, st);
   fpc::launch_solve(scratch, tau, n_cells, prm, prec, coeffs_out, flags_out, nullptr, st);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return static_fail(FP_ERR_CUDA, cudaGetErrorString(e));

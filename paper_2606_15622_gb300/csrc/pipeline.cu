@@ -156,7 +156,8 @@ int fp_step_host(fp_pipeline *pl, const fp_step_io *io, int v_dtype, int64_t n_p
     // ---- closure ----
     cudaStreamWaitEvent(pl->main, pl->ev_h2d[k], 0);
     double *mom = io->d_moments + c0 * FP_NMOM;
-    if ((rc = fp_moments(io->d_v, v_dtype, n_particles, io->d_offsets + c0, nc, prec, mom, pl->main))) break;
+    double *m6 = io->d_m6 ? io->d_m6 + c0 : nullptr;
+    if ((rc = fp_moments(io->d_v, v_dtype, n_particles, io->d_offsets + c0, nc, prec, mom, m6, pl->main))) break;
     double *lu = io->d_lu ? io->d_lu + (c0 / 32) * 32 * FP_LU_STRIDE : nullptr;
     if ((rc = fp_closure_solve(mom, io->d_tau + c0, nc, p, prec, io->d_coeffs + c0 * 9, io->d_flags + c0,
                                io->d_grad_coeffs ? lu : nullptr, pl->main)))
@@ -172,7 +173,7 @@ int fp_step_host(fp_pipeline *pl, const fp_step_io *io, int v_dtype, int64_t n_p
     cudaStreamWaitEvent(pl->vel, pl->ev_solve[k], 0);
     cudaMemcpyAsync(io->d_flags_v + c0, io->d_flags + c0, (size_t)nc * sizeof(int32_t), cudaMemcpyDeviceToDevice,
                     pl->vel);
-    if ((rc = fp_velocity_update(io->d_v, io->d_v_out, v_dtype, n_particles, io->d_offsets + c0, nc, mom,
+    if ((rc = fp_velocity_update(io->d_v, io->d_v_out, v_dtype, n_particles, io->d_offsets + c0, nc, mom, m6,
                                  io->d_coeffs + c0 * 9, io->d_tau + c0, dt, p, nullptr, seed, step, nullptr,
                                  io->d_flags_v + c0, pl->vel)))
       break;

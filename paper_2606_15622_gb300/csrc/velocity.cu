@@ -82,10 +82,48 @@ __device__ __forceinline__ void drift(const T *K, T m0, T m1, T m2, T &n0, T &n1
 
 // v and vout may be the same array (in-place update): every particle is read
 // before it is written, by the same lane.
-template <typename VT>
+// Cell averages of N.N and M'.N (Eq. update_N; M' = c = v - U, <c> = 0) in
+// closed form from the central moments, with A = C + I/tau (vals[VC..]),
+// Gamma, b, theta and eps^2 from the constant table:
+//   <M'.N> = tr(A u) + Gamma.b - eps^2 s4
+//   <N.N>  = tr(A^2 u) + |Gamma|^2 (s4 - 9 theta^2) + eps^4 (m6 - |b|^2)
+//            + 2 Gamma.A b - 2 eps^2 tr(A w) - 2 eps^2 Gamma.(z - 3 theta b)
+// (u_ij = <c_i c_j>, w_ij = <|c|^2 c_i c_j>, z_i = <|c|^4 c_i>, s4 = tr w,
+// m6 = <|c|^6>, b_i = <|c|^2 c_i>); symmetric tensors in sym2 slot order.
+template <typename T>
+__device__ __forceinline__ void cell_drift_averages(const T (&vals)[kVConst], const T (&u)[6], const T (&w)[6],
+                                                    const T (&z)[3], T m6, T &nn, T &mn) {
+  const T A[6] = {vals[VC00], vals[VC01], vals[VC02], vals[VC11], vals[VC12], vals[VC22]};
+  const T G[3] = {vals[VG0], vals[VG1], vals[VG2]};
+  const T b[3] = {vals[VB0], vals[VB1], vals[VB2]};
+  const T th = vals[VTH], e2 = vals[VEPS];
+  auto tr = [](const T (&X)[6], const T (&Y)[6]) -> T {  // sum_ij X_ij Y_ij
+    return X[0] * Y[0] + X[3] * Y[3] + X[5] * Y[5] + T(2) * (X[1] * Y[1] + X[2] * Y[2] + X[4] * Y[4]);
+  };
+  // A^2 (symmetric)
+  const T A2[6] = {A[0] * A[0] + A[1] * A[1] + A[2] * A[2], A[0] * A[1] + A[1] * A[3] + A[2] * A[4],
+                   A[0] * A[2] + A[1] * A[4] + A[2] * A[5], A[1] * A[1] + A[3] * A[3] + A[4] * A[4],
+                   A[1] * A[2] + A[3] * A[4] + A[4] * A[5], A[2] * A[2] + A[4] * A[4] + A[5] * A[5]};
+  const T Ab[3] = {A[0] * b[0] + A[1] * b[1] + A[2] * b[2], A[1] * b[0] + A[3] * b[1] + A[4] * b[2],
+                   A[2] * b[0] + A[4] * b[1] + A[5] * b[2]};
+  const T s4 = w[0] + w[3] + w[5];
+  const T gb = G[0] * b[0] + G[1] * b[1] + G[2] * b[2];
+  const T gg = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+  const T bb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+  const T gAb = G[0] * Ab[0] + G[1] * Ab[1] + G[2] * Ab[2];
+  const T gz = G[0] * z[0] + G[1] * z[1] + G[2] * z[2];
+  mn = tr(A, u) + gb - e2 * s4;
+  nn = tr(A2, u) + gg * (s4 - T(9) * th * th) + e2 * e2 * (m6 - bb) + T(2) * gAb - T(2) * e2 * tr(A, w) -
+       T(2) * e2 * (gz - T(3) * th * gb);
+}
+
+// With kOnePass the cell averages <N.N> and <M'.N> come from the moments (and
+// m6 = <|c|^6>) in closed form, so the particles are read once.
+template <typename VT, bool kOnePass>
 __global__ void __launch_bounds__(32 * kVWarps) velocity_kernel(const VT *v, VT *vout, int64_t np,
                                                                 const int64_t *__restrict__ off, int64_t n_cells,
                                                                 const double *__restrict__ mom,
+                                                                const double *__restrict__ m6,
                                                                 const double *__restrict__ coeffs,
                                                                 const double *__restrict__ tau, VelParams prm,
                                                                 const VT *__restrict__ xi,
@@ -134,6 +172,7 @@ __global__ void __launch_bounds__(32 * kVWarps) velocity_kernel(const VT *v, VT 
       return __shfl_sync(0xffffffffu, cv[slot / kVG], (lane & ~(kVG - 1)) + slot % kVG);
     };
     const bool linear = (fl & (FP_FLAG_FEW | FP_FLAG_SINGULAR | FP_FLAG_NONFINITE)) != 0;
+    T nn_mom = 0, mn_mom = 0;  // one-pass: <N.N>, <M'.N> from the moments
     {
       const T th = cst(3), tc = cst(23);
       const T itau = T(1) / tc;
@@ -158,6 +197,38 @@ __global__ void __launch_bounds__(32 * kVWarps) velocity_kernel(const VT *v, VT 
 #pragma unroll
         for (int q = 0; q < kVConst; ++q) tab[g][q] = vals[q];
       }
+      if (kOnePass) {
+        // lane lg also converts u_ij (slots 0..5), w_ij (6..11), z_i (12..14)
+        // and <|c|^6> (15) as slots lg and lg + 8
+        T cw[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int slot = lg + k * kVG;
+          double x = 0.0;
+          if (valid) {
+            if (slot < 6)
+              x = mom[c * FP_NMOM + kU2 + slot];
+            else if (slot < 12)
+              x = mom[c * FP_NMOM + kW + (slot - 6)];
+            else if (slot < 15)
+              x = mom[c * FP_NMOM + kZ + (slot - 12)];
+            else
+              x = m6[c];
+          }
+          cw[k] = (T)x;
+        }
+        auto cm = [&](int slot) -> T {
+          return __shfl_sync(0xffffffffu, cw[slot / kVG], (lane & ~(kVG - 1)) + slot % kVG);
+        };
+        T u[6], w[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          u[q] = cm(q);
+          w[q] = cm(6 + q);
+        }
+        const T z[3] = {cm(12), cm(13), cm(14)}, m6c = cm(15);
+        cell_drift_averages<T>(vals, u, w, z, m6c, nn_mom, mn_mom);
+      }
     }
     // the warp's contiguous particle range and the inner boundaries,
     // relative to its first particle
@@ -172,7 +243,7 @@ __global__ void __launch_bounds__(32 * kVWarps) velocity_kernel(const VT *v, VT 
     // ---- pass 1: <N.N>, <M'.N> per cell ----
     const unsigned nonlin = __ballot_sync(0xffffffffu, !linear && n > 0 && lg == 0);
     T s_nn[kVCells] = {}, s_mn[kVCells] = {};
-    if (nonlin) {
+    if (!kOnePass && nonlin) {
       // kVBatch particles per lane per round, all loads issued first
       for (int q0 = lane; q0 < i4; q0 += 32 * kVBatch) {
         T mx[kVBatch], my[kVBatch], mz[kVBatch];
@@ -224,7 +295,8 @@ __global__ void __launch_bounds__(32 * kVWarps) velocity_kernel(const VT *v, VT 
       if (valid && !linear && n > 0) {
         const T inv_n = T(1) / T(n);
         const T th = tab[g][VTH], tc = tab[g][VTAU], a = tab[g][VA], om = tab[g][VOMA];
-        const T alpha2 = T(1) + tc / (T(3) * th) * (tc * om * om * (snn * inv_n) + T(2) * (a * om) * (smn * inv_n));
+        const T nn_avg = kOnePass ? nn_mom : snn * inv_n, mn_avg = kOnePass ? mn_mom : smn * inv_n;
+        const T alpha2 = T(1) + tc / (T(3) * th) * (tc * om * om * nn_avg + T(2) * (a * om) * mn_avg);
         if (alpha2 > T(0) && alpha2 < T(INFINITY))
           alpha = sqrt(alpha2);
         else
@@ -297,9 +369,10 @@ static int vel_sm_count() {
   return n;
 }
 
-void launch_velocity(const void *v, void *v_out, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, const double *mom,
-                     const double *coeffs, const double *tau, double dt, double eps2_hat, const void *xi, uint64_t seed,
-                     uint64_t step, double *alpha_out, int32_t *flags, cudaStream_t st) {
+void launch_velocity(const void *v, void *v_out, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells,
+                     const double *mom, const double *m6, const double *coeffs, const double *tau, double dt,
+                     double eps2_hat, const void *xi, uint64_t seed, uint64_t step, double *alpha_out,
+                     int32_t *flags, cudaStream_t st) {
   VelParams prm{dt, eps2_hat, seed, step};
   const int threads = 32 * kVWarps;
   const int64_t cells_per_block = kVWarps * kVCells;
@@ -307,14 +380,22 @@ void launch_velocity(const void *v, void *v_out, int v_dtype, int64_t np, const 
   const int64_t cap = (int64_t)vel_sm_count() * 8;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
-  if (v_dtype == FP_V_F32)
-    velocity_kernel<float><<<(unsigned)blocks, threads, 0, st>>>((const float *)v, (float *)v_out, np, off, n_cells,
-                                                                 mom, coeffs, tau, prm, (const float *)xi, alpha_out,
-                                                                 flags);
-  else
-    velocity_kernel<double><<<(unsigned)blocks, threads, 0, st>>>((const double *)v, (double *)v_out, np, off,
-                                                                  n_cells, mom, coeffs, tau, prm, (const double *)xi,
-                                                                  alpha_out, flags);
+#define FP_VEL_LAUNCH(VT, ONE)                                                                                    \
+  velocity_kernel<VT, ONE><<<(unsigned)blocks, threads, 0, st>>>((const VT *)v, (VT *)v_out, np, off, n_cells, mom, \
+                                                                 m6, coeffs, tau, prm, (const VT *)xi, alpha_out,  \
+                                                                 flags)
+  if (v_dtype == FP_V_F32) {
+    if (m6)
+      FP_VEL_LAUNCH(float, true);
+    else
+      FP_VEL_LAUNCH(float, false);
+  } else {
+    if (m6)
+      FP_VEL_LAUNCH(double, true);
+    else
+      FP_VEL_LAUNCH(double, false);
+  }
+#undef FP_VEL_LAUNCH
 }
 
 }  // namespace fpc

@@ -210,3 +210,24 @@ def test_split_calls_match_fused_call(cavity_pop, prec):
     y2, f2 = api.fp_closure_solve(m2, tau, prec=prec)
     torch.cuda.synchronize()
     assert torch.equal(m1, m2) and torch.equal(y1, y2) and torch.equal(f1, f2)
+
+
+@pytest.mark.parametrize("prec,vdtype,tol", [("fp64", "f64", 1e-12), ("fp32", "f32", 2e-5)])
+def test_speed_moment6_matches_oracle(cavity_pop, prec, vdtype, tol):
+    """<|c|^6> from the gather (fp_moments' m6_out) against its definition."""
+    pop = cavity_pop.subset(np.arange(0, cavity_pop.n_cells, 13))
+    vh = pop.v64 if vdtype == "f64" else pop.v32
+    v = torch.from_numpy(np.ascontiguousarray(vh)).cuda()
+    off = torch.from_numpy(pop.offsets).cuda()
+    m6 = torch.full((pop.n_cells,), np.nan, dtype=torch.float64, device="cuda")
+    mom = api.fp_moments(v, off, prec=prec, m6_out=m6)
+    torch.cuda.synchronize()
+    ref = O.speed_moment6(vh, pop.offsets)
+    got = m6.cpu().numpy()
+    ok = pop.counts > 0
+    assert np.all(np.abs(got[ok] - ref[ok]) <= tol * ref[ok] + 1e-300)
+    assert np.all(got[~ok] == 0)
+    # the moment vector is unchanged by the extra output
+    ref_m = api.fp_moments(v, off, prec=prec)
+    torch.cuda.synchronize()
+    assert torch.equal(mom, ref_m)

@@ -28,11 +28,13 @@ def _reference(pop, v, prec, sur, dt, seed, step):
     dev = v.device
     off, tau = torch.from_numpy(pop.offsets).to(dev), torch.from_numpy(pop.tau).to(dev)
     mom, y, fl = api.fp_closure_exact(v, off, tau, prec=prec)
+    m6 = torch.empty(pop.n_cells, dtype=torch.float64, device=dev)
+    api.fp_moments(v, off, prec=prec, m6_out=m6)  # the pipeline's update reads the particles once
     lu = torch.empty(api.lu_doubles(pop.n_cells), dtype=torch.float64, device=dev)
     api.fp_closure_solve(mom, tau, prec=prec, lu_out=lu)  # the factors the pipeline's adjoint reuses
     fl_v = fl.clone()
     v_out = torch.empty_like(v)
-    api.fp_velocity_update(v, off, mom, y, tau, fl_v, dt, seed=seed, step=step, v_out=v_out)
+    api.fp_velocity_update(v, off, mom, y, tau, fl_v, dt, seed=seed, step=step, v_out=v_out, m6=m6)
     ys, fls = sur.closure(mom, tau, prec=prec)
     gY = torch.ones_like(y)
     gm, gv = api.fp_closure_backward(v, off, tau, mom, y, fl, gY, lu=lu)

@@ -31,13 +31,15 @@ def _oracle_state(pop, vdtype, eps2_hat=O.DEFAULT_EPS2_HAT):
     return v, m, y, fl
 
 
-def _gpu_update(pop, vdtype, m, y, fl, dt, xi=None, seed=0, step=0, eps2_hat=O.DEFAULT_EPS2_HAT):
+def _gpu_update(pop, vdtype, m, y, fl, dt, xi=None, seed=0, step=0, eps2_hat=O.DEFAULT_EPS2_HAT, one_pass=False):
     v = _dev(pop.v64 if vdtype == "f64" else pop.v32)
     x = None if xi is None else _dev(xi.astype(np.float64 if vdtype == "f64" else np.float32))
     alpha = torch.empty(pop.n_cells, dtype=torch.float64, device="cuda")
     flags = _dev(fl.astype(np.int32))
     api.fp_velocity_update(v, _dev(pop.offsets), _dev(m), _dev(y), _dev(pop.tau), flags, dt,
-                           params=api.default_params(eps2_hat=eps2_hat), xi=x, seed=seed, step=step, alpha_out=alpha)
+                           params=api.default_params(eps2_hat=eps2_hat), xi=x, seed=seed, step=step, alpha_out=alpha,
+                           m6=_dev(O.speed_moment6(pop.v64 if vdtype == "f64" else pop.v32, pop.offsets))
+                           if one_pass else None)
     torch.cuda.synchronize()
     return v.cpu().numpy().astype(np.float64), alpha.cpu().numpy(), flags.cpu().numpy()
 
@@ -56,25 +58,27 @@ def _check(pop, vref, aref, fref, vg, ag, fg, vdtype, m, noise_tol=0.0):
     assert np.abs(ag[aok] - aref[aok]).max() <= atol + noise_tol
 
 
+@pytest.mark.parametrize("one_pass", [False, True])
 @pytest.mark.parametrize("vdtype", ["f64", "f32"])
 @pytest.mark.parametrize("dt", [0.05, 0.7])
-def test_update_with_given_variates(cavity_pop, vdtype, dt):
+def test_update_with_given_variates(cavity_pop, vdtype, dt, one_pass):
     pop = cavity_pop.subset(np.arange(0, cavity_pop.n_cells, 5))
     v, m, y, fl = _oracle_state(pop, vdtype, eps2_hat=1e-2)
     xi = np.random.default_rng(1).standard_normal((3, pop.n_particles))
     if vdtype == "f32":
         xi = xi.astype(np.float32).astype(np.float64)
     vref, aref, fref = O.velocity_update(v, pop.offsets, m, y, pop.tau, fl, dt, eps2_hat=1e-2, xi=xi)
-    vg, ag, fg = _gpu_update(pop, vdtype, m, y, fl, dt, xi=xi, eps2_hat=1e-2)
+    vg, ag, fg = _gpu_update(pop, vdtype, m, y, fl, dt, xi=xi, eps2_hat=1e-2, one_pass=one_pass)
     _check(pop, vref, aref, fref, vg, ag, fg, vdtype, m)
 
 
+@pytest.mark.parametrize("one_pass", [False, True])
 @pytest.mark.parametrize("vdtype", ["f64", "f32"])
-def test_update_with_philox_variates(couette_pop, vdtype):
+def test_update_with_philox_variates(couette_pop, vdtype, one_pass):
     pop = couette_pop
     v, m, y, fl = _oracle_state(pop, vdtype)
     vref, aref, fref = O.velocity_update(v, pop.offsets, m, y, pop.tau, fl, 0.3, seed=2024, step=17)
-    vg, ag, fg = _gpu_update(pop, vdtype, m, y, fl, 0.3, seed=2024, step=17)
+    vg, ag, fg = _gpu_update(pop, vdtype, m, y, fl, 0.3, seed=2024, step=17, one_pass=one_pass)
     _check(pop, vref, aref, fref, vg, ag, fg, vdtype, m, noise_tol=2e-6)
 
 
@@ -86,8 +90,10 @@ def test_cylinder_full_size_pipeline_sampled():
     v = _dev(pop.v64)
     off, tau = _dev(pop.offsets), _dev(pop.tau)
     mom, y, fl = api.fp_closure_exact(v, off, tau, prec="fp64")
+    m6 = torch.empty(pop.n_cells, dtype=torch.float64, device="cuda")
+    api.fp_moments(v, off, prec="fp64", m6_out=m6)  # one-pass update: <|c|^6> from the gather
     alpha = torch.empty(pop.n_cells, dtype=torch.float64, device="cuda")
-    api.fp_velocity_update(v, off, mom, y, tau, fl, 0.2, seed=7, step=3, alpha_out=alpha)
+    api.fp_velocity_update(v, off, mom, y, tau, fl, 0.2, seed=7, step=3, alpha_out=alpha, m6=m6)
     torch.cuda.synchronize()
     vg, ag, fg = v.cpu().numpy(), alpha.cpu().numpy(), fl.cpu().numpy()
     rng = np.random.default_rng(5)

@@ -145,3 +145,41 @@ def test_small_step_is_nearly_identity(cavity_pop):
     vn, alpha, _ = O.velocity_update(pop.v64, pop.offsets, m, Y, pop.tau, fl, dt, seed=1, step=1)
     assert np.abs(alpha - 1).max() < 1e-7
     assert np.abs(vn - pop.v64).max() < 1e-3  # noise ~ sqrt(2 theta dt / tau)
+
+
+def test_drift_averages_from_moments_equal_particle_sums(cavity_pop):
+    """The cell averages of Eq. update_alpha in closed form from the moments
+    and <|c|^6> (what a one-pass update uses) against direct sums over the
+    particles of N.N and M'.N, N from Eq. update_N."""
+    pop = cavity_pop.subset(np.arange(0, cavity_pop.n_cells, 331))
+    eps2_hat = 0.05
+    m = O.moments(pop.v64, pop.offsets)
+    y, fl = O.closure(m, pop.tau, eps2_hat=eps2_hat)
+    m6 = O.speed_moment6(pop.v64, pop.offsets)
+    checked = 0
+    for k in np.flatnonzero(fl == 0):
+        a, b = pop.offsets[k], pop.offsets[k + 1]
+        tau, th = pop.tau[k], m[k, O.M_THETA]
+        e2 = eps2_hat / (tau * th)
+        C = np.array([[y[k, O.SYM2.index(tuple(sorted((i, j))))] for j in range(3)] for i in range(3)])
+        A = C + np.eye(3) / tau
+        G = y[k, 6:9]
+        c = pop.v64[:, a:b] - m[k, O.M_U:O.M_U + 3, None]
+        r2 = (c * c).sum(0)
+        u3 = m[k, O.M_U3:O.M_U3 + 10]
+        bvec = np.array([sum(u3[O.SYM3.index(tuple(sorted((i, j, j))))] for j in range(3)) for i in range(3)])
+        N = A @ c + G[:, None] * (r2 - 3 * th) - e2 * (c * r2 - bvec[:, None])
+        nn_p, mn_p = (N * N).sum(0).mean(), (c * N).sum(0).mean()
+        sym = lambda base: np.array([[m[k, base + O.SYM2.index(tuple(sorted((i, j))))] for j in range(3)]
+                                     for i in range(3)])
+        u, w = sym(O.M_U2), sym(O.M_W)
+        z = m[k, O.M_Z:O.M_Z + 3]
+        s4 = np.trace(w)
+        mn_m = np.sum(A * u) + G @ bvec - e2 * s4
+        nn_m = (np.sum((A @ A) * u) + G @ G * (s4 - 9 * th ** 2) + e2 ** 2 * (m6[k] - bvec @ bvec)
+                + 2 * G @ A @ bvec - 2 * e2 * np.sum(A * w) - 2 * e2 * G @ (z - 3 * th * bvec))
+        scale = np.mean((np.abs(A @ c) + np.abs(G[:, None] * r2) + e2 * np.abs(c * r2)).sum(0) ** 2)
+        assert abs(nn_m - nn_p) <= 1e-10 * scale
+        assert abs(mn_m - mn_p) <= 1e-10 * np.sqrt(scale * (r2.mean()))
+        checked += 1
+    assert checked > 20

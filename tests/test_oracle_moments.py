@@ -67,6 +67,9 @@ def test_gaussian_closed_forms_within_clt_bounds():
     assert abs(m[O.M_THETA] - theta) < bound(c2 / 3)
     # <c_1^4> = 3 theta^2 per component, from the same particles
     assert abs((c[0] ** 4).mean() - 3 * theta ** 2) < bound(c[0] ** 4)
+    # <|c|^6> = 3 * 5 * 7 theta^3 (chi-square with 3 degrees of freedom)
+    m6 = O.speed_moment6(pop.v64, pop.offsets)[0]
+    assert abs(m6 - 105 * theta ** 3) < bound(c2 ** 3)
 
 
 def test_galilean_invariance(cavity_pop):
@@ -115,3 +118,18 @@ def test_empty_and_single_particle_cells():
     assert m[1, O.M_N] == 1
     np.testing.assert_array_equal(m[1, 1:4], v[:, 0])
     assert np.all(m[1, 4:] == 0)
+
+
+def test_speed_moment6_matches_exact_rationals():
+    """<|c|^6> of small integer-velocity cells against exact rational
+    arithmetic (mean, centring and the sixth power done in fractions)."""
+    from fractions import Fraction
+    pop = P.integer_cells([1, 2, 5, 8, 13], lo=-4, hi=4, seed=3)
+    got = O.speed_moment6(pop.v64, pop.offsets)
+    for k in range(pop.n_cells):
+        a, b = pop.offsets[k], pop.offsets[k + 1]
+        vs = [[Fraction(int(x)) for x in pop.v64[d, a:b]] for d in range(3)]
+        n = b - a
+        mean = [sum(col) / n for col in vs]
+        ex = sum(sum((vs[d][p] - mean[d]) ** 2 for d in range(3)) ** 3 for p in range(n)) / n
+        assert abs(got[k] - float(ex)) <= 1e-12 * max(1.0, abs(float(ex)))
