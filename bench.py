@@ -178,7 +178,7 @@ def run_ours(args):
     torch.cuda.set_stream(stream)
     s_sur = torch.cuda.Stream(device=dev)            # learned closure
     s_vel = torch.cuda.Stream(device=dev)            # velocity update
-    ev_coef, ev_sur, ev_vel = (torch.cuda.Event() for _ in range(3))
+    ev_mom, ev_coef, ev_sur, ev_vel = (torch.cuda.Event() for _ in range(4))
     sur = S.Surrogate.load(WEIGHTS, device=dev)
     s_ws = torch.empty(int(api.lib().fp_surrogate_workspace_bytes(n_cells)), dtype=torch.uint8, device=dev)
     step_idx = [0]
@@ -221,17 +221,18 @@ def run_ours(args):
              ("velocity_update", c_velocity_call)]
 
     def step():
-        # Three streams.  Gather and FP64 solve run on the (high-priority)
-        # main stream; then the learned closure (needs only the moments), the
-        # velocity update (writes M^{n+1} to the other buffer) and the
-        # FP64-bound adjoint (still reads M^n) run side by side, and join
-        # before the step ends.
+        # Three streams.  The gather runs on the (high-priority) main stream;
+        # the learned closure, which needs only the moments, starts beside the
+        # FP64 solve; after the solve the velocity update (writes M^{n+1} to
+        # the other buffer) and the FP64-bound adjoint (still reads M^n) run
+        # side by side; all join before the step ends.
         c_moments()
-        c_solve()
-        ev_coef.record(stream)
-        s_sur.wait_event(ev_coef)
+        ev_mom.record(stream)
+        s_sur.wait_event(ev_mom)
         c_surrogate(on=s_sur)
         ev_sur.record(s_sur)
+        c_solve()
+        ev_coef.record(stream)
         s_vel.wait_event(ev_coef)
         with torch.cuda.stream(s_vel):
             flags_v.copy_(flags)
@@ -451,8 +452,8 @@ def run_ours(args):
                            "adjoint to moments and velocities + velocity update",
                    "cells": n_cells, "particles": n_p, "velocities": "f32 SoA", "eps2_hat": prm.eps2_hat,
                    "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{ws}",
-                   "streams": "after gather + solve, the learned closure, the velocity update (out of place) and "
-                              "the adjoint run concurrently on three streams"},
+                   "streams": "learned closure beside the FP64 solve; then velocity update (out of place) and "
+                              "adjoint side by side; three streams"},
         "particles_per_s": round(parts_per_s, 1),
         "per_call_ms": {k: round(v, 5) for k, v in per_call.items()},
         "kernels": kernels,

@@ -7,7 +7,7 @@
 //   copy-in  (H2D)   velocities of the chunk's particles, offsets, tau
 //   main     (high priority) gather -> solve (keeping its factors for the
 //            adjoint when asked) -> [adjoint]
-//   learned  [surrogate closure]                    after the solve
+//   learned  [surrogate closure]                    after the gather
 //   update   flags copy, velocity update M^n -> M^{n+1}  after the solve
 //   copy-out (D2H)   coefficients, flags, updated velocities
 // so chunk k's copies overlap the compute of its neighbours.  Each chunk's
@@ -28,7 +28,7 @@ struct fp_pipeline {
   static constexpr int kMaxChunks = 64;
   cudaStream_t h2d = nullptr, main = nullptr, sur = nullptr, vel = nullptr, d2h = nullptr;
   cudaEvent_t start = nullptr;
-  cudaEvent_t ev_h2d[kMaxChunks] = {}, ev_solve[kMaxChunks] = {}, ev_vel[kMaxChunks] = {};
+  cudaEvent_t ev_h2d[kMaxChunks] = {}, ev_mom[kMaxChunks] = {}, ev_solve[kMaxChunks] = {}, ev_vel[kMaxChunks] = {};
   cudaEvent_t done_main = nullptr, done_sur = nullptr, done_vel = nullptr, done_d2h = nullptr;
 };
 
@@ -43,6 +43,7 @@ int destroy_all(fp_pipeline *pl) {
     if (*e) cudaEventDestroy(*e);
   for (int k = 0; k < fp_pipeline::kMaxChunks; ++k) {
     if (pl->ev_h2d[k]) cudaEventDestroy(pl->ev_h2d[k]);
+    if (pl->ev_mom[k]) cudaEventDestroy(pl->ev_mom[k]);
     if (pl->ev_solve[k]) cudaEventDestroy(pl->ev_solve[k]);
     if (pl->ev_vel[k]) cudaEventDestroy(pl->ev_vel[k]);
   }
@@ -72,6 +73,7 @@ int fp_pipeline_create(fp_pipeline **out) {
   for (cudaEvent_t *e : es) ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
   for (int k = 0; ok && k < fp_pipeline::kMaxChunks; ++k) {
     ok = ok && cudaEventCreateWithFlags(&pl->ev_h2d[k], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&pl->ev_mom[k], cudaEventDisableTiming) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&pl->ev_solve[k], cudaEventDisableTiming) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&pl->ev_vel[k], cudaEventDisableTiming) == cudaSuccess;
   }
@@ -158,18 +160,20 @@ int fp_step_host(fp_pipeline *pl, const fp_step_io *io, int v_dtype, int64_t n_p
     double *mom = io->d_moments + c0 * FP_NMOM;
     double *m6 = io->d_m6 ? io->d_m6 + c0 : nullptr;
     if ((rc = fp_moments(io->d_v, v_dtype, n_particles, io->d_offsets + c0, nc, prec, mom, m6, pl->main))) break;
+    // ---- the learned closure (moments only) beside the FP64 solve ----
+    if (io->net) {
+      cudaEventRecord(pl->ev_mom[k], pl->main);
+      cudaStreamWaitEvent(pl->sur, pl->ev_mom[k], 0);
+      if ((rc = fp_closure_surrogate(io->net, mom, nc, io->d_tau + c0, p, prec, io->d_coeffs_s + c0 * 9,
+                                     io->d_flags_s + c0, io->d_surrogate_ws, io->surrogate_ws_bytes, pl->sur)))
+        break;
+    }
     double *lu = io->d_lu ? io->d_lu + (c0 / 32) * 32 * FP_LU_STRIDE : nullptr;
     if ((rc = fp_closure_solve(mom, io->d_tau + c0, nc, p, prec, io->d_coeffs + c0 * 9, io->d_flags + c0,
                                io->d_grad_coeffs ? lu : nullptr, pl->main)))
       break;
     cudaEventRecord(pl->ev_solve[k], pl->main);
-    // ---- learned closure, velocity update, adjoint side by side ----
-    if (io->net) {
-      cudaStreamWaitEvent(pl->sur, pl->ev_solve[k], 0);
-      if ((rc = fp_closure_surrogate(io->net, mom, nc, io->d_tau + c0, p, prec, io->d_coeffs_s + c0 * 9,
-                                     io->d_flags_s + c0, io->d_surrogate_ws, io->surrogate_ws_bytes, pl->sur)))
-        break;
-    }
+    // ---- velocity update and adjoint side by side ----
     cudaStreamWaitEvent(pl->vel, pl->ev_solve[k], 0);
     cudaMemcpyAsync(io->d_flags_v + c0, io->d_flags + c0, (size_t)nc * sizeof(int32_t), cudaMemcpyDeviceToDevice,
                     pl->vel);
