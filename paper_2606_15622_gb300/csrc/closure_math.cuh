@@ -39,6 +39,14 @@ struct SolveParams {
 
 // Assemble the augmented system [A | r] (moment-matching rows for psi =
 // c_i c_j and psi = c_i |c|^2; see fpclosure.h for the readings).
+//   stress rows (ij):  sum_k (C_ik u_kj + C_jk u_ki) + G_i b_j + G_j b_i
+//                      = -(2/tau) u_ij + 2 eps^2 w_ij
+//   heat rows (i):     sum_l C_il b_l + 2 sum_kl C_kl u_ikl + G_i (s4 - 9 theta^2)
+//                      + 2 sum_k G_k (w_ki - 3 theta u_ki)
+//                      = -(4/(3 tau)) b_i + eps^2 (3 z_i - 3 theta b_i - 2 u_ik b_k)
+// Every entry is written as its own closed expression (a copy where a single
+// moment is the coefficient): on this GPU each FP64 instruction is expensive,
+// and accumulating into zeroed entries would cost an FP64 add per term.
 __device__ __forceinline__ void assemble(const double (&m)[FP_NMOM], double tau, double eps2_hat,
                                          double (&a)[9][10]) {
   double u[3][3], w[3][3], b[3];
@@ -56,43 +64,65 @@ __device__ __forceinline__ void assemble(const double (&m)[FP_NMOM], double tau,
   const double s4 = w[0][0] + w[1][1] + w[2][2];
   const double eps2 = eps2_hat / (tau * theta);
   const double inv_tau = 1.0 / tau;
+  const double c_u = -2.0 * inv_tau, c_w = 2.0 * eps2;  // stress right-hand side
+  const double th3 = 3.0 * theta;
 #pragma unroll
   for (int r = 0; r < 9; ++r)
 #pragma unroll
     for (int col = 0; col < 10; ++col) a[r][col] = 0.0;
-  // stress rows: sum_k (C_ik u_kj + C_jk u_ki) + G_i b_j + G_j b_i
-  //              = -(2/tau) u_ij + 2 eps^2 w_ij
+  // stress rows
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = i; j < 3; ++j) {
       const int row = sym2(i, j);
+      if (i == j) {
+        // 2 sum_k C_ik u_ki + 2 G_i b_i
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        a[row][sym2(i, k)] += u[k][j];
-        a[row][sym2(j, k)] += u[k][i];
+        for (int k = 0; k < 3; ++k) a[row][sym2(i, k)] = 2.0 * u[k][i];
+        a[row][6 + i] = 2.0 * b[i];
+      } else {
+        // C_ii u_ij + C_jj u_ij + C_ij (u_ii + u_jj) + C_it u_tj + C_jt u_ti
+        const int t = 3 - i - j;
+        a[row][sym2(i, i)] = u[i][j];
+        a[row][sym2(j, j)] = u[i][j];
+        a[row][sym2(i, j)] = u[i][i] + u[j][j];
+        a[row][sym2(i, t)] = u[t][j];
+        a[row][sym2(j, t)] = u[t][i];
+        a[row][6 + i] = b[j];
+        a[row][6 + j] = b[i];
       }
-      a[row][6 + i] += b[j];
-      a[row][6 + j] += b[i];
-      a[row][9] = -2.0 * inv_tau * u[i][j] + 2.0 * eps2 * w[i][j];
+      a[row][9] = c_u * u[i][j] + c_w * w[i][j];
     }
-  // heat-flux rows: sum_l C_il b_l + 2 sum_kl C_kl u_ikl + G_i (s4 - 9 theta^2)
-  //                 + 2 sum_k G_k (w_ki - 3 theta u_ki)
-  //                 = -(4/(3 tau)) b_i + eps^2 (3 z_i - 3 theta b_i - 2 u_ik b_k)
+  // heat-flux rows
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const int row = 6 + i;
 #pragma unroll
-    for (int l = 0; l < 3; ++l) a[row][sym2(i, l)] += b[l];
+    for (int p = 0; p < 3; ++p)
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
+      for (int q = p; q < 3; ++q) {
+        // C_pq: b from sum_l C_il b_l (if i is p or q), then 2 u_ipp or 4 u_ipq
+        const double u3 = m[kU3 + sym3(i, p, q)];
+        double bterm = 0.0;
+        bool has_b = false;
+        if (p == i) {
+          bterm = b[q];
+          has_b = true;
+        } else if (q == i) {
+          bterm = b[p];
+          has_b = true;
+        }
+        const double f = p == q ? 2.0 : 4.0;
+        a[row][sym2(p, q)] = has_b ? fma(f, u3, bterm) : f * u3;
+      }
 #pragma unroll
-      for (int l = 0; l < 3; ++l) a[row][sym2(k, l)] += 2.0 * m[kU3 + sym3(i, k, l)];
-    a[row][6 + i] += s4 - 9.0 * theta * theta;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) a[row][6 + k] += 2.0 * (w[k][i] - 3.0 * theta * u[k][i]);
+    for (int k = 0; k < 3; ++k) {
+      const double gk = 2.0 * fma(-th3, u[k][i], w[k][i]);
+      a[row][6 + k] = k == i ? (s4 - 9.0 * theta * theta) + gk : gk;
+    }
     const double ub = u[i][0] * b[0] + u[i][1] * b[1] + u[i][2] * b[2];
-    a[row][9] = -(4.0 / 3.0) * inv_tau * b[i] + eps2 * (3.0 * m[kZ + i] - 3.0 * theta * b[i] - 2.0 * ub);
+    a[row][9] = -(4.0 / 3.0) * inv_tau * b[i] + eps2 * (3.0 * m[kZ + i] - th3 * b[i] - 2.0 * ub);
   }
 }
 
