@@ -32,28 +32,31 @@ constexpr int kVBatch = 4;          // particles per lane per round
 enum { VU0 = 0, VU1, VU2, VTH, VB0, VB1, VB2, VC00, VC01, VC02, VC11, VC12, VC22, VG0, VG1, VG2, VEPS, VA, VDRIFT,
        VNOISE, VIA, VLIN, VOMA, VTAU };
 
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
-__device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1) {
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  The key schedule
+// (k0 + r 0x9E3779B9, k1 + r 0xBB67AE85 for round r) depends on the seed
+// only, so the host computes it once and passes it as a kernel parameter.
+struct PhiloxKeys {
+  uint32_t k0[10], k1[10];
+};
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 x, const PhiloxKeys &key) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    if (r > 0) {
-      k0 += 0x9E3779B9u;
-      k1 += 0xBB67AE85u;
-    }
     // one 32x32 -> 64-bit multiply gives both halves of each product
     const uint64_t p0 = (uint64_t)0xD2511F53u * x.x, p1 = (uint64_t)0xCD9E8D57u * x.z;
-    x = make_uint4((uint32_t)(p1 >> 32) ^ x.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ x.w ^ k1, (uint32_t)p0);
+    x = make_uint4((uint32_t)(p1 >> 32) ^ x.y ^ key.k0[r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ x.w ^ key.k1[r],
+                   (uint32_t)p0);
   }
   return x;
 }
 
 // Three standard normals for particle p at `step`: uniforms
 // u = (floor(w / 2^8) + 1) 2^-24 (exact in FP32) from the four Philox words,
-// Box-Muller on (u0, u1) and (u2, u3) in FP32.
-__device__ __forceinline__ void philox_normals(uint64_t seed, uint64_t step, uint64_t p, float &x0, float &x1,
-                                               float &x2) {
+// Box-Muller in FP32 on (u0, u1) and (u2, u3).
+__device__ __forceinline__ void philox_normals(const PhiloxKeys &key, uint64_t step, uint64_t p, float &x0,
+                                               float &x1, float &x2) {
   const uint4 w = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)(p >> 32), (uint32_t)step, (uint32_t)(step >> 32)),
-                                (uint32_t)seed, (uint32_t)(seed >> 32));
+                                key);
   const float s24 = 5.9604644775390625e-08f;  // 2^-24
   const float u0 = ((float)(w.x >> 8) + 1.f) * s24, u1 = ((float)(w.y >> 8) + 1.f) * s24;
   const float u2 = ((float)(w.z >> 8) + 1.f) * s24, u3 = ((float)(w.w >> 8) + 1.f) * s24;
@@ -67,7 +70,8 @@ __device__ __forceinline__ void philox_normals(uint64_t seed, uint64_t step, uin
 
 struct VelParams {
   double dt, eps2_hat;
-  uint64_t seed, step;
+  uint64_t step;
+  PhiloxKeys key;
 };
 
 template <typename T>
@@ -120,7 +124,7 @@ __device__ __forceinline__ void cell_drift_averages(const T (&vals)[kVConst], co
 // With kOnePass the cell averages <N.N> and <M'.N> come from the moments (and
 // m6 = <|c|^6>) in closed form, so the particles are read once.
 template <typename VT, bool kOnePass>
-__global__ void __launch_bounds__(32 * kVWarps) velocity_kernel(const VT *v, VT *vout, int64_t np,
+__global__ void __launch_bounds__(32 * kVWarps, sizeof(VT) == 4 ? 4 : 2) velocity_kernel(const VT *v, VT *vout, int64_t np,
                                                                 const int64_t *__restrict__ off, int64_t n_cells,
                                                                 const double *__restrict__ mom,
                                                                 const double *__restrict__ m6,
@@ -342,7 +346,7 @@ __global__ void __launch_bounds__(32 * kVWarps) velocity_kernel(const VT *v, VT 
             x2 = xi[2 * np + p];
           } else {
             float f0, f1, f2;
-            philox_normals(prm.seed, prm.step, (uint64_t)p, f0, f1, f2);
+            philox_normals(prm.key, prm.step, (uint64_t)p, f0, f1, f2);
             x0 = f0;
             x1 = f1;
             x2 = f2;
@@ -373,7 +377,11 @@ void launch_velocity(const void *v, void *v_out, int v_dtype, int64_t np, const 
                      const double *mom, const double *m6, const double *coeffs, const double *tau, double dt,
                      double eps2_hat, const void *xi, uint64_t seed, uint64_t step, double *alpha_out,
                      int32_t *flags, cudaStream_t st) {
-  VelParams prm{dt, eps2_hat, seed, step};
+  VelParams prm{dt, eps2_hat, step, {}};
+  for (int r = 0; r < 10; ++r) {
+    prm.key.k0[r] = (uint32_t)seed + 0x9E3779B9u * (uint32_t)r;
+    prm.key.k1[r] = (uint32_t)(seed >> 32) + 0xBB67AE85u * (uint32_t)r;
+  }
   const int threads = 32 * kVWarps;
   const int64_t cells_per_block = kVWarps * kVCells;
   int64_t blocks = (n_cells + cells_per_block - 1) / cells_per_block;
