@@ -364,6 +364,38 @@ int fp_closure_exact_static(const void *v, int v_dtype, int64_t n_particles, con
 const char *fp_closure_exact_static_error(void);
 
 /* ------------------------------------------------------------------------
+ * Diagnostics and deployment options of the learned closure.
+ *
+ * fp_diagnostics: per-cell high-order nonequilibrium diagnostics (the
+ * normalised fields of the paper's cavity study: R_ij = <c_i c_j c_k c_k>,
+ * Delta_4 = <(c_k c_k)^2> - 15 theta^2, DM6 = <(c_k c_k)^3>, each divided by
+ * the local Maxwellian scale theta^2 or theta^3) and the covariance-based
+ * entropy proxies of its cylinder audit (Eqs. cyl_theta_def, cyl_entropy_eq,
+ * cyl_DG, cyl_entropy_kinG and the supplemental heat-flux term D_q).
+ *   moments   [n_cells][FP_NMOM] f64, m6 [n_cells] f64 (fp_moments' m6_out)
+ *   rho       [n_cells] f64 cell densities, or NULL: the particle count N
+ *   theta_inf, rho_inf, dg_inf   the reference (upstream) theta, rho, D_G
+ *   out       [n_cells][FP_NDIAG] f64:
+ *     0..5  R_ij / theta^2 (sym order 11,12,13,22,23,33; Maxwellian 5 delta_ij)
+ *     6     <|c|^4> / theta^2 - 15                   (Maxwellian 0)
+ *     7     <|c|^6> / theta^3                        (Maxwellian 105)
+ *     8     D_G = -1/2 log det(Theta / theta), Theta_ij = <c_i c_j>  (>= 0)
+ *     9     D_q = |q_hat|^2 / 5, q_hat = <c |c|^2> / (2 theta^1.5)
+ *     10    Delta s_eq / k_B = 3/2 log(theta / theta_inf) - log(rho / rho_inf)
+ *     11    Delta s_kin,G / k_B = Delta s_eq / k_B - (D_G - dg_inf)
+ *   Cells with N < 2, theta <= 0, det Theta <= 0, rho <= 0 or a non-finite
+ *   input get NaN in every entry.  No workspace. */
+#define FP_NDIAG 12
+int fp_diagnostics(const double *moments, const double *m6, const double *rho, int64_t n_cells, double theta_inf,
+                   double rho_inf, double dg_inf, double *out, fp_stream_t stream);
+
+/* fp_coeffs_relax: temporal under-relaxation of the coefficient field (the
+ * paper's cylinder deployment couples the network's prediction with w = 0.2):
+ * coeffs_prev <- w coeffs_new + (1 - w) coeffs_prev, [n_cells][9] f64 each,
+ * in place on coeffs_prev; w in [0, 1]. */
+int fp_coeffs_relax(const double *coeffs_new, double *coeffs_prev, int64_t n_cells, double w, fp_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Host-resident step (a runtime layer; the paper has no counterpart).
  *
  * fp_step_host runs one step of the hot path -- the exact closure (gather +

@@ -112,6 +112,50 @@ def speed_moment6(v, offsets):
     return out
 
 
+NDIAG = 12
+
+
+def diagnostics(m, m6, rho=None, theta_inf=1.0, rho_inf=1.0, dg_inf=0.0):
+    """Per-cell high-order diagnostics and covariance entropy proxies
+    [n_cells, 12], written out from their definitions (the cavity study's
+    normalised R_ij = <c_i c_j c_k c_k>, Delta_4 = <(c_k c_k)^2> - 15 theta^2,
+    DM6 = <(c_k c_k)^3>; the cylinder audit's Eqs. cyl_theta_def,
+    cyl_entropy_eq, cyl_DG, cyl_entropy_kinG and D_q = |q_hat|^2 / 5 with
+    q_hat = <c |c|^2> / (2 theta^1.5)).  Invalid cells (N < 2, theta <= 0,
+    det Theta <= 0, rho <= 0, non-finite input): NaN."""
+    m = np.atleast_2d(_f64(m))
+    m6 = np.atleast_1d(_f64(m6))
+    n = m.shape[0]
+    out = np.full((n, NDIAG), np.nan)
+    for k in range(n):
+        th = m[k, M_THETA]
+        Theta = np.array([[m[k, M_U2 + SYM2.index(tuple(sorted((i, j))))] for j in range(3)] for i in range(3)])
+        d = m[k, M_N] if rho is None else rho[k]
+        det = np.linalg.det(Theta)
+        if not (m[k, M_N] >= 2 and th > 0 and det > 0 and d > 0 and np.all(np.isfinite(m[k])) and np.isfinite(m6[k])):
+            continue
+        W = m[k, M_W:M_W + 6]
+        out[k, 0:6] = W / th ** 2
+        out[k, 6] = (W[0] + W[3] + W[5]) / th ** 2 - 15.0
+        out[k, 7] = m6[k] / th ** 3
+        dg = -0.5 * np.log(np.linalg.det(Theta / th))
+        out[k, 8] = dg
+        u3 = m[k, M_U3:M_U3 + 10]
+        b = np.array([sum(u3[SYM3.index(tuple(sorted((i, j, j))))] for j in range(3)) for i in range(3)])
+        qhat = b / (2.0 * th ** 1.5)
+        out[k, 9] = qhat @ qhat / 5.0
+        ds_eq = 1.5 * np.log(th / theta_inf) - np.log(d / rho_inf)
+        out[k, 10] = ds_eq
+        out[k, 11] = ds_eq - (dg - dg_inf)
+    return out
+
+
+def coeffs_relax(y_new, y_prev, w):
+    """Temporal under-relaxation of the coefficient field (the cylinder
+    deployment's w = 0.2): w y_new + (1 - w) y_prev."""
+    return w * _f64(y_new) + (1.0 - w) * _f64(y_prev)
+
+
 def assemble(m, tau, eps2_hat=DEFAULT_EPS2_HAT):
     """The 9x9 matrix and right-hand side of one cell."""
     m = _f64(m)

@@ -19,6 +19,7 @@ from . import build as _build
 NMOM = 30
 NCOEF = 9
 LU_STRIDE = 82
+NDIAG = 12
 
 
 def lu_doubles(n_cells: int) -> int:
@@ -73,6 +74,8 @@ class StepIO(ctypes.Structure):
 
 # name -> (restype, argtypes); the exported surface of include/fpclosure.h
 SIGNATURES = {
+    "fp_diagnostics": (_i32, [_vp, _vp, _vp, _i64, _dbl, _dbl, _dbl, _vp, _vp]),
+    "fp_coeffs_relax": (_i32, [_vp, _vp, _i64, _dbl, _vp]),
     "fp_pipeline_create": (_i32, [ctypes.POINTER(_vp)]),
     "fp_pipeline_destroy": (None, [_vp]),
     "fp_step_host": (_i32, [_vp, ctypes.POINTER(StepIO), _i32, _i64, _i64, ctypes.POINTER(Params), _i32, _dbl,
@@ -163,6 +166,30 @@ def fp_closure_backward(v, offsets, tau, moments, coeffs, flags, grad_coeffs, gr
                                    ws_bytes, _stream(stream))
     _check(rc, "fp_closure_backward")
     return grad_moments, grad_v
+
+
+def fp_diagnostics(moments, m6, rho=None, theta_inf=1.0, rho_inf=1.0, dg_inf=0.0, out=None, stream=None):
+    """Per-cell high-order diagnostics and entropy proxies [n_cells, NDIAG]:
+    R_ij / theta^2 (6), <|c|^4> / theta^2 - 15, <|c|^6> / theta^3, D_G, D_q,
+    Delta s_eq, Delta s_kin,G (fpclosure.h)."""
+    n_cells = moments.shape[0]
+    if out is None:
+        out = torch.empty((n_cells, NDIAG), dtype=torch.float64, device=moments.device)
+    _need_cuda(moments, m6, rho, out)
+    rc = lib().fp_diagnostics(_ptr(moments), _ptr(m6), _ptr(rho), n_cells, float(theta_inf), float(rho_inf),
+                              float(dg_inf), _ptr(out), _stream(stream))
+    _check(rc, "fp_diagnostics")
+    return out
+
+
+def fp_coeffs_relax(coeffs_new, coeffs_prev, w=0.2, stream=None):
+    """coeffs_prev <- w coeffs_new + (1 - w) coeffs_prev (in place)."""
+    _need_cuda(coeffs_new, coeffs_prev)
+    if coeffs_new.shape != coeffs_prev.shape or coeffs_new.dtype != torch.float64:
+        raise FPError("coeffs_new and coeffs_prev must be float64 of the same shape")
+    rc = lib().fp_coeffs_relax(_ptr(coeffs_new), _ptr(coeffs_prev), coeffs_prev.shape[0], float(w), _stream(stream))
+    _check(rc, "fp_coeffs_relax")
+    return coeffs_prev
 
 
 class HostStep:

@@ -25,6 +25,9 @@ int launch_mlp_forward(const fp_mlp &net, const void *x, int64_t n, int standard
 void launch_surrogate_tail(const float *tpred, const double *mom, const double *tau, int64_t n, double eps2_hat,
                            double energy_tol, const fp_params &p, int prec, double *coeffs, int32_t *flags,
                            int32_t *list, uint32_t *count, cudaStream_t st);
+void launch_diagnostics(const double *mom, const double *m6, const double *rho, int64_t n_cells, double theta_inf,
+                        double rho_inf, double dg_inf, double *out, cudaStream_t st);
+void launch_relax(const double *y_new, double *y_prev, int64_t n, double w, cudaStream_t st);
 int64_t mlp_param_offset(int which, int layer);
 int64_t mlp_param_count();
 size_t mlp_backward_ws(int64_t n);
@@ -344,6 +347,27 @@ int fp_adam_step(float *params, const float *grads, float *m, float *v, int64_t 
   const float bc2 = (float)(1.0 - pow((double)beta2, (double)t));
   fpc::launch_adam(params, grads, m, v, n_params, lr, beta1, beta2, eps, bc1, bc2, shadow_bf16, (cudaStream_t)stream);
   return check_launch("adam");
+}
+
+int fp_diagnostics(const double *moments, const double *m6, const double *rho, int64_t n_cells, double theta_inf,
+                   double rho_inf, double dg_inf, double *out, fp_stream_t stream) {
+  g_err[0] = 0;
+  if (n_cells < 0) return fail(FP_ERR_ARG, "negative size");
+  if (n_cells == 0) return FP_OK;
+  if (!moments || !m6 || !out) return fail(FP_ERR_ARG, "null array pointer");
+  if (!(theta_inf > 0.0) || !(rho_inf > 0.0)) return fail(FP_ERR_ARG, "theta_inf and rho_inf must be positive");
+  fpc::launch_diagnostics(moments, m6, rho, n_cells, theta_inf, rho_inf, dg_inf, out, (cudaStream_t)stream);
+  return check_launch("diagnostics");
+}
+
+int fp_coeffs_relax(const double *coeffs_new, double *coeffs_prev, int64_t n_cells, double w, fp_stream_t stream) {
+  g_err[0] = 0;
+  if (n_cells < 0) return fail(FP_ERR_ARG, "negative size");
+  if (n_cells == 0) return FP_OK;
+  if (!coeffs_new || !coeffs_prev) return fail(FP_ERR_ARG, "null array pointer");
+  if (!(w >= 0.0 && w <= 1.0)) return fail(FP_ERR_ARG, "w must lie in [0, 1]");
+  fpc::launch_relax(coeffs_new, coeffs_prev, n_cells * 9, w, (cudaStream_t)stream);
+  return check_launch("relax");
 }
 
 }  // extern "C"
