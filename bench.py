@@ -48,10 +48,12 @@ L2_FLUSH_BYTES = 256 << 20
 NCU_DRAM_BYTES = {"velocity_update": None, "gather_fp32": None, "solve_fp64": None, "mlp_forward": 8.5e6}
 E2E_CHUNKS = 4                 # chunks of the host-resident step (copy / compute overlap)
 WEIGHTS = os.path.join(ROOT, "paper_2606_15622_gb300", "weights", "surrogate_couette_cavity.fpw")
+WEIGHTS_LITE = os.path.join(ROOT, "paper_2606_15622_gb300", "weights", "surrogate_lite_couette_cavity.fpw")
 
 # algorithmic work per unit ("Roofline accounting")
 GATHER_BYTES_PER_PARTICLE = 12          # three FP32 components read once
-GATHER_BYTES_PER_CELL = 8 + 8 * 30      # one offset read, the moment vector written
+GATHER_BYTES_PER_CELL = 8 + 8 * 31      # one offset read, the moment vector and <|c|^6> written
+LITE_BYTES_PER_CELL = 8 + 8 * 14        # one offset read, the LITE moment vector written
 VEL_BYTES_PER_PARTICLE = 24             # read + write three FP32 components
 VEL_BYTES_PER_CELL = 8 + 8 * 24 + 4 + 4 + 8  # offset, 24 FP64 constants, flags in/out, alpha
 SOLVE_FLOPS_PER_CELL = 658              # FP64: assembly + elimination + back substitution (FMA = 2)
@@ -277,6 +279,13 @@ def run_ours(args):
         xf, _ = sur.features(mom, tau, params=prm)
         of = torch.empty((n_cells, 16), dtype=torch.float32, device=dev)
         fns["mlp"] = lambda: sur.forward(xf, standardized=False, out=of, stream=stream)
+        lite = torch.empty((n_cells, api.NLITE), dtype=torch.float64, device=dev)
+        fns["gather_lite"] = lambda: api.fp_moments_lite(vb[cur[0]], off, out=lite, stream=stream)
+        if os.path.exists(WEIGHTS_LITE):
+            sl = S.Surrogate.load(WEIGHTS_LITE, device=dev)
+            fns["lite"] = lambda: (api.fp_moments_lite(vb[cur[0]], off, out=lite, stream=stream),
+                                   sl.closure_lite(lite, tau, params=prm, coeffs_out=coeffs_s, flags_out=flags_s,
+                                                   stream=stream))
         for _ in range(args.steps):
             fns[args.only]()
         torch.cuda.synchronize()
@@ -341,6 +350,9 @@ def run_ours(args):
                 "unit": dk["unit"], "frac": dk["frac"], "traffic": NCU_DRAM_BYTES.get(dom),
                 "peak_src": "measured (FP64 FMA chain, DESIGN.md)" if dk["bound"] == "alu" else peaks["src"]}
 
+    def q(x, p):
+        return round(float(torch.quantile(x, p)), 6)
+
     # ---- the exact FP64 path on the same cells ----------------------------------
     t64 = float(np.median(timed(lambda: api.fp_closure_exact(v64, off, tau, params=prm, prec="fp64",
                                                              moments_out=mom, coeffs_out=coeffs, flags_out=flags,
@@ -384,6 +396,45 @@ def run_ours(args):
     ob = torch.empty((nb, 16), dtype=torch.float32, device=dev)
     t_mlp_1m = float(np.median(timed(lambda: sur.forward(xb, standardized=False, out=ob, stream=stream), 10, 2)))
     fb_rate = float(((ifl_s & api.FLAG_FALLBACK) != 0).double().mean())
+
+    # ---- the LITE path: low-order moment pass + network on 16 inputs --------
+    lite_rep = None
+    if os.path.exists(WEIGHTS_LITE):
+        sl = S.Surrogate.load(WEIGHTS_LITE, device=dev)
+        lite = torch.empty((n_cells, api.NLITE), dtype=torch.float64, device=dev)
+        l_ws = torch.empty(int(api.lib().fp_surrogate_lite_workspace_bytes(n_cells)), dtype=torch.uint8, device=dev)
+
+        def c_gather_lite():
+            api.fp_moments_lite(vb[cur[0]], off, out=lite, stream=stream)
+
+        def c_lite():
+            c_gather_lite()
+            sl.closure_lite(lite, tau, params=prm, coeffs_out=coeffs_s, flags_out=flags_s, workspace=l_ws,
+                            stream=stream)
+
+        t_gl = float(np.median(timed(c_gather_lite, 10, 2)))
+        t_lite = float(np.median(timed(c_lite, 10, 2)))
+        lite_bytes = GATHER_BYTES_PER_PARTICLE * n_p + LITE_BYTES_PER_CELL * n_cells
+        kernels["gather_lite"] = kern(t_gl, "hbm", lite_bytes / (t_gl * 1e-3) / 1e9, "GB/s", peaks["hbm_gbs"],
+                                      {"algorithmic_bytes": lite_bytes})
+        torch.cuda.synchronize()
+        lfb = float(((flags_s & api.FALLBACK_FLAGS) != 0).double().mean())
+        lrng = float(((flags_s & api.FLAG_RANGE) != 0).double().mean())
+        # accuracy on the held-out cells of the training distributions, beside the full-input network
+        il = api.fp_moments_lite(iv, ioff)
+        ly, lfl = sl.closure_lite(il, itau, params=prm)
+        torch.cuda.synchronize()
+        t_l = S.dimensionless(ly, imom, itau)
+        rel_l = ((t_l - t_ex).norm(dim=1) / t_ex.norm(dim=1))[ok].float().cpu()
+        lite_rep = {"ms": round(t_lite, 5), "gather_lite_ms": round(t_gl, 5),
+                    "cells_per_s": round(n_cells / (t_lite * 1e-3), 1),
+                    "speedup_vs_exact_fp32_moments": round(per_call["exact_closure"] / t_lite, 3),
+                    "linear_drift_rate_cylinder": round(lfb, 5), "range_flag_rate_cylinder": round(lrng, 5),
+                    "held_out_rel_err_vs_exact": {"median": q(rel_l, 0.5), "p95": q(rel_l, 0.95),
+                                                  "max": round(float(rel_l.max()), 6)},
+                    "full_input_network_rel_err": {"median": q(rel, 0.5), "p95": q(rel, 0.95)},
+                    "note": "LITE moment pass (N, U, theta, u_ij, heat flux) + network on the 16 low-order "
+                            "inputs; no exact fallback (flagged cells take the linear drift)"}
 
     # ---- adjoint on the cavity-shaped population (C4) -----------------------
     cav = P.cavity(seed=4)
@@ -430,9 +481,6 @@ def run_ours(args):
     h2d = h_v.numel() * 4 + h_off.numel() * 8 + h_tau.numel() * 8
     d2h = h_coeffs.numel() * 8 + h_flags.numel() * 4 + h_vout.numel() * 4
     launches_per_step = 2 + 6 + 2 + 1
-
-    def q(x, p):
-        return round(float(torch.quantile(x, p)), 6)
 
     out = {
         "metric": METRIC,
@@ -482,6 +530,7 @@ def run_ours(args):
                              "energy_residual_abs": {"median": q(e.abs().float().cpu(), 0.5),
                                                      "max": round(float(e.abs().max()), 6)},
                              "inputs": "131072 held-out cells of the training distributions, tiled x8"},
+            "lite_on_cylinder": lite_rep if lite_rep is not None else {"unavailable": "no LITE weight file"},
             "adjoint_cavity": {"cells": cav.n_cells, "particles": cav.n_particles,
                                "forward_ms": round(t_fwd_c4, 5), "backward_ms": round(t_bwd_c4, 5),
                                "fwd_bwd_cells_per_s": round(cav.n_cells / ((t_fwd_c4 + t_bwd_c4) * 1e-3), 1)},
@@ -570,7 +619,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default=None,
                     choices=["gather", "gather64", "solve", "exact_closure", "surrogate_closure", "adjoint",
-                             "velocity_update", "step", "mlp"],
+                             "velocity_update", "step", "mlp", "gather_lite", "lite"],
                     help="profiling mode: launch one call --steps times, print no bench line")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -364,6 +364,45 @@ int fp_closure_exact_static(const void *v, int v_dtype, int64_t n_particles, con
 const char *fp_closure_exact_static_error(void);
 
 /* ------------------------------------------------------------------------
+ * The LITE path (Sec. 4, Phase 3 item 2, and Phase 1-2 item 1): the moment
+ * pass stops at the heat flux, and the network reads the paper's 16 low-order
+ * inputs rho, T, U (3), Pi (6), q (3), DM2, nu.  Read here as rho = N (the
+ * cell's particle count), T = theta, Pi_ij = u_ij - theta delta_ij,
+ * q_i = <c_i |c|^2> / 2, DM2 = det(u) (determinant of the second-moment
+ * tensor), nu = 1 / tau; inputs 16..31 of the network are zero.  A network
+ * trained on these inputs (same fp_mlp shape as the full-moment one) maps
+ * them to the same dimensionless targets (tau C, tau sqrt(theta) G).
+ * ------------------------------------------------------------------------ */
+#define FP_NLITE 14  /* LITE moment vector: N, U1..3, theta, u11,u12,u13,u22,u23,u33, b1..3 (b_i = <c_i |c|^2>) */
+
+/* fp_moments_lite: the LITE moment vectors [n_cells][FP_NLITE] f64 (required)
+ * of the velocities (FP32 compensated sums as in FP_PREC_FP32_MOMENTS, any
+ * velocity dtype).  No workspace. */
+int fp_moments_lite(const void *v, int v_dtype, int64_t n_particles, const int64_t *cell_offsets, int64_t n_cells,
+                    double *lite_out, fp_stream_t stream);
+
+/* fp_surrogate_lite_features: the network inputs [n_cells][32] BF16
+ * (standardised with net's scalers, zero padded) and flags (FP_FLAG_FEW,
+ * FP_FLAG_SINGULAR for theta <= 0, FP_FLAG_NONFINITE, FP_FLAG_RANGE outside
+ * the training box widened by p->surr_range_margin sigma) from LITE vectors
+ * and tau.  x_out 16-byte aligned.  No workspace. */
+int fp_surrogate_lite_features(const fp_mlp *net, const double *lite, int64_t n_cells, const double *tau,
+                               const fp_params *p, void *x_out, int32_t *flags_out, fp_stream_t stream);
+
+size_t fp_surrogate_lite_workspace_bytes(int64_t n_cells);
+
+/* fp_closure_surrogate_lite: the learned closure on the LITE inputs:
+ * features, the network (tcgen05), and coefficients C = t_C / tau,
+ * G = t_G / (tau sqrt(theta)).  There are no high-order moments to fall back
+ * on: cells flagged FP_FLAG_FEW, FP_FLAG_SINGULAR or FP_FLAG_NONFINITE (also
+ * for a non-finite prediction) take the linear drift C = -I/tau, G = 0;
+ * FP_FLAG_RANGE is reported and the prediction kept.  ws >=
+ * fp_surrogate_lite_workspace_bytes(n_cells), 256-byte aligned. */
+int fp_closure_surrogate_lite(const fp_mlp *net, const double *lite, int64_t n_cells, const double *tau,
+                              const fp_params *p, double *coeffs_out, int32_t *flags_out, void *ws, size_t ws_bytes,
+                              fp_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Diagnostics and deployment options of the learned closure.
  *
  * fp_diagnostics: per-cell high-order nonequilibrium diagnostics (the

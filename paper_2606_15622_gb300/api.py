@@ -20,6 +20,7 @@ NMOM = 30
 NCOEF = 9
 LU_STRIDE = 82
 NDIAG = 12
+NLITE = 14
 
 
 def lu_doubles(n_cells: int) -> int:
@@ -109,6 +110,12 @@ SIGNATURES = {
     "fp_closure_exact_static": (_i32, [_vp, _i32, _i64, _vp, _i64, _vp, ctypes.POINTER(Params), _i32, _vp, _vp,
                                        _vp]),
     "fp_closure_exact_static_error": (ctypes.c_char_p, []),
+    "fp_moments_lite": (_i32, [_vp, _i32, _i64, _vp, _i64, _vp, _vp]),
+    "fp_surrogate_lite_features": (_i32, [ctypes.POINTER(FpMlp), _vp, _i64, _vp, ctypes.POINTER(Params), _vp, _vp,
+                                          _vp]),
+    "fp_surrogate_lite_workspace_bytes": (_sz, [_i64]),
+    "fp_closure_surrogate_lite": (_i32, [ctypes.POINTER(FpMlp), _vp, _i64, _vp, ctypes.POINTER(Params), _vp, _vp,
+                                         _vp, _sz, _vp]),
 }
 
 STATIC_MAX_CELLS = 32768
@@ -382,6 +389,21 @@ def fp_moments(v, offsets, prec="fp32", moments_out=None, stream=None, m6_out=No
                           _ptr(moments_out), _ptr(m6_out), _stream(stream))
     _check(rc, "fp_moments")
     return moments_out
+
+
+def fp_moments_lite(v, offsets, out=None, stream=None):
+    """LITE moment vectors [n_cells, NLITE] (f64): N, U (3), theta, u_ij
+    (6), b_i = <c_i |c|^2> (3), from FP32 compensated sums."""
+    n_cells = offsets.numel() - 1
+    n_p = v.shape[-1] if v.dim() == 2 else v.numel() // 3
+    if out is None:
+        out = torch.empty((n_cells, NLITE), dtype=torch.float64, device=offsets.device)
+    _need_cuda(v, offsets, out)
+    if out.dtype != torch.float64 or out.numel() < n_cells * NLITE:
+        raise FPError("out must be float64 [n_cells, NLITE]")
+    rc = lib().fp_moments_lite(_ptr(v), _vdtype(v), n_p, _ptr(offsets), n_cells, _ptr(out), _stream(stream))
+    _check(rc, "fp_moments_lite")
+    return out
 
 
 def fp_closure_solve(moments, tau, params: Params | None = None, prec="fp32", coeffs_out=None, flags_out=None,

@@ -25,6 +25,12 @@ int launch_mlp_forward(const fp_mlp &net, const void *x, int64_t n, int standard
 void launch_surrogate_tail(const float *tpred, const double *mom, const double *tau, int64_t n, double eps2_hat,
                            double energy_tol, const fp_params &p, int prec, double *coeffs, int32_t *flags,
                            int32_t *list, uint32_t *count, cudaStream_t st);
+void launch_gather_lite(const void *v, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, double *lite,
+                        cudaStream_t st);
+void launch_lite_features(const fp_mlp &net, const double *lite, const double *tau, int64_t n, int min_particles,
+                          double margin, void *x, int32_t *flags, cudaStream_t st);
+void launch_lite_epilogue(const float *tpred, const double *lite, const double *tau, int64_t n, double *coeffs,
+                          int32_t *flags, cudaStream_t st);
 void launch_diagnostics(const double *mom, const double *m6, const double *rho, int64_t n_cells, double theta_inf,
                         double rho_inf, double dg_inf, double *out, cudaStream_t st);
 void launch_relax(const double *y_new, double *y_prev, int64_t n, double w, cudaStream_t st);
@@ -368,6 +374,64 @@ int fp_coeffs_relax(const double *coeffs_new, double *coeffs_prev, int64_t n_cel
   if (!(w >= 0.0 && w <= 1.0)) return fail(FP_ERR_ARG, "w must lie in [0, 1]");
   fpc::launch_relax(coeffs_new, coeffs_prev, n_cells * 9, w, (cudaStream_t)stream);
   return check_launch("relax");
+}
+
+int fp_moments_lite(const void *v, int v_dtype, int64_t n_particles, const int64_t *cell_offsets, int64_t n_cells,
+                    double *lite_out, fp_stream_t stream) {
+  g_err[0] = 0;
+  if (n_cells < 0 || n_particles < 0) return fail(FP_ERR_ARG, "negative size");
+  if (n_cells == 0) return FP_OK;
+  if (v_dtype != FP_V_F32 && v_dtype != FP_V_F64) return fail(FP_ERR_ARG, "v_dtype %d", v_dtype);
+  if (!cell_offsets || !lite_out) return fail(FP_ERR_ARG, "null array pointer");
+  if (n_particles > 0 && !v) return fail(FP_ERR_ARG, "null velocity pointer");
+  fpc::launch_gather_lite(v, v_dtype, n_particles, cell_offsets, n_cells, lite_out, (cudaStream_t)stream);
+  return check_launch("gather_lite");
+}
+
+int fp_surrogate_lite_features(const fp_mlp *net, const double *lite, int64_t n_cells, const double *tau,
+                               const fp_params *p, void *x_out, int32_t *flags_out, fp_stream_t stream) {
+  g_err[0] = 0;
+  if (int rc = check_net(net)) return rc;
+  if (n_cells < 0) return fail(FP_ERR_ARG, "negative size");
+  if (n_cells == 0) return FP_OK;
+  if (!lite || !tau || !x_out || !flags_out) return fail(FP_ERR_ARG, "null array pointer");
+  if ((uintptr_t)x_out % 16) return fail(FP_ERR_ARG, "features not 16-byte aligned");
+  fp_params prm;
+  fp_default_params(&prm);
+  if (p) prm = *p;
+  fpc::launch_lite_features(*net, lite, tau, n_cells, prm.min_particles, prm.surr_range_margin, x_out, flags_out,
+                            (cudaStream_t)stream);
+  return check_launch("lite_features");
+}
+
+size_t fp_surrogate_lite_workspace_bytes(int64_t n_cells) {
+  if (n_cells < 0) return 0;
+  return align_up((size_t)n_cells * 32 * 2) + align_up((size_t)n_cells * 16 * 4);
+}
+
+int fp_closure_surrogate_lite(const fp_mlp *net, const double *lite, int64_t n_cells, const double *tau,
+                              const fp_params *p, double *coeffs_out, int32_t *flags_out, void *ws, size_t ws_bytes,
+                              fp_stream_t stream) {
+  g_err[0] = 0;
+  if (int rc = check_net(net)) return rc;
+  if (n_cells < 0) return fail(FP_ERR_ARG, "negative size");
+  if (n_cells == 0) return FP_OK;
+  if (!lite || !tau || !coeffs_out || !flags_out) return fail(FP_ERR_ARG, "null array pointer");
+  const size_t need = fp_surrogate_lite_workspace_bytes(n_cells);
+  if (!ws || ws_bytes < need) return fail(FP_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", need, ws_bytes);
+  if ((uintptr_t)ws % kAlign) return fail(FP_ERR_ARG, "workspace not 256-byte aligned");
+  fp_params prm;
+  fp_default_params(&prm);
+  if (p) prm = *p;
+  const cudaStream_t st = (cudaStream_t)stream;
+  char *w = (char *)ws;
+  void *x = w;
+  float *tpred = (float *)(w + align_up((size_t)n_cells * 32 * 2));
+  fpc::launch_lite_features(*net, lite, tau, n_cells, prm.min_particles, prm.surr_range_margin, x, flags_out, st);
+  if (fpc::launch_mlp_forward(*net, x, n_cells, 0, tpred, nullptr, nullptr, st))
+    return fail(FP_ERR_CUDA, "could not raise the shared-memory limit of the MLP kernel");
+  fpc::launch_lite_epilogue(tpred, lite, tau, n_cells, coeffs_out, flags_out, st);
+  return check_launch("surrogate_lite");
 }
 
 }  // extern "C"

@@ -6,10 +6,19 @@ kernels (features, fused BF16 MLP forward, loss + gradient, BF16 backward
 GEMMs, Adam, exact fallback); torch provides device memory, the data
 shuffling and the scaler statistics of the training set.
 
+Two input sets share the network shape (inputs padded to 32):
+  "full": the 25 normalised high-order moments (u/theta, u3/theta^1.5,
+          w/theta^2, z/theta^2.5) of the full moment vector;
+  "lite": the 16 low-order inputs rho, T, U, Pi, q, DM2, nu of the LITE
+          moment vector (fp_moments_lite; Sec. 4, Phase 1-2 item 1 and
+          Phase 3 item 2).
+Both predict the same dimensionless targets (tau C, tau sqrt(theta) G).
+
 Weight file (little-endian): magic b"FPCW", u32 version, u32 dims (32, 128,
-4, 16), f64 eps2_hat, u64 training seed, then FP32 arrays: the flat
-parameters (fp_mlp_param_count), x_mu, x_sigma, x_min, x_max [32],
-y_mu, y_sigma [16].
+4, 16), f64 eps2_hat, u64 training seed, [version 2: u32 input set, 0 full,
+1 lite], then FP32 arrays: the flat parameters (fp_mlp_param_count), x_mu,
+x_sigma, x_min, x_max [32], y_mu, y_sigma [16].  Version 1 files hold a
+full-input network.
 """
 
 from __future__ import annotations
@@ -26,8 +35,10 @@ import torch
 from . import api
 
 IN, HID, OUT, DEPTH, NFEAT, NOUT = 32, 128, 16, 4, 25, 9
+NFEAT_LITE = 16
+FEATURE_SETS = {"full": (0, NFEAT), "lite": (1, NFEAT_LITE)}
 MAGIC = b"FPCW"
-VERSION = 1
+VERSION = 2
 
 
 FpMlp = api.FpMlp
@@ -52,7 +63,11 @@ def _p(t):
 class Surrogate:
     """Parameters (FP32 master + BF16 shadow), scalers and the fp_mlp view."""
 
-    def __init__(self, device="cuda", eps2_hat=1e-3, seed=0):
+    def __init__(self, device="cuda", eps2_hat=1e-3, seed=0, features="full"):
+        if features not in FEATURE_SETS:
+            raise api.FPError(f"unknown input set {features!r}")
+        self.features_set = features
+        self.nfeat = FEATURE_SETS[features][1]
         self.device = torch.device(device)
         self.eps2_hat = float(eps2_hat)
         self.seed = int(seed)
@@ -80,10 +95,10 @@ class Surrogate:
         g = torch.Generator(device="cpu").manual_seed(self.seed if seed is None else seed)
         W, b = self.layer_views()
         for l, w in enumerate(W):
-            fan_in = w.shape[1] if l > 0 else NFEAT
+            fan_in = w.shape[1] if l > 0 else self.nfeat
             w.copy_((torch.rand(w.shape, generator=g) * 2 - 1) * np.sqrt(3.0 / fan_in))
             b[l].zero_()
-        W[0][:, NFEAT:] = 0
+        W[0][:, self.nfeat:] = 0
         W[4][NOUT:, :] = 0
         self.sync_shadow()
 
@@ -113,7 +128,12 @@ class Surrogate:
         return self._net
 
     # ---- kernels -------------------------------------------------------
+    def _want(self, features):
+        if self.features_set != features:
+            raise api.FPError(f"this network reads the {self.features_set!r} inputs, not {features!r}")
+
     def features(self, moments, tau, params=None, x_out=None, flags_out=None, stream=None):
+        self._want("full")
         n = moments.shape[0]
         x = x_out if x_out is not None else torch.empty((n, IN), dtype=torch.bfloat16, device=self.device)
         fl = flags_out if flags_out is not None else torch.empty(n, dtype=torch.int32, device=self.device)
@@ -138,6 +158,7 @@ class Surrogate:
     def closure(self, moments, tau, params=None, prec="fp64", coeffs_out=None, flags_out=None, workspace=None,
                 stream=None):
         """The surrogate closure with exact fallback -> (coeffs, flags)."""
+        self._want("full")
         n = moments.shape[0]
         y = coeffs_out if coeffs_out is not None else torch.empty((n, 9), dtype=torch.float64, device=self.device)
         fl = flags_out if flags_out is not None else torch.empty(n, dtype=torch.int32, device=self.device)
@@ -150,11 +171,39 @@ class Surrogate:
         api._check(rc, "fp_closure_surrogate")
         return y, fl
 
+    def lite_features(self, lite, tau, params=None, x_out=None, flags_out=None, stream=None):
+        """Standardised BF16 inputs [n, 32] and flags from LITE vectors."""
+        self._want("lite")
+        n = lite.shape[0]
+        x = x_out if x_out is not None else torch.empty((n, IN), dtype=torch.bfloat16, device=self.device)
+        fl = flags_out if flags_out is not None else torch.empty(n, dtype=torch.int32, device=self.device)
+        p = params if params is not None else api.default_params(eps2_hat=self.eps2_hat)
+        rc = _lib().fp_surrogate_lite_features(ctypes.byref(self.net()), _p(lite), n, _p(tau), ctypes.byref(p),
+                                               _p(x), _p(fl), api._stream(stream))
+        api._check(rc, "fp_surrogate_lite_features")
+        return x, fl
+
+    def closure_lite(self, lite, tau, params=None, coeffs_out=None, flags_out=None, workspace=None, stream=None):
+        """The learned closure on LITE vectors -> (coeffs, flags); cells it
+        cannot serve take the linear drift -I/tau."""
+        self._want("lite")
+        n = lite.shape[0]
+        y = coeffs_out if coeffs_out is not None else torch.empty((n, 9), dtype=torch.float64, device=self.device)
+        fl = flags_out if flags_out is not None else torch.empty(n, dtype=torch.int32, device=self.device)
+        need = int(_lib().fp_surrogate_lite_workspace_bytes(n))
+        ws = workspace if workspace is not None else torch.empty(need, dtype=torch.uint8, device=self.device)
+        p = params if params is not None else api.default_params(eps2_hat=self.eps2_hat)
+        rc = _lib().fp_closure_surrogate_lite(ctypes.byref(self.net()), _p(lite), n, _p(tau), ctypes.byref(p),
+                                              _p(y), _p(fl), _p(ws), ws.numel(), api._stream(stream))
+        api._check(rc, "fp_closure_surrogate_lite")
+        return y, fl
+
     # ---- persistence ---------------------------------------------------
     def save(self, path):
         buf = io.BytesIO()
         buf.write(MAGIC)
         buf.write(struct.pack("<IIIIIdQ", VERSION, IN, HID, DEPTH, OUT, self.eps2_hat, self.seed))
+        buf.write(struct.pack("<I", FEATURE_SETS[self.features_set][0]))
         for t in (self.params, self.x_mu, self.x_sigma, self.x_min, self.x_max, self.y_mu, self.y_sigma):
             buf.write(t.detach().cpu().numpy().astype("<f4").tobytes())
         tmp = path + ".tmp"
@@ -168,10 +217,17 @@ class Surrogate:
         if raw[:4] != MAGIC:
             raise api.FPError(f"{path}: not a weight file")
         ver, i, h, d, o, eps2_hat, seed = struct.unpack("<IIIIIdQ", raw[4:4 + 36])
-        if ver != VERSION or (i, h, d, o) != (IN, HID, DEPTH, OUT):
+        if ver not in (1, 2) or (i, h, d, o) != (IN, HID, DEPTH, OUT):
             raise api.FPError(f"{path}: unsupported version/shape")
-        s = cls(device=device, eps2_hat=eps2_hat, seed=seed)
-        arr = np.frombuffer(raw[40:], dtype="<f4")
+        pos0, features = 40, "full"
+        if ver == 2:
+            (fid,) = struct.unpack("<I", raw[40:44])
+            names = {v[0]: k for k, v in FEATURE_SETS.items()}
+            if fid not in names:
+                raise api.FPError(f"{path}: unknown input set {fid}")
+            pos0, features = 44, names[fid]
+        s = cls(device=device, eps2_hat=eps2_hat, seed=seed, features=features)
+        arr = np.frombuffer(raw[pos0:], dtype="<f4")
         n = param_count()
         parts = [n, IN, IN, IN, IN, OUT, OUT]
         if arr.size != sum(parts):
@@ -199,6 +255,19 @@ def dimensionless(coeffs, mom, tau):
     return torch.cat([coeffs[:, :6] * tau[:, None], coeffs[:, 6:] * (tau * th.sqrt())[:, None]], dim=1)
 
 
+def lite_raw_features_t(lite, tau):
+    """[n, 16] LITE network inputs rho = N, T = theta, U, Pi = u - theta I,
+    q = b / 2, DM2 = det u, nu = 1 / tau (FP64)."""
+    th = lite[:, 4:5]
+    u = lite[:, 5:11]
+    pi = u.clone()
+    pi[:, [0, 3, 5]] -= th
+    U3 = torch.stack([torch.stack([u[:, 0], u[:, 1], u[:, 2]], 1), torch.stack([u[:, 1], u[:, 3], u[:, 4]], 1),
+                      torch.stack([u[:, 2], u[:, 4], u[:, 5]], 1)], 1)
+    det = torch.linalg.det(U3)[:, None]
+    return torch.cat([lite[:, 0:1], th, lite[:, 1:4], pi, 0.5 * lite[:, 11:14], det, (1.0 / tau)[:, None]], dim=1)
+
+
 def aux_from_features(f):
     """(u_hat (6), b_hat (3), s4_hat, 0 x 6) per row, FP32 [n, 16]."""
     b = torch.stack([f[:, 6] + f[:, 9] + f[:, 11], f[:, 7] + f[:, 12] + f[:, 14], f[:, 8] + f[:, 13] + f[:, 15]],
@@ -212,14 +281,16 @@ def aux_from_features(f):
 
 
 class TrainingSet:
-    """Cells labelled by the exact FP64 GPU closure: raw features, targets,
-    aux moments; cells the exact closure flags, and coefficients beyond
-    1e6 in magnitude (dimensionless), are dropped."""
+    """Cells labelled by the exact FP64 GPU closure: raw inputs of the
+    chosen set, targets, aux moments (always from the full moment vector:
+    the energy term of the loss needs s4); cells the exact closure flags,
+    and coefficients beyond 1e6 in magnitude (dimensionless), are dropped.
+    LITE inputs come from fp_moments_lite, the kernel that serves them."""
 
-    def __init__(self, pop, eps2_hat=1e-3, device="cuda", chunk=262144):
+    def __init__(self, pop, eps2_hat=1e-3, device="cuda", chunk=262144, features="full"):
         dev = torch.device(device)
         prm = api.default_params(eps2_hat=eps2_hat)
-        feats, targs = [], []
+        feats, targs, auxs = [], [], []
         n_cells = pop.n_cells
         for c0 in range(0, n_cells, chunk):
             c1 = min(n_cells, c0 + chunk)
@@ -229,13 +300,17 @@ class TrainingSet:
             tau = torch.from_numpy(pop.tau[c0:c1]).to(dev)
             mom, y, fl = api.fp_closure_exact(v, off, tau, params=prm, prec="fp64")
             t = dimensionless(y, mom, tau)
-            f = raw_features_t(mom)
-            keep = (fl == 0) & torch.isfinite(t).all(1) & (t.abs() <= 1e6).all(1) & torch.isfinite(f).all(1)
+            f_full = raw_features_t(mom)
+            f = f_full if features == "full" else lite_raw_features_t(api.fp_moments_lite(v, off), tau)
+            keep = ((fl == 0) & torch.isfinite(t).all(1) & (t.abs() <= 1e6).all(1) & torch.isfinite(f).all(1)
+                    & torch.isfinite(f_full).all(1))
             feats.append(f[keep].float())
             targs.append(t[keep].float())
+            auxs.append(aux_from_features(f_full[keep].float()))
         self.f = torch.cat(feats)
         self.t = torch.cat(targs)
-        self.aux = aux_from_features(self.f)
+        self.aux = torch.cat(auxs)
+        self.features = features
         self.eps2_hat = eps2_hat
 
     def __len__(self):
@@ -243,17 +318,20 @@ class TrainingSet:
 
 
 def fit_scalers(s: Surrogate, ts: TrainingSet):
+    if ts.f.shape[1] != s.nfeat:
+        raise api.FPError("training inputs and network input set differ")
     f, t = ts.f.double(), ts.t.double()
+    nf = s.nfeat
     mu = f.mean(0)
     sd = f.std(0).clamp_min(1e-6)
-    s.x_mu[:NFEAT] = mu.float()
-    s.x_sigma[:NFEAT] = sd.float()
-    s.x_min[:NFEAT] = f.min(0).values.float()
-    s.x_max[:NFEAT] = f.max(0).values.float()
-    s.x_mu[NFEAT:] = 0
-    s.x_sigma[NFEAT:] = 1
-    s.x_min[NFEAT:] = -1
-    s.x_max[NFEAT:] = 1
+    s.x_mu[:nf] = mu.float()
+    s.x_sigma[:nf] = sd.float()
+    s.x_min[:nf] = f.min(0).values.float()
+    s.x_max[:nf] = f.max(0).values.float()
+    s.x_mu[nf:] = 0
+    s.x_sigma[nf:] = 1
+    s.x_min[nf:] = -1
+    s.x_max[nf:] = 1
     s.y_mu[:NOUT] = t.mean(0).float()
     s.y_sigma[:NOUT] = t.std(0).clamp_min(1e-6).float()
     s.y_mu[NOUT:] = 0
@@ -263,8 +341,9 @@ def fit_scalers(s: Surrogate, ts: TrainingSet):
 
 def standardized_inputs(s: Surrogate, f):
     """BF16 standardised features [n, 32] (the layout the forward reads)."""
+    nf = s.nfeat
     x = torch.zeros((f.shape[0], IN), dtype=torch.float32, device=f.device)
-    x[:, :NFEAT] = (f - s.x_mu[:NFEAT]) / s.x_sigma[:NFEAT]
+    x[:, :nf] = (f - s.x_mu[:nf]) / s.x_sigma[:nf]
     return x.to(torch.bfloat16)
 
 

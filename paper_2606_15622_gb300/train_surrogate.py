@@ -11,6 +11,13 @@ in libfpclosure's kernels (forward, loss + gradient, backward, Adam).  A
 held-out set (fresh seeds) measures the error of the network alone and of
 the surrogate closure with its exact fallback; the report is written beside
 the weights as JSON.
+
+    python -m paper_2606_15622_gb300.train_surrogate --features lite \
+        --out paper_2606_15622_gb300/weights/surrogate_lite_couette_cavity.fpw
+
+trains the network on the 16 LITE inputs instead (same cells, same targets,
+same loss); its held-out report measures what the low-order inputs lose
+against the exact closure, beside the full-input network's.
 """
 
 from __future__ import annotations
@@ -28,7 +35,7 @@ from . import populations as P
 from . import surrogate as S
 
 
-def build_training_set(n_cells, seed, eps2_hat, chunk=250_000, log=print):
+def build_training_set(n_cells, seed, eps2_hat, chunk=250_000, log=print, features="full"):
     parts = []
     done = 0
     k = 0
@@ -36,7 +43,7 @@ def build_training_set(n_cells, seed, eps2_hat, chunk=250_000, log=print):
         n = min(chunk, n_cells - done)
         t0 = time.time()
         pop = P.training_cells(n, seed=seed * 1000 + k)
-        ts = S.TrainingSet(pop, eps2_hat=eps2_hat)
+        ts = S.TrainingSet(pop, eps2_hat=eps2_hat, features=features)
         parts.append(ts)
         done += n
         k += 1
@@ -58,13 +65,17 @@ def evaluate(s: S.Surrogate, n_cells, seed, eps2_hat):
     tau = torch.from_numpy(pop.tau).to(dev)
     prm = api.default_params(eps2_hat=eps2_hat)
     mom, y_ex, fl_ex = api.fp_closure_exact(v, off, tau, params=prm, prec="fp64")
-    y_s, fl_s = s.closure(mom, tau, params=prm)
+    if s.features_set == "lite":
+        y_s, fl_s = s.closure_lite(api.fp_moments_lite(v, off), tau, params=prm)
+        fb = (fl_s & api.FALLBACK_FLAGS) != 0     # cells given the linear drift
+    else:
+        y_s, fl_s = s.closure(mom, tau, params=prm)
+        fb = (fl_s & api.FLAG_FALLBACK) != 0
     torch.cuda.synchronize()
     t_ex = S.dimensionless(y_ex, mom, tau)
     t_s = S.dimensionless(y_s, mom, tau)
     ok = fl_ex == 0
     rel = ((t_s - t_ex).norm(dim=1) / t_ex.norm(dim=1))[ok]
-    fb = ((fl_s & api.FLAG_FALLBACK) != 0)
     net = ~fb & ok
     rel_net = ((t_s - t_ex).norm(dim=1) / t_ex.norm(dim=1))[net]
     sd = s.y_sigma[:9].double()
@@ -77,7 +88,7 @@ def evaluate(s: S.Surrogate, n_cells, seed, eps2_hat):
         return float(torch.quantile(x.float().cpu(), p)) if x.numel() else float("nan")
 
     return {
-        "cells": n_cells, "seed": seed,
+        "cells": n_cells, "seed": seed, "inputs": s.features_set,
         "fallback_rate": float(fb.double().mean()),
         "range_flag_rate": float(((fl_s & api.FLAG_RANGE) != 0).double().mean()),
         "energy_flag_rate": float(((fl_s & api.FLAG_ENERGY) != 0).double().mean()),
@@ -99,15 +110,17 @@ def main():
     ap.add_argument("--eps2-hat", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--eval-cells", type=int, default=131072)
+    ap.add_argument("--features", choices=sorted(S.FEATURE_SETS), default="full",
+                    help="network inputs: the 25 high-order moments or the 16 LITE inputs")
     ap.add_argument("--out", default=os.path.join(os.path.dirname(__file__), "weights",
                                                   "surrogate_couette_cavity.fpw"))
     args = ap.parse_args()
     torch.cuda.set_device(0)
     t0 = time.time()
     print(f"labelling {args.cells} training cells")
-    ts = build_training_set(args.cells, args.seed, args.eps2_hat)
+    ts = build_training_set(args.cells, args.seed, args.eps2_hat, features=args.features)
     t_label = time.time() - t0
-    s = S.Surrogate(eps2_hat=args.eps2_hat, seed=args.seed)
+    s = S.Surrogate(eps2_hat=args.eps2_hat, seed=args.seed, features=args.features)
     s.init_params()
     S.fit_scalers(s, ts)
     tr = S.Trainer(s, batch=args.batch, lr=args.lr)
@@ -116,7 +129,7 @@ def main():
     t_train = time.time() - t1
     os.makedirs(os.path.dirname(args.out), exist_ok=True)
     s.save(args.out)
-    rep = {"training_cells": len(ts), "epochs": args.epochs, "batch": args.batch, "lr": args.lr,
+    rep = {"inputs": args.features, "training_cells": len(ts), "epochs": args.epochs, "batch": args.batch, "lr": args.lr,
            "lr_decay": args.lr_decay,
            "loss_history": hist, "label_seconds": t_label, "train_seconds": t_train,
            "held_out": evaluate(s, args.eval_cells, seed=987654, eps2_hat=args.eps2_hat)}
