@@ -21,6 +21,10 @@
 // folded with two-sum; lanes combine by a reduce-scatter.  Promotion to FP64
 // scales by the power of two in FP32 (exact), converts hi and lo parts and
 // adds them: one FP64-pipe instruction per moment.
+//
+// The same kernel, instantiated with kLite, serves the LITE moment pass:
+// only the 9 sums of u_ij and b_i = <c_i |c|^2> a particle, written as the
+// FP_NLITE vector (N, U, theta, u_ij, b_i).
 #include <cstdint>
 
 #include "fp_device.cuh"
@@ -51,11 +55,20 @@ struct SlotMeta {
 
 // One cell per kTileG-lane group, the warp's groups in lockstep; px/py/pz
 // point at the cell's first particle (shared or global memory).
-template <bool kShared>
+constexpr int kLiteSum = 9;  // u_ij (6, order 2), c_i |c|^2 (3, order 3)
+
+template <bool kLite>
+__device__ __forceinline__ int tile_order(int q) {
+  if (kLite) return q < 6 ? 2 : 3;
+  return sum_order(q);
+}
+
+template <bool kShared, bool kLite>
 __device__ __forceinline__ void reduce_cells(bool valid, int n, const float *px, const float *py, const float *pz,
                                              int64_t c, double *__restrict__ mom, double *__restrict__ m6,
                                              int lane) {
   constexpr int G = kTileG;
+  constexpr int NS = kLite ? kLiteSum : kNSum;
   constexpr int K = 32 / G;
   constexpr int BLK = 32;  // particles per lane summed plainly before a two-sum fold
   const int lg = lane & (G - 1);
@@ -115,9 +128,9 @@ __device__ __forceinline__ void reduce_cells(bool valid, int n, const float *px,
     lo[q] = 0.f;
   }
   for (int it0 = 0; it0 < itmax; it0 += BLK) {
-    float t[kNSum];
+    float t[NS];
 #pragma unroll
-    for (int q = 0; q < kNSum; ++q) t[q] = 0.f;
+    for (int q = 0; q < NS; ++q) t[q] = 0.f;
     const int itend = min(it0 + BLK, itmax);
     for (int it = it0; it < itend; ++it) {
       const int i = it * G + lg;
@@ -129,23 +142,28 @@ __device__ __forceinline__ void reduce_cells(bool valid, int n, const float *px,
       const float wz = ((ld(pz, ii) - v0z) - mz) * sm;
       const float xx = wx * wx, xy = wx * wy, xz = wx * wz, yy = wy * wy, yz = wy * wz, zz = wz * wz;
       t[0] += xx; t[1] += xy; t[2] += xz; t[3] += yy; t[4] += yz; t[5] += zz;
-      t[6] = fmaf(xx, wx, t[6]);  t[7] = fmaf(xx, wy, t[7]);   t[8] = fmaf(xx, wz, t[8]);
-      t[9] = fmaf(xy, wy, t[9]);  t[10] = fmaf(xy, wz, t[10]); t[11] = fmaf(xz, wz, t[11]);
-      t[12] = fmaf(yy, wy, t[12]); t[13] = fmaf(yy, wz, t[13]); t[14] = fmaf(yz, wz, t[14]);
-      t[15] = fmaf(zz, wz, t[15]);
-      const float r2 = xx + yy + zz;
-      t[16] = fmaf(r2, xx, t[16]); t[17] = fmaf(r2, xy, t[17]); t[18] = fmaf(r2, xz, t[18]);
-      t[19] = fmaf(r2, yy, t[19]); t[20] = fmaf(r2, yz, t[20]); t[21] = fmaf(r2, zz, t[21]);
-      const float r4 = r2 * r2;
-      t[22] = fmaf(r4, wx, t[22]); t[23] = fmaf(r4, wy, t[23]); t[24] = fmaf(r4, wz, t[24]);
-      t[25] = fmaf(r4, r2, t[25]);
+      if constexpr (kLite) {
+        const float r2 = xx + yy + zz;
+        t[6] = fmaf(r2, wx, t[6]); t[7] = fmaf(r2, wy, t[7]); t[8] = fmaf(r2, wz, t[8]);
+      } else {
+        t[6] = fmaf(xx, wx, t[6]);  t[7] = fmaf(xx, wy, t[7]);   t[8] = fmaf(xx, wz, t[8]);
+        t[9] = fmaf(xy, wy, t[9]);  t[10] = fmaf(xy, wz, t[10]); t[11] = fmaf(xz, wz, t[11]);
+        t[12] = fmaf(yy, wy, t[12]); t[13] = fmaf(yy, wz, t[13]); t[14] = fmaf(yz, wz, t[14]);
+        t[15] = fmaf(zz, wz, t[15]);
+        const float r2 = xx + yy + zz;
+        t[16] = fmaf(r2, xx, t[16]); t[17] = fmaf(r2, xy, t[17]); t[18] = fmaf(r2, xz, t[18]);
+        t[19] = fmaf(r2, yy, t[19]); t[20] = fmaf(r2, yz, t[20]); t[21] = fmaf(r2, zz, t[21]);
+        const float r4 = r2 * r2;
+        t[22] = fmaf(r4, wx, t[22]); t[23] = fmaf(r4, wy, t[23]); t[24] = fmaf(r4, wz, t[24]);
+        t[25] = fmaf(r4, r2, t[25]);
+      }
     }
     if (it0 == 0) {
 #pragma unroll
-      for (int q = 0; q < kNSum; ++q) hi[q] = t[q];
+      for (int q = 0; q < NS; ++q) hi[q] = t[q];
     } else {
 #pragma unroll
-      for (int q = 0; q < kNSum; ++q) {
+      for (int q = 0; q < NS; ++q) {
         float sum, err;
         two_sum(hi[q], t[q], sum, err);
         hi[q] = sum;
@@ -162,7 +180,7 @@ __device__ __forceinline__ void reduce_cells(bool valid, int n, const float *px,
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     const int q = lg * K + j;
-    const int ord = q < kNSum ? sum_order(q) : 0;
+    const int ord = q < NS ? tile_order<kLite>(q) : 0;
     float p, e;
     df_scale(hi[j], lo[j], rh, rl, p, e);
     const float sc = ldexpf(1.f, -ks * ord);
@@ -173,12 +191,16 @@ __device__ __forceinline__ void reduce_cells(bool valid, int n, const float *px,
   const double u22 = __shfl_sync(0xffffffffu, val[3 % K], gbase + 3 / K);
   const double u33 = __shfl_sync(0xffffffffu, val[5 % K], gbase + 5 / K);
   if (!valid) return;
-  double *mo = mom + c * FP_NMOM;
+  double *mo = mom + c * (kLite ? FP_NLITE : FP_NMOM);
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     const int q = lg * K + j;
-    if (q < kNMomSum) mo[kU2 + q] = val[j];
-    if (q == kM6Sum && m6) m6[c] = val[j];
+    if (kLite) {
+      if (q < kLiteSum) mo[kU2 + q] = val[j];  // u_ij at 5..10, b_i at 11..13
+    } else {
+      if (q < kNMomSum) mo[kU2 + q] = val[j];
+      if (q == kM6Sum && m6) m6[c] = val[j];
+    }
   }
   if (lg >= 1 && lg <= 3) {
     const float v0 = lg == 1 ? v0x : (lg == 2 ? v0y : v0z);
@@ -193,11 +215,11 @@ __device__ __forceinline__ void reduce_cells(bool valid, int n, const float *px,
 
 // Mark every cell of this CTA's chunks non-finite (theta = NaN): used when a
 // bounded wait ran out, so the closure flags the cells FP_FLAG_NONFINITE.
-__device__ void mark_failed(int64_t n_cells, int64_t n_chunks, double *__restrict__ mom, int tid) {
+__device__ void mark_failed(int64_t n_cells, int64_t n_chunks, double *__restrict__ mom, int stride, int tid) {
   for (int64_t j = blockIdx.x; j < n_chunks; j += gridDim.x) {
     const int64_t c0 = j * kChunkCells;
     const int64_t c1 = c0 + kChunkCells < n_cells ? c0 + kChunkCells : n_cells;
-    for (int64_t c = c0 + tid; c < c1; c += kTileThreads) mom[c * FP_NMOM + kTheta] = __longlong_as_double(-1ll);
+    for (int64_t c = c0 + tid; c < c1; c += kTileThreads) mom[c * stride + kTheta] = __longlong_as_double(-1ll);
   }
 }
 
@@ -233,6 +255,7 @@ __device__ __forceinline__ void rank_cells(int ncell, int na, int nb, uint8_t *o
   if (lane + 32 < ncell) order[lane + 32] = (uint8_t)(63 - (kb & 63u));
 }
 
+template <bool kLite>
 __global__ void __launch_bounds__(kTileThreads, 2)
     gather_tile_kernel(const float *__restrict__ v, int64_t np, const int64_t *__restrict__ off, int64_t n_cells,
                        double *__restrict__ mom, double *__restrict__ m6, int64_t n_chunks) {
@@ -423,10 +446,10 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         const int64_t a = M.offs[rc];
         const int n = valid ? (int)(M.offs[rc + 1] - a) : 0;
         if (M.big) {
-          reduce_cells<false>(valid, n, v + a, v + np + a, v + 2 * np + a, c, mom, m6, lane);
+          reduce_cells<false, kLite>(valid, n, v + a, v + np + a, v + 2 * np + a, c, mom, m6, lane);
         } else {
           const int64_t rel = a - M.pa;
-          reduce_cells<true>(valid, n, bx + M.lead[0] + rel, bx + kCapF + M.lead[1] + rel,
+          reduce_cells<true, kLite>(valid, n, bx + M.lead[0] + rel, bx + kCapF + M.lead[1] + rel,
                              bx + 2 * kCapF + M.lead[2] + rel, c, mom, m6, lane);
         }
       }
@@ -436,28 +459,41 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     if (!ok && lane == 0) atomicExch(&failed, 1);
   }
   __syncthreads();
-  if (failed) mark_failed(n_cells, n_chunks, mom, tid);
+  if (failed) mark_failed(n_cells, n_chunks, mom, kLite ? FP_NLITE : FP_NMOM, tid);
 }
 
-static int g_tile_attr_done[64];
+static int g_tile_attr_done[2][64];
 
-bool launch_gather_tile(const float *v, int64_t np, const int64_t *off, int64_t n_cells, double *mom, double *m6,
+template <bool kLite>
+static bool launch_tile(const float *v, int64_t np, const int64_t *off, int64_t n_cells, double *mom, double *m6,
                         cudaStream_t st, int sm_count) {
   if (((uintptr_t)v & 15) != 0) return false;
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !g_tile_attr_done[dev]) {
-    if (cudaFuncSetAttribute(gather_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem) !=
-        cudaSuccess)
+  if (dev >= 0 && dev < 64 && !g_tile_attr_done[kLite][dev]) {
+    if (cudaFuncSetAttribute(gather_tile_kernel<kLite>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kTileSmem) != cudaSuccess)
       return false;
-    g_tile_attr_done[dev] = 1;
+    g_tile_attr_done[kLite][dev] = 1;
   }
   const int64_t n_chunks = (n_cells + kChunkCells - 1) / kChunkCells;
   int64_t grid = (int64_t)sm_count * 2;
   if (grid > n_chunks) grid = n_chunks;
   if (grid < 1) grid = 1;
-  gather_tile_kernel<<<(unsigned)grid, kTileThreads, kTileSmem, st>>>(v, np, off, n_cells, mom, m6, n_chunks);
+  gather_tile_kernel<kLite><<<(unsigned)grid, kTileThreads, kTileSmem, st>>>(v, np, off, n_cells, mom, m6,
+                                                                              n_chunks);
   return true;
+}
+
+bool launch_gather_tile(const float *v, int64_t np, const int64_t *off, int64_t n_cells, double *mom, double *m6,
+                        cudaStream_t st, int sm_count) {
+  return launch_tile<false>(v, np, off, n_cells, mom, m6, st, sm_count);
+}
+
+// LITE vectors [n_cells][FP_NLITE] from FP32 velocities
+bool launch_gather_tile_lite(const float *v, int64_t np, const int64_t *off, int64_t n_cells, double *lite,
+                             cudaStream_t st, int sm_count) {
+  return launch_tile<true>(v, np, off, n_cells, lite, nullptr, st, sm_count);
 }
 
 }  // namespace fpc

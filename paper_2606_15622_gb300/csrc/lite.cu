@@ -271,8 +271,15 @@ static int lite_sm_count() {
   return n;
 }
 
+bool launch_gather_tile_lite(const float *v, int64_t np, const int64_t *off, int64_t n_cells, double *lite,
+                             cudaStream_t st, int sm_count);
+
+// FP32 velocities (16-byte aligned) take the shared-memory streamed gather;
+// FP64 velocities the direct one below.
 void launch_gather_lite(const void *v, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, double *lite,
                         cudaStream_t st) {
+  if (v_dtype == FP_V_F32 && launch_gather_tile_lite((const float *)v, np, off, n_cells, lite, st, lite_sm_count()))
+    return;
   constexpr int G = 8;
   const int threads = 256;
   const int64_t cells_per_block = (threads / 32) * (32 / G);

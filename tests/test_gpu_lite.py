@@ -48,11 +48,27 @@ def test_lite_moments_match_oracle(vdtype):
     _check_lite(got, ref)
 
 
-def test_lite_moments_match_oracle_on_cavity(cavity_pop):
+@pytest.mark.parametrize("vdtype", ["f32", "f64"])
+def test_lite_moments_match_oracle_on_cavity(cavity_pop, vdtype):
+    """FP32 velocities take the shared-memory streamed gather, FP64 ones the
+    direct one."""
     pop = cavity_pop
-    got = api.fp_moments_lite(torch.from_numpy(pop.v64).cuda(), torch.from_numpy(pop.offsets).cuda())
+    v = pop.v32 if vdtype == "f32" else pop.v64
+    got = api.fp_moments_lite(torch.from_numpy(v).cuda(), torch.from_numpy(pop.offsets).cuda())
     torch.cuda.synchronize()
-    _check_lite(got.cpu().numpy(), L.lite_moments(pop.v64, pop.offsets))
+    _check_lite(got.cpu().numpy(), L.lite_moments(v.astype(np.float64), pop.offsets))
+
+
+def test_lite_moments_unaligned_velocities():
+    """Velocities not 16-byte aligned (a view one float into a buffer) take
+    the direct gather; results agree all the same."""
+    pop = P.maxwellian_cells([5, 300, 0, 3000, 17], theta=1.3, seed=8)
+    n = pop.n_particles
+    buf = torch.zeros(3 * n + 1, dtype=torch.float32, device="cuda")
+    buf[1:].copy_(torch.from_numpy(pop.v32.reshape(-1)))
+    v = buf[1:].view(3, n)
+    got = api.fp_moments_lite(v, torch.from_numpy(pop.offsets).cuda()).cpu().numpy()
+    _check_lite(got, L.lite_moments(pop.v32.astype(np.float64), pop.offsets))
 
 
 def test_lite_moments_full_size_sampled():
