@@ -280,6 +280,16 @@ def run_ours(args):
         xf, _ = sur.features(mom, tau, params=prm)
         of = torch.empty((n_cells, 16), dtype=torch.float32, device=dev)
         fns["mlp"] = lambda: sur.forward(xf, standardized=False, out=of, stream=stream)
+        cell_sorted = np.repeat(np.arange(n_cells), pop.counts)
+        rng_cs = np.random.default_rng(17)
+        moved = rng_cs.random(n_p) < 0.03
+        c_near = np.where(moved, np.clip(cell_sorted + rng_cs.integers(-1, 2, n_p), 0, n_cells - 1), cell_sorted)
+        c_near_d = torch.from_numpy(c_near.astype(np.int32)).to(dev)
+        vs_b = torch.empty_like(v0)
+        fns["sort"] = lambda: api.fp_sort_by_cell(c_near_d, n_cells, v=v0, v_sorted=vs_b, stream=stream)
+        fns["collision"] = lambda: api.fp_collision_step(c_near_d, v0, n_cells, tau, 0.1, params=prm, prec="fp32",
+                                                         v_out=vs_b, coeffs_out=coeffs, flags_out=flags,
+                                                         stream=stream)
         lite = torch.empty((n_cells, api.NLITE), dtype=torch.float64, device=dev)
         fns["gather_lite"] = lambda: api.fp_moments_lite(vb[cur[0]], off, out=lite, stream=stream)
         if os.path.exists(WEIGHTS_LITE):
@@ -437,6 +447,48 @@ def run_ours(args):
                     "note": "LITE moment pass (N, U, theta, u_ij, heat flux) + network on the 16 low-order "
                             "inputs; no exact fallback (flagged cells take the linear drift)"}
 
+    # ---- collision step from particles in any order (sort + closure + update) --
+    # "nearly sorted": the cell order of the previous step with 3 % of the
+    # particles moved to a neighbouring cell; "shuffled": random order
+    cell_sorted = np.repeat(np.arange(n_cells), pop.counts)
+    rng_cs = np.random.default_rng(17)
+    moved = rng_cs.random(n_p) < 0.03
+    c_near = np.where(moved, np.clip(cell_sorted + rng_cs.integers(-1, 2, n_p), 0, n_cells - 1), cell_sorted)
+    c_near_d = torch.from_numpy(c_near.astype(np.int32)).to(dev)
+    shuf = rng_cs.permutation(n_p)
+    c_shuf_d = torch.from_numpy(cell_sorted[shuf].astype(np.int32)).to(dev)
+    sort_ws = torch.empty(int(api.lib().fp_sort_workspace_bytes(n_p, n_cells)), dtype=torch.uint8, device=dev)
+    perm_b = torch.empty(n_p, dtype=torch.int32, device=dev)
+    off_b = torch.empty(n_cells + 1, dtype=torch.int64, device=dev)
+    vs_b = torch.empty_like(v0)
+    t_sort_near = float(np.median(timed(lambda: api.fp_sort_by_cell(c_near_d, n_cells, v=v0, v_sorted=vs_b,
+                                                                    perm_out=perm_b, offsets_out=off_b,
+                                                                    workspace=sort_ws, stream=stream), 10, 2)))
+    t_sort_shuf = float(np.median(timed(lambda: api.fp_sort_by_cell(c_shuf_d, n_cells, v=v0, v_sorted=vs_b,
+                                                                    perm_out=perm_b, offsets_out=off_b,
+                                                                    workspace=sort_ws, stream=stream), 10, 2)))
+    cs_ws = torch.empty(int(api.lib().fp_collision_step_workspace_bytes(n_p, n_cells, api.V_F32, 1)),
+                        dtype=torch.uint8, device=dev)
+    cs_ws_ex = torch.empty(int(api.lib().fp_collision_step_workspace_bytes(n_p, n_cells, api.V_F32, 0)),
+                           dtype=torch.uint8, device=dev)
+
+    def c_collision(lite_net=None, cells=c_near_d):
+        api.fp_collision_step(cells, v0, n_cells, tau, 0.1, params=prm, prec="fp32", net_lite=lite_net, seed=1234,
+                              step=step_idx[0], v_out=vs_b, perm_out=perm_b, offsets_out=off_b, coeffs_out=coeffs,
+                              flags_out=flags, workspace=cs_ws if lite_net is not None else cs_ws_ex, stream=stream)
+
+    t_cs_ex = float(np.median(timed(lambda: c_collision(None), 10, 2)))
+    t_cs_lite = float(np.median(timed(lambda: c_collision(sl.net()), 10, 2))) if lite_rep is not None else None
+    collision_rep = {
+        "input": "cylinder particles; nearly sorted = previous cell order with 3 % moved to a neighbouring cell",
+        "sort_nearly_sorted_ms": round(t_sort_near, 5), "sort_shuffled_ms": round(t_sort_shuf, 5),
+        "sort_particles_per_s": round(n_p / (t_sort_near * 1e-3), 1),
+        "exact_step_ms": round(t_cs_ex, 5), "exact_step_particles_per_s": round(n_p / (t_cs_ex * 1e-3), 1),
+        "lite_step_ms": round(t_cs_lite, 5) if t_cs_lite else None,
+        "lite_step_particles_per_s": round(n_p / (t_cs_lite * 1e-3), 1) if t_cs_lite else None,
+        "note": "one fp_collision_step call: stable radix sort by cell, velocity gather, moments, closure "
+                "(exact FP32-moment / FP64 solve, or the learned closure on LITE inputs), velocity update"}
+
     # ---- adjoint on the cavity-shaped population (C4) -----------------------
     cav = P.cavity(seed=4)
     cv = torch.from_numpy(cav.v32).to(dev)
@@ -532,6 +584,7 @@ def run_ours(args):
                                                      "max": round(float(e.abs().max()), 6)},
                              "inputs": "131072 held-out cells of the training distributions, tiled x8"},
             "lite_on_cylinder": lite_rep if lite_rep is not None else {"unavailable": "no LITE weight file"},
+            "collision_step_cylinder": collision_rep,
             "adjoint_cavity": {"cells": cav.n_cells, "particles": cav.n_particles,
                                "forward_ms": round(t_fwd_c4, 5), "backward_ms": round(t_bwd_c4, 5),
                                "fwd_bwd_cells_per_s": round(cav.n_cells / ((t_fwd_c4 + t_bwd_c4) * 1e-3), 1)},
@@ -620,7 +673,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default=None,
                     choices=["gather", "gather64", "solve", "exact_closure", "surrogate_closure", "adjoint",
-                             "velocity_update", "step", "mlp", "gather_lite", "lite"],
+                             "velocity_update", "step", "mlp", "gather_lite", "lite", "sort", "collision"],
                     help="profiling mode: launch one call --steps times, print no bench line")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -389,6 +389,15 @@ int fp_moments_lite(const void *v, int v_dtype, int64_t n_particles, const int64
 int fp_surrogate_lite_features(const fp_mlp *net, const double *lite, int64_t n_cells, const double *tau,
                                const fp_params *p, void *x_out, int32_t *flags_out, fp_stream_t stream);
 
+/* fp_velocity_update_lite: fp_velocity_update from LITE vectors
+ * [n_cells][FP_NLITE] (U, theta and b_i are all the update reads; the cell
+ * averages of Eq. update_alpha are summed over the particles in a first
+ * pass).  Other arguments as fp_velocity_update (without m6). */
+int fp_velocity_update_lite(void *v, void *v_out, int v_dtype, int64_t n_particles, const int64_t *cell_offsets,
+                            int64_t n_cells, const double *lite, const double *coeffs, const double *tau, double dt,
+                            const fp_params *p, const void *xi, uint64_t seed, uint64_t step, double *alpha_out,
+                            int32_t *flags, fp_stream_t stream);
+
 size_t fp_surrogate_lite_workspace_bytes(int64_t n_cells);
 
 /* fp_closure_surrogate_lite: the learned closure on the LITE inputs:
@@ -401,6 +410,56 @@ size_t fp_surrogate_lite_workspace_bytes(int64_t n_cells);
 int fp_closure_surrogate_lite(const fp_mlp *net, const double *lite, int64_t n_cells, const double *tau,
                               const fp_params *p, double *coeffs_out, int32_t *flags_out, void *ws, size_t ws_bytes,
                               fp_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Cell sort and the collision step (Alg. 1 and Alg. 2: particles sorted by
+ * cell, moments, closure, velocity update).
+ *
+ * fp_sort_by_cell: the stable permutation that orders particles by cell
+ * index, the CSR offsets and (optionally) the velocities in that order.
+ *   cell_of      [n_particles] int32 cell index per particle; an index outside
+ *                [0, n_cells) puts the particle behind the last cell, in no
+ *                cell (cell_offsets_out[n_cells] < n_particles counts them)
+ *   v            [3][n_particles] SoA (FP_V_F32 / FP_V_F64), or NULL
+ *   v_sorted     [3][n_particles] (same dtype; required when v is given, must
+ *                not alias v): v_sorted[d][i] = v[d][perm_out[i]]
+ *   perm_out     [n_particles] int32: input index of the particle at sorted
+ *                position i; equal cell indices keep their input order
+ *   cell_offsets_out [n_cells + 1] int64: first sorted position of each cell,
+ *                offsets[n_cells] = particles inside the cells
+ *   ws           >= fp_sort_workspace_bytes(n_particles, n_cells), 256-byte
+ *                aligned (keys and indices twice, digit counts)
+ * n_particles <= 2^31 - 1 and n_cells <= 2^31 - 2, else FP_ERR_UNSUPPORTED.
+ * Result identical on every run (integer work only). */
+size_t fp_sort_workspace_bytes(int64_t n_particles, int64_t n_cells);
+int fp_sort_by_cell(const int32_t *cell_of, int64_t n_particles, int64_t n_cells, const void *v, int v_dtype,
+                    void *v_sorted, int32_t *perm_out, int64_t *cell_offsets_out, void *ws, size_t ws_bytes,
+                    fp_stream_t stream);
+
+/* fp_collision_step: one collision step of unsorted particles in one call:
+ * fp_sort_by_cell, then either the exact cubic-FP closure (net_lite NULL:
+ * moments in `prec` with <|c|^6>, FP64 assembly and solve, the velocity update
+ * with alpha from the moments) or the learned closure on LITE inputs (net_lite
+ * a network trained on them: LITE moment pass, fp_closure_surrogate_lite,
+ * the velocity update with alpha from a pass over the particles), with
+ * Philox noise keyed by (seed, step) on the sorted particle index.
+ *   v          [3][n_particles] input velocities, any order
+ *   v_out      [3][n_particles] updated velocities in sorted order (may alias
+ *              v; particles in no cell are copied unchanged)
+ *   perm_out, cell_offsets_out   as fp_sort_by_cell (reorder other particle
+ *              arrays of the caller with perm_out)
+ *   tau        [n_cells] f64; coeffs_out [n_cells][9] f64; flags_out
+ *              [n_cells] int32 (closure flags | FP_FLAG_ALPHA)
+ *   moments_out  [n_cells][FP_NMOM] (exact) or [n_cells][FP_NLITE] (LITE)
+ *              f64, or NULL (kept in the workspace)
+ *   ws         >= fp_collision_step_workspace_bytes(n_particles, n_cells,
+ *              v_dtype, net_lite != NULL), 256-byte aligned */
+size_t fp_collision_step_workspace_bytes(int64_t n_particles, int64_t n_cells, int v_dtype, int lite);
+int fp_collision_step(const int32_t *cell_of, const void *v, int v_dtype, int64_t n_particles, int64_t n_cells,
+                      const double *tau, const fp_params *p, int prec, const fp_mlp *net_lite, double dt,
+                      uint64_t seed, uint64_t step, void *v_out, int32_t *perm_out, int64_t *cell_offsets_out,
+                      double *coeffs_out, int32_t *flags_out, double *moments_out, void *ws, size_t ws_bytes,
+                      fp_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Diagnostics and deployment options of the learned closure.

@@ -115,6 +115,19 @@ def speed_moment6(v, offsets):
 NDIAG = 12
 
 
+def sort_by_cell(cell_of, n_cells):
+    """The cell sort of Alg. 1 / Alg. 2 (particles ordered by cell index),
+    stable: (perm, offsets) with perm[i] the input index of the particle at
+    sorted position i and offsets[c] the first sorted position of cell c
+    (c = 0..n_cells).  Indices outside [0, n_cells) count as n_cells: those
+    particles follow the last cell and belong to none."""
+    cell_of = np.asarray(cell_of, dtype=np.int64)
+    key = np.where((cell_of >= 0) & (cell_of < n_cells), cell_of, n_cells)
+    perm = np.argsort(key, kind="stable")
+    offsets = np.searchsorted(key[perm], np.arange(n_cells + 1), side="left")
+    return perm.astype(np.int64), offsets.astype(np.int64)
+
+
 def diagnostics(m, m6, rho=None, theta_inf=1.0, rho_inf=1.0, dg_inf=0.0):
     """Per-cell high-order diagnostics and covariance entropy proxies
     [n_cells, 12], written out from their definitions (the cavity study's

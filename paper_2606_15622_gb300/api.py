@@ -111,6 +111,14 @@ SIGNATURES = {
                                        _vp]),
     "fp_closure_exact_static_error": (ctypes.c_char_p, []),
     "fp_moments_lite": (_i32, [_vp, _i32, _i64, _vp, _i64, _vp, _vp]),
+    "fp_velocity_update_lite": (_i32, [_vp, _vp, _i32, _i64, _vp, _i64, _vp, _vp, _vp, _dbl,
+                                       ctypes.POINTER(Params), _vp, _u64, _u64, _vp, _vp, _vp]),
+    "fp_sort_workspace_bytes": (_sz, [_i64, _i64]),
+    "fp_sort_by_cell": (_i32, [_vp, _i64, _i64, _vp, _i32, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "fp_collision_step_workspace_bytes": (_sz, [_i64, _i64, _i32, _i32]),
+    "fp_collision_step": (_i32, [_vp, _vp, _i32, _i64, _i64, _vp, ctypes.POINTER(Params), _i32,
+                                 ctypes.POINTER(FpMlp), _dbl, _u64, _u64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz,
+                                 _vp]),
     "fp_surrogate_lite_features": (_i32, [ctypes.POINTER(FpMlp), _vp, _i64, _vp, ctypes.POINTER(Params), _vp, _vp,
                                           _vp]),
     "fp_surrogate_lite_workspace_bytes": (_sz, [_i64]),
@@ -406,6 +414,54 @@ def fp_moments_lite(v, offsets, out=None, stream=None):
     return out
 
 
+def fp_sort_by_cell(cell_of, n_cells, v=None, v_sorted=None, perm_out=None, offsets_out=None, workspace=None,
+                    stream=None):
+    """Stable order of the particles by cell -> (perm int32 [n_p], offsets
+    int64 [n_cells + 1], v_sorted or None).  Cell indices outside
+    [0, n_cells) go behind the last cell."""
+    n_p = cell_of.numel()
+    dev = cell_of.device
+    if cell_of.dtype != torch.int32:
+        raise FPError("cell_of must be int32")
+    perm = perm_out if perm_out is not None else torch.empty(n_p, dtype=torch.int32, device=dev)
+    off = offsets_out if offsets_out is not None else torch.empty(n_cells + 1, dtype=torch.int64, device=dev)
+    if v is not None and v_sorted is None:
+        v_sorted = torch.empty_like(v)
+    need = int(lib().fp_sort_workspace_bytes(n_p, n_cells))
+    ws = workspace if workspace is not None else torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    _need_cuda(cell_of, perm, off, v, v_sorted, ws)
+    rc = lib().fp_sort_by_cell(_ptr(cell_of), n_p, n_cells, _ptr(v), _vdtype(v) if v is not None else 0,
+                               _ptr(v_sorted), _ptr(perm), _ptr(off), _ptr(ws), ws.numel(), _stream(stream))
+    _check(rc, "fp_sort_by_cell")
+    return perm, off, v_sorted
+
+
+def fp_collision_step(cell_of, v, n_cells, tau, dt, params: Params | None = None, prec="fp32", net_lite=None,
+                      seed=0, step=0, v_out=None, perm_out=None, offsets_out=None, coeffs_out=None, flags_out=None,
+                      moments_out=None, workspace=None, stream=None):
+    """Sort by cell, closure (exact, or the learned one on LITE inputs when
+    net_lite -- an FpMlp -- is given) and velocity update in one call ->
+    (v_out in sorted order, perm, offsets, coeffs, flags)."""
+    n_p = cell_of.numel()
+    dev = v.device
+    lite = net_lite is not None
+    v_out = v_out if v_out is not None else torch.empty_like(v)
+    perm = perm_out if perm_out is not None else torch.empty(n_p, dtype=torch.int32, device=dev)
+    off = offsets_out if offsets_out is not None else torch.empty(n_cells + 1, dtype=torch.int64, device=dev)
+    y = coeffs_out if coeffs_out is not None else torch.empty((n_cells, 9), dtype=torch.float64, device=dev)
+    fl = flags_out if flags_out is not None else torch.empty(n_cells, dtype=torch.int32, device=dev)
+    need = int(lib().fp_collision_step_workspace_bytes(n_p, n_cells, _vdtype(v), int(lite)))
+    ws = workspace if workspace is not None else torch.empty(need, dtype=torch.uint8, device=dev)
+    _need_cuda(cell_of, v, tau, v_out, perm, off, y, fl, moments_out, ws)
+    p = params if params is not None else default_params()
+    rc = lib().fp_collision_step(_ptr(cell_of), _ptr(v), _vdtype(v), n_p, n_cells, _ptr(tau), ctypes.byref(p),
+                                 _PREC.get(prec, prec), ctypes.byref(net_lite) if lite else None, float(dt),
+                                 int(seed), int(step), _ptr(v_out), _ptr(perm), _ptr(off), _ptr(y), _ptr(fl),
+                                 _ptr(moments_out), _ptr(ws), ws.numel(), _stream(stream))
+    _check(rc, "fp_collision_step")
+    return v_out, perm, off, y, fl
+
+
 def fp_closure_solve(moments, tau, params: Params | None = None, prec="fp32", coeffs_out=None, flags_out=None,
                      stream=None, lu_out=None):
     """Assembly + pivoted FP64 solve from moment vectors -> (coeffs, flags).
@@ -449,4 +505,25 @@ def fp_velocity_update(v, offsets, moments, coeffs, tau, flags, dt, params: Para
                                   _ptr(coeffs), _ptr(tau), float(dt), ctypes.byref(p), _ptr(xi), int(seed), int(step),
                                   _ptr(alpha_out), _ptr(flags), _stream(stream))
     _check(rc, "fp_velocity_update")
+    return (v if v_out is None else v_out), alpha_out, flags
+
+
+def fp_velocity_update_lite(v, offsets, lite, coeffs, tau, flags, dt, params: Params | None = None, xi=None,
+                            seed=0, step=0, alpha_out=None, stream=None, v_out=None):
+    """fp_velocity_update from LITE moment vectors [n_cells, NLITE] (alpha's
+    cell averages summed over the particles)."""
+    n_cells = offsets.numel() - 1
+    n_p = v.shape[-1] if v.dim() == 2 else v.numel() // 3
+    _need_cuda(v, offsets, lite, coeffs, tau, flags, xi, alpha_out, v_out)
+    if v_out is not None and (v_out.dtype != v.dtype or v_out.numel() != v.numel()):
+        raise FPError("v_out must be an array of v's shape and dtype")
+    if xi is not None and xi.dtype != v.dtype:
+        raise FPError("xi must have the velocity dtype")
+    if flags.dtype != torch.int32:
+        raise FPError("flags must be int32")
+    p = params if params is not None else default_params()
+    rc = lib().fp_velocity_update_lite(_ptr(v), _ptr(v_out), _vdtype(v), n_p, _ptr(offsets), n_cells, _ptr(lite),
+                                       _ptr(coeffs), _ptr(tau), float(dt), ctypes.byref(p), _ptr(xi), int(seed),
+                                       int(step), _ptr(alpha_out), _ptr(flags), _stream(stream))
+    _check(rc, "fp_velocity_update_lite")
     return (v if v_out is None else v_out), alpha_out, flags

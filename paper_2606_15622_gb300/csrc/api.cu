@@ -1,5 +1,6 @@
 // api.cu -- the C ABI of libfpclosure.so (declarations and contracts in
 // include/fpclosure.h): argument validation, workspace carving, launches.
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -31,6 +32,16 @@ void launch_lite_features(const fp_mlp &net, const double *lite, const double *t
                           double margin, void *x, int32_t *flags, cudaStream_t st);
 void launch_lite_epilogue(const float *tpred, const double *lite, const double *tau, int64_t n, double *coeffs,
                           int32_t *flags, cudaStream_t st);
+size_t sort_workspace_bytes(int64_t n, int64_t n_cells);
+void launch_sort_by_cell(const int32_t *cell_of, int64_t n, int64_t n_cells, int32_t *perm, int64_t *offsets,
+                         void *ws, cudaStream_t st, const uint32_t **sorted_keys);
+void launch_gather_sorted(const void *v, int v_dtype, int64_t n, const int32_t *perm, void *v_sorted,
+                          cudaStream_t st);
+void launch_copy_tail(const void *v, void *v_out, int v_dtype, int64_t n, const int64_t *first, cudaStream_t st);
+void launch_velocity_lite(const void *v, void *v_out, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells,
+                          const double *lite, const double *coeffs, const double *tau, double dt, double eps2_hat,
+                          const void *xi, uint64_t seed, uint64_t step, double *alpha_out, int32_t *flags,
+                          cudaStream_t st);
 void launch_diagnostics(const double *mom, const double *m6, const double *rho, int64_t n_cells, double theta_inf,
                         double rho_inf, double dg_inf, double *out, cudaStream_t st);
 void launch_relax(const double *y_new, double *y_prev, int64_t n, double w, cudaStream_t st);
@@ -186,13 +197,11 @@ int fp_closure_solve(const double *moments, const double *tau, int64_t n_cells, 
   return check_launch("solve");
 }
 
-int fp_velocity_update(void *v, void *v_out, int v_dtype, int64_t n_particles, const int64_t *cell_offsets,
-                       int64_t n_cells, const double *moments, const double *m6, const double *coeffs,
-                       const double *tau, double dt, const fp_params *p, const void *xi, uint64_t seed,
-                       uint64_t step, double *alpha_out, int32_t *flags, fp_stream_t stream) {
-  g_err[0] = 0;
+namespace {
+int check_update_args(const void *v, const void *v_out, int v_dtype, int64_t n_particles, const int64_t *cell_offsets,
+                      int64_t n_cells, const double *moments, const double *coeffs, const double *tau, double dt,
+                      const int32_t *flags) {
   if (n_cells < 0 || n_particles < 0) return fail(FP_ERR_ARG, "negative size");
-  if (n_cells == 0) return FP_OK;
   if (v_dtype != FP_V_F32 && v_dtype != FP_V_F64) return fail(FP_ERR_ARG, "v_dtype %d", v_dtype);
   if (!cell_offsets || !moments || !coeffs || !tau || !flags) return fail(FP_ERR_ARG, "null array pointer");
   if (n_particles > 0 && !v) return fail(FP_ERR_ARG, "null velocity pointer");
@@ -202,12 +211,41 @@ int fp_velocity_update(void *v, void *v_out, int v_dtype, int64_t n_particles, c
     const char *a = (const char *)v, *b = (const char *)v_out;
     if (a < b + bytes && b < a + bytes) return fail(FP_ERR_ARG, "v_out overlaps v without being v");
   }
+  return FP_OK;
+}
+}  // namespace
+
+int fp_velocity_update(void *v, void *v_out, int v_dtype, int64_t n_particles, const int64_t *cell_offsets,
+                       int64_t n_cells, const double *moments, const double *m6, const double *coeffs,
+                       const double *tau, double dt, const fp_params *p, const void *xi, uint64_t seed,
+                       uint64_t step, double *alpha_out, int32_t *flags, fp_stream_t stream) {
+  g_err[0] = 0;
+  if (n_cells == 0 && n_particles >= 0) return FP_OK;
+  if (int rc = check_update_args(v, v_out, v_dtype, n_particles, cell_offsets, n_cells, moments, coeffs, tau, dt,
+                                 flags))
+    return rc;
   fp_params prm;
   fp_default_params(&prm);
   if (p) prm = *p;
   fpc::launch_velocity(v, v_out ? v_out : v, v_dtype, n_particles, cell_offsets, n_cells, moments, m6, coeffs, tau,
                        dt, prm.eps2_hat, xi, seed, step, alpha_out, flags, (cudaStream_t)stream);
   return check_launch("velocity");
+}
+
+int fp_velocity_update_lite(void *v, void *v_out, int v_dtype, int64_t n_particles, const int64_t *cell_offsets,
+                            int64_t n_cells, const double *lite, const double *coeffs, const double *tau, double dt,
+                            const fp_params *p, const void *xi, uint64_t seed, uint64_t step, double *alpha_out,
+                            int32_t *flags, fp_stream_t stream) {
+  g_err[0] = 0;
+  if (n_cells == 0 && n_particles >= 0) return FP_OK;
+  if (int rc = check_update_args(v, v_out, v_dtype, n_particles, cell_offsets, n_cells, lite, coeffs, tau, dt, flags))
+    return rc;
+  fp_params prm;
+  fp_default_params(&prm);
+  if (p) prm = *p;
+  fpc::launch_velocity_lite(v, v_out ? v_out : v, v_dtype, n_particles, cell_offsets, n_cells, lite, coeffs, tau, dt,
+                            prm.eps2_hat, xi, seed, step, alpha_out, flags, (cudaStream_t)stream);
+  return check_launch("velocity_lite");
 }
 
 int fp_closure_backward(const void *v, int v_dtype, int64_t n_particles, const int64_t *cell_offsets,
@@ -432,6 +470,125 @@ int fp_closure_surrogate_lite(const fp_mlp *net, const double *lite, int64_t n_c
     return fail(FP_ERR_CUDA, "could not raise the shared-memory limit of the MLP kernel");
   fpc::launch_lite_epilogue(tpred, lite, tau, n_cells, coeffs_out, flags_out, st);
   return check_launch("surrogate_lite");
+}
+
+size_t fp_sort_workspace_bytes(int64_t n_particles, int64_t n_cells) {
+  if (n_particles < 0 || n_cells < 0) return 0;
+  return fpc::sort_workspace_bytes(n_particles, n_cells);
+}
+
+namespace {
+int check_sort_args(const int32_t *cell_of, int64_t n_particles, int64_t n_cells, const void *v, int v_dtype,
+                    const void *v_sorted, const int32_t *perm, const int64_t *offsets) {
+  if (n_particles < 0 || n_cells < 0) return fail(FP_ERR_ARG, "negative size");
+  if (n_particles > 2147483647ll || n_cells > 2147483646ll)
+    return fail(FP_ERR_UNSUPPORTED, "sort limited to 2^31 - 1 particles and 2^31 - 2 cells");
+  if (!offsets) return fail(FP_ERR_ARG, "null offsets pointer");
+  if (n_particles > 0 && (!cell_of || !perm)) return fail(FP_ERR_ARG, "null array pointer");
+  if (v) {
+    if (v_dtype != FP_V_F32 && v_dtype != FP_V_F64) return fail(FP_ERR_ARG, "v_dtype %d", v_dtype);
+    if (!v_sorted) return fail(FP_ERR_ARG, "null sorted-velocity pointer");
+    if (v_sorted == v && n_particles > 0) return fail(FP_ERR_ARG, "v_sorted aliases v");
+  }
+  return FP_OK;
+}
+}  // namespace
+
+int fp_sort_by_cell(const int32_t *cell_of, int64_t n_particles, int64_t n_cells, const void *v, int v_dtype,
+                    void *v_sorted, int32_t *perm_out, int64_t *cell_offsets_out, void *ws, size_t ws_bytes,
+                    fp_stream_t stream) {
+  g_err[0] = 0;
+  if (int rc = check_sort_args(cell_of, n_particles, n_cells, v, v_dtype, v_sorted, perm_out, cell_offsets_out))
+    return rc;
+  const size_t need = fpc::sort_workspace_bytes(n_particles, n_cells);
+  if (!ws || ws_bytes < need) return fail(FP_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", need, ws_bytes);
+  if ((uintptr_t)ws % kAlign) return fail(FP_ERR_ARG, "workspace not 256-byte aligned");
+  const cudaStream_t st = (cudaStream_t)stream;
+  fpc::launch_sort_by_cell(cell_of, n_particles, n_cells, perm_out, cell_offsets_out, ws, st, nullptr);
+  if (v) fpc::launch_gather_sorted(v, v_dtype, n_particles, perm_out, v_sorted, st);
+  return check_launch("sort_by_cell");
+}
+
+namespace {
+struct StepLayout {
+  size_t sort, vs, mom, m6, sur, total;
+};
+StepLayout step_layout(int64_t n_particles, int64_t n_cells, int v_dtype, int lite) {
+  StepLayout L{};
+  size_t o = align_up(fpc::sort_workspace_bytes(n_particles, n_cells));
+  L.vs = o;
+  o += align_up((size_t)n_particles * 3 * (v_dtype == FP_V_F64 ? 8 : 4));
+  L.mom = o;
+  o += align_up((size_t)n_cells * (lite ? FP_NLITE : FP_NMOM) * 8);
+  L.m6 = o;
+  if (!lite) o += align_up((size_t)n_cells * 8);
+  L.sur = o;
+  if (lite) o += align_up(fp_surrogate_lite_workspace_bytes(n_cells));
+  L.total = o;
+  return L;
+}
+}  // namespace
+
+size_t fp_collision_step_workspace_bytes(int64_t n_particles, int64_t n_cells, int v_dtype, int lite) {
+  if (n_particles < 0 || n_cells < 0) return 0;
+  return step_layout(n_particles, n_cells, v_dtype, lite).total;
+}
+
+int fp_collision_step(const int32_t *cell_of, const void *v, int v_dtype, int64_t n_particles, int64_t n_cells,
+                      const double *tau, const fp_params *p, int prec, const fp_mlp *net_lite, double dt,
+                      uint64_t seed, uint64_t step, void *v_out, int32_t *perm_out, int64_t *cell_offsets_out,
+                      double *coeffs_out, int32_t *flags_out, double *moments_out, void *ws, size_t ws_bytes,
+                      fp_stream_t stream) {
+  g_err[0] = 0;
+  if (v_dtype != FP_V_F32 && v_dtype != FP_V_F64) return fail(FP_ERR_ARG, "v_dtype %d", v_dtype);
+  if (n_particles > 0 && !v) return fail(FP_ERR_ARG, "null velocity pointer");
+  if (n_particles > 0 && !v_out) return fail(FP_ERR_ARG, "null output velocity pointer");
+  if (int rc = check_sort_args(cell_of, n_particles, n_cells, nullptr, v_dtype, nullptr, perm_out, cell_offsets_out))
+    return rc;
+  if (prec != FP_PREC_FP64 && prec != FP_PREC_FP32_MOMENTS) return fail(FP_ERR_ARG, "prec %d", prec);
+  if (n_cells > 0 && (!tau || !coeffs_out || !flags_out)) return fail(FP_ERR_ARG, "null array pointer");
+  if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(FP_ERR_ARG, "dt %g", dt);
+  const int lite = net_lite != nullptr;
+  if (lite)
+    if (int rc = check_net(net_lite)) return rc;
+  const StepLayout L = step_layout(n_particles, n_cells, v_dtype, lite);
+  if (!ws || ws_bytes < L.total)
+    return fail(FP_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", L.total, ws_bytes);
+  if ((uintptr_t)ws % kAlign) return fail(FP_ERR_ARG, "workspace not 256-byte aligned");
+  fp_params prm;
+  fp_default_params(&prm);
+  if (p) prm = *p;
+  if (prm.min_particles < 1) prm.min_particles = 1;
+  const cudaStream_t st = (cudaStream_t)stream;
+  char *w = (char *)ws;
+  void *vs = w + L.vs;
+  double *mom = moments_out ? moments_out : (double *)(w + L.mom);
+  fpc::launch_sort_by_cell(cell_of, n_particles, n_cells, perm_out, cell_offsets_out, ws, st, nullptr);
+  fpc::launch_gather_sorted(v, v_dtype, n_particles, perm_out, vs, st);
+  if (int rc = check_launch("sort_by_cell")) return rc;
+  if (n_cells > 0) {
+    if (!lite) {
+      double *m6 = (double *)(w + L.m6);
+      fpc::launch_gather(vs, v_dtype, n_particles, cell_offsets_out, n_cells, prec, mom, m6, st);
+      fpc::launch_solve(mom, tau, n_cells, prm, prec, coeffs_out, flags_out, nullptr, st);
+      fpc::launch_velocity(vs, v_out, v_dtype, n_particles, cell_offsets_out, n_cells, mom, m6, coeffs_out, tau, dt,
+                           prm.eps2_hat, nullptr, seed, step, nullptr, flags_out, st);
+    } else {
+      char *sw = w + L.sur;
+      void *x = sw;
+      float *tpred = (float *)(sw + align_up((size_t)n_cells * 32 * 2));
+      fpc::launch_gather_lite(vs, v_dtype, n_particles, cell_offsets_out, n_cells, mom, st);
+      fpc::launch_lite_features(*net_lite, mom, tau, n_cells, prm.min_particles, prm.surr_range_margin, x, flags_out,
+                                st);
+      if (fpc::launch_mlp_forward(*net_lite, x, n_cells, 0, tpred, nullptr, nullptr, st))
+        return fail(FP_ERR_CUDA, "could not raise the shared-memory limit of the MLP kernel");
+      fpc::launch_lite_epilogue(tpred, mom, tau, n_cells, coeffs_out, flags_out, st);
+      fpc::launch_velocity_lite(vs, v_out, v_dtype, n_particles, cell_offsets_out, n_cells, mom, coeffs_out, tau, dt,
+                                prm.eps2_hat, nullptr, seed, step, nullptr, flags_out, st);
+    }
+  }
+  fpc::launch_copy_tail(vs, v_out, v_dtype, n_particles, cell_offsets_out + n_cells, st);
+  return check_launch("collision_step");
 }
 
 }  // extern "C"

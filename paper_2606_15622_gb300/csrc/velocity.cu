@@ -122,8 +122,10 @@ __device__ __forceinline__ void cell_drift_averages(const T (&vals)[kVConst], co
 }
 
 // With kOnePass the cell averages <N.N> and <M'.N> come from the moments (and
-// m6 = <|c|^6>) in closed form, so the particles are read once.
-template <typename VT, bool kOnePass>
+// m6 = <|c|^6>) in closed form, so the particles are read once.  With kLite
+// the moment vectors are LITE vectors (FP_NLITE: U, theta, b_i stored
+// directly), and the averages come from a pass over the particles.
+template <typename VT, bool kOnePass, bool kLite = false>
 __global__ void __launch_bounds__(32 * kVWarps, sizeof(VT) == 4 ? 4 : 2) velocity_kernel(const VT *v, VT *vout, int64_t np,
                                                                 const int64_t *__restrict__ off, int64_t n_cells,
                                                                 const double *__restrict__ mom,
@@ -161,10 +163,12 @@ __global__ void __launch_bounds__(32 * kVWarps, sizeof(VT) == 4 ? 4 : 2) velocit
       const int slot = lg + k * kVG;
       double x = 0.0;
       if (valid) {
+        // (a LITE vector puts b_i in slot 4 + i and zeros in 7..13: the sums
+        //  u_ikk below then give b_i as they do for the third moments)
         if (slot < 4)
-          x = mom[c * FP_NMOM + kU + slot];
+          x = mom[c * (kLite ? FP_NLITE : FP_NMOM) + kU + slot];
         else if (slot < 14)
-          x = mom[c * FP_NMOM + kU3 + (slot - 4)];
+          x = kLite ? (slot < 7 ? mom[c * FP_NLITE + 11 + (slot - 4)] : 0.0) : mom[c * FP_NMOM + kU3 + (slot - 4)];
         else if (slot < 23)
           x = coeffs[c * 9 + (slot - 14)];
         else
@@ -362,6 +366,15 @@ __global__ void __launch_bounds__(32 * kVWarps, sizeof(VT) == 4 ? 4 : 2) velocit
   }
 }
 
+static VelParams make_vel_params(double dt, double eps2_hat, uint64_t seed, uint64_t step) {
+  VelParams prm{dt, eps2_hat, step, {}};
+  for (int r = 0; r < 10; ++r) {
+    prm.key.k0[r] = (uint32_t)seed + 0x9E3779B9u * (uint32_t)r;
+    prm.key.k1[r] = (uint32_t)(seed >> 32) + 0xBB67AE85u * (uint32_t)r;
+  }
+  return prm;
+}
+
 static int vel_sm_count() {
   static int n = 0;
   if (!n) {
@@ -377,11 +390,7 @@ void launch_velocity(const void *v, void *v_out, int v_dtype, int64_t np, const 
                      const double *mom, const double *m6, const double *coeffs, const double *tau, double dt,
                      double eps2_hat, const void *xi, uint64_t seed, uint64_t step, double *alpha_out,
                      int32_t *flags, cudaStream_t st) {
-  VelParams prm{dt, eps2_hat, step, {}};
-  for (int r = 0; r < 10; ++r) {
-    prm.key.k0[r] = (uint32_t)seed + 0x9E3779B9u * (uint32_t)r;
-    prm.key.k1[r] = (uint32_t)(seed >> 32) + 0xBB67AE85u * (uint32_t)r;
-  }
+  const VelParams prm = make_vel_params(dt, eps2_hat, seed, step);
   const int threads = 32 * kVWarps;
   const int64_t cells_per_block = kVWarps * kVCells;
   int64_t blocks = (n_cells + cells_per_block - 1) / cells_per_block;
@@ -404,6 +413,29 @@ void launch_velocity(const void *v, void *v_out, int v_dtype, int64_t np, const 
       FP_VEL_LAUNCH(double, false);
   }
 #undef FP_VEL_LAUNCH
+}
+
+// The update from LITE moment vectors (U, theta, b_i), alpha by a pass over
+// the particles.
+void launch_velocity_lite(const void *v, void *v_out, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells,
+                          const double *lite, const double *coeffs, const double *tau, double dt, double eps2_hat,
+                          const void *xi, uint64_t seed, uint64_t step, double *alpha_out, int32_t *flags,
+                          cudaStream_t st) {
+  const VelParams prm = make_vel_params(dt, eps2_hat, seed, step);
+  const int threads = 32 * kVWarps;
+  const int64_t cells_per_block = kVWarps * kVCells;
+  int64_t blocks = (n_cells + cells_per_block - 1) / cells_per_block;
+  const int64_t cap = (int64_t)vel_sm_count() * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  if (v_dtype == FP_V_F32)
+    velocity_kernel<float, false, true><<<(unsigned)blocks, threads, 0, st>>>(
+        (const float *)v, (float *)v_out, np, off, n_cells, lite, nullptr, coeffs, tau, prm, (const float *)xi,
+        alpha_out, flags);
+  else
+    velocity_kernel<double, false, true><<<(unsigned)blocks, threads, 0, st>>>(
+        (const double *)v, (double *)v_out, np, off, n_cells, lite, nullptr, coeffs, tau, prm, (const double *)xi,
+        alpha_out, flags);
 }
 
 }  // namespace fpc
