@@ -6,15 +6,18 @@
 // Keys are cell indices; an index outside [0, n_cells) becomes n_cells, so
 // such particles (left the domain, say) end up behind the last cell and
 // belong to no cell.  The key has B = bit_length(n_cells) bits, sorted in
-// P = ceil(B / 8) passes of ceil(B / P) bits each.  One pass:
-//   * radix_hist_kernel: each tile of 2048 keys counts its digits into
-//     counts[digit][tile] (digit-major);
+// P = ceil(B / 9) passes of ceil(B / P) bits each (two passes up to 2^18
+// cells).  One pass:
+//   * radix_hist_kernel: each tile of 4096 keys counts its digits into
+//     counts[digit][tile] (digit-major), one shared-memory atomic per
+//     distinct digit of a warp (match_any);
 //   * an exclusive scan of counts (three kernels) gives every (digit, tile)
 //     its first output position;
-//   * radix_scatter_kernel: each tile ranks its keys stably (in rounds of 256
-//     consecutive keys: match_any within a warp, per-warp digit counts across
-//     the block), places them sorted by digit in shared memory and writes
-//     each digit's run to its position, so stores are contiguous runs.
+//   * radix_scatter_kernel: each warp ranks a strip of 256 consecutive keys
+//     of the tile stably, 32 at a time (match_any, a per-warp running count
+//     per digit); one block-wide step turns the per-warp counts into offsets;
+//     the tile is placed sorted by digit in shared memory and each digit's
+//     run written to its position, so stores are contiguous runs.
 // Ranks only count keys that come earlier in the input, so equal keys keep
 // their input order: the result is the stable permutation, the same on
 // every run.
@@ -24,11 +27,13 @@
 
 namespace fpc {
 
-constexpr int kSortThreads = 256;
+constexpr int kSortThreads = 512;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortItems = 8;                          // keys per thread (one per round)
-constexpr int kSortTile = kSortThreads * kSortItems;   // 2048 keys per tile
-constexpr int kMaxRadix = 256;
+constexpr int kSortItems = 8;                          // keys per thread
+constexpr int kSortTile = kSortThreads * kSortItems;   // 4096 keys per tile
+constexpr int kWarpStrip = kSortTile / kSortWarps;     // 256 consecutive keys per warp
+constexpr int kMaxBits = 9;
+constexpr int kMaxRadix = 1 << kMaxBits;
 
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
@@ -47,13 +52,30 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const int32_t 
   const int radix = 1 << bits;
   for (int d = threadIdx.x; d < radix; d += kSortThreads) h[d] = 0u;
   __syncthreads();
-  const int64_t t0 = (int64_t)blockIdx.x * kSortTile;
+  // each warp counts a strip of consecutive keys 32 at a time (coalesced
+  // loads); a lane whose digit differs from its left neighbour's starts a
+  // run, and each run adds its length with one shared-memory atomic
+  // (cell-ordered input has long runs)
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t s0 = (int64_t)blockIdx.x * kSortTile + (int64_t)w * kWarpStrip;
+  uint32_t k[kSortItems];
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
-    const int64_t i = t0 + r * kSortThreads + threadIdx.x;
-    if (i < n) {
-      const uint32_t k = kFirst ? cell_key(cell_of[i], n_cells) : keys[i];
-      atomicAdd(&h[(k >> shift) & (uint32_t)(radix - 1)], 1u);
+    const int64_t i = s0 + r * 32 + lane;
+    k[r] = i < n ? (kFirst ? cell_key(cell_of[i], n_cells) : keys[i]) : 0xffffffffu;
+  }
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const bool valid = k[r] != 0xffffffffu;
+    const uint32_t d = valid ? (k[r] >> shift) & (uint32_t)(radix - 1) : (uint32_t)kMaxRadix;
+    const uint32_t dl = __shfl_up_sync(0xffffffffu, d, 1);
+    const unsigned starts = __ballot_sync(0xffffffffu, lane == 0 || d != dl);
+    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+    if (valid && ((starts >> lane) & 1u)) {
+      const unsigned after = starts & ~((2u << lane) - 1u);  // run starts above this lane (lane 31: none)
+      const int end = lane == 31 ? 32 : (after ? __ffs(after) - 1 : 32);
+      const int last = 32 - __clz(vmask);                   // valid lanes are 0 .. last - 1
+      atomicAdd(&h[d], (uint32_t)((end < last ? end : last) - lane));
     }
   }
   __syncthreads();
@@ -162,68 +184,73 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(uint32_t *__res
 }
 
 template <bool kFirst>
-__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
+__global__ void __launch_bounds__(kSortThreads, 2) radix_scatter_kernel(
     const int32_t *__restrict__ cell_of, const uint32_t *__restrict__ keys_in, const int32_t *__restrict__ idx_in,
     int64_t n, int64_t n_cells, int shift, int bits, int64_t n_tiles, const uint32_t *__restrict__ pos,
     uint32_t *__restrict__ keys_out, int32_t *__restrict__ idx_out) {
-  __shared__ uint32_t run[kMaxRadix];                   // keys of each digit in earlier rounds
-  __shared__ uint16_t wcnt[kSortWarps][kMaxRadix];      // this round's keys of each digit, per warp
-  __shared__ uint32_t sk[kSortTile];
-  __shared__ int32_t si[kSortTile];
+  // the per-warp digit counts are dead once every key knows its place, so
+  // the tile staged sorted by digit reuses their memory
+  constexpr int kCountBytes = kSortWarps * kMaxRadix * 2, kStageBytes = kSortTile * 8;
+  __shared__ __align__(16) unsigned char raw[kCountBytes > kStageBytes ? kCountBytes : kStageBytes];
+  uint16_t(*wc)[kMaxRadix] = reinterpret_cast<uint16_t(*)[kMaxRadix]>(raw);  // per warp: keys of each digit
+  uint32_t *sk = reinterpret_cast<uint32_t *>(raw);
+  int32_t *si = reinterpret_cast<int32_t *>(raw + kSortTile * 4);
+  __shared__ uint32_t lstart[kMaxRadix];  // tile-local start of each digit
+  __shared__ int32_t gbase[kMaxRadix];    // output position of the tile's digit d, minus lstart[d]
   const int radix = 1 << bits;
   const uint32_t mask = (uint32_t)(radix - 1);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int d = threadIdx.x; d < kMaxRadix; d += kSortThreads) {
-    run[d] = 0u;
 #pragma unroll
-    for (int q = 0; q < kSortWarps; ++q) wcnt[q][d] = 0;
+    for (int q = 0; q < kSortWarps; ++q) wc[q][d] = 0;
   }
   __syncthreads();
   const int64_t t0 = (int64_t)blockIdx.x * kSortTile;
+  const int64_t s0 = t0 + (int64_t)w * kWarpStrip;  // this warp's strip
   uint32_t key[kSortItems];
   int32_t idx[kSortItems];
-  uint32_t rank[kSortItems];
+  uint16_t rank[kSortItems];
 #pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
-    const int64_t i = t0 + r * kSortThreads + threadIdx.x;
-    const bool valid = i < n;
-    if (valid) {
+  for (int r = 0; r < kSortItems; ++r) {  // all loads first
+    const int64_t i = s0 + r * 32 + lane;
+    key[r] = 0u;
+    idx[r] = 0;
+    if (i < n) {
       key[r] = kFirst ? cell_key(cell_of[i], n_cells) : keys_in[i];
       idx[r] = kFirst ? (int32_t)i : idx_in[i];
-    } else {
-      key[r] = 0u;
-      idx[r] = 0;
     }
-    // invalid lanes share the out-of-range digit `radix` and are not counted
-    const uint32_t d = valid ? (key[r] >> shift) & mask : (uint32_t)radix;
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
-    const uint32_t wrank = (uint32_t)__popc(peers & ((1u << lane) - 1u));
-    if (valid && wrank == 0) wcnt[w][d] = (uint16_t)__popc(peers);
-    __syncthreads();
-    uint32_t rk = 0;
-    if (valid) {
-      rk = run[d] + wrank;
-      for (int q = 0; q < w; ++q) rk += wcnt[q][d];
-    }
-    rank[r] = rk;
-    __syncthreads();
-    for (int dd = threadIdx.x; dd < radix; dd += kSortThreads) {
-      uint32_t s = 0;
-#pragma unroll
-      for (int q = 0; q < kSortWarps; ++q) {
-        s += wcnt[q][dd];
-        wcnt[q][dd] = 0;
-      }
-      run[dd] += s;
-    }
-    __syncthreads();
   }
-  // tile-local start of each digit: exclusive scan of run[] (one warp)
-  __shared__ uint32_t lstart[kMaxRadix];
-  if (w == 0) {
+  // warp-local stable ranks: key s0 + 32 r + lane comes after every key of
+  // rounds < r and after the lanes below it with the same digit
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const int64_t i = s0 + r * 32 + lane;
+    const bool valid = i < n;
+    const uint32_t d = valid ? (key[r] >> shift) & mask : (uint32_t)kMaxRadix;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t base = valid ? wc[w][d] : 0u;
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) wc[w][d] = (uint16_t)(base + __popc(peers));
+    __syncwarp();
+    rank[r] = (uint16_t)(base + __popc(peers & ((1u << lane) - 1u)));
+  }
+  __syncthreads();
+  // per digit: the warps' exclusive offsets (in place) and the tile total
+  for (int d = threadIdx.x; d < radix; d += kSortThreads) {
+    uint32_t run = 0;
+#pragma unroll
+    for (int q = 0; q < kSortWarps; ++q) {
+      const uint32_t c = wc[q][d];
+      wc[q][d] = (uint16_t)run;
+      run += c;
+    }
+    lstart[d] = run;
+  }
+  __syncthreads();
+  if (w == 0) {  // exclusive scan of the digit totals
     uint32_t carry = 0;
     for (int b = 0; b < radix; b += 32) {
-      const uint32_t x = b + lane < radix ? run[b + lane] : 0u;
+      const uint32_t x = b + lane < radix ? lstart[b + lane] : 0u;
       uint32_t inc = x;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -235,36 +262,52 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
     }
   }
   __syncthreads();
+  for (int d = threadIdx.x; d < radix; d += kSortThreads)
+    gbase[d] = (int32_t)((int64_t)pos[(int64_t)d * n_tiles + blockIdx.x] - (int64_t)lstart[d]);
+  uint32_t lp[kSortItems];
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
-    const int64_t i = t0 + r * kSortThreads + threadIdx.x;
+    const uint32_t d = (key[r] >> shift) & mask;
+    lp[r] = lstart[d] + wc[w][d] + rank[r];
+  }
+  __syncthreads();  // the counts are read; their memory becomes the staging tile
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const int64_t i = s0 + r * 32 + lane;
     if (i < n) {
-      const uint32_t d = (key[r] >> shift) & mask;
-      const uint32_t lp = lstart[d] + rank[r];
-      sk[lp] = key[r];
-      si[lp] = idx[r];
+      sk[lp[r]] = key[r];
+      si[lp[r]] = idx[r];
     }
   }
   __syncthreads();
   const int cnt = (int)(n - t0 < kSortTile ? n - t0 : kSortTile);
   for (int k = threadIdx.x; k < cnt; k += kSortThreads) {
     const uint32_t d = (sk[k] >> shift) & mask;
-    const int64_t g = (int64_t)pos[(int64_t)d * n_tiles + blockIdx.x] + (k - (int64_t)lstart[d]);
-    if (g < n) {  // always true for a consistent count / scan; keeps every store in bounds
+    const int64_t g = (int64_t)gbase[d] + k;
+    if (g >= 0 && g < n) {  // always true for a consistent count / scan; keeps every store in bounds
       keys_out[g] = sk[k];
       idx_out[g] = si[k];
     }
   }
 }
 
-// offsets[c] = first sorted position whose key is >= c, for c in [0, n_cells]
+// offsets[c] = first sorted position whose key is >= c, for c in [0, n_cells];
+// each thread takes 8 consecutive positions (positions 0..n, n meaning "past
+// the end" with key n_cells)
+constexpr int kOffItems = 8;
 __global__ void __launch_bounds__(256) cell_offsets_kernel(const uint32_t *__restrict__ keys, int64_t n,
                                                            int64_t n_cells, int64_t *__restrict__ offsets) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i > n) return;
-  const int64_t prev = i == 0 ? -1 : min((int64_t)keys[i - 1], n_cells);
-  const int64_t cur = i == n ? n_cells : min((int64_t)keys[i], n_cells);
-  for (int64_t c = prev + 1; c <= cur; ++c) offsets[c] = i;
+  const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kOffItems;
+  if (i0 > n) return;
+  int64_t prev = i0 == 0 ? -1 : min((int64_t)keys[i0 - 1], n_cells);
+#pragma unroll
+  for (int j = 0; j < kOffItems; ++j) {
+    const int64_t i = i0 + j;
+    if (i > n) break;
+    const int64_t cur = i == n ? n_cells : min((int64_t)keys[i], n_cells);
+    for (int64_t c = prev + 1; c <= cur; ++c) offsets[c] = i;
+    prev = cur;
+  }
 }
 
 template <typename VT>
@@ -313,7 +356,7 @@ static SortPlan sort_plan(int64_t n, int64_t n_cells) {
   int B = 0;
   while (B < 32 && ((uint64_t)n_cells >> B) != 0) ++B;  // keys are 0..n_cells
   if (B == 0) B = 1;
-  P.passes = (B + 7) / 8;
+  P.passes = (B + kMaxBits - 1) / kMaxBits;
   const int per = (B + P.passes - 1) / P.passes;
   int left = B;
   for (int q = 0; q < P.passes; ++q) {
@@ -380,7 +423,7 @@ void launch_sort_by_cell(const int32_t *cell_of, int64_t n, int64_t n_cells, int
     cur ^= 1;
     shift += bits;
   }
-  const int64_t blocks = (n + 1 + 255) / 256;
+  const int64_t blocks = (n + 1 + 256 * kOffItems - 1) / (256 * kOffItems);
   cell_offsets_kernel<<<(unsigned)blocks, 256, 0, st>>>(keys[cur], n, n_cells, offsets);
   if (sorted_keys) *sorted_keys = keys[cur];
 }
