@@ -437,7 +437,17 @@ def run_ours(args):
         torch.cuda.synchronize()
         t_l = S.dimensionless(ly, imom, itau)
         rel_l = ((t_l - t_ex).norm(dim=1) / t_ex.norm(dim=1))[ok].float().cpu()
+        # the coefficient-sensitivity probe of the cylinder study: 50 dropout passes at rate 0.2
+        sens_ws = torch.empty(int(api.lib().fp_surrogate_sensitivity_workspace_bytes(n_cells)), dtype=torch.uint8,
+                              device=dev)
+        sens_o = torch.empty((n_cells, api.NSENS), dtype=torch.float64, device=dev)
+        c_gather_lite()
+        t_sens = float(np.median(timed(lambda: sl.sensitivity(lite, tau, n_passes=50, rate=0.2, seed=5, params=prm,
+                                                              sens_out=sens_o, workspace=sens_ws, stream=stream),
+                                       3, 1)))
         lite_rep = {"ms": round(t_lite, 5), "gather_lite_ms": round(t_gl, 5),
+                    "sensitivity_probe": {"passes": 50, "rate": 0.2, "ms": round(t_sens, 4),
+                                          "cell_passes_per_s": round(50 * n_cells / (t_sens * 1e-3), 1)},
                     "cells_per_s": round(n_cells / (t_lite * 1e-3), 1),
                     "speedup_vs_exact_fp32_moments": round(per_call["exact_closure"] / t_lite, 3),
                     "linear_drift_rate_cylinder": round(lfb, 5), "range_flag_rate_cylinder": round(lrng, 5),

@@ -412,6 +412,38 @@ int fp_closure_surrogate_lite(const fp_mlp *net, const double *lite, int64_t n_c
                               fp_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Heuristic coefficient-sensitivity probe of the learned closure (the
+ * cylinder study's dropout probe): n_passes forward passes with the hidden
+ * activations dropped at `rate` (kept ones scaled by 1 / (1 - rate)); per
+ * cell sigma_i = sqrt(1/N sum_k (y_i^(k) - mean_i)^2) of each predicted
+ * coefficient y_i (C11, C12, C13, C22, C23, C33, Gamma1..3, in physical
+ * units: the network's tau C and tau sqrt(theta) Gamma divided back), and
+ * sigma_Stress = sqrt(sum over the six C entries of sigma_i^2), sigma_Heat =
+ * sqrt(sum over the three Gamma entries).  The masks of pass k come from
+ * Philox4x32-10 keyed by `seed`: activation j of hidden layer l (0..3) of
+ * cell r is dropped when word j % 4 of the generator on counter (r lo, r hi,
+ * k, 32 l + j / 4) gives (floor(w / 2^8) + 1) 2^-24 <= rate.
+ *   moments        [n_cells][moment_stride] f64: moment_stride FP_NMOM for a
+ *                  network on the full inputs (fp_moments), FP_NLITE for one
+ *                  on the LITE inputs (fp_moments_lite)
+ *   tau            [n_cells]; p: min_particles and surr_range_margin are read
+ *   n_passes >= 1, 0 <= rate < 1
+ *   sens_out       [n_cells][FP_NSENS] f64: sigma_1..9, sigma_Stress,
+ *                  sigma_Heat; NaN for cells flagged FP_FLAG_FEW,
+ *                  FP_FLAG_SINGULAR or FP_FLAG_NONFINITE
+ *   mean_out       [n_cells][9] f64 mean coefficients over the passes, or NULL
+ *   flags_out      [n_cells] int32 input flags (as fp_surrogate_features), or
+ *                  NULL
+ *   ws             >= fp_surrogate_sensitivity_workspace_bytes(n_cells),
+ *                  256-byte aligned */
+#define FP_NSENS 11
+size_t fp_surrogate_sensitivity_workspace_bytes(int64_t n_cells);
+int fp_surrogate_sensitivity(const fp_mlp *net, const double *moments, int moment_stride, int64_t n_cells,
+                             const double *tau, const fp_params *p, int n_passes, double rate, uint64_t seed,
+                             double *sens_out, double *mean_out, int32_t *flags_out, void *ws, size_t ws_bytes,
+                             fp_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Cell sort and the collision step (Alg. 1 and Alg. 2: particles sorted by
  * cell, moments, closure, velocity update).
  *

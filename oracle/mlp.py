@@ -201,3 +201,90 @@ def adam_step(p, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     mh = m / (1 - b1 ** t)
     vh = v / (1 - b2 ** t)
     return p - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+# ---------------------------------------------------------------------------
+# heuristic coefficient-sensitivity probe (the cylinder study's dropout probe)
+# ---------------------------------------------------------------------------
+PHILOX_M0, PHILOX_M1 = 0xD2511F53, 0xCD9E8D57
+PHILOX_W0, PHILOX_W1 = 0x9E3779B9, 0xBB67AE85
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) on many counters at
+    once: ctr [..., 4] uint32, key (k0, k1) -> [..., 4] uint32.  Each round
+    multiplies words 0 and 2 by the Philox constants (64-bit products), mixes
+    the high halves with words 1, 3 and the round key, and bumps the key by
+    the Weyl constants."""
+    x = np.asarray(ctr, dtype=np.uint64) & 0xFFFFFFFF
+    x0, x1, x2, x3 = x[..., 0], x[..., 1], x[..., 2], x[..., 3]
+    k0, k1 = np.uint64(key[0] & 0xFFFFFFFF), np.uint64(key[1] & 0xFFFFFFFF)
+    mask = np.uint64(0xFFFFFFFF)
+    for _ in range(10):
+        p0 = np.uint64(PHILOX_M0) * x0
+        p1 = np.uint64(PHILOX_M1) * x2
+        x0, x1, x2, x3 = ((p1 >> np.uint64(32)) ^ x1 ^ k0) & mask, p1 & mask, \
+                         ((p0 >> np.uint64(32)) ^ x3 ^ k1) & mask, p0 & mask
+        k0 = (k0 + np.uint64(PHILOX_W0)) & mask
+        k1 = (k1 + np.uint64(PHILOX_W1)) & mask
+    return np.stack([x0, x1, x2, x3], axis=-1).astype(np.uint32)
+
+
+def dropout_scales(cells, k, seed, rate):
+    """Dropout factors of pass k for the given cell indices: [4 layers][n][128],
+    0 for a dropped activation, 1/(1 - rate) (FP32) for a kept one.  Unit j of
+    hidden layer l of cell r uses word j % 4 of Philox4x32-10 (key = seed) on
+    counter (r lo, r hi, k, 32 l + j / 4); u = (floor(w / 2^8) + 1) 2^-24 and
+    the unit is dropped when u <= rate (rate rounded to FP32)."""
+    cells = np.asarray(cells, dtype=np.int64)
+    n = cells.size
+    ctr = np.zeros((4, n, 32, 4), dtype=np.uint64)
+    ctr[..., 0] = (cells & 0xFFFFFFFF)[None, :, None]
+    ctr[..., 1] = (cells >> 32)[None, :, None]
+    ctr[..., 2] = k
+    ctr[..., 3] = 32 * np.arange(4)[:, None, None] + np.arange(32)[None, None, :]
+    w = philox4x32_10(ctr, (seed & 0xFFFFFFFF, seed >> 32)).reshape(4, n, 128)
+    u = ((w >> 8).astype(np.float64) + 1.0) * 2.0 ** -24
+    keep_scale = float(np.float32(1.0 / (1.0 - rate)))
+    return np.where(u <= float(np.float32(rate)), 0.0, keep_scale)
+
+
+def forward_dropout(params, x, scales, bf16=True):
+    """forward() with each hidden activation multiplied by its dropout factor
+    (scales [4][n][128]) after the SiLU and before the BF16 rounding."""
+    W, b = params["W"], params["b"]
+    h = bf16_round(x).astype(np.float64) if bf16 else np.asarray(x, dtype=np.float64)
+    for l in range(5):
+        Wl = bf16_round(W[l]).astype(np.float64) if bf16 else W[l]
+        z = h @ Wl.T + b[l]
+        if bf16:
+            z = z.astype(np.float32).astype(np.float64)
+        if l < 4:
+            h = silu(z) * scales[l]
+            if bf16:
+                h = bf16_round(h).astype(np.float64)
+        else:
+            h = z
+    return h
+
+
+def sensitivity(params, x, y_mu, y_sigma, tau, theta, cells, n_passes, rate, seed):
+    """The probe: n_passes dropout forward passes of the standardised inputs
+    x [n][32]; per cell sigma_i (1/N) of each physical coefficient (outputs
+    un-standardised to (tau C, tau sqrt(theta) Gamma), divided by tau and
+    tau sqrt(theta)), sigma_Stress = |sigma_C|, sigma_Heat = |sigma_Gamma|:
+    [n][11]; and the mean coefficients [n][9]."""
+    ys = []
+    for k in range(n_passes):
+        out = forward_dropout(params, x, dropout_scales(cells, k, seed, rate))[:, :NOUT]
+        ys.append(out * np.asarray(y_sigma[:NOUT], np.float64) + np.asarray(y_mu[:NOUT], np.float64))
+    ys = np.stack(ys)                                    # [passes][n][9]
+    f = np.empty((x.shape[0], NOUT))
+    f[:, :6] = 1.0 / np.asarray(tau)[:, None]
+    f[:, 6:] = 1.0 / (np.asarray(tau) * np.sqrt(theta))[:, None]
+    sig = ys.std(axis=0) * f                              # numpy std: 1/N
+    out = np.empty((x.shape[0], 11))
+    out[:, :9] = sig
+    out[:, 9] = np.sqrt((sig[:, :6] ** 2).sum(1))
+    out[:, 10] = np.sqrt((sig[:, 6:] ** 2).sum(1))
+    return out, ys.mean(axis=0) * f

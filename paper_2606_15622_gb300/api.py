@@ -21,6 +21,7 @@ NCOEF = 9
 LU_STRIDE = 82
 NDIAG = 12
 NLITE = 14
+NSENS = 11
 
 
 def lu_doubles(n_cells: int) -> int:
@@ -113,6 +114,9 @@ SIGNATURES = {
     "fp_moments_lite": (_i32, [_vp, _i32, _i64, _vp, _i64, _vp, _vp]),
     "fp_velocity_update_lite": (_i32, [_vp, _vp, _i32, _i64, _vp, _i64, _vp, _vp, _vp, _dbl,
                                        ctypes.POINTER(Params), _vp, _u64, _u64, _vp, _vp, _vp]),
+    "fp_surrogate_sensitivity_workspace_bytes": (_sz, [_i64]),
+    "fp_surrogate_sensitivity": (_i32, [ctypes.POINTER(FpMlp), _vp, _i32, _i64, _vp, ctypes.POINTER(Params), _i32,
+                                        _dbl, _u64, _vp, _vp, _vp, _vp, _sz, _vp]),
     "fp_sort_workspace_bytes": (_sz, [_i64, _i64]),
     "fp_sort_by_cell": (_i32, [_vp, _i64, _i64, _vp, _i32, _vp, _vp, _vp, _vp, _sz, _vp]),
     "fp_collision_step_workspace_bytes": (_sz, [_i64, _i64, _i32, _i32]),

@@ -32,6 +32,12 @@ void launch_lite_features(const fp_mlp &net, const double *lite, const double *t
                           double margin, void *x, int32_t *flags, cudaStream_t st);
 void launch_lite_epilogue(const float *tpred, const double *lite, const double *tau, int64_t n, double *coeffs,
                           int32_t *flags, cudaStream_t st);
+int launch_mlp_forward_dropout(const fp_mlp &net, const void *x, int64_t n, float *out, double rate, uint64_t seed,
+                               uint32_t pass, cudaStream_t st);
+void launch_sens_accumulate(const float *tpred, int64_t n, int k, double *mean, double *m2, cudaStream_t st);
+void launch_sens_finalize(const double *mean, const double *m2, const double *mom, int stride, const double *tau,
+                          int64_t n, int n_passes, const int32_t *flags, double *out, double *mean_out,
+                          cudaStream_t st);
 size_t sort_workspace_bytes(int64_t n, int64_t n_cells);
 void launch_sort_by_cell(const int32_t *cell_of, int64_t n, int64_t n_cells, int32_t *perm, int64_t *offsets,
                          void *ws, cudaStream_t st, const uint32_t **sorted_keys);
@@ -589,6 +595,74 @@ int fp_collision_step(const int32_t *cell_of, const void *v, int v_dtype, int64_
   }
   fpc::launch_copy_tail(vs, v_out, v_dtype, n_particles, cell_offsets_out + n_cells, st);
   return check_launch("collision_step");
+}
+
+namespace {
+struct SensLayout {
+  size_t x, fl, tp, mean, m2, total;
+};
+SensLayout sens_layout(int64_t n) {
+  SensLayout L{};
+  size_t o = 0;
+  L.x = o;
+  o += align_up((size_t)n * 32 * 2);
+  L.fl = o;
+  o += align_up((size_t)n * 4);
+  L.tp = o;
+  o += align_up((size_t)n * 16 * 4);
+  L.mean = o;
+  o += align_up((size_t)n * 9 * 8);
+  L.m2 = o;
+  o += align_up((size_t)n * 9 * 8);
+  L.total = o;
+  return L;
+}
+}  // namespace
+
+size_t fp_surrogate_sensitivity_workspace_bytes(int64_t n_cells) {
+  if (n_cells < 0) return 0;
+  return sens_layout(n_cells).total;
+}
+
+int fp_surrogate_sensitivity(const fp_mlp *net, const double *moments, int moment_stride, int64_t n_cells,
+                             const double *tau, const fp_params *p, int n_passes, double rate, uint64_t seed,
+                             double *sens_out, double *mean_out, int32_t *flags_out, void *ws, size_t ws_bytes,
+                             fp_stream_t stream) {
+  g_err[0] = 0;
+  if (int rc = check_net(net)) return rc;
+  if (n_cells < 0) return fail(FP_ERR_ARG, "negative size");
+  if (moment_stride != FP_NMOM && moment_stride != FP_NLITE)
+    return fail(FP_ERR_ARG, "moment_stride %d (FP_NMOM or FP_NLITE)", moment_stride);
+  if (n_passes < 1) return fail(FP_ERR_ARG, "n_passes %d", n_passes);
+  if (!(rate >= 0.0 && rate < 1.0)) return fail(FP_ERR_ARG, "rate %g", rate);
+  if (n_cells == 0) return FP_OK;
+  if (!moments || !tau || !sens_out) return fail(FP_ERR_ARG, "null array pointer");
+  const SensLayout L = sens_layout(n_cells);
+  if (!ws || ws_bytes < L.total) return fail(FP_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", L.total, ws_bytes);
+  if ((uintptr_t)ws % kAlign) return fail(FP_ERR_ARG, "workspace not 256-byte aligned");
+  fp_params prm;
+  fp_default_params(&prm);
+  if (p) prm = *p;
+  if (prm.min_particles < 1) prm.min_particles = 1;
+  const cudaStream_t st = (cudaStream_t)stream;
+  char *w = (char *)ws;
+  void *x = w + L.x;
+  int32_t *fl = flags_out ? flags_out : (int32_t *)(w + L.fl);
+  float *tp = (float *)(w + L.tp);
+  double *mean = (double *)(w + L.mean), *m2 = (double *)(w + L.m2);
+  if (moment_stride == FP_NMOM)
+    fpc::launch_features(*net, moments, tau, n_cells, prm.min_particles, prm.surr_range_margin, x, fl, st);
+  else
+    fpc::launch_lite_features(*net, moments, tau, n_cells, prm.min_particles, prm.surr_range_margin, x, fl, st);
+  cudaMemsetAsync(mean, 0, (size_t)n_cells * 9 * 8, st);
+  cudaMemsetAsync(m2, 0, (size_t)n_cells * 9 * 8, st);
+  for (int k = 0; k < n_passes; ++k) {
+    if (fpc::launch_mlp_forward_dropout(*net, x, n_cells, tp, rate, seed, (uint32_t)k, st))
+      return fail(FP_ERR_CUDA, "could not raise the shared-memory limit of the MLP kernel");
+    fpc::launch_sens_accumulate(tp, n_cells, k + 1, mean, m2, st);
+  }
+  fpc::launch_sens_finalize(mean, m2, moments, moment_stride, tau, n_cells, n_passes, fl, sens_out, mean_out, st);
+  return check_launch("surrogate_sensitivity");
 }
 
 }  // extern "C"

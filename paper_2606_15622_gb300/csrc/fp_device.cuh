@@ -14,6 +14,35 @@ constexpr int kNSum = 26;   // gathered central sums: u2 (6), u3 (10), w (6), z 
 constexpr int kNMomSum = 25;  // of those, the ones stored in the moment vector (from slot kU2)
 constexpr int kM6Sum = 25;    // the sum slot of <|c|^6> (its own optional output array)
 
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): the counter-based
+// generator of the noise variates and of the dropout masks.  The key
+// schedule (k0 + r 0x9E3779B9, k1 + r 0xBB67AE85 for round r) depends on the
+// seed only, so the host computes it once (philox_keys) and passes it as a
+// kernel parameter.
+struct PhiloxKeys {
+  uint32_t k0[10], k1[10];
+};
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 x, const PhiloxKeys &key) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    // one 32x32 -> 64-bit multiply gives both halves of each product
+    const uint64_t p0 = (uint64_t)0xD2511F53u * x.x, p1 = (uint64_t)0xCD9E8D57u * x.z;
+    x = make_uint4((uint32_t)(p1 >> 32) ^ x.y ^ key.k0[r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ x.w ^ key.k1[r],
+                   (uint32_t)p0);
+  }
+  return x;
+}
+
+inline PhiloxKeys philox_keys(uint64_t seed) {
+  PhiloxKeys k;
+  for (int r = 0; r < 10; ++r) {
+    k.k0[r] = (uint32_t)seed + 0x9E3779B9u * (uint32_t)r;
+    k.k1[r] = (uint32_t)(seed >> 32) + 0xBB67AE85u * (uint32_t)r;
+  }
+  return k;
+}
+
 // Error-free transformation a + b = s + e (Knuth two-sum).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   s = a + b;

@@ -335,6 +335,22 @@ void launch_features(const fp_mlp &net, const double *mom, const double *tau, in
                                                      reinterpret_cast<__nv_bfloat16 *>(x), flags);
 }
 
+int launch_mlp_forward_tc_dropout(const MlpDev &net, const __nv_bfloat16 *x, int64_t n, int standardized_out,
+                                  float *out, const DropoutCfg &dc, cudaStream_t st);
+
+// One inference pass with dropout masks (pass `pass` of the sensitivity
+// probe); un-standardised outputs.
+int launch_mlp_forward_dropout(const fp_mlp &net, const void *x, int64_t n, float *out, double rate, uint64_t seed,
+                               uint32_t pass, cudaStream_t st) {
+  DropoutCfg dc;
+  dc.key = philox_keys(seed);
+  dc.rate = (float)rate;
+  dc.scale = (float)(1.0 / (1.0 - rate));
+  dc.pass = pass;
+  return launch_mlp_forward_tc_dropout(make_mlp_dev(net), reinterpret_cast<const __nv_bfloat16 *>(x), n, 0, out, dc,
+                                       st);
+}
+
 int launch_mlp_forward(const fp_mlp &net, const void *x, int64_t n, int standardized_out, float *out, void *h_save,
                        float *z_save, cudaStream_t st) {
   const MlpDev d = make_mlp_dev(net);

@@ -6,9 +6,18 @@
 #include <cstdint>
 #include <cuda_bf16.h>
 
+#include "fp_device.cuh"
+
 namespace fpc {
 
 constexpr int kIn = 32, kHid = 128, kOut = 16, kDepth = 4, kNFeat = 25, kNOut = 9;
+
+// dropout of the hidden activations in one forward pass (sensitivity probe)
+struct DropoutCfg {
+  PhiloxKeys key;
+  float rate, scale;  // drop probability, 1 / (1 - rate)
+  uint32_t pass;
+};
 
 // device pointers of the network (weights W[l] are [out][in] row-major)
 struct MlpDev {

@@ -24,6 +24,12 @@
 // along M/N at K * 16 bytes (stride byte offset); enumerating (8-row group,
 // K-chunk, row) makes that layout linear, so the staging copies (cp.async,
 // all in flight at once) write contiguous shared memory.
+// With kDrop (the coefficient-sensitivity probe) every hidden activation is
+// kept with probability 1 - rate and scaled by 1 / (1 - rate), or set to
+// zero, after the SiLU and before the BF16 rounding.  The decision for row
+// r, pass k, layer l, column j uses word j % 4 of Philox4x32-10 (key = the
+// probe's seed) on counter (r lo, r hi, k, 32 l + j / 4): dropped when
+// (floor(w / 2^8) + 1) 2^-24 <= rate.
 // Only the group's leader waits on the mbarrier, with a bound, and passes its
 // verdict to the group through shared memory at the next group barrier; a
 // wait that runs out writes NaN outputs for the group's tile (the surrogate
@@ -143,10 +149,26 @@ __device__ __forceinline__ float silu_tanh(float a, float hb) {
   return fmaf(hz, t, hz);
 }
 
-// bias + SiLU of 16 accumulators (columns 16 h16 .. 16 h16 + 15) -> two
-// 16-byte chunks of BF16 in the next layer's A operand (row `row`)
+// bias + SiLU (+ dropout) of 16 accumulators (columns 16 h16 .. 16 h16 + 15)
+// -> two 16-byte chunks of BF16 in the next layer's A operand (row `row`)
+template <bool kDrop>
 __device__ __forceinline__ void epilogue16(const uint32_t (&r)[16], const float *__restrict__ hb, unsigned char *A,
-                                           int row, int h16) {
+                                           int row, int h16, const DropoutCfg &dc, int64_t cell, int layer) {
+  float keep[16];
+  if (kDrop) {
+#pragma unroll
+    for (int g4 = 0; g4 < 4; ++g4) {
+      const uint32_t ctr3 = (uint32_t)(32 * layer + (h16 * 16 + 4 * g4) / 4);
+      const uint4 w = philox4x32_10(make_uint4((uint32_t)cell, (uint32_t)((uint64_t)cell >> 32), dc.pass, ctr3),
+                                    dc.key);
+      const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float u = ((float)(ws[e] >> 8) + 1.f) * 5.9604644775390625e-08f;  // (0, 1], exact
+        keep[4 * g4 + e] = u <= dc.rate ? 0.f : dc.scale;
+      }
+    }
+  }
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const float4 b0 = *reinterpret_cast<const float4 *>(hb + h16 * 16 + q * 8);
@@ -154,9 +176,15 @@ __device__ __forceinline__ void epilogue16(const uint32_t (&r)[16], const float 
     const float bq[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
     uint32_t pk[4];
 #pragma unroll
-    for (int e = 0; e < 4; ++e)
-      pk[e] = pack_bf16(silu_tanh(__uint_as_float(r[q * 8 + 2 * e]), bq[2 * e]),
-                        silu_tanh(__uint_as_float(r[q * 8 + 2 * e + 1]), bq[2 * e + 1]));
+    for (int e = 0; e < 4; ++e) {
+      float a0 = silu_tanh(__uint_as_float(r[q * 8 + 2 * e]), bq[2 * e]);
+      float a1 = silu_tanh(__uint_as_float(r[q * 8 + 2 * e + 1]), bq[2 * e + 1]);
+      if (kDrop) {
+        a0 *= keep[q * 8 + 2 * e];
+        a1 *= keep[q * 8 + 2 * e + 1];
+      }
+      pk[e] = pack_bf16(a0, a1);
+    }
     *reinterpret_cast<uint4 *>(A + cm_off(row, h16 * 2 + q, kHid)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
   }
 }
@@ -183,9 +211,10 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 }  // namespace
 
+template <bool kDrop>
 __global__ void __launch_bounds__(kTcThreads, 1)
     mlp_forward_tc_kernel(MlpDev net, const __nv_bfloat16 *__restrict__ x, int64_t n, int standardized_out,
-                          float *__restrict__ out) {
+                          float *__restrict__ out, DropoutCfg dc) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   float *bias = reinterpret_cast<float *>(sm + kOffBias);
@@ -292,7 +321,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         uint32_t(&cur)[16] = (c32 & 1) ? rb : ra;
         uint32_t(&nxt)[16] = (c32 & 1) ? ra : rb;
         if (c32 + 1 < kHid / 32) tc_ld16(d_in + lane_off + (uint32_t)((c32 + 1) * 32 + half * 16), nxt);
-        epilogue16(cur, hb, A, row, c32 * 2 + half);
+        epilogue16<kDrop>(cur, hb, A, row, c32 * 2 + half, dc, row0 + row, l);
         if (c32 & 1) {
           // these 64 columns are the next layer's K-steps 2 c32 - 2 .. 2 c32 + 1
           fence_proxy_async_smem();
@@ -343,7 +372,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                  : "memory");
 }
 
-static int g_tc_attr_done[64];
+static int g_tc_attr_done[2][64];
 
 static int tc_sm_count() {
   static int n = 0;
@@ -356,23 +385,35 @@ static int tc_sm_count() {
   return n;
 }
 
-// Returns -1 if the shared-memory limit could not be raised.
-int launch_mlp_forward_tc(const MlpDev &net, const __nv_bfloat16 *x, int64_t n, int standardized_out, float *out,
-                          cudaStream_t st) {
+template <bool kDrop>
+static int launch_tc(const MlpDev &net, const __nv_bfloat16 *x, int64_t n, int standardized_out, float *out,
+                     const DropoutCfg &dc, cudaStream_t st) {
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !g_tc_attr_done[dev]) {
-    if (cudaFuncSetAttribute(mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem) !=
-        cudaSuccess)
+  if (dev >= 0 && dev < 64 && !g_tc_attr_done[kDrop][dev]) {
+    if (cudaFuncSetAttribute(mlp_forward_tc_kernel<kDrop>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kTcSmem) != cudaSuccess)
       return -1;
-    g_tc_attr_done[dev] = 1;
+    g_tc_attr_done[kDrop][dev] = 1;
   }
   const int64_t n_tiles = (n + kTcRows - 1) / kTcRows;
   int64_t grid = (n_tiles + kTcGroups - 1) / kTcGroups;
   if (grid > tc_sm_count()) grid = tc_sm_count();
   if (grid < 1) grid = 1;
-  mlp_forward_tc_kernel<<<(unsigned)grid, kTcThreads, kTcSmem, st>>>(net, x, n, standardized_out, out);
+  mlp_forward_tc_kernel<kDrop><<<(unsigned)grid, kTcThreads, kTcSmem, st>>>(net, x, n, standardized_out, out, dc);
   return 0;
+}
+
+// Returns -1 if the shared-memory limit could not be raised.
+int launch_mlp_forward_tc(const MlpDev &net, const __nv_bfloat16 *x, int64_t n, int standardized_out, float *out,
+                          cudaStream_t st) {
+  return launch_tc<false>(net, x, n, standardized_out, out, DropoutCfg{}, st);
+}
+
+// The forward pass with the dropout masks of pass `dc.pass` (sensitivity probe).
+int launch_mlp_forward_tc_dropout(const MlpDev &net, const __nv_bfloat16 *x, int64_t n, int standardized_out,
+                                  float *out, const DropoutCfg &dc, cudaStream_t st) {
+  return launch_tc<true>(net, x, n, standardized_out, out, dc, st);
 }
 
 }  // namespace fpc

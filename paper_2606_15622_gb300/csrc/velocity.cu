@@ -32,24 +32,6 @@ constexpr int kVBatch = 4;          // particles per lane per round
 enum { VU0 = 0, VU1, VU2, VTH, VB0, VB1, VB2, VC00, VC01, VC02, VC11, VC12, VC22, VG0, VG1, VG2, VEPS, VA, VDRIFT,
        VNOISE, VIA, VLIN, VOMA, VTAU };
 
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  The key schedule
-// (k0 + r 0x9E3779B9, k1 + r 0xBB67AE85 for round r) depends on the seed
-// only, so the host computes it once and passes it as a kernel parameter.
-struct PhiloxKeys {
-  uint32_t k0[10], k1[10];
-};
-
-__device__ __forceinline__ uint4 philox4x32_10(uint4 x, const PhiloxKeys &key) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    // one 32x32 -> 64-bit multiply gives both halves of each product
-    const uint64_t p0 = (uint64_t)0xD2511F53u * x.x, p1 = (uint64_t)0xCD9E8D57u * x.z;
-    x = make_uint4((uint32_t)(p1 >> 32) ^ x.y ^ key.k0[r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ x.w ^ key.k1[r],
-                   (uint32_t)p0);
-  }
-  return x;
-}
-
 // Three standard normals for particle p at `step`: uniforms
 // u = (floor(w / 2^8) + 1) 2^-24 (exact in FP32) from the four Philox words,
 // Box-Muller in FP32 on (u0, u1) and (u2, u3).
@@ -367,12 +349,7 @@ __global__ void __launch_bounds__(32 * kVWarps, sizeof(VT) == 4 ? 4 : 2) velocit
 }
 
 static VelParams make_vel_params(double dt, double eps2_hat, uint64_t seed, uint64_t step) {
-  VelParams prm{dt, eps2_hat, step, {}};
-  for (int r = 0; r < 10; ++r) {
-    prm.key.k0[r] = (uint32_t)seed + 0x9E3779B9u * (uint32_t)r;
-    prm.key.k1[r] = (uint32_t)(seed >> 32) + 0xBB67AE85u * (uint32_t)r;
-  }
-  return prm;
+  return VelParams{dt, eps2_hat, step, philox_keys(seed)};
 }
 
 static int vel_sm_count() {

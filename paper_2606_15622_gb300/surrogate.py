@@ -198,6 +198,30 @@ class Surrogate:
         api._check(rc, "fp_closure_surrogate_lite")
         return y, fl
 
+    def sensitivity(self, moments, tau, n_passes=50, rate=0.2, seed=0, params=None, sens_out=None, mean_out=None,
+                    flags_out=None, workspace=None, stream=None):
+        """The heuristic coefficient-sensitivity probe (dropout at inference,
+        n_passes forward passes) -> (sens [n, 11]: sigma of the nine
+        coefficients, sigma_Stress, sigma_Heat; mean coefficients [n, 9];
+        input flags).  moments: full vectors [n, 30] or LITE vectors [n, 14],
+        as the network's input set requires."""
+        n = moments.shape[0]
+        stride = api.NMOM if self.features_set == "full" else api.NLITE
+        if moments.shape[1] != stride:
+            raise api.FPError(f"a {self.features_set!r} network reads [n, {stride}] moment vectors")
+        dev = self.device
+        sens = sens_out if sens_out is not None else torch.empty((n, api.NSENS), dtype=torch.float64, device=dev)
+        mean = mean_out if mean_out is not None else torch.empty((n, 9), dtype=torch.float64, device=dev)
+        fl = flags_out if flags_out is not None else torch.empty(n, dtype=torch.int32, device=dev)
+        need = int(_lib().fp_surrogate_sensitivity_workspace_bytes(n))
+        ws = workspace if workspace is not None else torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+        p = params if params is not None else api.default_params(eps2_hat=self.eps2_hat)
+        rc = _lib().fp_surrogate_sensitivity(ctypes.byref(self.net()), _p(moments), stride, n, _p(tau),
+                                             ctypes.byref(p), int(n_passes), float(rate), int(seed), _p(sens),
+                                             _p(mean), _p(fl), _p(ws), ws.numel(), api._stream(stream))
+        api._check(rc, "fp_surrogate_sensitivity")
+        return sens, mean, fl
+
     # ---- persistence ---------------------------------------------------
     def save(self, path):
         buf = io.BytesIO()

@@ -99,3 +99,57 @@ def test_adam_first_step_is_sign_times_lr():
     p2, m, v = M.adam_step(p, g, np.zeros(3), np.zeros(3), 1, lr=0.1)
     np.testing.assert_allclose(p2[:2], p[:2] - 0.1 * np.sign(g[:2]), rtol=1e-6)
     assert p2[2] == p[2]
+
+
+def test_vectorised_philox_known_answers():
+    """The numpy Philox of the dropout probe against the published known
+    answers (the same file that pins the C generator of the noise)."""
+    import os
+    golden = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "philox4x32_10_kat.txt")
+    rows = [[int(x, 16) for x in ln.split()] for ln in open(golden) if ln.strip() and not ln.startswith("#")]
+    for w in rows:
+        out = M.philox4x32_10(np.array(w[0:4], dtype=np.uint64), (w[4], w[5]))
+        assert list(out) == w[6:10]
+
+
+def test_dropout_masks_rate_and_independence():
+    n, rate = 2000, 0.2
+    s = M.dropout_scales(np.arange(n), 3, seed=99, rate=rate)
+    dropped = s == 0.0
+    # Bernoulli(rate) within 5 standard errors, per layer; kept units scaled by 1/(1-rate)
+    for l in range(4):
+        assert abs(dropped[l].mean() - rate) < 5 * np.sqrt(rate * (1 - rate) / dropped[l].size)
+    assert np.allclose(s[~dropped], np.float32(1.25))
+    # other passes, seeds and cells draw other masks
+    assert (M.dropout_scales(np.arange(n), 4, 99, rate) != s).mean() > 0.2
+    assert (M.dropout_scales(np.arange(n), 3, 98, rate) != s).mean() > 0.2
+    assert (s[:, :-1] != s[:, 1:]).mean() > 0.2
+    # a cell's masks depend on its index, not on its place in the batch
+    assert np.array_equal(M.dropout_scales(np.arange(n) + 1, 3, 99, rate)[:, :-1], s[:, 1:])
+    # rate 0 keeps everything unscaled
+    assert np.all(M.dropout_scales(np.arange(10), 0, 1, 0.0) == 1.0)
+
+
+def test_sensitivity_special_cases():
+    prm = M.init_params(3)
+    rng = np.random.default_rng(0)
+    x = M.bf16_round(rng.standard_normal((50, M.IN)).astype(np.float32)).astype(np.float64)
+    x[:, M.NFEAT:] = 0
+    y_mu, y_sigma = np.zeros(16), np.ones(16)
+    tau, theta = np.full(50, 2.0), np.full(50, 4.0)
+    # rate 0: every pass is the plain forward; no spread, mean = forward / scale
+    sig, mean = M.sensitivity(prm, x, y_mu, y_sigma, tau, theta, np.arange(50), 3, 0.0, seed=1)
+    assert np.all(sig == 0.0)
+    ref = M.forward(prm, x, bf16=True)[:, :9]
+    np.testing.assert_allclose(mean[:, :6], ref[:, :6] / 2.0, rtol=1e-15)
+    np.testing.assert_allclose(mean[:, 6:], ref[:, 6:] / 4.0, rtol=1e-15)
+    # with dropout: the aggregates are the norms of the per-coefficient sigmas,
+    # sigma equals the 1/N spread of the passes computed by hand
+    sig, _ = M.sensitivity(prm, x, y_mu, y_sigma, tau, theta, np.arange(50), 5, 0.2, seed=7)
+    ys = np.stack([M.forward_dropout(prm, x, M.dropout_scales(np.arange(50), k, 7, 0.2))[:, :9] for k in range(5)])
+    by_hand = np.sqrt(((ys - ys.mean(0)) ** 2).mean(0))
+    np.testing.assert_allclose(sig[:, :6], by_hand[:, :6] / 2.0, rtol=1e-12)
+    np.testing.assert_allclose(sig[:, 6:9], by_hand[:, 6:] / 4.0, rtol=1e-12)
+    np.testing.assert_allclose(sig[:, 9], np.linalg.norm(sig[:, :6], axis=1), rtol=1e-14)
+    np.testing.assert_allclose(sig[:, 10], np.linalg.norm(sig[:, 6:9], axis=1), rtol=1e-14)
+    assert np.all(sig[:, 9] > 0)
