@@ -24,12 +24,6 @@ __host__ __device__ __forceinline__ constexpr int sym3(int i, int j, int k) {
 static_assert(sym2(2, 1) == 4 && sym2(1, 1) == 3 && sym2(0, 2) == 2, "sym2");
 static_assert(sym3(2, 0, 1) == 4 && sym3(1, 2, 2) == 8 && sym3(2, 1, 1) == 7 && sym3(0, 2, 0) == 2, "sym3");
 
-__device__ __forceinline__ uint64_t abs_bits(double x) {
-  return (uint64_t)__double_as_longlong(x) & 0x7fffffffffffffffull;
-}
-__device__ __forceinline__ bool finite_d(double x) {
-  return (abs_bits(x) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
-}
 
 struct SolveParams {
   double eps2_hat;

@@ -43,6 +43,50 @@ inline PhiloxKeys philox_keys(uint64_t seed) {
   return k;
 }
 
+// Conversions between binary64 and binary32 done with integer operations on
+// the IEEE-754 bit layouts.  On this chip the FP64 pipe executes conversion
+// instructions too, and it is the scarcest pipe; these keep per-cell
+// bookkeeping off it.
+//   f2d_exact:  float -> double, exact (below);
+//   d2f_rn:     double -> float rounded to nearest, ties to even; results
+//               below the smallest normal float are flushed to a signed zero,
+//               beyond the largest give infinity, NaN stays NaN;
+//   u2d_exact:  32-bit unsigned integer -> double, exact.
+__device__ __forceinline__ float d2f_rn(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const uint32_t sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (((hi & 0xfffffu) | lo) ? 0x400000u : 0u));
+  const int eb = e - 896;  // biased binary32 exponent
+  if (eb >= 255) return __uint_as_float(sign | 0x7f800000u);
+  if (eb <= 0) return __uint_as_float(sign);
+  const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);  // the top 23 of the 52 fraction bits
+  const uint32_t rest = lo & 0x1fffffffu;                   // the 29 bits below them
+  const uint32_t up = (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  // a carry out of the fraction moves into the exponent (and to infinity at the top)
+  return __uint_as_float(sign | ((((uint32_t)eb << 23) | m) + up));
+}
+
+__device__ __forceinline__ double u2d_exact(uint32_t n) {
+  if (n == 0u) return 0.0;
+  const int e = 31 - __clz(n);                                             // 2^e <= n < 2^(e+1)
+  const uint64_t frac = ((uint64_t)n << (52 - e)) & 0xfffffffffffffull;  // drop the leading one
+  return __longlong_as_double((long long)(((uint64_t)(e + 1023) << 52) | frac));
+}
+
+__device__ __forceinline__ uint64_t abs_bits(double x) {
+  return (uint64_t)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ bool finite_d(double x) {
+  return (abs_bits(x) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
+
+// x > 0 for a double (false for NaN), on its bits
+__device__ __forceinline__ bool positive_d(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b <= 0x7ff0000000000000ll;
+}
+
 // Error-free transformation a + b = s + e (Knuth two-sum).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   s = a + b;

@@ -174,8 +174,8 @@ __device__ __forceinline__ void reduce_cells(bool valid, int n, const float *px,
   group_reduce_scatter<G>(hi, lane);
   if (itmax > BLK) group_reduce_scatter<G>(lo, lane);  // warp-uniform branch
 
-  // promote: mean = (hi + lo) / n with the 2^(ks * order) scaling undone in
-  // FP32 (a power of two: exact), then two conversions and one FP64 add
+  // promote: mean = (hi + lo) / n as a double-float, the 2^(ks * order)
+  // scaling undone in the exponent (exact), one FP64 add
   double val[K];
 #pragma unroll
   for (int j = 0; j < K; ++j) {
@@ -183,8 +183,9 @@ __device__ __forceinline__ void reduce_cells(bool valid, int n, const float *px,
     const int ord = q < NS ? tile_order<kLite>(q) : 0;
     float p, e;
     df_scale(hi[j], lo[j], rh, rl, p, e);
-    const float sc = ldexpf(1.f, -ks * ord);
-    val[j] = (double)(p * sc) + (double)(e * sc);
+    // exact widening on the integer pipe with the power-of-two scale folded
+    // into the exponent, then one FP64 add; slots past the set skip it
+    val[j] = q < NS ? f2d_exact(p, -ks * ord) + f2d_exact(e, -ks * ord) : 0.0;
   }
   const int gbase = lane & ~(G - 1);
   const double u11 = __shfl_sync(0xffffffffu, val[0 % K], gbase + 0 / K);
@@ -205,10 +206,10 @@ __device__ __forceinline__ void reduce_cells(bool valid, int n, const float *px,
   if (lg >= 1 && lg <= 3) {
     const float v0 = lg == 1 ? v0x : (lg == 2 ? v0y : v0z);
     const float m = lg == 1 ? mx : (lg == 2 ? my : mz);
-    mo[kU + lg - 1] = (double)v0 + (double)m;
+    mo[kU + lg - 1] = f2d_exact(v0) + f2d_exact(m);
   }
   if (lg == 0) {
-    mo[kN] = (double)n;
+    mo[kN] = u2d_exact((uint32_t)n);
     mo[kTheta] = (u11 + u22 + u33) * (1.0 / 3.0);
   }
 }

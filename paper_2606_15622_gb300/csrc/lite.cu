@@ -160,26 +160,28 @@ __global__ void __launch_bounds__(256) gather_lite_kernel(const VT *__restrict__
   }
 }
 
-// The 16 raw inputs of one cell from its LITE vector and tau.
+// The 16 raw inputs of one cell from its LITE vector and tau, in FP32 (the
+// entries narrowed on the integer pipe: d2f_rn).
 __device__ __forceinline__ void lite_raw_features(const double *__restrict__ m, double tau, float (&f)[16]) {
-  const double th = m[4];
-  const double u00 = m[5], u01 = m[6], u02 = m[7], u11 = m[8], u12 = m[9], u22 = m[10];
-  f[0] = (float)m[0];
-  f[1] = (float)th;
-  f[2] = (float)m[1];
-  f[3] = (float)m[2];
-  f[4] = (float)m[3];
-  f[5] = (float)(u00 - th);
-  f[6] = (float)u01;
-  f[7] = (float)u02;
-  f[8] = (float)(u11 - th);
-  f[9] = (float)u12;
-  f[10] = (float)(u22 - th);
-  f[11] = (float)(0.5 * m[11]);
-  f[12] = (float)(0.5 * m[12]);
-  f[13] = (float)(0.5 * m[13]);
-  f[14] = (float)(u00 * (u11 * u22 - u12 * u12) - u01 * (u01 * u22 - u12 * u02) + u02 * (u01 * u12 - u11 * u02));
-  f[15] = (float)(1.0 / tau);
+  const float th = d2f_rn(m[4]);
+  const float u00 = d2f_rn(m[5]), u01 = d2f_rn(m[6]), u02 = d2f_rn(m[7]), u11 = d2f_rn(m[8]), u12 = d2f_rn(m[9]),
+              u22 = d2f_rn(m[10]);
+  f[0] = d2f_rn(m[0]);
+  f[1] = th;
+  f[2] = d2f_rn(m[1]);
+  f[3] = d2f_rn(m[2]);
+  f[4] = d2f_rn(m[3]);
+  f[5] = u00 - th;
+  f[6] = u01;
+  f[7] = u02;
+  f[8] = u11 - th;
+  f[9] = u12;
+  f[10] = u22 - th;
+  f[11] = 0.5f * d2f_rn(m[11]);
+  f[12] = 0.5f * d2f_rn(m[12]);
+  f[13] = 0.5f * d2f_rn(m[13]);
+  f[14] = fmaf(u00, fmaf(u11, u22, -u12 * u12), fmaf(-u01, fmaf(u01, u22, -u12 * u02), u02 * fmaf(u01, u12, -u11 * u02)));
+  f[15] = 1.f / d2f_rn(tau);
 }
 
 __global__ void __launch_bounds__(256) lite_features_kernel(MlpDev net, const double *__restrict__ lite,
@@ -191,12 +193,12 @@ __global__ void __launch_bounds__(256) lite_features_kernel(MlpDev net, const do
   if (c >= n) return;
   const double *m = lite + c * FP_NLITE;
   int fl = 0;
-  bool fin = isfinite(tau[c]) && tau[c] > 0.0;
+  bool fin = finite_d(tau[c]) && positive_d(tau[c]);
 #pragma unroll
-  for (int k = 0; k < FP_NLITE; ++k) fin = fin && isfinite(m[k]);
+  for (int k = 0; k < FP_NLITE; ++k) fin = fin && finite_d(m[k]);
   if (!fin) fl |= FP_FLAG_NONFINITE;
-  if (m[0] < (double)min_particles) fl |= FP_FLAG_FEW;
-  if (!(m[4] > 0.0)) fl |= FP_FLAG_SINGULAR;
+  if (d2f_rn(m[0]) < (float)min_particles) fl |= FP_FLAG_FEW;  // N is a whole number
+  if (!positive_d(m[4])) fl |= FP_FLAG_SINGULAR;
   float f[16];
   lite_raw_features(m, tau[c], f);
   uint32_t packed[kIn / 2];
@@ -243,19 +245,20 @@ __global__ void __launch_bounds__(256) lite_epilogue_kernel(const float *__restr
   }
   if (!fin) fl |= FP_FLAG_NONFINITE;
   if (fl & (FP_FLAG_FEW | FP_FLAG_SINGULAR | FP_FLAG_NONFINITE)) {
-    const double c0 = (isfinite(tc) && tc > 0.0) ? -1.0 / tc : 0.0;
+    const double c0 = (finite_d(tc) && positive_d(tc)) ? -1.0 / tc : 0.0;
 #pragma unroll
     for (int q = 0; q < 9; ++q) y[q] = 0.0;
     y[0] = c0;
     y[3] = c0;
     y[5] = c0;
   } else {
-    const double itc = 1.0 / tc;
-    const double ig = itc / sqrt(lite[c * FP_NLITE + 4]);
+    // the predictions carry FP32 (network) precision: scale in FP32, widen exactly
+    const float itc = 1.f / d2f_rn(tc);
+    const float ig = itc / sqrtf(d2f_rn(lite[c * FP_NLITE + 4]));
 #pragma unroll
-    for (int a = 0; a < 6; ++a) y[a] = (double)tp[a] * itc;
+    for (int a = 0; a < 6; ++a) y[a] = f2d_exact(tp[a] * itc);
 #pragma unroll
-    for (int a = 6; a < 9; ++a) y[a] = (double)tp[a] * ig;
+    for (int a = 6; a < 9; ++a) y[a] = f2d_exact(tp[a] * ig);
   }
   flags[c] = fl;
 }

@@ -37,19 +37,20 @@ constexpr size_t kMlpSmem =
 // ---------------------------------------------------------------------------
 // features
 // ---------------------------------------------------------------------------
+// (the moments are narrowed to FP32 on the integer pipe: d2f_rn)
 __device__ __forceinline__ void cell_features(const double *__restrict__ m, float (&f)[kNFeat]) {
-  const float th = (float)m[kTheta];
+  const float th = d2f_rn(m[kTheta]);
   const float i1 = 1.f / th;
   const float ih = rsqrtf(th);
   const float i15 = i1 * ih, i2 = i1 * i1, i25 = i2 * ih;
 #pragma unroll
-  for (int a = 0; a < 6; ++a) f[a] = (float)m[kU2 + a] * i1;
+  for (int a = 0; a < 6; ++a) f[a] = d2f_rn(m[kU2 + a]) * i1;
 #pragma unroll
-  for (int a = 0; a < 10; ++a) f[6 + a] = (float)m[kU3 + a] * i15;
+  for (int a = 0; a < 10; ++a) f[6 + a] = d2f_rn(m[kU3 + a]) * i15;
 #pragma unroll
-  for (int a = 0; a < 6; ++a) f[16 + a] = (float)m[kW + a] * i2;
+  for (int a = 0; a < 6; ++a) f[16 + a] = d2f_rn(m[kW + a]) * i2;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) f[22 + a] = (float)m[kZ + a] * i25;
+  for (int a = 0; a < 3; ++a) f[22 + a] = d2f_rn(m[kZ + a]) * i25;
 }
 
 __global__ void __launch_bounds__(256) features_kernel(MlpDev net, const double *__restrict__ mom,
@@ -60,12 +61,12 @@ __global__ void __launch_bounds__(256) features_kernel(MlpDev net, const double 
   if (c >= n) return;
   const double *m = mom + c * FP_NMOM;
   int fl = 0;
-  bool fin = finite_d(tau[c]) && tau[c] > 0.0;
+  bool fin = finite_d(tau[c]) && positive_d(tau[c]);
 #pragma unroll
   for (int k = 0; k < FP_NMOM; ++k) fin = fin && finite_d(m[k]);
   if (!fin) fl |= FP_FLAG_NONFINITE;
-  if (m[kN] < (double)min_particles) fl |= FP_FLAG_FEW;
-  if (!(m[kTheta] > 0.0)) fl |= FP_FLAG_SINGULAR;
+  if (d2f_rn(m[kN]) < (float)min_particles) fl |= FP_FLAG_FEW;  // N is a whole number
+  if (!positive_d(m[kTheta])) fl |= FP_FLAG_SINGULAR;
   float f[kNFeat];
   cell_features(m, f);
   uint32_t packed[kIn / 2];
@@ -249,13 +250,14 @@ __global__ void __launch_bounds__(256) surrogate_epilogue_kernel(const float *__
   const float e = 1.f + (cu + tp[6] * b0 + tp[7] * b1 + tp[8] * b2 - eps2_hat * s4) * (1.f / 3.f);
   if (!fin) fl |= FP_FLAG_NONFINITE;
   if (!(fabsf(e) <= energy_tol)) fl |= FP_FLAG_ENERGY;
-  const double itc = 1.0 / tau[c];
-  const double ig = itc / sqrt(mom[c * FP_NMOM + kTheta]);
+  // the predictions carry FP32 (network) precision: scale in FP32, widen exactly
+  const float itc = 1.f / d2f_rn(tau[c]);
+  const float ig = itc / sqrtf(d2f_rn(mom[c * FP_NMOM + kTheta]));
   double *y = coeffs + c * 9;
 #pragma unroll
-  for (int a = 0; a < 6; ++a) y[a] = (double)tp[a] * itc;
+  for (int a = 0; a < 6; ++a) y[a] = f2d_exact(tp[a] * itc);
 #pragma unroll
-  for (int a = 6; a < 9; ++a) y[a] = (double)tp[a] * ig;
+  for (int a = 6; a < 9; ++a) y[a] = f2d_exact(tp[a] * ig);
   flags[c] = fl;
 }
 
