@@ -150,10 +150,11 @@ __device__ __forceinline__ void adjoint_cell(int64_t c, const double *__restrict
   for (int k = 0; k < FP_NMOM; ++k) gm_out[c * FP_NMOM + k] = gm[k];
 }
 
-// One thread per cell, grid-stride, one 128-thread block per SM (FP64-bound:
-// see solve_kernel).
+// One thread per cell, grid-stride, two 128-thread blocks per SM (FP64-bound:
+// see solve_kernel; a third of the register file stays free for the kernels
+// of the other streams).
 template <bool kLU>
-__global__ void __launch_bounds__(128, 1) adjoint_cell_kernel(const double *__restrict__ mom,
+__global__ void __launch_bounds__(128, 2) adjoint_cell_kernel(const double *__restrict__ mom,
                                                               const double *__restrict__ coeffs,
                                                               const int32_t *__restrict__ flags,
                                                               const double *__restrict__ lu,
@@ -372,7 +373,7 @@ void launch_adjoint(const void *v, int v_dtype, int64_t np, const int64_t *off, 
   {
     const int threads = 128;
     int64_t blocks = (n_cells + threads - 1) / threads;
-    if (blocks > adj_sm_count()) blocks = adj_sm_count();
+    if (blocks > 2 * adj_sm_count()) blocks = 2 * adj_sm_count();
     if (lu)
       adjoint_cell_kernel<true><<<(unsigned)blocks, threads, 0, st>>>(mom, coeffs, flags, lu, tau, gY, gm_in,
                                                                       n_cells, eps2_hat, gm_out);
