@@ -36,7 +36,7 @@ constexpr int kChunkCells = 64;
 constexpr int kSubP = 2048;                  // particles per sub-tile (max)
 constexpr int kCapF = kSubP + 8;             // floats per component slot (alignment slack)
 constexpr int kSlots = 4;
-constexpr int kConsumerWarps = 4;
+constexpr int kConsumerWarps = 7;          // 8 warps a CTA, 2 CTAs per SM: the register cap of 128 still holds the sums
 constexpr int kTileThreads = 32 * (1 + kConsumerWarps);
 constexpr int kTileG = 8;                    // lanes per cell (measured best of 4, 8, 16, 32)
 constexpr int kCellsPerTask = 32 / kTileG;   // cells per warp task
