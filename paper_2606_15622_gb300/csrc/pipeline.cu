@@ -2,15 +2,19 @@
 // in host memory, with the host <-> device copies overlapped with the work.
 //
 // The cells are split into contiguous chunks (cells are independent, so a
-// chunk is the closure problem of its own cells).  For every chunk, on five
-// streams ordered by events:
-//   copy-in  (H2D)   velocities of the chunk's particles, offsets, tau
+// chunk is the closure problem of its own cells).  The offsets and tau of all
+// cells go first (two copies), the coefficients and flags of all cells last;
+// for every chunk, on five streams ordered by events:
+//   copy-in  (H2D)   velocities of the chunk's particles (the three
+//                    components in one strided copy)
 //   main     (high priority) gather -> solve (keeping its factors for the
 //            adjoint when asked) -> [adjoint]
 //   learned  [surrogate closure]                    after the gather
 //   update   flags copy, velocity update M^n -> M^{n+1}  after the solve
-//   copy-out (D2H)   coefficients, flags, updated velocities
-// so chunk k's copies overlap the compute of its neighbours.  Each chunk's
+//   copy-out (D2H)   updated velocities (one strided copy)
+// so chunk k's copies overlap the compute of its neighbours.  Few large
+// copies keep the host link busy in both directions: every copy costs a
+// few microseconds of setup on its engine.  Each chunk's
 // calls are the public entry points on slices of caller-owned, full-size
 // device arrays: offsets stay absolute particle indices, the Philox counter
 // of a particle is its global index, and the results are those of the
@@ -133,6 +137,10 @@ int fp_step_host(fp_pipeline *pl, const fp_step_io *io, int v_dtype, int64_t n_p
   const char *hv = (const char *)io->h_v;
   char *hvo = (char *)io->h_v_out;
   char *dv = (char *)io->d_v, *dvo = (char *)io->d_v_out;
+  const size_t pitch = (size_t)n_particles * sv;  // bytes between velocity components
+  cudaMemcpyAsync(io->d_offsets, io->h_offsets, (size_t)(n_cells + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                  pl->h2d);
+  cudaMemcpyAsync(io->d_tau, io->h_tau, (size_t)n_cells * sizeof(double), cudaMemcpyHostToDevice, pl->h2d);
   int rc = FP_OK;
   for (int k = 0; k < n_chunks && rc == FP_OK; ++k) {
     // chunk boundaries on multiples of 32 cells (the tiles of stored factors)
@@ -147,13 +155,10 @@ int fp_step_host(fp_pipeline *pl, const fp_step_io *io, int v_dtype, int64_t n_p
     }
     const size_t vb = (size_t)(p1 - p0) * sv;
     // ---- copy in ----
-    for (int d = 0; d < 3 && vb; ++d) {
-      const size_t o = ((size_t)d * (size_t)n_particles + (size_t)p0) * sv;
-      cudaMemcpyAsync(dv + o, hv + o, vb, cudaMemcpyHostToDevice, pl->h2d);
+    if (vb) {
+      const size_t o = (size_t)p0 * sv;
+      cudaMemcpy2DAsync(dv + o, pitch, hv + o, pitch, vb, 3, cudaMemcpyHostToDevice, pl->h2d);
     }
-    cudaMemcpyAsync(io->d_offsets + c0, io->h_offsets + c0, (size_t)(nc + 1) * sizeof(int64_t),
-                    cudaMemcpyHostToDevice, pl->h2d);
-    cudaMemcpyAsync(io->d_tau + c0, io->h_tau + c0, (size_t)nc * sizeof(double), cudaMemcpyHostToDevice, pl->h2d);
     cudaEventRecord(pl->ev_h2d[k], pl->h2d);
     // ---- closure ----
     cudaStreamWaitEvent(pl->main, pl->ev_h2d[k], 0);
@@ -190,14 +195,15 @@ int fp_step_host(fp_pipeline *pl, const fp_step_io *io, int v_dtype, int64_t n_p
     }
     // ---- copy out ----
     cudaStreamWaitEvent(pl->d2h, pl->ev_vel[k], 0);
-    cudaMemcpyAsync(io->h_coeffs + c0 * 9, io->d_coeffs + c0 * 9, (size_t)nc * 9 * sizeof(double),
-                    cudaMemcpyDeviceToHost, pl->d2h);
-    cudaMemcpyAsync(io->h_flags + c0, io->d_flags_v + c0, (size_t)nc * sizeof(int32_t), cudaMemcpyDeviceToHost,
-                    pl->d2h);
-    for (int d = 0; d < 3 && vb; ++d) {
-      const size_t o = ((size_t)d * (size_t)n_particles + (size_t)p0) * sv;
-      cudaMemcpyAsync(hvo + o, dvo + o, vb, cudaMemcpyDeviceToHost, pl->d2h);
+    if (vb) {
+      const size_t o = (size_t)p0 * sv;
+      cudaMemcpy2DAsync(hvo + o, pitch, dvo + o, pitch, vb, 3, cudaMemcpyDeviceToHost, pl->d2h);
     }
+  }
+  if (rc == FP_OK) {  // every chunk's update has been waited for on the copy-out stream
+    cudaMemcpyAsync(io->h_coeffs, io->d_coeffs, (size_t)n_cells * 9 * sizeof(double), cudaMemcpyDeviceToHost,
+                    pl->d2h);
+    cudaMemcpyAsync(io->h_flags, io->d_flags_v, (size_t)n_cells * sizeof(int32_t), cudaMemcpyDeviceToHost, pl->d2h);
   }
   // the caller's stream resumes after all of it (also after an error, so no
   // queued work outlives the call unordered)
