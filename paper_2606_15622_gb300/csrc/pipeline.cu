@@ -8,7 +8,8 @@
 //   copy-in  (H2D)   velocities of the chunk's particles (the three
 //                    components in one strided copy)
 //   main     (high priority) gather -> solve (keeping its factors for the
-//            adjoint when asked) -> [adjoint]
+//            adjoint when asked)
+//   adjoint  [adjoint]                                after the solve
 //   learned  [surrogate closure]                    after the gather
 //   update   flags copy, velocity update M^n -> M^{n+1}  after the solve
 //   copy-out (D2H)   updated velocities (one strided copy)
@@ -30,19 +31,19 @@ int report(int code, const char *msg);
 
 struct fp_pipeline {
   static constexpr int kMaxChunks = 64;
-  cudaStream_t h2d = nullptr, main = nullptr, sur = nullptr, vel = nullptr, d2h = nullptr;
+  cudaStream_t h2d = nullptr, main = nullptr, sur = nullptr, vel = nullptr, d2h = nullptr, adj = nullptr;
   cudaEvent_t start = nullptr;
   cudaEvent_t ev_h2d[kMaxChunks] = {}, ev_mom[kMaxChunks] = {}, ev_solve[kMaxChunks] = {}, ev_vel[kMaxChunks] = {};
-  cudaEvent_t done_main = nullptr, done_sur = nullptr, done_vel = nullptr, done_d2h = nullptr;
+  cudaEvent_t done_main = nullptr, done_sur = nullptr, done_vel = nullptr, done_d2h = nullptr, done_adj = nullptr;
 };
 
 namespace {
 
 int destroy_all(fp_pipeline *pl) {
-  cudaStream_t *ss[5] = {&pl->h2d, &pl->main, &pl->sur, &pl->vel, &pl->d2h};
+  cudaStream_t *ss[6] = {&pl->h2d, &pl->main, &pl->sur, &pl->vel, &pl->d2h, &pl->adj};
   for (cudaStream_t *s : ss)
     if (*s) cudaStreamDestroy(*s);
-  cudaEvent_t *es[5] = {&pl->start, &pl->done_main, &pl->done_sur, &pl->done_vel, &pl->done_d2h};
+  cudaEvent_t *es[6] = {&pl->start, &pl->done_main, &pl->done_sur, &pl->done_vel, &pl->done_d2h, &pl->done_adj};
   for (cudaEvent_t *e : es)
     if (*e) cudaEventDestroy(*e);
   for (int k = 0; k < fp_pipeline::kMaxChunks; ++k) {
@@ -73,7 +74,8 @@ int fp_pipeline_create(fp_pipeline **out) {
   ok = ok && cudaStreamCreateWithFlags(&pl->sur, cudaStreamNonBlocking) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&pl->vel, cudaStreamNonBlocking) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&pl->d2h, cudaStreamNonBlocking) == cudaSuccess;
-  cudaEvent_t *es[5] = {&pl->start, &pl->done_main, &pl->done_sur, &pl->done_vel, &pl->done_d2h};
+  ok = ok && cudaStreamCreateWithPriority(&pl->adj, cudaStreamNonBlocking, hi) == cudaSuccess;
+  cudaEvent_t *es[6] = {&pl->start, &pl->done_main, &pl->done_sur, &pl->done_vel, &pl->done_d2h, &pl->done_adj};
   for (cudaEvent_t *e : es) ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
   for (int k = 0; ok && k < fp_pipeline::kMaxChunks; ++k) {
     ok = ok && cudaEventCreateWithFlags(&pl->ev_h2d[k], cudaEventDisableTiming) == cudaSuccess;
@@ -98,6 +100,7 @@ void fp_pipeline_destroy(fp_pipeline *pl) {
   cudaStreamSynchronize(pl->sur);
   cudaStreamSynchronize(pl->vel);
   cudaStreamSynchronize(pl->d2h);
+  cudaStreamSynchronize(pl->adj);
   destroy_all(pl);
 }
 
@@ -133,6 +136,7 @@ int fp_step_host(fp_pipeline *pl, const fp_step_io *io, int v_dtype, int64_t n_p
   cudaStreamWaitEvent(pl->sur, pl->start, 0);
   cudaStreamWaitEvent(pl->vel, pl->start, 0);
   cudaStreamWaitEvent(pl->d2h, pl->start, 0);
+  cudaStreamWaitEvent(pl->adj, pl->start, 0);
 
   const char *hv = (const char *)io->h_v;
   char *hvo = (char *)io->h_v_out;
@@ -187,10 +191,11 @@ int fp_step_host(fp_pipeline *pl, const fp_step_io *io, int v_dtype, int64_t n_p
                                  io->d_flags_v + c0, pl->vel)))
       break;
     cudaEventRecord(pl->ev_vel[k], pl->vel);
-    if (io->d_grad_coeffs) {
+    if (io->d_grad_coeffs) {  // on its own stream: the next chunk's gather and solve need not wait for it
+      cudaStreamWaitEvent(pl->adj, pl->ev_solve[k], 0);
       if ((rc = fp_closure_backward(io->d_v, v_dtype, n_particles, io->d_offsets + c0, nc, io->d_tau + c0, p, mom,
                                     io->d_coeffs + c0 * 9, io->d_flags + c0, lu, io->d_grad_coeffs + c0 * 9, nullptr,
-                                    io->d_grad_moments + c0 * FP_NMOM, io->d_grad_v, nullptr, 0, pl->main)))
+                                    io->d_grad_moments + c0 * FP_NMOM, io->d_grad_v, nullptr, 0, pl->adj)))
         break;
     }
     // ---- copy out ----
@@ -211,10 +216,12 @@ int fp_step_host(fp_pipeline *pl, const fp_step_io *io, int v_dtype, int64_t n_p
   cudaEventRecord(pl->done_sur, pl->sur);
   cudaEventRecord(pl->done_vel, pl->vel);
   cudaEventRecord(pl->done_d2h, pl->d2h);
+  cudaEventRecord(pl->done_adj, pl->adj);
   cudaStreamWaitEvent(caller, pl->done_main, 0);
   cudaStreamWaitEvent(caller, pl->done_sur, 0);
   cudaStreamWaitEvent(caller, pl->done_vel, 0);
   cudaStreamWaitEvent(caller, pl->done_d2h, 0);
+  cudaStreamWaitEvent(caller, pl->done_adj, 0);
   if (rc) return rc;
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fpc::report(FP_ERR_CUDA, cudaGetErrorString(e));
