@@ -174,7 +174,10 @@ def run_ours(args):
     gv = torch.empty_like(v0)
     alpha = torch.empty(n_cells, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    prm = api.default_params()
+    # weak scaling: the global problem is one population per rank; rank r owns
+    # population r (its shard: no collective on the data path) and draws its
+    # variates from its own counter range
+    prm = api.default_params(particle_offset=rank << 40)
     # the gather -> solve -> adjoint chain is the critical path: its stream
     # gets the highest priority, so its blocks are dispatched first
     stream = torch.cuda.Stream(device=dev, priority=-3)

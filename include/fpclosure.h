@@ -98,10 +98,15 @@ typedef struct {
   double surr_energy_tol;   /* surrogate: max |energy residual| accepted     */
   double surr_range_margin; /* surrogate: feature box widened by this margin
                                (in standard deviations)                      */
+  uint64_t particle_offset; /* velocity update: the Philox counter of particle
+                               i of a call is particle_offset + i; a run that
+                               splits the particles over several calls or GPUs
+                               passes each slice's first global index and draws
+                               the variates of the unsplit run                */
 } fp_params;
 
 /* Defaults: eps2_hat 1e-3, min_particles 4, pivot_rtol 1e-13,
- * surr_energy_tol 0.05, surr_range_margin 0.5. */
+ * surr_energy_tol 0.05, surr_range_margin 0.5, particle_offset 0. */
 void fp_default_params(fp_params *p);
 
 /* Text for a return code; text of the last error of the calling thread. */
@@ -187,7 +192,8 @@ int fp_closure_solve(const double *moments, const double *tau, int64_t n_cells, 
  *   p            eps2_hat is read (NULL = defaults)
  *   xi           [3][n_particles] standard normals of v's dtype, or NULL: then
  *                xi comes from Philox4x32-10 with key (seed lo, seed hi) on
- *                counter (particle index lo, hi, step lo, hi); the four words
+ *                counter (particle index lo, hi, step lo, hi), the particle
+ *                index counted from p->particle_offset; the four words
  *                w map to uniforms (floor(w / 2^8) + 1) 2^-24 and Box-Muller
  *                in FP32 gives xi_0, xi_1 from (u0, u1) and xi_2 from (u2, u3)
  *   alpha_out    [n_cells] f64 or NULL

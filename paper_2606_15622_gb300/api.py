@@ -44,7 +44,7 @@ class FPError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("eps2_hat", ctypes.c_double), ("min_particles", ctypes.c_int32),
                 ("pivot_rtol", ctypes.c_double), ("surr_energy_tol", ctypes.c_double),
-                ("surr_range_margin", ctypes.c_double)]
+                ("surr_range_margin", ctypes.c_double), ("particle_offset", ctypes.c_uint64)]
 
 
 class FpMlp(ctypes.Structure):

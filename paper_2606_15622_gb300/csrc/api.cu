@@ -14,8 +14,8 @@ void launch_solve(const double *mom, const double *tau, int64_t n_cells, const f
                   double *coeffs, int32_t *flags, double *lu, cudaStream_t st);
 void launch_velocity(const void *v, void *v_out, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells,
                      const double *mom, const double *m6, const double *coeffs, const double *tau, double dt,
-                     double eps2_hat, const void *xi, uint64_t seed, uint64_t step, double *alpha_out,
-                     int32_t *flags, cudaStream_t st);
+                     double eps2_hat, const void *xi, uint64_t seed, uint64_t step, uint64_t particle_offset,
+                     double *alpha_out, int32_t *flags, cudaStream_t st);
 void launch_adjoint(const void *v, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, const double *tau,
                     double eps2_hat, const double *mom, const double *coeffs, const int32_t *flags, const double *lu,
                     const double *gY, const double *gm_in, double *gm_out, void *gv, cudaStream_t st);
@@ -46,8 +46,8 @@ void launch_gather_sorted(const void *v, int v_dtype, int64_t n, const int32_t *
 void launch_copy_tail(const void *v, void *v_out, int v_dtype, int64_t n, const int64_t *first, cudaStream_t st);
 void launch_velocity_lite(const void *v, void *v_out, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells,
                           const double *lite, const double *coeffs, const double *tau, double dt, double eps2_hat,
-                          const void *xi, uint64_t seed, uint64_t step, double *alpha_out, int32_t *flags,
-                          cudaStream_t st);
+                          const void *xi, uint64_t seed, uint64_t step, uint64_t particle_offset,
+                          double *alpha_out, int32_t *flags, cudaStream_t st);
 void launch_diagnostics(const double *mom, const double *m6, const double *rho, int64_t n_cells, double theta_inf,
                         double rho_inf, double dg_inf, double *out, cudaStream_t st);
 void launch_relax(const double *y_new, double *y_prev, int64_t n, double w, cudaStream_t st);
@@ -121,6 +121,7 @@ void fp_default_params(fp_params *p) {
   p->pivot_rtol = 1e-13;
   p->surr_energy_tol = 0.05;
   p->surr_range_margin = 0.5;
+  p->particle_offset = 0;
 }
 
 const char *fp_status_string(int status) {
@@ -234,7 +235,7 @@ int fp_velocity_update(void *v, void *v_out, int v_dtype, int64_t n_particles, c
   fp_default_params(&prm);
   if (p) prm = *p;
   fpc::launch_velocity(v, v_out ? v_out : v, v_dtype, n_particles, cell_offsets, n_cells, moments, m6, coeffs, tau,
-                       dt, prm.eps2_hat, xi, seed, step, alpha_out, flags, (cudaStream_t)stream);
+                       dt, prm.eps2_hat, xi, seed, step, prm.particle_offset, alpha_out, flags, (cudaStream_t)stream);
   return check_launch("velocity");
 }
 
@@ -250,7 +251,8 @@ int fp_velocity_update_lite(void *v, void *v_out, int v_dtype, int64_t n_particl
   fp_default_params(&prm);
   if (p) prm = *p;
   fpc::launch_velocity_lite(v, v_out ? v_out : v, v_dtype, n_particles, cell_offsets, n_cells, lite, coeffs, tau, dt,
-                            prm.eps2_hat, xi, seed, step, alpha_out, flags, (cudaStream_t)stream);
+                            prm.eps2_hat, xi, seed, step, prm.particle_offset, alpha_out, flags,
+                            (cudaStream_t)stream);
   return check_launch("velocity_lite");
 }
 
@@ -578,7 +580,7 @@ int fp_collision_step(const int32_t *cell_of, const void *v, int v_dtype, int64_
       fpc::launch_gather(vs, v_dtype, n_particles, cell_offsets_out, n_cells, prec, mom, m6, st);
       fpc::launch_solve(mom, tau, n_cells, prm, prec, coeffs_out, flags_out, nullptr, st);
       fpc::launch_velocity(vs, v_out, v_dtype, n_particles, cell_offsets_out, n_cells, mom, m6, coeffs_out, tau, dt,
-                           prm.eps2_hat, nullptr, seed, step, nullptr, flags_out, st);
+                           prm.eps2_hat, nullptr, seed, step, prm.particle_offset, nullptr, flags_out, st);
     } else {
       char *sw = w + L.sur;
       void *x = sw;
@@ -590,7 +592,7 @@ int fp_collision_step(const int32_t *cell_of, const void *v, int v_dtype, int64_
         return fail(FP_ERR_CUDA, "could not raise the shared-memory limit of the MLP kernel");
       fpc::launch_lite_epilogue(tpred, mom, tau, n_cells, coeffs_out, flags_out, st);
       fpc::launch_velocity_lite(vs, v_out, v_dtype, n_particles, cell_offsets_out, n_cells, mom, coeffs_out, tau, dt,
-                                prm.eps2_hat, nullptr, seed, step, nullptr, flags_out, st);
+                                prm.eps2_hat, nullptr, seed, step, prm.particle_offset, nullptr, flags_out, st);
     }
   }
   fpc::launch_copy_tail(vs, v_out, v_dtype, n_particles, cell_offsets_out + n_cells, st);

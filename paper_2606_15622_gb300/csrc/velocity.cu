@@ -53,6 +53,7 @@ __device__ __forceinline__ void philox_normals(const PhiloxKeys &key, uint64_t s
 struct VelParams {
   double dt, eps2_hat;
   uint64_t step;
+  uint64_t particle_offset;  // Philox counter of particle i: particle_offset + i
   PhiloxKeys key;
 };
 
@@ -332,7 +333,7 @@ __global__ void __launch_bounds__(32 * kVWarps, sizeof(VT) == 4 ? 4 : 2) velocit
             x2 = xi[2 * np + p];
           } else {
             float f0, f1, f2;
-            philox_normals(prm.key, prm.step, (uint64_t)p, f0, f1, f2);
+            philox_normals(prm.key, prm.step, prm.particle_offset + (uint64_t)p, f0, f1, f2);
             x0 = f0;
             x1 = f1;
             x2 = f2;
@@ -348,8 +349,8 @@ __global__ void __launch_bounds__(32 * kVWarps, sizeof(VT) == 4 ? 4 : 2) velocit
   }
 }
 
-static VelParams make_vel_params(double dt, double eps2_hat, uint64_t seed, uint64_t step) {
-  return VelParams{dt, eps2_hat, step, philox_keys(seed)};
+static VelParams make_vel_params(double dt, double eps2_hat, uint64_t seed, uint64_t step, uint64_t poff) {
+  return VelParams{dt, eps2_hat, step, poff, philox_keys(seed)};
 }
 
 static int vel_sm_count() {
@@ -365,9 +366,9 @@ static int vel_sm_count() {
 
 void launch_velocity(const void *v, void *v_out, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells,
                      const double *mom, const double *m6, const double *coeffs, const double *tau, double dt,
-                     double eps2_hat, const void *xi, uint64_t seed, uint64_t step, double *alpha_out,
-                     int32_t *flags, cudaStream_t st) {
-  const VelParams prm = make_vel_params(dt, eps2_hat, seed, step);
+                     double eps2_hat, const void *xi, uint64_t seed, uint64_t step, uint64_t particle_offset,
+                     double *alpha_out, int32_t *flags, cudaStream_t st) {
+  const VelParams prm = make_vel_params(dt, eps2_hat, seed, step, particle_offset);
   const int threads = 32 * kVWarps;
   const int64_t cells_per_block = kVWarps * kVCells;
   int64_t blocks = (n_cells + cells_per_block - 1) / cells_per_block;
@@ -396,9 +397,9 @@ void launch_velocity(const void *v, void *v_out, int v_dtype, int64_t np, const 
 // the particles.
 void launch_velocity_lite(const void *v, void *v_out, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells,
                           const double *lite, const double *coeffs, const double *tau, double dt, double eps2_hat,
-                          const void *xi, uint64_t seed, uint64_t step, double *alpha_out, int32_t *flags,
-                          cudaStream_t st) {
-  const VelParams prm = make_vel_params(dt, eps2_hat, seed, step);
+                          const void *xi, uint64_t seed, uint64_t step, uint64_t particle_offset,
+                          double *alpha_out, int32_t *flags, cudaStream_t st) {
+  const VelParams prm = make_vel_params(dt, eps2_hat, seed, step, particle_offset);
   const int threads = 32 * kVWarps;
   const int64_t cells_per_block = kVWarps * kVCells;
   int64_t blocks = (n_cells + cells_per_block - 1) / cells_per_block;

@@ -169,3 +169,31 @@ def test_out_of_place_matches_in_place(cavity_pop, vdtype):
     assert torch.equal(v_dst, v_in)
     assert torch.equal(v_src, v0)
     assert torch.equal(f_out, f_in) and torch.equal(a_out, a_in)
+
+
+@pytest.mark.parametrize("vdtype", ["f64", "f32"])
+def test_split_update_with_particle_offset_equals_whole(cavity_pop, vdtype):
+    """The update of two cell ranges, each on its own particle slice with
+    fp_params.particle_offset = the slice's first global particle, equals the
+    update of the whole population bit for bit (the sharded multi-GPU run)."""
+    from paper_2606_15622_gb300 import shard as SH
+    pop = cavity_pop
+    v = pop.v64 if vdtype == "f64" else pop.v32
+    mom = O.moments(v.astype(np.float64), pop.offsets)
+    y, fl = O.closure(mom, pop.tau)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    whole = dev(v)
+    fw = dev(fl.astype(np.int32))
+    api.fp_velocity_update(whole, dev(pop.offsets), dev(mom), dev(y), dev(pop.tau), fw, 0.25, seed=31, step=6)
+    pieces = []
+    for rank in range(2):
+        c0, c1, p0, p1 = SH.shard_bounds(pop.offsets, 2, rank)
+        part = dev(v[:, p0:p1])
+        fp = dev(fl[c0:c1].astype(np.int32))
+        prm = api.default_params(particle_offset=p0)
+        api.fp_velocity_update(part, dev(pop.offsets[c0:c1 + 1] - p0), dev(mom[c0:c1]), dev(y[c0:c1]),
+                               dev(pop.tau[c0:c1]), fp, 0.25, params=prm, seed=31, step=6)
+        pieces.append((part, fp))
+    torch.cuda.synchronize()
+    assert torch.equal(torch.cat([q[0] for q in pieces], dim=1), whole)
+    assert torch.equal(torch.cat([q[1] for q in pieces]), fw)
