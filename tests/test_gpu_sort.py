@@ -189,3 +189,40 @@ def test_collision_step_argument_errors():
         api.fp_collision_step(c, v, 2, tau, 0.1, workspace=torch.empty(8, dtype=torch.uint8, device="cuda"))
     with pytest.raises(api.FPError):
         api.fp_sort_by_cell(c.long(), 2)
+
+
+def test_sort_and_step_degenerate_sizes():
+    """No particles; no cells (every particle outside); one cell."""
+    tau1 = torch.ones(1, dtype=torch.float64, device="cuda")
+    # no particles
+    c = torch.zeros(0, dtype=torch.int32, device="cuda")
+    v = torch.zeros((3, 0), dtype=torch.float32, device="cuda")
+    perm, off, vs = api.fp_sort_by_cell(c, 3, v=v)
+    assert perm.numel() == 0 and off.cpu().tolist() == [0, 0, 0, 0]
+    tau3 = torch.ones(3, dtype=torch.float64, device="cuda")
+    v_out, perm, off, y, fl = api.fp_collision_step(c, v, 3, tau3, 0.1)
+    torch.cuda.synchronize()
+    assert off.cpu().tolist() == [0, 0, 0, 0] and torch.all((fl & api.FLAG_FEW) != 0)
+    # no cells: every particle is outside and comes back unchanged
+    rng = np.random.default_rng(3)
+    vv = torch.from_numpy(rng.standard_normal((3, 50)).astype(np.float32)).cuda()
+    cc = torch.from_numpy(rng.integers(0, 5, 50).astype(np.int32)).cuda()
+    v_out, perm, off, y, fl = api.fp_collision_step(cc, vv, 0, tau1[:0], 0.1)
+    torch.cuda.synchronize()
+    assert off.cpu().tolist() == [0]
+    assert torch.equal(v_out, vv[:, perm.long()])
+    np.testing.assert_array_equal(perm.cpu().numpy(), np.arange(50))
+    # one cell: the sort keeps the input order
+    c1 = torch.zeros(40, dtype=torch.int32, device="cuda")
+    v1 = torch.from_numpy(rng.standard_normal((3, 40))).cuda()
+    perm, off, vs = api.fp_sort_by_cell(c1, 1, v=v1)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(perm.cpu().numpy(), np.arange(40))
+    assert off.cpu().tolist() == [0, 40] and torch.equal(vs, v1)
+
+
+def test_sort_rejects_too_many_cells():
+    c = torch.zeros(4, dtype=torch.int32, device="cuda")
+    with pytest.raises(api.FPError):
+        api.fp_sort_by_cell(c, 2 ** 31, offsets_out=torch.empty(1, dtype=torch.int64, device="cuda"),
+                            workspace=torch.empty(1024, dtype=torch.uint8, device="cuda"))
