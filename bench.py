@@ -546,7 +546,7 @@ def run_ours(args):
     e2e_ms = float(np.median(te))
     h2d = h_v.numel() * 4 + h_off.numel() * 8 + h_tau.numel() * 8
     d2h = h_coeffs.numel() * 8 + h_flags.numel() * 4 + h_vout.numel() * 4
-    launches_per_step = 2 + 6 + 2 + 1
+    launches_per_step = 2 + 5 + 1 + 2  # gather, solve; features, MLP, epilogue, compact, fallback; update; adjoint x2
 
     out = {
         "metric": METRIC,
