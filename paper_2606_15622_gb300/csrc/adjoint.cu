@@ -151,10 +151,11 @@ __device__ __forceinline__ void adjoint_cell(int64_t c, const double *__restrict
 }
 
 // One thread per cell, grid-stride, two 128-thread blocks per SM (FP64-bound:
-// see solve_kernel; a third of the register file stays free for the kernels
-// of the other streams).
+// see solve_kernel), registers capped at 128 a thread (the rest spills to
+// L1): half the register file stays free for the velocity update and the
+// learned closure running beside it.
 template <bool kLU>
-__global__ void __launch_bounds__(128, 2) adjoint_cell_kernel(const double *__restrict__ mom,
+__global__ void __launch_bounds__(128, 4) adjoint_cell_kernel(const double *__restrict__ mom,
                                                               const double *__restrict__ coeffs,
                                                               const int32_t *__restrict__ flags,
                                                               const double *__restrict__ lu,

@@ -262,13 +262,15 @@ __global__ void __launch_bounds__(256) gather_fp64_kernel(const VT *__restrict__
 // ---------------------------------------------------------------------------
 // assembly + solve (closure_math.cuh)
 // ---------------------------------------------------------------------------
-// One thread per cell, grid-stride over two resident 128-thread blocks per SM
-// (254 registers a thread: the whole register file); two warps per SM
-// sub-partition keep its FP64 unit busy through each other's dependency
-// stalls.  With kLU the factors of P A = L U of every unflagged cell go to lu
-// for the adjoint.
+// One thread per cell, grid-stride over two resident 128-thread blocks per SM;
+// two warps per SM sub-partition keep its FP64 unit busy through each
+// other's dependency stalls.  The registers are capped at 168 a thread (some
+// of the 9 x 10 system spills to L1): alone the kernel is as fast as with
+// the whole register file, and the third of the file it leaves free lets the
+// learned closure's kernels run beside it in the step.  With kLU the factors
+// of P A = L U of every unflagged cell go to lu for the adjoint.
 template <bool kLU>
-__global__ void __launch_bounds__(128, 2) solve_kernel(const double *__restrict__ mom, const double *__restrict__ tau,
+__global__ void __launch_bounds__(128, 3) solve_kernel(const double *__restrict__ mom, const double *__restrict__ tau,
                                                        int64_t n_cells, SolveParams prm, double *__restrict__ coeffs,
                                                        int32_t *__restrict__ flags, double *__restrict__ lu) {
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells;
