@@ -8,6 +8,8 @@ step's update is compared with the oracle's update (FP32 tolerances of the
 velocity tests) on the same coefficients.
 """
 
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -226,3 +228,40 @@ def test_sort_rejects_too_many_cells():
     with pytest.raises(api.FPError):
         api.fp_sort_by_cell(c, 2 ** 31, offsets_out=torch.empty(1, dtype=torch.int64, device="cuda"),
                             workspace=torch.empty(1024, dtype=torch.uint8, device="cuda"))
+
+
+def test_collision_steps_full_size_cylinder():
+    """The cylinder population at full size (12M particles, 3 % moved to a
+    neighbouring cell, in the previous step's order): both collision steps
+    equal their separate calls bit for bit; the sort equals the oracle's."""
+    pop = P.cylinder()
+    cell_sorted = np.repeat(np.arange(pop.n_cells), pop.counts)
+    rng = np.random.default_rng(17)
+    moved = rng.random(pop.n_particles) < 0.03
+    cell_of = np.where(moved, np.clip(cell_sorted + rng.integers(-1, 2, pop.n_particles), 0, pop.n_cells - 1),
+                       cell_sorted).astype(np.int32)
+    vd, cd = torch.from_numpy(pop.v32).cuda(), torch.from_numpy(cell_of).cuda()
+    tau = torch.from_numpy(pop.tau).cuda()
+    perm_r, off_r, vs = api.fp_sort_by_cell(cd, pop.n_cells, v=vd)
+    pr, offr = O.sort_by_cell(cell_of, pop.n_cells)
+    np.testing.assert_array_equal(perm_r.cpu().numpy(), pr)
+    np.testing.assert_array_equal(off_r.cpu().numpy(), offr)
+    # exact
+    v_out, perm, off, y, fl = api.fp_collision_step(cd, vd, pop.n_cells, tau, 0.1, prec="fp32", seed=3, step=9)
+    m6 = torch.empty(pop.n_cells, dtype=torch.float64, device="cuda")
+    mom = api.fp_moments(vs, off_r, prec="fp32", m6_out=m6)
+    yr, flr = api.fp_closure_solve(mom, tau, prec="fp32")
+    vr = torch.empty_like(vs)
+    api.fp_velocity_update(vs, off_r, mom, yr, tau, flr, 0.1, seed=3, step=9, v_out=vr, m6=m6)
+    torch.cuda.synchronize()
+    assert torch.equal(perm, perm_r) and torch.equal(y, yr) and torch.equal(fl, flr) and torch.equal(v_out, vr)
+    # learned closure on LITE inputs
+    s = S.Surrogate.load(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                      "paper_2606_15622_gb300", "weights", "surrogate_lite_couette_cavity.fpw"))
+    v_out, perm, off, y, fl = api.fp_collision_step(cd, vd, pop.n_cells, tau, 0.1, net_lite=s.net(), seed=3, step=9)
+    lr = api.fp_moments_lite(vs, off_r)
+    yr, flr = s.closure_lite(lr, tau)
+    vr = torch.empty_like(vs)
+    api.fp_velocity_update_lite(vs, off_r, lr, yr, tau, flr, 0.1, seed=3, step=9, v_out=vr)
+    torch.cuda.synchronize()
+    assert torch.equal(y, yr) and torch.equal(fl, flr) and torch.equal(v_out, vr)
