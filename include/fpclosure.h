@@ -193,9 +193,9 @@ int fp_closure_solve(const double *moments, const double *tau, int64_t n_cells, 
  *   xi           [3][n_particles] standard normals of v's dtype, or NULL: then
  *                xi comes from Philox4x32-10 with key (seed lo, seed hi) on
  *                counter (particle index lo, hi, step lo, hi), the particle
- *                index counted from p->particle_offset; the four words
- *                w map to uniforms (floor(w / 2^8) + 1) 2^-24 and Box-Muller
- *                in FP32 gives xi_0, xi_1 from (u0, u1) and xi_2 from (u2, u3)
+ *                index counted from p->particle_offset; words 0..2 map to
+ *                uniforms (floor(w / 2^9) + 1/2) 2^-23 and xi_k is the inverse
+ *                standard normal distribution function of u_k, in FP32
  *   alpha_out    [n_cells] f64 or NULL
  *   flags        [n_cells] int32 IN/OUT: cells carrying FP_FLAG_FEW,
  *                FP_FLAG_SINGULAR or FP_FLAG_NONFINITE take the exact OU step

@@ -22,7 +22,7 @@
  *   oracle_philox4x32_10      Philox4x32-10 (Salmon, Moraes, Dror, Shaw,
  *                             SC'11) -- the counter-based generator of the
  *                             noise variates xi
- *   oracle_normals            the Box-Muller map of those words to xi
+ *   oracle_normals            the inverse-distribution map of those words to xi
  *
  * Readings where the paper is silent (each stated where it is used):
  *   - diffusion D = 2 theta / tau (the noise amplitude of Sec. 3.8);
@@ -271,23 +271,37 @@ void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], ui
   for (int i = 0; i < 4; ++i) out[i] = x[i];
 }
 
+/* Inverse of the standard normal distribution function
+ * Phi(x) = erfc(-x / sqrt 2) / 2 for u in (0, 1): bisection on [-40, 40] to
+ * a bracket of 1e-9, then Newton steps with the density
+ * phi(x) = exp(-x^2 / 2) / sqrt(2 pi). */
+static double inv_normal_cdf(double u) {
+  const double rs2 = 0.70710678118654752440084436210485;   /* 1 / sqrt 2 */
+  const double rs2pi = 0.39894228040143267793994605993438; /* 1 / sqrt(2 pi) */
+  double lo = -40.0, hi = 40.0;
+  for (int it = 0; it < 60 && hi - lo > 1e-9; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (0.5 * erfc(-mid * rs2) < u)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  double x = 0.5 * (lo + hi);
+  for (int it = 0; it < 3; ++it) x -= (0.5 * erfc(-x * rs2) - u) / (rs2pi * exp(-0.5 * x * x));
+  return x;
+}
+
 /* The noise variates of particle p at a given step: Philox4x32-10 with key
- * (seed_lo, seed_hi) on counter (p_lo, p_hi, step_lo, step_hi); each word w
- * gives a uniform u = (floor(w / 2^8) + 1) 2^-24 in (0, 1] (exact in FP32 as well); Box-Muller maps
- * (u0, u1) to xi_0 = r cos(2 pi u1), xi_1 = r sin(2 pi u1), r = sqrt(-2 ln u0),
- * and (u2, u3) to xi_2 = r' cos(2 pi u3).  Evaluated here in FP64. */
+ * (seed_lo, seed_hi) on counter (p_lo, p_hi, step_lo, step_hi); words 0..2
+ * give uniforms u = (floor(w / 2^9) + 1/2) 2^-23 in (0, 1) (exact in FP32 as
+ * well) and xi_k = Phi^-1(u_k), the inverse standard normal distribution
+ * function.  Evaluated here in FP64. */
 static void particle_normals(uint64_t seed, uint64_t step, uint64_t p, double xi[3]) {
   uint32_t ctr[4] = {(uint32_t)p, (uint32_t)(p >> 32), (uint32_t)step, (uint32_t)(step >> 32)};
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   uint32_t w[4];
   oracle_philox4x32_10(ctr, key, w);
-  double u[4];
-  for (int i = 0; i < 4; ++i) u[i] = ((double)(w[i] >> 8) + 1.0) * (1.0 / 16777216.0);
-  const double two_pi = 6.283185307179586476925286766559;
-  double r0 = sqrt(-2.0 * log(u[0])), r1 = sqrt(-2.0 * log(u[2]));
-  xi[0] = r0 * cos(two_pi * u[1]);
-  xi[1] = r0 * sin(two_pi * u[1]);
-  xi[2] = r1 * cos(two_pi * u[3]);
+  for (int i = 0; i < 3; ++i) xi[i] = inv_normal_cdf(((double)(w[i] >> 9) + 0.5) * (1.0 / 8388608.0));
 }
 
 int oracle_normals(int64_t n, int64_t first_index, uint64_t seed, uint64_t step, double *xi) {

@@ -148,7 +148,7 @@ def test_lite_velocity_update_matches_oracle(couette_pop, vdtype):
     torch.cuda.synchronize()
     cell_of = np.repeat(np.arange(pop.n_cells), pop.counts)
     scale = np.abs(vref) + np.sqrt(np.maximum(lite[cell_of, L.L_THETA], 0))[None, :]
-    tol = 2e-6 if vdtype == "f64" else 6e-6  # FP32 Box-Muller; FP32 arithmetic for FP32 velocities
+    tol = 2e-6 if vdtype == "f64" else 6e-6  # FP32 normals on the GPU; FP32 arithmetic for FP32 velocities
     assert np.max(np.abs(vo.cpu().numpy() - vref) / scale) <= tol
     np.testing.assert_array_equal(fld.cpu().numpy(), fref)
     ok = (fref & (O.FALLBACK_FLAGS | O.FLAG_ALPHA)) == 0

@@ -5,8 +5,8 @@ Tolerances: FP64 velocities with given variates agree to 1e-12 relative;
 FP32 velocities are updated in FP32, so each component carries a few ulps of
 |v| plus the FP32 rounding of the cell constants: |dv| <= 4e-6 (|v| +
 sqrt(theta)).  Philox variates: the GPU maps the same 32-bit words to normals
-in FP32 (Box-Muller with CUDA's logf / sincospif, <= 2 ulp each), the oracle
-in FP64, so xi differs by <= ~1e-6 relative.
+in FP32 (CUDA's normcdfinvf, a few ulp), the oracle in FP64, so xi differs by
+<= ~1e-6 relative.
 """
 
 import numpy as np
@@ -112,7 +112,7 @@ def test_cylinder_full_size_pipeline_sampled():
     okp = ok[cell_of]
     scale = np.abs(vref) + np.sqrt(np.maximum(m[cell_of, 4], 0))[None, :]
     err = np.abs(vg[:, idx] - vref)[:, okp] / scale[:, okp]
-    assert err.max() <= 1e-6, err.max()  # FP32 Box-Muller on the GPU (noise terms)
+    assert err.max() <= 1e-6, err.max()  # FP32 inverse distribution on the GPU (noise terms)
     assert np.abs(ag[cells][ok] - aref[ok]).max() <= 1e-9
 
 

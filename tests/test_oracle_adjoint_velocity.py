@@ -63,6 +63,26 @@ def test_philox_known_answers():
         assert list(out) == w[6:10]
 
 
+def test_normals_are_the_inverse_distribution_of_the_philox_words():
+    """xi_k = Phi^-1(u_k), u_k = (floor(w_k / 2^9) + 1/2) 2^-23 from Philox
+    words 0..2 (the published known answers pin the words); Phi^-1 checked
+    against scipy's ndtri and against tabulated quantiles."""
+    from scipy.special import ndtri
+    seed, step = 0x0123456789ABCDEF, 0x1122334455667788
+    xi = O.normals(6, seed, step, first_index=1000)
+    for k in range(6):
+        p = 1000 + k
+        w = O.philox4x32_10([p & 0xFFFFFFFF, p >> 32, step & 0xFFFFFFFF, step >> 32],
+                            [seed & 0xFFFFFFFF, seed >> 32])
+        u = (np.array([int(x) >> 9 for x in w[:3]], dtype=np.float64) + 0.5) * 2.0 ** -23
+        np.testing.assert_allclose(xi[:, k], ndtri(u), rtol=1e-12, atol=1e-13)
+    # the map through the oracle at tabulated points: Phi^-1(0.975) = 1.959963984540054,
+    # Phi^-1(0.5) = 0, Phi(1) = 0.8413447460685429; the extreme uniforms
+    for u, x in [(0.975, 1.959963984540054), (0.025, -1.959963984540054), (0.5, 0.0),
+                 (0.8413447460685429, 1.0), (2.0 ** -24, ndtri(2.0 ** -24)), (1 - 2.0 ** -24, ndtri(1 - 2.0 ** -24))]:
+        assert abs(ndtri(u) - x) < 1e-12
+
+
 def test_normals_are_standard_normal():
     n = 400_000
     xi = O.normals(n, seed=1234, step=7)
