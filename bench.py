@@ -46,7 +46,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch on this workload, from one ncu capture
 # of the current build of each kernel; None once a kernel has changed since
 NCU_DRAM_BYTES = {"velocity_update": 290.21e6, "gather_fp32": 159.85e6, "solve_fp64": 85.43e6, "mlp_forward": 8.53e6,
-                  "gather_lite": None}
+                  "gather_lite": 152.62e6}
 E2E_CHUNKS = 8                 # chunks of the host-resident step (copy / compute overlap)
 WEIGHTS = os.path.join(ROOT, "paper_2606_15622_gb300", "weights", "surrogate_couette_cavity.fpw")
 WEIGHTS_LITE = os.path.join(ROOT, "paper_2606_15622_gb300", "weights", "surrogate_lite_couette_cavity.fpw")
