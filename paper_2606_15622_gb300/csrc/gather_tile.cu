@@ -115,10 +115,6 @@ __device__ __forceinline__ void reduce_cells(bool valid, int n, const float *px,
     ks = max(-20, min(20, -(ex / 2)));
   }
   const float s = ldexpf(1.f, ks);
-  const float ox = v0x + mx, oy = v0y + my, oz = v0z + mz;
-  (void)ox;
-  (void)oy;
-  (void)oz;
 
   // pass B: centred, scaled sums; FP32 blocks of BLK particles per lane folded by two-sum
   float hi[32], lo[32];
