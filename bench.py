@@ -20,7 +20,7 @@ rate; the end-to-end step through the C ABI with host buffers; nvidia-smi
 clocks sampled during the timed region; and the CPU oracle timed on host
 cores on a bounded sample.
 
---impl reference times the CPU oracle (this build's reference) on the same
+--impl reference times the CPU oracle (the reference of the CUDA path) on the same
 workload, a bounded sample per step.
 """
 
@@ -47,11 +47,12 @@ L2_FLUSH_BYTES = 256 << 20
 # of the current build of each kernel; None once a kernel has changed since
 NCU_DRAM_BYTES = {"velocity_update": 290.21e6, "gather_fp32": 159.85e6, "solve_fp64": 85.43e6, "mlp_forward": 8.53e6,
                   "gather_lite": 152.62e6}
+ORACLE_BLOCK = 4096            # cells per block of the CPU oracle's timing
 E2E_CHUNKS = 8                 # chunks of the host-resident step (copy / compute overlap)
 WEIGHTS = os.path.join(ROOT, "paper_2606_15622_gb300", "weights", "surrogate_couette_cavity.fpw")
 WEIGHTS_LITE = os.path.join(ROOT, "paper_2606_15622_gb300", "weights", "surrogate_lite_couette_cavity.fpw")
 
-# algorithmic work per unit ("Roofline accounting")
+# algorithmic work per unit of each kernel
 GATHER_BYTES_PER_PARTICLE = 12          # three FP32 components read once
 GATHER_BYTES_PER_CELL = 8 + 8 * 31      # one offset read, the moment vector and <|c|^6> written
 LITE_BYTES_PER_CELL = 8 + 8 * 14        # one offset read, the LITE moment vector written
@@ -59,7 +60,7 @@ VEL_BYTES_PER_PARTICLE = 24             # read + write three FP32 components
 VEL_BYTES_PER_CELL = 8 + 8 * 24 + 4 + 4 + 8  # offset, 24 FP64 constants, flags in/out, alpha
 SOLVE_FLOPS_PER_CELL = 658              # FP64: assembly + elimination + back substitution (FMA = 2)
 MLP_FLOPS_PER_CELL = 2 * (32 * 128 + 3 * 128 * 128 + 128 * 16)  # padded layer shapes
-FP64_PEAK_TFLOPS = 1.197                # FP64 FMA-chain peak measured on this machine's GB300
+FP64_PEAK_TFLOPS = 1.197                # FP64 peak of a GB300, measured with independent DFMA chains
 
 
 def _peaks():
@@ -362,7 +363,7 @@ def run_ours(args):
     dk = kernels[dom]
     roofline = {"kernel": dom, "bound": dk["bound"], "achieved": dk["achieved"], "peak": dk["peak"],
                 "unit": dk["unit"], "frac": dk["frac"], "traffic": NCU_DRAM_BYTES.get(dom),
-                "peak_src": "measured (FP64 FMA chain, DESIGN.md)" if dk["bound"] == "alu" else peaks["src"]}
+                "peak_src": "measured (FP64 FMA chain)" if dk["bound"] == "alu" else peaks["src"]}
 
     def q(x, p):
         return round(float(torch.quantile(x, p)), 6)
@@ -560,7 +561,7 @@ def run_ours(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32 moments, f64 solve, bf16/f32 MLP",
-        "data": "synthetic (seeded Mach-10 cylinder-shaped population; no paper data)",
+        "data": f"synthetic (seeded population {pop.name}; no paper data)",
         "config": {"workload": f"{pop.name}: {n_cells} cells, {n_p} particles per GPU",
                    "step": "exact closure (FP32 moments, FP64 solve) + learned closure with exact fallback + "
                            "adjoint to moments and velocities + velocity update",
@@ -613,7 +614,7 @@ def run_ours(args):
         "clocks": clk.summary(),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(pop, budget_s=args.cpu_seconds)
+        out["cpu_baseline"] = cpu_baseline(pop, budget_s=args.cpu_seconds, workers=args.cpu_workers)
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -621,33 +622,136 @@ def run_ours(args):
         print(json.dumps(out))
 
 
-def cpu_baseline(pop, budget_s=15.0):
-    """The oracle as it stands, single-threaded on this host: moments, exact
-    closure and velocity update over consecutive blocks of cells until the
-    time budget is used (the learned closure and the adjoint have no CPU
-    counterpart at this scale)."""
+def _oracle_block(v32, offs, tau):
+    """One block of cells through the oracle as it stands: FP64 moments, exact
+    closure and velocity update."""
+    import oracle as O
+    v = np.asarray(v32, dtype=np.float64)
+    m = O.moments(v, offs)
+    y, fl = O.closure(m, tau)
+    O.velocity_update(v, offs, m, y, tau, fl, 0.1, seed=1234, step=0)
+
+
+def _oracle_blocks(v32, offsets, tau, n_cells, blocks, budget_s, blk=ORACLE_BLOCK):
+    """Runs the blocks of cells in `blocks` (indices of `blk`-cell blocks),
+    cycling, until `budget_s` seconds have passed -> (cells, particles, s)."""
+    t0 = time.perf_counter()
+    cells = parts = 0
+    i = 0
+    while time.perf_counter() - t0 < budget_s:
+        start = blocks[i % len(blocks)] * blk
+        end = min(start + blk, n_cells)
+        a, b = int(offsets[start]), int(offsets[end])
+        _oracle_block(v32[:, a:b], np.asarray(offsets[start:end + 1]) - a, np.asarray(tau[start:end]))
+        cells += end - start
+        parts += b - a
+        i += 1
+    return cells, parts, time.perf_counter() - t0
+
+
+_ORACLE_WORKER = {}
+
+
+def _oracle_worker_init(folder):
+    import oracle as O
+    O.lib()
+    for k in ("v", "off", "tau"):
+        _ORACLE_WORKER[k] = np.load(os.path.join(folder, k + ".npy"), mmap_mode="r")
+
+
+def _oracle_worker_ping(_):
+    time.sleep(0.2)
+    return os.getpid()
+
+
+def oracle_share(w, n_workers, n_blocks):
+    """The blocks process w of n_workers times: w, w + n_workers, ... (one
+    block, w mod n_blocks, when there are more processes than blocks)."""
+    return list(range(w % n_blocks, n_blocks, n_workers)) or [w % n_blocks]
+
+
+def _oracle_worker_share(w, n_workers, t_start, budget_s):
+    """Worker w's share of the blocks, from wall time t_start."""
+    v, off, tau = _ORACLE_WORKER["v"], _ORACLE_WORKER["off"], _ORACLE_WORKER["tau"]
+    n_cells = tau.shape[0]
+    mine = oracle_share(w, n_workers, (n_cells + ORACLE_BLOCK - 1) // ORACLE_BLOCK)
+    while time.time() < t_start:
+        time.sleep(0.002)
+    return _oracle_blocks(v, off, tau, n_cells, mine, budget_s)
+
+
+class OracleCores:
+    """The oracle as it stands on `workers` host processes at once, each over
+    its own share of the population's cells.  The processes are started with
+    the spawn method (nothing of the parent's CUDA state is inherited) and
+    read the population from memory-mapped files."""
+
+    def __init__(self, pop, workers):
+        import multiprocessing as mp
+        import tempfile
+        self.workers = int(workers)
+        self.folder = tempfile.mkdtemp(prefix="fp_oracle_")
+        np.save(os.path.join(self.folder, "v.npy"), pop.v32)
+        np.save(os.path.join(self.folder, "off.npy"), np.asarray(pop.offsets, dtype=np.int64))
+        np.save(os.path.join(self.folder, "tau.npy"), np.asarray(pop.tau, dtype=np.float64))
+        self.pool = mp.get_context("spawn").Pool(self.workers, initializer=_oracle_worker_init,
+                                                 initargs=(self.folder,))
+        seen = set()
+        for _ in range(20):  # until every process has started and loaded the oracle
+            seen.update(self.pool.map(_oracle_worker_ping, range(self.workers), chunksize=1))
+            if len(seen) >= self.workers:
+                break
+
+    def run(self, budget_s):
+        """All processes at once for `budget_s` -> (cells/s, particles/s, cells, particles)
+        summed over the processes."""
+        t_start = time.time() + 0.2
+        res = self.pool.starmap(_oracle_worker_share,
+                                [(w, self.workers, t_start, budget_s) for w in range(self.workers)], chunksize=1)
+        return (sum(c / t for c, _, t in res), sum(p / t for _, p, t in res), sum(c for c, _, _ in res),
+                sum(p for _, p, _ in res))
+
+    def close(self):
+        import shutil
+        self.pool.close()
+        self.pool.join()
+        shutil.rmtree(self.folder, ignore_errors=True)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(pop, budget_s=15.0, workers=None):
+    """The oracle as it stands on this host: moments, exact closure and velocity
+    update over blocks of cells for `budget_s` seconds, first on one thread
+    (consecutive blocks), then on every host core at once (one process a core,
+    each over its share of the blocks); `value` is the all-cores figure.  The
+    learned closure and the adjoint have no CPU counterpart at this scale."""
     import oracle as O
     O.build()
-    t0 = time.perf_counter()
-    done_cells = done_parts = 0
-    blk = 4096
-    start = 0
-    while time.perf_counter() - t0 < budget_s:
-        end = min(start + blk, pop.n_cells)
-        a, b = int(pop.offsets[start]), int(pop.offsets[end])
-        offs = pop.offsets[start:end + 1] - a
-        v = pop.v32[:, a:b].astype(np.float64)
-        m = O.moments(v, offs)
-        y, fl = O.closure(m, pop.tau[start:end])
-        O.velocity_update(v, offs, m, y, pop.tau[start:end], fl, 0.1, seed=1234, step=0)
-        done_cells += end - start
-        done_parts += b - a
-        start = end % pop.n_cells
-    el = time.perf_counter() - t0
-    return {"value": round(done_cells / el, 1), "unit": "cells/s", "cores": 1, "kind": "oracle",
-            "particles_per_s": round(done_parts / el, 1),
-            "sample": f"{done_cells} cells ({done_parts} particles) of {pop.name} in {el:.1f} s: FP64 moments, "
-                      "exact closure and velocity update, 1 thread"}
+    n_blocks = (pop.n_cells + ORACLE_BLOCK - 1) // ORACLE_BLOCK
+    c1, p1, el = _oracle_blocks(pop.v32, pop.offsets, pop.tau, pop.n_cells, list(range(n_blocks)), budget_s)
+    single = {"value": round(c1 / el, 1), "unit": "cells/s", "cores": 1, "particles_per_s": round(p1 / el, 1),
+              "sample": f"{c1} cells ({p1} particles) of {pop.name} in {el:.1f} s"}
+    workers = host_cores() if workers is None else workers
+    if workers <= 1:
+        return dict(single, kind="oracle", sample=single["sample"] + ": FP64 moments, exact closure and velocity "
+                                                                   "update, 1 thread")
+    cores = OracleCores(pop, workers)
+    try:
+        rate, prate, cn, pn = cores.run(budget_s)
+    finally:
+        cores.close()
+    return {"value": round(rate, 1), "unit": "cells/s", "cores": workers, "kind": "oracle",
+            "particles_per_s": round(prate, 1),
+            "sample": f"{cn} cells ({pn} particles) of {pop.name} in {budget_s:.0f} s on {workers} processes, one a "
+                      f"core, each over its share of {ORACLE_BLOCK}-cell blocks: FP64 moments, exact closure and "
+                      "velocity update",
+            "single_thread": single}
 
 
 def run_reference(args):
@@ -655,21 +759,30 @@ def run_reference(args):
     if rank != 0:
         return
     pop = _population(args.config, seed=3)
+    import oracle as O
+    O.build()
+    workers = host_cores() if args.cpu_workers is None else args.cpu_workers
     budget = max(1.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
-    for _ in range(args.warmup):
-        cpu_baseline(pop, budget_s=budget / 4)
-    per = [cpu_baseline(pop, budget_s=budget) for _ in range(args.steps)]
-    value = float(np.median([p["value"] for p in per]))
+    cores = OracleCores(pop, workers)
+    try:
+        for _ in range(args.warmup):
+            cores.run(budget / 4)
+        per = [cores.run(budget) for _ in range(args.steps)]
+    finally:
+        cores.close()
+    value = float(np.median([r[0] for r in per]))
     ms_per_step = pop.n_cells / value * 1e3
+    sample = (f"{per[0][2]} cells ({per[0][3]} particles) of {pop.name} in {budget:.1f} s per step on {workers} "
+              f"processes, one a core: FP64 moments, exact closure and velocity update")
     out = {
         "metric": METRIC, "impl": "reference", "value": round(value, 1), "unit": "cells/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded Mach-10 cylinder-shaped population; no paper data)",
+        "data": f"synthetic (seeded population {pop.name}; no paper data)",
         "config": {"workload": f"{pop.name}: {pop.n_cells} cells, {pop.n_particles} particles "
                                "(bounded sample per step)", "cells": pop.n_cells, "particles": pop.n_particles},
-        "cpu_baseline": {"value": round(value, 1), "unit": "cells/s", "cores": 1, "kind": "oracle",
-                         "sample": per[0]["sample"]},
+        "cpu_baseline": {"value": round(value, 1), "unit": "cells/s", "cores": workers, "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": round(value, 1), "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -684,6 +797,8 @@ def main():
     ap.add_argument("--config", default="cylinder", choices=["cylinder", "cavity", "couette"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-workers", type=int, default=None,
+                    help="host processes for the oracle's all-cores timing (default: every core)")
     ap.add_argument("--only", default=None,
                     choices=["gather", "gather64", "solve", "exact_closure", "surrogate_closure", "adjoint",
                              "velocity_update", "step", "mlp", "gather_lite", "lite", "sort", "collision"],

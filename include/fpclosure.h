@@ -61,7 +61,7 @@ enum {
   FP_ERR_ARG = -1,         /* invalid argument (size, pointer, enum)        */
   FP_ERR_CUDA = -2,        /* a CUDA launch or runtime call failed           */
   FP_ERR_WORKSPACE = -3,   /* workspace missing or smaller than required     */
-  FP_ERR_UNSUPPORTED = -4  /* valid request this build does not implement   */
+  FP_ERR_UNSUPPORTED = -4  /* valid request the library does not implement  */
 };
 
 /* particle velocity storage type */
