@@ -16,7 +16,7 @@
 // updated in FP32 arithmetic, FP64 velocities in FP64.
 // Noise: the caller's variates, or Philox4x32-10 keyed by the seed on the
 // counter (particle index, step), mapped to normals by the inverse normal
-// distribution function in FP32.
+// distribution function in FP32 (normal_quantile).
 #include <cstdint>
 
 #include "fp_device.cuh"
@@ -33,20 +33,66 @@ constexpr int kVBatch = 4;          // particles per lane per round
 enum { VU0 = 0, VU1, VU2, VTH, VB0, VB1, VB2, VC00, VC01, VC02, VC11, VC12, VC22, VG0, VG1, VG2, VEPS, VA, VDRIFT,
        VNOISE, VIA, VLIN, VOMA, VTAU };
 
-// Three standard normals for particle p at `step`: Philox words 0..2 give
-// uniforms u = (floor(w / 2^9) + 1/2) 2^-23 in (0, 1) (exact in FP32), mapped
-// by the inverse standard normal distribution function (CUDA's normcdfinvf).
-// Three evaluations of it cost fewer instructions than Box-Muller's two
-// logarithms, two square roots and the sine-cosine pair for the same three
-// normals.
+// Standard normal quantile of a Philox word w: u = (k + 1/2) 2^-23 with
+// k = w >> 9, x = 2u - 1 = (2k + 1 - 2^23) 2^-23 (exact in FP32) and
+// lg = log2(1 - x^2); z = Phi^-1(u) = sqrt(2) erfinv(x) = x P(lg + 4) for
+// lg >= -8 and x Q(sqrt(-lg) - 3.75) below (0.2 % of the words), the form of
+// Giles' erfinv approximation (GPU Computing Gems, 2011).  P and Q were fitted
+// to scipy's ndtri for this kernel by normal_quantile_fit.py, which also
+// evaluates this FP32 arithmetic for all 2^23 words: |dz| <= 1.3e-6 and
+// |dz| / |z| <= 3.3e-7 with lg2.approx anywhere within its error bound.
+
+// P (degree 9, in lg + 4) and Q (degree 8, in sqrt(-lg) - 3.75) by Horner's rule
+__device__ __forceinline__ float quantile_p(float v) {
+  float p = 3.862574705e-10f;
+  p = fmaf(p, v, 4.549878529e-10f);
+  p = fmaf(p, v, -5.210529963e-08f);
+  p = fmaf(p, v, -4.056917646e-07f);
+  p = fmaf(p, v, 2.225996695e-06f);
+  p = fmaf(p, v, 6.797097012e-05f);
+  p = fmaf(p, v, 4.802460899e-04f);
+  p = fmaf(p, v, -3.469289979e-03f);
+  p = fmaf(p, v, -2.392821312e-01f);
+  p = fmaf(p, v, 2.217919827e+00f);
+  return p;
+}
+
+__device__ __forceinline__ float quantile_q(float v) {
+  float p = -6.398928963e-05f;
+  p = fmaf(p, v, -6.059690350e-05f);
+  p = fmaf(p, v, 6.303846603e-04f);
+  p = fmaf(p, v, -1.477855956e-03f);
+  p = fmaf(p, v, 2.589873038e-03f);
+  p = fmaf(p, v, -4.353985656e-03f);
+  p = fmaf(p, v, 6.956293248e-03f);
+  p = fmaf(p, v, 1.181739330e+00f);
+  p = fmaf(p, v, 4.179551601e+00f);
+  return p;
+}
+
+__device__ __forceinline__ float normal_quantile(uint32_t w) {
+  const int m = (int)((w >> 9) << 1) + 1 - (1 << 23);
+  const float x = (float)m * 1.1920928955078125e-07f;  // times 2^-23, exact
+  const float t = fmaf(-x, x, 1.0f);                   // 1 - x^2 in [2^-22, 1]
+  float lg;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(t));
+  float p;
+  if (__builtin_expect(t < 0.00390625f, 0))  // 2^-8: the tails, one word in 500
+    p = quantile_q(sqrtf(-lg) - 3.75f);
+  else
+    p = quantile_p(lg + 4.0f);
+  return x * p;
+}
+
+// Three standard normals for particle p at `step`: the quantiles of Philox
+// words 0..2 on the counter (p, step).
 __device__ __forceinline__ void philox_normals(const PhiloxKeys &key, uint64_t step, uint64_t p, float &x0,
                                                float &x1, float &x2) {
   const uint4 w = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)(p >> 32), (uint32_t)step, (uint32_t)(step >> 32)),
                                 key);
-  const float s23 = 1.1920928955078125e-07f;  // 2^-23
-  x0 = normcdfinvf(((float)(w.x >> 9) + 0.5f) * s23);
-  x1 = normcdfinvf(((float)(w.y >> 9) + 0.5f) * s23);
-  x2 = normcdfinvf(((float)(w.z >> 9) + 0.5f) * s23);
+  x0 = normal_quantile(w.x);
+  x1 = normal_quantile(w.y);
+  x2 = normal_quantile(w.z);
 }
 
 struct VelParams {
