@@ -197,3 +197,31 @@ def test_split_update_with_particle_offset_equals_whole(cavity_pop, vdtype):
     torch.cuda.synchronize()
     assert torch.equal(torch.cat([q[0] for q in pieces], dim=1), whole)
     assert torch.equal(torch.cat([q[1] for q in pieces]), fw)
+
+
+def test_update_normals_are_the_quantiles_of_the_philox_words():
+    """The update's own variates, read out exactly: every cell flagged linear
+    (no drift), every velocity at U = 0 in FP64 storage, so M^{n+1} = nz xi
+    with nz = sqrt(theta (1 - a^2)) and one rounding.  Against the oracle's
+    quantile (an FP64 inversion of Phi) of the same Philox words: 3M variates,
+    about 6000 of them in the kernel's tail branch (|xi| > 3.1)."""
+    n_cells, ppc, dt = 256, 4096, 0.5
+    n_p = n_cells * ppc
+    off = np.arange(n_cells + 1, dtype=np.int64) * ppc
+    mom = np.zeros((n_cells, api.NMOM))
+    mom[:, 0] = ppc
+    mom[:, 4] = 1.0  # theta
+    flags = _dev(np.full(n_cells, api.FLAG_FEW, dtype=np.int32))
+    v = torch.zeros((3, n_p), dtype=torch.float64, device="cuda")
+    api.fp_velocity_update(v, _dev(off), _dev(mom), _dev(np.zeros((n_cells, 9))), _dev(np.ones(n_cells)), flags, dt,
+                           seed=99, step=4)
+    a = np.exp(-dt)
+    xi_gpu = (v.cpu().numpy() / np.sqrt((1 - a) * (1 + a))).astype(np.float32).astype(np.float64)
+    xi = O.normals(n_p, 99, 4)
+    err = np.abs(xi_gpu - xi)
+    assert err.max() <= 1.5e-6, err.max()
+    assert (err / np.abs(xi)).max() <= 4e-7
+    tail = np.abs(xi) > 3.1
+    assert tail.sum() > 3000
+    assert err[tail].max() <= 1.5e-6
+    np.testing.assert_array_equal(flags.cpu().numpy(), api.FLAG_FEW)
