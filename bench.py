@@ -329,6 +329,10 @@ def run_ours(args):
     ms_per_step = ms / args.steps
     cells_per_s = ws * n_cells / (ms_per_step * 1e-3)
     parts_per_s = ws * n_p / (ms_per_step * 1e-3)
+    # the learned closure's flags of the last step (later legs reuse the buffer)
+    step_fallback_rate = float(((flags_s & api.FLAG_FALLBACK) != 0).double().mean())
+    step_range_rate = float(((flags_s & api.FLAG_RANGE) != 0).double().mean())
+    step_energy_rate = float(((flags_s & api.FLAG_ENERGY) != 0).double().mean())
 
     # ---- per call, per kernel ------------------------------------------------
     peaks = _peaks()
@@ -582,10 +586,12 @@ def run_ours(args):
                            "particles_per_s": round(n_p / (t64 * 1e-3), 1), "velocities": "f64",
                            "error_vs_oracle": "<= 1e-10 relative (parity tests)"},
             "surrogate_on_cylinder": {"ms": round(per_call["surrogate_closure"], 5),
-                                      "fallback_rate": round(float(((flags_s & api.FLAG_FALLBACK) != 0)
-                                                                   .double().mean()), 4),
-                                      "note": "Mach-10 cells lie outside the training distributions; the range "
-                                              "check sends them to the exact closure"},
+                                      "fallback_rate": round(step_fallback_rate, 5),
+                                      "range_flag_rate": round(step_range_rate, 5),
+                                      "energy_flag_rate": round(step_energy_rate, 5),
+                                      "note": "flags of the step's learned closure: cells outside the training "
+                                              "box (range) or with a large energy residual are recomputed by the "
+                                              "exact closure"},
             "surrogate_1M": {"cells": nb, "ms": round(t_sur_1m, 5), "cells_per_s": round(nb / (t_sur_1m * 1e-3), 1),
                              "mlp_forward_ms": round(t_mlp_1m, 5),
                              "exact_solve_same_moments_ms": round(t_ex_1m, 5),
