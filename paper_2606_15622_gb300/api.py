@@ -139,13 +139,14 @@ def fp_closure_exact_static(v, offsets, tau, params: Params | None = None, prec=
     caller memory (for callers that may not allocate; at most
     STATIC_MAX_CELLS cells) -> (coeffs, flags)."""
     n_cells = offsets.numel() - 1
-    n_p = v.shape[-1] if v.dim() == 2 else v.numel() // 3
+    n_p = _nv(v)
     dev = offsets.device
     if coeffs_out is None:
         coeffs_out = torch.empty((n_cells, NCOEF), dtype=torch.float64, device=dev)
     if flags_out is None:
         flags_out = torch.empty((n_cells,), dtype=torch.int32, device=dev)
     _need_cuda(v, offsets, tau, coeffs_out, flags_out)
+    _want_cells(n_cells, offsets, tau, None, coeffs_out, flags_out)
     p = params if params is not None else default_params()
     rc = lib().fp_closure_exact_static(_ptr(v), _vdtype(v), n_p, _ptr(offsets), n_cells, _ptr(tau),
                                        ctypes.byref(p), _PREC.get(prec, prec), _ptr(coeffs_out), _ptr(flags_out),
@@ -162,7 +163,7 @@ def fp_closure_backward(v, offsets, tau, moments, coeffs, flags, grad_coeffs, gr
     """Adjoint of the closure -> (grad_moments or None, grad_v or None).
     lu: the factors fp_closure_solve kept for the same moments (optional)."""
     n_cells = offsets.numel() - 1
-    n_p = v.shape[-1] if v.dim() == 2 else v.numel() // 3
+    n_p = _nv(v)
     dev = offsets.device
     if want_grad_moments and grad_moments is None:
         grad_moments = torch.empty((n_cells, NMOM), dtype=torch.float64, device=dev)
@@ -172,8 +173,11 @@ def fp_closure_backward(v, offsets, tau, moments, coeffs, flags, grad_coeffs, gr
                lu)
     if lu is not None and (lu.dtype != torch.float64 or lu.numel() < lu_doubles(n_cells)):
         raise FPError(f"lu must be float64 with lu_doubles(n_cells) = {lu_doubles(n_cells)} entries")
-    if grad_v is not None and grad_v.dtype != v.dtype:
-        raise FPError("grad_v must have the velocity dtype")
+    _want_cells(n_cells, offsets, tau, moments, coeffs, flags)
+    _want(grad_coeffs, "grad_coeffs", torch.float64, n_cells * NCOEF)
+    _want(grad_moments_in, "grad_moments_in", torch.float64, n_cells * NMOM)
+    _want(grad_moments, "grad_moments", torch.float64, n_cells * NMOM)
+    _want(grad_v, "grad_v", v.dtype, 3 * n_p)
     need = workspace_bytes(n_cells, n_p, "fp64", grad_moments is not None) if grad_v is not None else 0
     if need and workspace is None:
         workspace = torch.empty(need, dtype=torch.uint8, device=dev)
@@ -195,6 +199,10 @@ def fp_diagnostics(moments, m6, rho=None, theta_inf=1.0, rho_inf=1.0, dg_inf=0.0
     if out is None:
         out = torch.empty((n_cells, NDIAG), dtype=torch.float64, device=moments.device)
     _need_cuda(moments, m6, rho, out)
+    _want_cells(n_cells, moments=moments)
+    _want(m6, "m6", torch.float64, n_cells)
+    _want(rho, "rho", torch.float64, n_cells)
+    _want(out, "out", torch.float64, n_cells * NDIAG)
     rc = lib().fp_diagnostics(_ptr(moments), _ptr(m6), _ptr(rho), n_cells, float(theta_inf), float(rho_inf),
                               float(dg_inf), _ptr(out), _stream(stream))
     _check(rc, "fp_diagnostics")
@@ -206,6 +214,7 @@ def fp_coeffs_relax(coeffs_new, coeffs_prev, w=0.2, stream=None):
     _need_cuda(coeffs_new, coeffs_prev)
     if coeffs_new.shape != coeffs_prev.shape or coeffs_new.dtype != torch.float64:
         raise FPError("coeffs_new and coeffs_prev must be float64 of the same shape")
+    _want(coeffs_prev, "coeffs_prev", torch.float64, coeffs_prev.shape[0] * NCOEF)
     rc = lib().fp_coeffs_relax(_ptr(coeffs_new), _ptr(coeffs_prev), coeffs_prev.shape[0], float(w), _stream(stream))
     _check(rc, "fp_coeffs_relax")
     return coeffs_prev
@@ -256,8 +265,13 @@ class HostStep:
         for t in (h_v, h_offsets, h_tau, h_v_out, h_coeffs, h_flags):
             if t.is_cuda or not t.is_contiguous():
                 raise FPError("fp_step_host takes contiguous host tensors")
-        if h_v.dtype != self.dtype or h_v_out.dtype != self.dtype:
-            raise FPError("host velocities must have the pipeline's dtype")
+        nc, npart = self.n_cells, self.n_particles
+        _want(h_v, "h_v", self.dtype, 3 * npart)
+        _want(h_v_out, "h_v_out", self.dtype, 3 * npart)
+        _want(h_offsets, "h_offsets", torch.int64, nc + 1)
+        _want(h_tau, "h_tau", torch.float64, nc)
+        _want(h_coeffs, "h_coeffs", torch.float64, nc * NCOEF)
+        _want(h_flags, "h_flags", torch.int32, nc)
         io = StepIO()
         io.h_v, io.h_v_out = h_v.data_ptr(), h_v_out.data_ptr()
         io.h_offsets, io.h_tau = h_offsets.data_ptr(), h_tau.data_ptr()
@@ -356,6 +370,36 @@ def _vdtype(v):
     raise FPError(f"velocity dtype {v.dtype} (float32 or float64 expected)")
 
 
+def _nv(v):
+    """Particle count of velocities [3, n_particles] (or the flat SoA array
+    of 3 n_particles entries)."""
+    _vdtype(v)
+    if (v.dim() == 2 and v.shape[0] != 3) or v.numel() % 3:
+        raise FPError(f"velocities must be [3, n_particles], not {tuple(v.shape)}")
+    return v.numel() // 3
+
+
+def _want(t, name, dtype, numel):
+    """Checks a tensor before its pointer crosses the C ABI, which takes plain
+    pointers: the dtype the call reads or writes, and at least the entries it
+    touches.  None passes (the entry point treats it as absent)."""
+    if t is None:
+        return
+    if t.dtype != dtype:
+        raise FPError(f"{name} must be {dtype}, not {t.dtype}")
+    if t.numel() < numel:
+        raise FPError(f"{name} must hold at least {numel} entries, not {t.numel()}")
+
+
+def _want_cells(n_cells, offsets=None, tau=None, moments=None, coeffs=None, flags=None, stride=NMOM):
+    """The per-cell arrays of a call on n_cells cells."""
+    _want(offsets, "offsets", torch.int64, n_cells + 1)
+    _want(tau, "tau", torch.float64, n_cells)
+    _want(moments, "moments", torch.float64, n_cells * stride)
+    _want(coeffs, "coeffs", torch.float64, n_cells * NCOEF)
+    _want(flags, "flags", torch.int32, n_cells)
+
+
 def workspace_bytes(n_cells, n_particles, prec="fp32", moments_out_given=False) -> int:
     return int(lib().fp_workspace_bytes(n_cells, n_particles, _PREC.get(prec, prec), int(bool(moments_out_given))))
 
@@ -366,7 +410,7 @@ def fp_closure_exact(v, offsets, tau, params: Params | None = None, prec="fp32",
     tau [n_cells] f64 -> (moments [n_cells, 30] or None, coeffs [n_cells, 9],
     flags [n_cells])."""
     n_cells = offsets.numel() - 1
-    n_p = v.shape[-1] if v.dim() == 2 else v.numel() // 3
+    n_p = _nv(v)
     dev = offsets.device
     if want_moments and moments_out is None:
         moments_out = torch.empty((n_cells, NMOM), dtype=torch.float64, device=dev)
@@ -375,6 +419,7 @@ def fp_closure_exact(v, offsets, tau, params: Params | None = None, prec="fp32",
     if flags_out is None:
         flags_out = torch.empty((n_cells,), dtype=torch.int32, device=dev)
     _need_cuda(v, offsets, tau, moments_out, coeffs_out, flags_out, workspace)
+    _want_cells(n_cells, offsets, tau, moments_out, coeffs_out, flags_out)
     need = workspace_bytes(n_cells, n_p, prec, moments_out is not None)
     if need and workspace is None:
         workspace = torch.empty(need, dtype=torch.uint8, device=dev)
@@ -391,12 +436,12 @@ def fp_moments(v, offsets, prec="fp32", moments_out=None, stream=None, m6_out=No
     """Per-cell moment vectors [n_cells, 30] (f64); m6_out (float64
     [n_cells], optional) receives <|c|^6> for a one-pass velocity update."""
     n_cells = offsets.numel() - 1
-    n_p = v.shape[-1] if v.dim() == 2 else v.numel() // 3
+    n_p = _nv(v)
     if moments_out is None:
         moments_out = torch.empty((n_cells, NMOM), dtype=torch.float64, device=offsets.device)
     _need_cuda(v, offsets, moments_out, m6_out)
-    if m6_out is not None and (m6_out.dtype != torch.float64 or m6_out.numel() < n_cells):
-        raise FPError("m6_out must be float64 with one entry per cell")
+    _want_cells(n_cells, offsets, moments=moments_out)
+    _want(m6_out, "m6_out", torch.float64, n_cells)
     rc = lib().fp_moments(_ptr(v), _vdtype(v), n_p, _ptr(offsets), n_cells, _PREC.get(prec, prec),
                           _ptr(moments_out), _ptr(m6_out), _stream(stream))
     _check(rc, "fp_moments")
@@ -407,12 +452,12 @@ def fp_moments_lite(v, offsets, out=None, stream=None):
     """LITE moment vectors [n_cells, NLITE] (f64): N, U (3), theta, u_ij
     (6), b_i = <c_i |c|^2> (3), from FP32 compensated sums."""
     n_cells = offsets.numel() - 1
-    n_p = v.shape[-1] if v.dim() == 2 else v.numel() // 3
+    n_p = _nv(v)
     if out is None:
         out = torch.empty((n_cells, NLITE), dtype=torch.float64, device=offsets.device)
     _need_cuda(v, offsets, out)
-    if out.dtype != torch.float64 or out.numel() < n_cells * NLITE:
-        raise FPError("out must be float64 [n_cells, NLITE]")
+    _want_cells(n_cells, offsets)
+    _want(out, "out", torch.float64, n_cells * NLITE)
     rc = lib().fp_moments_lite(_ptr(v), _vdtype(v), n_p, _ptr(offsets), n_cells, _ptr(out), _stream(stream))
     _check(rc, "fp_moments_lite")
     return out
@@ -434,6 +479,12 @@ def fp_sort_by_cell(cell_of, n_cells, v=None, v_sorted=None, perm_out=None, offs
     need = int(lib().fp_sort_workspace_bytes(n_p, n_cells))
     ws = workspace if workspace is not None else torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
     _need_cuda(cell_of, perm, off, v, v_sorted, ws)
+    _want(perm, "perm_out", torch.int32, n_p)
+    _want(off, "offsets_out", torch.int64, n_cells + 1)
+    if v is not None:
+        if _nv(v) != n_p:
+            raise FPError("v must hold the velocities of the cell_of particles")
+        _want(v_sorted, "v_sorted", v.dtype, 3 * n_p)
     rc = lib().fp_sort_by_cell(_ptr(cell_of), n_p, n_cells, _ptr(v), _vdtype(v) if v is not None else 0,
                                _ptr(v_sorted), _ptr(perm), _ptr(off), _ptr(ws), ws.numel(), _stream(stream))
     _check(rc, "fp_sort_by_cell")
@@ -457,6 +508,12 @@ def fp_collision_step(cell_of, v, n_cells, tau, dt, params: Params | None = None
     need = int(lib().fp_collision_step_workspace_bytes(n_p, n_cells, _vdtype(v), int(lite)))
     ws = workspace if workspace is not None else torch.empty(need, dtype=torch.uint8, device=dev)
     _need_cuda(cell_of, v, tau, v_out, perm, off, y, fl, moments_out, ws)
+    _want(cell_of, "cell_of", torch.int32, n_p)
+    if _nv(v) != n_p:
+        raise FPError("v must hold the velocities of the cell_of particles")
+    _want(v_out, "v_out", v.dtype, 3 * n_p)
+    _want(perm, "perm_out", torch.int32, n_p)
+    _want_cells(n_cells, off, tau, moments_out, y, fl, stride=NLITE if lite else NMOM)
     p = params if params is not None else default_params()
     rc = lib().fp_collision_step(_ptr(cell_of), _ptr(v), _vdtype(v), n_p, n_cells, _ptr(tau), ctypes.byref(p),
                                  _PREC.get(prec, prec), ctypes.byref(net_lite) if lite else None, float(dt),
@@ -478,6 +535,7 @@ def fp_closure_solve(moments, tau, params: Params | None = None, prec="fp32", co
     if flags_out is None:
         flags_out = torch.empty((n_cells,), dtype=torch.int32, device=dev)
     _need_cuda(moments, tau, coeffs_out, flags_out, lu_out)
+    _want_cells(n_cells, None, tau, moments, coeffs_out, flags_out)
     if lu_out is not None and (lu_out.dtype != torch.float64 or lu_out.numel() < lu_doubles(n_cells)):
         raise FPError(f"lu_out must be float64 with lu_doubles(n_cells) = {lu_doubles(n_cells)} entries")
     p = params if params is not None else default_params()
@@ -495,14 +553,14 @@ def fp_velocity_update(v, offsets, moments, coeffs, tau, flags, dt, params: Para
     m6 (fp_moments' m6_out of the same velocities) the particles are read
     once."""
     n_cells = offsets.numel() - 1
-    n_p = v.shape[-1] if v.dim() == 2 else v.numel() // 3
+    n_p = _nv(v)
     _need_cuda(v, offsets, moments, coeffs, tau, flags, xi, alpha_out, v_out, m6)
-    if v_out is not None and (v_out.dtype != v.dtype or v_out.numel() != v.numel() or not v_out.is_contiguous()):
-        raise FPError("v_out must be a contiguous array of v's shape and dtype")
-    if xi is not None and xi.dtype != v.dtype:
-        raise FPError("xi must have the velocity dtype")
-    if flags.dtype != torch.int32:
-        raise FPError("flags must be int32")
+    if v_out is not None and (v_out.dtype != v.dtype or v_out.numel() != v.numel()):
+        raise FPError("v_out must be an array of v's shape and dtype")
+    _want(xi, "xi", v.dtype, 3 * n_p)
+    _want_cells(n_cells, offsets, tau, moments, coeffs, flags)
+    _want(alpha_out, "alpha_out", torch.float64, n_cells)
+    _want(m6, "m6", torch.float64, n_cells)
     p = params if params is not None else default_params()
     rc = lib().fp_velocity_update(_ptr(v), _ptr(v_out), _vdtype(v), n_p, _ptr(offsets), n_cells, _ptr(moments),
                                   _ptr(m6),
@@ -517,14 +575,13 @@ def fp_velocity_update_lite(v, offsets, lite, coeffs, tau, flags, dt, params: Pa
     """fp_velocity_update from LITE moment vectors [n_cells, NLITE] (alpha's
     cell averages summed over the particles)."""
     n_cells = offsets.numel() - 1
-    n_p = v.shape[-1] if v.dim() == 2 else v.numel() // 3
+    n_p = _nv(v)
     _need_cuda(v, offsets, lite, coeffs, tau, flags, xi, alpha_out, v_out)
     if v_out is not None and (v_out.dtype != v.dtype or v_out.numel() != v.numel()):
         raise FPError("v_out must be an array of v's shape and dtype")
-    if xi is not None and xi.dtype != v.dtype:
-        raise FPError("xi must have the velocity dtype")
-    if flags.dtype != torch.int32:
-        raise FPError("flags must be int32")
+    _want(xi, "xi", v.dtype, 3 * n_p)
+    _want_cells(n_cells, offsets, tau, lite, coeffs, flags, stride=NLITE)
+    _want(alpha_out, "alpha_out", torch.float64, n_cells)
     p = params if params is not None else default_params()
     rc = lib().fp_velocity_update_lite(_ptr(v), _ptr(v_out), _vdtype(v), n_p, _ptr(offsets), n_cells, _ptr(lite),
                                        _ptr(coeffs), _ptr(tau), float(dt), ctypes.byref(p), _ptr(xi), int(seed),

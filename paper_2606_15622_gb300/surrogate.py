@@ -137,6 +137,9 @@ class Surrogate:
         n = moments.shape[0]
         x = x_out if x_out is not None else torch.empty((n, IN), dtype=torch.bfloat16, device=self.device)
         fl = flags_out if flags_out is not None else torch.empty(n, dtype=torch.int32, device=self.device)
+        api._need_cuda(moments, tau, x, fl)
+        api._want_cells(n, None, tau, moments, None, fl)
+        api._want(x, "x_out", torch.bfloat16, n * IN)
         p = params if params is not None else api.default_params(eps2_hat=self.eps2_hat)
         rc = _lib().fp_surrogate_features(ctypes.byref(self.net()), _p(moments), n, _p(tau), ctypes.byref(p),
                                           _p(x), _p(fl), api._stream(stream))
@@ -150,6 +153,9 @@ class Surrogate:
         if save:
             h = torch.empty((DEPTH, n, HID), dtype=torch.bfloat16, device=self.device)
             z = torch.empty((DEPTH, n, HID), dtype=torch.float32, device=self.device)
+        api._need_cuda(x, o)
+        api._want(x, "x", torch.bfloat16, n * IN)
+        api._want(o, "out", torch.float32, n * OUT)
         rc = _lib().fp_mlp_forward(ctypes.byref(self.net()), _p(x), n, int(bool(standardized)), _p(o), _p(h), _p(z),
                                    api._stream(stream))
         api._check(rc, "fp_mlp_forward")
@@ -164,6 +170,8 @@ class Surrogate:
         fl = flags_out if flags_out is not None else torch.empty(n, dtype=torch.int32, device=self.device)
         need = int(_lib().fp_surrogate_workspace_bytes(n))
         ws = workspace if workspace is not None else torch.empty(need, dtype=torch.uint8, device=self.device)
+        api._need_cuda(moments, tau, y, fl, ws)
+        api._want_cells(n, None, tau, moments, y, fl)
         p = params if params is not None else api.default_params(eps2_hat=self.eps2_hat)
         rc = _lib().fp_closure_surrogate(ctypes.byref(self.net()), _p(moments), n, _p(tau), ctypes.byref(p),
                                          api._PREC.get(prec, prec), _p(y), _p(fl), _p(ws), ws.numel(),
@@ -177,6 +185,9 @@ class Surrogate:
         n = lite.shape[0]
         x = x_out if x_out is not None else torch.empty((n, IN), dtype=torch.bfloat16, device=self.device)
         fl = flags_out if flags_out is not None else torch.empty(n, dtype=torch.int32, device=self.device)
+        api._need_cuda(lite, tau, x, fl)
+        api._want_cells(n, None, tau, lite, None, fl, stride=api.NLITE)
+        api._want(x, "x_out", torch.bfloat16, n * IN)
         p = params if params is not None else api.default_params(eps2_hat=self.eps2_hat)
         rc = _lib().fp_surrogate_lite_features(ctypes.byref(self.net()), _p(lite), n, _p(tau), ctypes.byref(p),
                                                _p(x), _p(fl), api._stream(stream))
@@ -192,6 +203,8 @@ class Surrogate:
         fl = flags_out if flags_out is not None else torch.empty(n, dtype=torch.int32, device=self.device)
         need = int(_lib().fp_surrogate_lite_workspace_bytes(n))
         ws = workspace if workspace is not None else torch.empty(need, dtype=torch.uint8, device=self.device)
+        api._need_cuda(lite, tau, y, fl, ws)
+        api._want_cells(n, None, tau, lite, y, fl, stride=api.NLITE)
         p = params if params is not None else api.default_params(eps2_hat=self.eps2_hat)
         rc = _lib().fp_closure_surrogate_lite(ctypes.byref(self.net()), _p(lite), n, _p(tau), ctypes.byref(p),
                                               _p(y), _p(fl), _p(ws), ws.numel(), api._stream(stream))
@@ -215,6 +228,9 @@ class Surrogate:
         fl = flags_out if flags_out is not None else torch.empty(n, dtype=torch.int32, device=dev)
         need = int(_lib().fp_surrogate_sensitivity_workspace_bytes(n))
         ws = workspace if workspace is not None else torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+        api._need_cuda(moments, tau, sens, mean, fl, ws)
+        api._want_cells(n, None, tau, moments, mean, fl, stride=stride)
+        api._want(sens, "sens_out", torch.float64, n * api.NSENS)
         p = params if params is not None else api.default_params(eps2_hat=self.eps2_hat)
         rc = _lib().fp_surrogate_sensitivity(ctypes.byref(self.net()), _p(moments), stride, n, _p(tau),
                                              ctypes.byref(p), int(n_passes), float(rate), int(seed), _p(sens),

@@ -46,3 +46,31 @@ def test_host_only_calls_work_without_gpu():
     assert p.min_particles == 4 and p.pivot_rtol == 1e-13
     assert api.workspace_bytes(1000, 5000, "fp32") == 256 * ((1000 * 30 * 8 + 255) // 256)
     assert api.workspace_bytes(1000, 5000, "fp32", moments_out_given=True) == 0
+
+
+def test_binding_checks_tensor_arguments_before_the_abi():
+    """The C ABI takes plain pointers, so the binding refuses host tensors,
+    wrong dtypes and too-short arrays before anything reaches the library."""
+    import torch
+
+    from paper_2606_15622_gb300 import api
+    with pytest.raises(api.FPError, match="CUDA tensors"):
+        api.fp_moments(torch.zeros((3, 8)), torch.zeros(3, dtype=torch.int64), moments_out=torch.zeros((2, 30)))
+    assert api._nv(torch.zeros((3, 7))) == 7 and api._nv(torch.zeros(21, dtype=torch.float64)) == 7
+    for bad in (torch.zeros((4, 7)), torch.zeros(20), torch.zeros((3, 7), dtype=torch.float16)):
+        with pytest.raises(api.FPError):
+            api._nv(bad)
+    api._want(None, "x", torch.float64, 10)
+    api._want(torch.zeros(10, dtype=torch.float64), "x", torch.float64, 10)
+    with pytest.raises(api.FPError, match="must be torch.float64"):
+        api._want(torch.zeros(10, dtype=torch.float32), "x", torch.float64, 10)
+    with pytest.raises(api.FPError, match="at least 11"):
+        api._want(torch.zeros(10, dtype=torch.float64), "x", torch.float64, 11)
+    api._want_cells(4, torch.zeros(5, dtype=torch.int64), torch.zeros(4, dtype=torch.float64),
+                    torch.zeros((4, api.NMOM), dtype=torch.float64), torch.zeros((4, 9), dtype=torch.float64),
+                    torch.zeros(4, dtype=torch.int32))
+    with pytest.raises(api.FPError, match="offsets"):
+        api._want_cells(4, offsets=torch.zeros(5, dtype=torch.int32))
+    with pytest.raises(api.FPError, match="moments"):
+        api._want_cells(4, moments=torch.zeros((4, api.NLITE), dtype=torch.float64))
+    api._want_cells(4, moments=torch.zeros((4, api.NLITE), dtype=torch.float64), stride=api.NLITE)

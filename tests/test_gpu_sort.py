@@ -224,10 +224,19 @@ def test_sort_and_step_degenerate_sizes():
 
 
 def test_sort_rejects_too_many_cells():
+    """2^31 cells: the binding refuses the short offsets array, and the
+    library itself answers FP_ERR_UNSUPPORTED before touching any buffer."""
+    import ctypes
     c = torch.zeros(4, dtype=torch.int32, device="cuda")
+    off = torch.empty(1, dtype=torch.int64, device="cuda")
+    perm = torch.empty(4, dtype=torch.int32, device="cuda")
+    ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
     with pytest.raises(api.FPError):
-        api.fp_sort_by_cell(c, 2 ** 31, offsets_out=torch.empty(1, dtype=torch.int64, device="cuda"),
-                            workspace=torch.empty(1024, dtype=torch.uint8, device="cuda"))
+        api.fp_sort_by_cell(c, 2 ** 31, offsets_out=off, workspace=ws)
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    rc = api.lib().fp_sort_by_cell(ptr(c), 4, 2 ** 31, None, 0, None, ptr(perm), ptr(off), ptr(ws), ws.numel(),
+                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == api.FP_ERR_UNSUPPORTED
 
 
 def test_collision_steps_full_size_cylinder():
