@@ -561,6 +561,7 @@ def run_ours(args):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": round(ms_per_step, 5),
+        "step_ms": step_stats(times),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -724,6 +725,38 @@ class OracleCores:
         shutil.rmtree(self.folder, ignore_errors=True)
 
 
+def host_cpu():
+    """The host's CPU model (lscpu's model name, else /proc/cpuinfo's, else
+    the machine type) and its online CPUs, for the CPU baseline's record."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith("model name"):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    import platform
+    return {"model": model or platform.machine(), "nproc": os.cpu_count()}
+
+
+def step_stats(times_ms):
+    """Median and best of the timed steps (ms), beside the mean the bench line
+    reports as ms_per_step."""
+    t = np.asarray(times_ms, dtype=np.float64)
+    return {"median": round(float(np.median(t)), 5), "best": round(float(np.min(t)), 5)}
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -745,15 +778,15 @@ def cpu_baseline(pop, budget_s=15.0, workers=None):
               "sample": f"{c1} cells ({p1} particles) of {pop.name} in {el:.1f} s"}
     workers = host_cores() if workers is None else workers
     if workers <= 1:
-        return dict(single, kind="oracle", sample=single["sample"] + ": FP64 moments, exact closure and velocity "
-                                                                   "update, 1 thread")
+        return dict(single, kind="oracle", host=host_cpu(),
+                    sample=single["sample"] + ": FP64 moments, exact closure and velocity update, 1 thread")
     cores = OracleCores(pop, workers)
     try:
         rate, prate, cn, pn = cores.run(budget_s)
     finally:
         cores.close()
     return {"value": round(rate, 1), "unit": "cells/s", "cores": workers, "kind": "oracle",
-            "particles_per_s": round(prate, 1),
+            "particles_per_s": round(prate, 1), "host": host_cpu(),
             "sample": f"{cn} cells ({pn} particles) of {pop.name} in {budget_s:.0f} s on {workers} processes, one a "
                       f"core, each over its share of {ORACLE_BLOCK}-cell blocks: FP64 moments, exact closure and "
                       "velocity update",
@@ -788,7 +821,7 @@ def run_reference(args):
         "config": {"workload": f"{pop.name}: {pop.n_cells} cells, {pop.n_particles} particles "
                                "(bounded sample per step)", "cells": pop.n_cells, "particles": pop.n_particles},
         "cpu_baseline": {"value": round(value, 1), "unit": "cells/s", "cores": workers, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "host": host_cpu()},
         "e2e": {"value": round(value, 1), "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))

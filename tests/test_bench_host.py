@@ -13,6 +13,7 @@ def test_cpu_baseline_single_and_all_cores():
     assert "2 processes" in out["sample"]
     one = bench.cpu_baseline(pop, budget_s=0.3, workers=1)
     assert one["cores"] == 1 and one["value"] > 0 and "single_thread" not in one
+    assert out["host"]["nproc"] >= 1 and one["host"]["model"]
 
 
 def test_worker_shares_cover_every_block_once():
@@ -24,3 +25,10 @@ def test_worker_shares_cover_every_block_once():
             assert set(flat) == set(range(n_blocks))
             if workers <= n_blocks:
                 assert len(flat) == n_blocks
+
+
+def test_host_record_and_step_statistics():
+    h = bench.host_cpu()
+    assert isinstance(h["model"], str) and h["model"] and h["nproc"] >= 1
+    st = bench.step_stats([0.7, 0.6, 0.65, 0.9])
+    assert st == {"median": 0.675, "best": 0.6}
