@@ -1,7 +1,8 @@
 """CPU FP64 oracle of the cubic Fokker-Planck closure -- TEST INFRASTRUCTURE.
 
-Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
-``bench.py`` may import this package.  The product path (the CUDA library and
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline and
+reference legs of ``bench.py`` (with their worker processes) may import this
+package.  The product path (the CUDA library and
 its Python binding) never does, and this package imports nothing from it.
 
 The arithmetic lives in ``fp_oracle.c`` / ``closure_core.h`` (plain C99,

@@ -1,7 +1,7 @@
 """CPU FP64 oracle of the LITE path -- TEST INFRASTRUCTURE.
 
-Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
-``bench.py`` may import this module.  Plain numpy, one cell at a time.
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline and
+reference legs of ``bench.py`` may import this module.  Plain numpy, one cell at a time.
 
 The LITE moment pass (Sec. 4, Phase 3 item 2) computes only the moments up
 to the heat flux that the network's 16 inputs need (Sec. 4, Phase 1-2
