@@ -3,8 +3,8 @@
  * TEST INFRASTRUCTURE ONLY.  A plain, slow, obviously-correct CPU reference
  * of the cubic Fokker-Planck moment closure and its particle velocity update,
  * in FP64, written from the paper's equations.  Only the tests, the smoke
- * check and the CPU-baseline leg of the benchmark may load it; the product
- * path never does.  It shares no code, header or table with the CUDA library.
+ * check and the CPU-baseline and reference legs of the benchmark may load it;
+ * the product path never does.  It shares no code, header or table with the CUDA library.
  *
  * What each entry point follows:
  *   oracle_moments            central moments, Sec. 3.6 (u^(p) definition)
