@@ -598,6 +598,19 @@ int fp_step_host(fp_pipeline *pl, const fp_step_io *io, int v_dtype, int64_t n_p
                  const fp_params *p, int prec, double dt, uint64_t seed, uint64_t step, int n_chunks,
                  fp_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Self-test of the bounded waits (a runtime check; the paper has no
+ * counterpart).  Every kernel that consumes bulk copies waits on mbarriers
+ * with a limit on the global timer and reports a wait that runs out in band
+ * instead of spinning.  fp_selftest_wait_timeout launches one CTA that waits
+ * on an mbarrier nothing completes, with limit_ns in (0, 1e9]:
+ *   status_out     device int32: 0 when the wait gave up (the expected
+ *                  answer), 1 if the barrier had completed
+ *   waited_ns_out  device uint64: the time the wait took (>= limit_ns)
+ * Asynchronous on `stream`; FP_ERR_ARG for a null pointer or a limit out of
+ * range. */
+int fp_selftest_wait_timeout(uint64_t limit_ns, int32_t *status_out, uint64_t *waited_ns_out, fp_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -128,6 +128,7 @@ SIGNATURES = {
     "fp_surrogate_lite_workspace_bytes": (_sz, [_i64]),
     "fp_closure_surrogate_lite": (_i32, [ctypes.POINTER(FpMlp), _vp, _i64, _vp, ctypes.POINTER(Params), _vp, _vp,
                                          _vp, _sz, _vp]),
+    "fp_selftest_wait_timeout": (_i32, [_u64, _vp, _vp, _vp]),
 }
 
 STATIC_MAX_CELLS = 32768
@@ -588,3 +589,16 @@ def fp_velocity_update_lite(v, offsets, lite, coeffs, tau, flags, dt, params: Pa
                                        int(step), _ptr(alpha_out), _ptr(flags), _stream(stream))
     _check(rc, "fp_velocity_update_lite")
     return (v if v_out is None else v_out), alpha_out, flags
+
+
+def fp_selftest_wait_timeout(limit_ns=1_000_000, stream=None):
+    """Self-test of the library's bounded mbarrier wait: a wait on a barrier
+    nothing completes, limited to limit_ns -> (status, waited_ns); status 0
+    means the wait gave up as it should."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    status = torch.full((1,), -1, dtype=torch.int32, device=dev)
+    waited = torch.zeros(1, dtype=torch.int64, device=dev)
+    _check(lib().fp_selftest_wait_timeout(int(limit_ns), _ptr(status), _ptr(waited), _stream(stream)),
+           "fp_selftest_wait_timeout")
+    return int(status.item()), int(waited.item())
+

@@ -52,6 +52,7 @@ void launch_diagnostics(const double *mom, const double *m6, const double *rho, 
                         double rho_inf, double dg_inf, double *out, cudaStream_t st);
 void launch_relax(const double *y_new, double *y_prev, int64_t n, double w, cudaStream_t st);
 int64_t mlp_param_offset(int which, int layer);
+void launch_wait_timeout(uint64_t limit_ns, int32_t *status, uint64_t *waited_ns, cudaStream_t st);
 int64_t mlp_param_count();
 size_t mlp_backward_ws(int64_t n);
 void launch_mlp_backward(const fp_mlp &net, const void *x, const void *h_save, const float *z_save,
@@ -665,6 +666,14 @@ int fp_surrogate_sensitivity(const fp_mlp *net, const double *moments, int momen
   }
   fpc::launch_sens_finalize(mean, m2, moments, moment_stride, tau, n_cells, n_passes, fl, sens_out, mean_out, st);
   return check_launch("surrogate_sensitivity");
+}
+
+int fp_selftest_wait_timeout(uint64_t limit_ns, int32_t *status_out, uint64_t *waited_ns_out, fp_stream_t stream) {
+  if (!status_out || !waited_ns_out) return fail(FP_ERR_ARG, "null pointer");
+  if (limit_ns == 0 || limit_ns > 1000000000ull) return fail(FP_ERR_ARG, "limit %llu ns outside (0, 1 s]",
+                                                             (unsigned long long)limit_ns);
+  fpc::launch_wait_timeout(limit_ns, status_out, waited_ns_out, (cudaStream_t)stream);
+  return check_launch("selftest_wait_timeout");
 }
 
 }  // extern "C"
