@@ -57,7 +57,7 @@ GATHER_BYTES_PER_PARTICLE = 12          # three FP32 components read once
 GATHER_BYTES_PER_CELL = 8 + 8 * 31      # one offset read, the moment vector and <|c|^6> written
 LITE_BYTES_PER_CELL = 8 + 8 * 14        # one offset read, the LITE moment vector written
 VEL_BYTES_PER_PARTICLE = 24             # read + write three FP32 components
-VEL_BYTES_PER_CELL = 8 + 8 * 24 + 4 + 4 + 8  # offset, 24 FP64 constants, flags in/out, alpha
+VEL_BYTES_PER_CELL = 8 + 8 * (3 + 1 + 3 + 9 + 1) + 4 + 4 + 8  # offset; U, theta, q, C, Gamma, tau; flags in/out; alpha
 SOLVE_FLOPS_PER_CELL = 658              # FP64: assembly + elimination + back substitution (FMA = 2)
 MLP_FLOPS_PER_CELL = 2 * (32 * 128 + 3 * 128 * 128 + 128 * 16)  # padded layer shapes
 FP64_PEAK_TFLOPS = 1.197                # FP64 peak of a GB300, measured with independent DFMA chains
