@@ -359,7 +359,12 @@ int fp_adam_step(float *params, const float *grads, float *m, float *v, int64_t 
  *     until the process exits.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress, with that device current); make that first call
- *     before any stream capture.
+ *     before any stream capture.  The address is kept for the process:
+ *     after cudaDeviceReset on a device (or from a second driver-API context
+ *     on it) the library's module may load at another address, so do not
+ *     call this entry point on that device again in the same process.
+ *   - If the moment gather fails to launch, the call returns FP_ERR_CUDA
+ *     before the solve runs, leaving coeffs_out and flags_out untouched.
  *   - Every call on a device shares the one array and it keeps the last
  *     call's contents; nothing needs clearing (each call overwrites every
  *     slot it reads).  Calls whose executions overlap on the GPU (different

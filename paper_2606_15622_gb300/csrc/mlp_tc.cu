@@ -363,7 +363,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int q = 0; q < kOut / 2; ++q) o[q] = make_float2(nan, nan);
     }
   }
-  // ---- teardown: every tcgen05 operation of this CTA has completed ----
+  // ---- teardown ----
+  // Normally every MMA batch of this CTA has been waited for.  A group whose
+  // wait ran out (its rows were written as NaN) may still have the batch it
+  // gave up on in flight: its leader waits for that commit once more, bounded,
+  // before the tensor memory is released.  Should that wait run out too, the
+  // release below precedes the MMA's completion, which leaves the tensor
+  // memory's state undefined; the NaN rows tell the caller to treat the
+  // context as suspect.
+  if (failed && leader) (void)mbar_wait_bounded(&bar[g], phase ^ 1u, 200000000ull);
+  cp_async_wait();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();

@@ -44,7 +44,11 @@ int static_fail(int code, const char *msg) {
 }
 
 // Device address of the scratch array on the current device (looked up on
-// the first call per device).
+// the first call per device).  The address belongs to the device's primary
+// context.  cudaDeviceReset ends that context; the library's module is then
+// loaded again, possibly at another address, and the cached one is stale.
+// The header therefore states that a process which resets a device must not
+// call this entry point on that device afterwards.
 int scratch_address(double **out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
@@ -91,8 +95,12 @@ int fp_closure_exact_static(const void *v, int v_dtype, int64_t n_particles, con
   // the gather writes every slot of cells [0, n_cells) before the solve
   // reads them, so the scratch needs no clearing between calls
   fpc::launch_gather(v, v_dtype, n_particles, cell_offsets, n_cells, prec, scratch, nullptr, st);
+  // a gather that failed to launch left another call's moments in the array:
+  // stop before the solve reads them into the caller's outputs
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return static_fail(FP_ERR_CUDA, cudaGetErrorString(e));
   fpc::launch_solve(scratch, tau, n_cells, prm, prec, coeffs_out, flags_out, nullptr, st);
-  const cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return static_fail(FP_ERR_CUDA, cudaGetErrorString(e));
   return FP_OK;
 }
