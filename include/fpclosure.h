@@ -76,8 +76,13 @@ enum { FP_V_F32 = 0, FP_V_F64 = 1 };
  * The 9x9 assembly and the pivoted solve are FP64 in both modes.  With FP32
  * moments (relative error ~1e-7) a pivot below ~1e-6 max|A| cannot be told
  * from zero, so that mode flags a cell singular when a pivot is
- * <= max(pivot_rtol, FP_FP32_PIVOT_FLOOR) * max|A|. */
+ * <= max(pivot_rtol, FP_FP32_PIVOT_FLOOR) * max|A|.  A cell of four
+ * particles gives a singular 9x9 system whatever its velocities (its pivot
+ * ratio is ~1e-15 with exact moments), but with FP32 moments its smallest
+ * pivot carries the moment noise (1e-7..1e-5 of max|A|), so that mode flags
+ * cells with fewer than FP_FP32_MIN_REGULAR particles singular directly. */
 #define FP_FP32_PIVOT_FLOOR 1e-6
+#define FP_FP32_MIN_REGULAR 5
 enum { FP_PREC_FP64 = 0, FP_PREC_FP32_MOMENTS = 1 };
 
 /* per-cell flag bits */

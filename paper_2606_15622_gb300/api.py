@@ -33,6 +33,7 @@ PREC_FP64, PREC_FP32_MOMENTS = 0, 1
 FLAG_FEW, FLAG_SINGULAR, FLAG_NONFINITE, FLAG_RANGE, FLAG_ENERGY, FLAG_FALLBACK, FLAG_ALPHA = 1, 2, 4, 8, 16, 32, 64
 FALLBACK_FLAGS = FLAG_FEW | FLAG_SINGULAR | FLAG_NONFINITE
 FP32_PIVOT_FLOOR = 1e-6
+FP32_MIN_REGULAR = 5  # FP32-moment mode flags cells with fewer particles singular
 
 _PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32_MOMENTS, PREC_FP64: PREC_FP64, PREC_FP32_MOMENTS: PREC_FP32_MOMENTS}
 

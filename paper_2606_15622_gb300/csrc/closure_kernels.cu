@@ -339,7 +339,7 @@ void launch_solve(const double *mom, const double *tau, int64_t n_cells, const f
                   double *coeffs, int32_t *flags, double *lu, cudaStream_t st) {
   double rtol = p.pivot_rtol;
   if (prec == FP_PREC_FP32_MOMENTS && rtol < FP_FP32_PIVOT_FLOOR) rtol = FP_FP32_PIVOT_FLOOR;
-  SolveParams prm{p.eps2_hat, rtol, p.min_particles};
+  SolveParams prm{p.eps2_hat, rtol, p.min_particles, prec == FP_PREC_FP32_MOMENTS ? FP_FP32_MIN_REGULAR : 0};
   const int threads = 128;
   int64_t blocks = (n_cells + threads - 1) / threads;
   if (blocks > 2 * sm_count()) blocks = 2 * sm_count();

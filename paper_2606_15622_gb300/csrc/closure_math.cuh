@@ -29,6 +29,7 @@ struct SolveParams {
   double eps2_hat;
   double pivot_rtol;
   int min_particles;
+  int min_regular;  // cells with fewer particles are flagged singular without a solve
 };
 
 // Assemble the augmented system [A | r] (moment-matching rows for psi =
@@ -262,6 +263,7 @@ __device__ __forceinline__ int closure_cell(const double *__restrict__ mc, doubl
   if (!fin) fl |= FP_FLAG_NONFINITE;
   if (m[kN] < (double)prm.min_particles) fl |= FP_FLAG_FEW;
   if (!(m[kTheta] > 0.0)) fl |= FP_FLAG_SINGULAR;
+  if (!fl && m[kN] < (double)prm.min_regular) fl |= FP_FLAG_SINGULAR;
   if (!fl) {
     double a[9][10], rinv[9];
     uint64_t perm;

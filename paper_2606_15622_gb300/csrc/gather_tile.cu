@@ -9,18 +9,24 @@
 //     component ranges (widened to 16-byte boundaries) into a ring of kSlots
 //     shared-memory slots with cp.async.bulk, completing on the slot's `full`
 //     mbarrier;
-//   * consumer warps take the sub-tiles in the same order and reduce eight
-//     cells per warp task (four lanes per cell, the eight cells of a task
+//   * consumer warps take the sub-tiles in the same order and reduce four
+//     cells per warp task (eight lanes per cell, the four cells of a task
 //     consecutive in size order so their loops have similar trip counts)
 //     from shared memory, then release the slot on its `empty` mbarrier.
 // A cell larger than a sub-tile is reduced straight from global memory.  No
 // global-memory round trip sits on a consumer's path; the producer runs up
 // to kSlots sub-tiles ahead.
 //
-// Per lane the sums are plain FP32 over blocks of BLK particles, blocks
-// folded with two-sum; lanes combine by a reduce-scatter.  Promotion to FP64
-// scales by the power of two in FP32 (exact), converts hi and lo parts and
-// adds them: one FP64-pipe instruction per moment.
+// A lane takes two steps of its group at once (particles i and i + 8) and does
+// their arithmetic packed as FP32x2 (__fadd2_rn / __fmul2_rn / __ffma2_rn: one
+// instruction for both); steps whose particles all lie in their cells skip the
+// masking.  Per lane the sums are plain FP32 over blocks of 16 pair steps;
+// each block is reduced over the group's eight lanes through a swizzled
+// shared-memory transpose (a lane writes its row, the owner of four sums adds
+// eight float4s), and owners fold the blocks with two-sum.  Promotion to FP64
+// scales by the power of two in FP32 (exact), widens hi and lo parts on the
+// integer pipe with the scale folded into the exponent and adds them: one
+// FP64-pipe instruction per moment.
 //
 // The same kernel, instantiated with kLite, serves the LITE moment pass:
 // only the 9 sums of u_ij and b_i = <c_i |c|^2> a particle, written as the
@@ -35,13 +41,14 @@ namespace fpc {
 constexpr int kChunkCells = 64;
 constexpr int kSubP = 2048;                  // particles per sub-tile (max)
 constexpr int kCapF = kSubP + 8;             // floats per component slot (alignment slack)
-constexpr int kSlots = 4;
+constexpr int kSlots = 3;
 constexpr int kConsumerWarps = 7;          // 8 warps a CTA, 2 CTAs per SM: the register cap of 128 still holds the sums
 constexpr int kTileThreads = 32 * (1 + kConsumerWarps);
 constexpr int kTileG = 8;                    // lanes per cell (measured best of 4, 8, 16, 32)
 constexpr int kCellsPerTask = 32 / kTileG;   // cells per warp task
 constexpr int kSlotFloats = 3 * kCapF;
-constexpr size_t kTileSmem = (size_t)kSlots * kSlotFloats * sizeof(float);
+constexpr int kScratchFloats = 32 * 32;  // transpose scratch per consumer warp
+constexpr size_t kTileSmem = (size_t)kSlots * kSlotFloats * sizeof(float) + (size_t)kConsumerWarps * kScratchFloats * 4;
 
 struct SlotMeta {
   int64_t cs, ce;                 // cells [cs, ce) of the sub-tile
@@ -63,43 +70,108 @@ __device__ __forceinline__ int tile_order(int q) {
   return sum_order(q);
 }
 
+// physical float4 chunk of logical chunk c in transpose-scratch row r: the
+// eight rows of a quarter-warp put a given chunk on eight different bank groups
+__device__ __forceinline__ int swz(int c, int r) { return c ^ (((r & 3) << 1) | ((r >> 2) & 1)); }
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// The monomials of one pair of particles (w packed as FP32x2) added to the
+// packed sums T (sum slot order of sum_order; the LITE set is u_ij, c_i |c|^2).
+template <bool kLite, int NS>
+__device__ __forceinline__ void accumulate2(float2 (&T)[NS], float2 wx, float2 wy, float2 wz) {
+  const float2 xx = __fmul2_rn(wx, wx), xy = __fmul2_rn(wx, wy), xz = __fmul2_rn(wx, wz);
+  const float2 yy = __fmul2_rn(wy, wy), yz = __fmul2_rn(wy, wz), zz = __fmul2_rn(wz, wz);
+  T[0] = __fadd2_rn(T[0], xx); T[1] = __fadd2_rn(T[1], xy); T[2] = __fadd2_rn(T[2], xz);
+  T[3] = __fadd2_rn(T[3], yy); T[4] = __fadd2_rn(T[4], yz); T[5] = __fadd2_rn(T[5], zz);
+  const float2 r2 = __fadd2_rn(__fadd2_rn(xx, yy), zz);
+  if constexpr (kLite) {
+    T[6] = __ffma2_rn(r2, wx, T[6]); T[7] = __ffma2_rn(r2, wy, T[7]); T[8] = __ffma2_rn(r2, wz, T[8]);
+  } else {
+    T[6] = __ffma2_rn(xx, wx, T[6]);   T[7] = __ffma2_rn(xx, wy, T[7]);   T[8] = __ffma2_rn(xx, wz, T[8]);
+    T[9] = __ffma2_rn(xy, wy, T[9]);   T[10] = __ffma2_rn(xy, wz, T[10]); T[11] = __ffma2_rn(xz, wz, T[11]);
+    T[12] = __ffma2_rn(yy, wy, T[12]); T[13] = __ffma2_rn(yy, wz, T[13]); T[14] = __ffma2_rn(yz, wz, T[14]);
+    T[15] = __ffma2_rn(zz, wz, T[15]);
+    T[16] = __ffma2_rn(r2, xx, T[16]); T[17] = __ffma2_rn(r2, xy, T[17]); T[18] = __ffma2_rn(r2, xz, T[18]);
+    T[19] = __ffma2_rn(r2, yy, T[19]); T[20] = __ffma2_rn(r2, yz, T[20]); T[21] = __ffma2_rn(r2, zz, T[21]);
+    const float2 r4 = __fmul2_rn(r2, r2);
+    T[22] = __ffma2_rn(r4, wx, T[22]); T[23] = __ffma2_rn(r4, wy, T[23]); T[24] = __ffma2_rn(r4, wz, T[24]);
+    T[25] = __ffma2_rn(r4, r2, T[25]);
+  }
+}
+
+// Exact float -> double times 2^e_add (|e_add| < 700) on the integer pipe:
+// zeros and FP32 subnormals give 0, inf and NaN stay inf and NaN.
+__device__ __forceinline__ double f2d_scaled(float f, int e_add) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t a = u & 0x7fffffffu;
+  uint32_t hi = (a >> 3) + ((uint32_t)(896 + e_add) << 20);
+  uint32_t lo = u << 29;
+  if (a < 0x00800000u) hi = lo = 0u;
+  if (a >= 0x7f800000u) {
+    hi = 0x7ff00000u | (a > 0x7f800000u ? 0x80000u : 0u);
+    lo = 0u;
+  }
+  return __hiloint2double((int)(hi | (u & 0x80000000u)), (int)lo);
+}
+
 template <bool kShared, bool kLite>
 __device__ __forceinline__ void reduce_cells(bool valid, int n, const float *px, const float *py, const float *pz,
                                              int64_t c, double *__restrict__ mom, double *__restrict__ m6,
-                                             int lane) {
+                                             float *scratch, const float *zeros, int lane) {
   constexpr int G = kTileG;
   constexpr int NS = kLite ? kLiteSum : kNSum;
-  constexpr int K = 32 / G;
-  constexpr int BLK = 32;  // particles per lane summed plainly before a two-sum fold
+  constexpr int K = 32 / G;             // sums a lane owns after the reduction (one float4 chunk)
+  constexpr int NCH = (NS + K - 1) / K;  // chunks in use
+  constexpr int BLK = 16;               // pair steps per lane summed plainly before a two-sum fold
+  static_assert(K == 4, "one float4 chunk per lane");
   const int lg = lane & (G - 1);
+  const int gbase = lane & ~(G - 1);
   auto ld = [](const float *p, int i) -> float {
     if (kShared) return p[i];
     return __ldg(p + i);
   };
   if (!valid) n = 0;
-  float v0x = 0.f, v0y = 0.f, v0z = 0.f;
-  if (n > 0) {
-    v0x = ld(px, 0);
-    v0y = ld(py, 0);
-    v0z = ld(pz, 0);
-  }
+  // an empty staged cell reads zeros (its offsets from v0 are then exactly 0);
+  // the groups of a huge cell read that cell's data, in range
+  if (kShared && n == 0) px = py = pz = zeros;
+  const float v0x = ld(px, 0), v0y = ld(py, 0), v0z = ld(pz, 0);
   const int itmax = __reduce_max_sync(0xffffffffu, (n + G - 1) / G);
-  // pass A: offsets from the first particle (out-of-range slots read particle
-  // 0 and are zeroed, which keeps the loop free of branches)
-  float sx = 0.f, sy = 0.f, sz = 0.f, sq = 0.f;
-  for (int it = 0; it < itmax; ++it) {
-    const int i = it * G + lg;
-    const bool in = i < n;
-    const int ii = in ? i : 0;
-    float dx = ld(px, ii) - v0x, dy = ld(py, ii) - v0y, dz = ld(pz, ii) - v0z;
-    dx = in ? dx : 0.f;
-    dy = in ? dy : 0.f;
-    dz = in ? dz : 0.f;
-    sx += dx;
-    sy += dy;
-    sz += dz;
-    sq = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, sq)));
+  const int npair = (itmax + 1) >> 1;
+  // pair steps below pfull have both particles in range for every group
+  const int pfull = (int)__reduce_min_sync(0xffffffffu, (unsigned)(n / G)) >> 1;
+  const float2 nv0x = f2(-v0x), nv0y = f2(-v0y), nv0z = f2(-v0z);
+  // pass A on pairs of steps (it, it + 1): out-of-range particles read particle
+  // 0, whose offset from v0 is exactly zero
+  float2 SDx = f2(0.f), SDy = f2(0.f), SDz = f2(0.f), SQx = f2(0.f), SQy = f2(0.f), SQz = f2(0.f);
+#pragma unroll 2
+  for (int pp = 0; pp < pfull; ++pp) {
+    const int j0 = 2 * pp * G + lg, j1 = j0 + G;
+    const float2 dx = __fadd2_rn(make_float2(ld(px, j0), ld(px, j1)), nv0x);
+    const float2 dy = __fadd2_rn(make_float2(ld(py, j0), ld(py, j1)), nv0y);
+    const float2 dz = __fadd2_rn(make_float2(ld(pz, j0), ld(pz, j1)), nv0z);
+    SDx = __fadd2_rn(SDx, dx);
+    SDy = __fadd2_rn(SDy, dy);
+    SDz = __fadd2_rn(SDz, dz);
+    SQx = __ffma2_rn(dx, dx, SQx);
+    SQy = __ffma2_rn(dy, dy, SQy);
+    SQz = __ffma2_rn(dz, dz, SQz);
   }
+  for (int pp = pfull; pp < npair; ++pp) {
+    const int i0 = 2 * pp * G + lg, i1 = i0 + G;
+    const int j0 = i0 < n ? i0 : 0, j1 = i1 < n ? i1 : 0;
+    const float2 dx = __fadd2_rn(make_float2(ld(px, j0), ld(px, j1)), nv0x);
+    const float2 dy = __fadd2_rn(make_float2(ld(py, j0), ld(py, j1)), nv0y);
+    const float2 dz = __fadd2_rn(make_float2(ld(pz, j0), ld(pz, j1)), nv0z);
+    SDx = __fadd2_rn(SDx, dx);
+    SDy = __fadd2_rn(SDy, dy);
+    SDz = __fadd2_rn(SDz, dz);
+    SQx = __ffma2_rn(dx, dx, SQx);
+    SQy = __ffma2_rn(dy, dy, SQy);
+    SQz = __ffma2_rn(dz, dz, SQz);
+  }
+  float sx = SDx.x + SDx.y, sy = SDy.x + SDy.y, sz = SDz.x + SDz.y;
+  float sq = (SQx.x + SQx.y) + (SQy.x + SQy.y) + (SQz.x + SQz.y);
   sx = group_allreduce<G>(sx);
   sy = group_allreduce<G>(sy);
   sz = group_allreduce<G>(sz);
@@ -115,60 +187,80 @@ __device__ __forceinline__ void reduce_cells(bool valid, int n, const float *px,
     ks = max(-20, min(20, -(ex / 2)));
   }
   const float s = ldexpf(1.f, ks);
+  const float2 nmx = f2(-mx), nmy = f2(-my), nmz = f2(-mz);
+  // full steps: ((v - v0) - m) s as one fused multiply-add, exact because s
+  // is a power of two (d s and m s are exact, one rounding as before)
+  const float2 S2f = f2(s), nmsx = f2(-mx * s), nmsy = f2(-my * s), nmsz = f2(-mz * s);
 
-  // pass B: centred, scaled sums; FP32 blocks of BLK particles per lane folded by two-sum
-  float hi[32], lo[32];
+  // pass B: centred, scaled sums w = ((v - v0) - m) s, pairs of steps packed
+  // FP32x2, blocks of BLK pair steps; each block is reduced over the group's
+  // lanes through a swizzled shared-memory transpose, and the owner of a sum
+  // folds the blocks with two-sum
+  float hi[K], lo[K];
 #pragma unroll
-  for (int q = 0; q < 32; ++q) {
-    hi[q] = 0.f;
-    lo[q] = 0.f;
+  for (int j = 0; j < K; ++j) {
+    hi[j] = 0.f;
+    lo[j] = 0.f;
   }
-  for (int it0 = 0; it0 < itmax; it0 += BLK) {
-    float t[NS];
+  float4 *sc4 = reinterpret_cast<float4 *>(scratch);
+  for (int b0 = 0; b0 < npair; b0 += BLK) {  // warp-uniform
+    float2 T[NS];
 #pragma unroll
-    for (int q = 0; q < NS; ++q) t[q] = 0.f;
-    const int itend = min(it0 + BLK, itmax);
-    for (int it = it0; it < itend; ++it) {
-      const int i = it * G + lg;
-      const bool in = i < n;
-      const int ii = in ? i : 0;
-      const float sm = in ? s : 0.f;
-      const float wx = ((ld(px, ii) - v0x) - mx) * sm;
-      const float wy = ((ld(py, ii) - v0y) - my) * sm;
-      const float wz = ((ld(pz, ii) - v0z) - mz) * sm;
-      const float xx = wx * wx, xy = wx * wy, xz = wx * wz, yy = wy * wy, yz = wy * wz, zz = wz * wz;
-      t[0] += xx; t[1] += xy; t[2] += xz; t[3] += yy; t[4] += yz; t[5] += zz;
-      if constexpr (kLite) {
-        const float r2 = xx + yy + zz;
-        t[6] = fmaf(r2, wx, t[6]); t[7] = fmaf(r2, wy, t[7]); t[8] = fmaf(r2, wz, t[8]);
-      } else {
-        t[6] = fmaf(xx, wx, t[6]);  t[7] = fmaf(xx, wy, t[7]);   t[8] = fmaf(xx, wz, t[8]);
-        t[9] = fmaf(xy, wy, t[9]);  t[10] = fmaf(xy, wz, t[10]); t[11] = fmaf(xz, wz, t[11]);
-        t[12] = fmaf(yy, wy, t[12]); t[13] = fmaf(yy, wz, t[13]); t[14] = fmaf(yz, wz, t[14]);
-        t[15] = fmaf(zz, wz, t[15]);
-        const float r2 = xx + yy + zz;
-        t[16] = fmaf(r2, xx, t[16]); t[17] = fmaf(r2, xy, t[17]); t[18] = fmaf(r2, xz, t[18]);
-        t[19] = fmaf(r2, yy, t[19]); t[20] = fmaf(r2, yz, t[20]); t[21] = fmaf(r2, zz, t[21]);
-        const float r4 = r2 * r2;
-        t[22] = fmaf(r4, wx, t[22]); t[23] = fmaf(r4, wy, t[23]); t[24] = fmaf(r4, wz, t[24]);
-        t[25] = fmaf(r4, r2, t[25]);
+    for (int q = 0; q < NS; ++q) T[q] = f2(0.f);
+    const int b1 = min(b0 + BLK, npair);
+    const int bf = min(b1, max(b0, pfull));
+#pragma unroll 2
+    for (int pp = b0; pp < bf; ++pp) {
+      const int j0 = 2 * pp * G + lg, j1 = j0 + G;
+      const float2 wx = __ffma2_rn(__fadd2_rn(make_float2(ld(px, j0), ld(px, j1)), nv0x), S2f, nmsx);
+      const float2 wy = __ffma2_rn(__fadd2_rn(make_float2(ld(py, j0), ld(py, j1)), nv0y), S2f, nmsy);
+      const float2 wz = __ffma2_rn(__fadd2_rn(make_float2(ld(pz, j0), ld(pz, j1)), nv0z), S2f, nmsz);
+      accumulate2<kLite, NS>(T, wx, wy, wz);
+    }
+    for (int pp = bf; pp < b1; ++pp) {
+      const int i0 = 2 * pp * G + lg, i1 = i0 + G;
+      const bool in0 = i0 < n, in1 = i1 < n;
+      const int j0 = in0 ? i0 : 0, j1 = in1 ? i1 : 0;
+      const float2 S2 = make_float2(in0 ? s : 0.f, in1 ? s : 0.f);
+      const float2 wx = __fmul2_rn(__fadd2_rn(__fadd2_rn(make_float2(ld(px, j0), ld(px, j1)), nv0x), nmx), S2);
+      const float2 wy = __fmul2_rn(__fadd2_rn(__fadd2_rn(make_float2(ld(py, j0), ld(py, j1)), nv0y), nmy), S2);
+      const float2 wz = __fmul2_rn(__fadd2_rn(__fadd2_rn(make_float2(ld(pz, j0), ld(pz, j1)), nv0z), nmz), S2);
+      accumulate2<kLite, NS>(T, wx, wy, wz);
+    }
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) {
+      float t4[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) t4[k] = 4 * ch + k < NS ? T[4 * ch + k].x + T[4 * ch + k].y : 0.f;
+      sc4[lane * 8 + swz(ch, lane)] = make_float4(t4[0], t4[1], t4[2], t4[3]);
+    }
+    __syncwarp();
+    float bs[K] = {0.f, 0.f, 0.f, 0.f};
+    if (lg < NCH) {
+#pragma unroll
+      for (int i = 0; i < G; ++i) {
+        const int rr = gbase + i;
+        const float4 t = sc4[rr * 8 + swz(lg, rr)];
+        bs[0] += t.x;
+        bs[1] += t.y;
+        bs[2] += t.z;
+        bs[3] += t.w;
       }
     }
-    if (it0 == 0) {
+    __syncwarp();
+    if (b0 == 0) {
 #pragma unroll
-      for (int q = 0; q < NS; ++q) hi[q] = t[q];
+      for (int j = 0; j < K; ++j) hi[j] = bs[j];
     } else {
 #pragma unroll
-      for (int q = 0; q < NS; ++q) {
+      for (int j = 0; j < K; ++j) {
         float sum, err;
-        two_sum(hi[q], t[q], sum, err);
-        hi[q] = sum;
-        lo[q] += err;
+        two_sum(hi[j], bs[j], sum, err);
+        hi[j] = sum;
+        lo[j] += err;
       }
     }
   }
-  group_reduce_scatter<G>(hi, lane);
-  if (itmax > BLK) group_reduce_scatter<G>(lo, lane);  // warp-uniform branch
 
   // promote: mean = (hi + lo) / n as a double-float, the 2^(ks * order)
   // scaling undone in the exponent (exact), one FP64 add
@@ -179,11 +271,8 @@ __device__ __forceinline__ void reduce_cells(bool valid, int n, const float *px,
     const int ord = q < NS ? tile_order<kLite>(q) : 0;
     float p, e;
     df_scale(hi[j], lo[j], rh, rl, p, e);
-    // exact widening on the integer pipe with the power-of-two scale folded
-    // into the exponent, then one FP64 add; slots past the set skip it
-    val[j] = q < NS ? f2d_exact(p, -ks * ord) + f2d_exact(e, -ks * ord) : 0.0;
+    val[j] = q < NS ? f2d_scaled(p, -ks * ord) + f2d_scaled(e, -ks * ord) : 0.0;
   }
-  const int gbase = lane & ~(G - 1);
   const double u11 = __shfl_sync(0xffffffffu, val[0 % K], gbase + 0 / K);
   const double u22 = __shfl_sync(0xffffffffu, val[3 % K], gbase + 3 / K);
   const double u33 = __shfl_sync(0xffffffffu, val[5 % K], gbase + 5 / K);
@@ -200,7 +289,7 @@ __device__ __forceinline__ void reduce_cells(bool valid, int n, const float *px,
     }
   }
   if (lg >= 1 && lg <= 3) {
-    const float v0 = lg == 1 ? v0x : (lg == 2 ? v0y : v0z);
+    const float v0 = n > 0 ? (lg == 1 ? v0x : (lg == 2 ? v0y : v0z)) : 0.f;
     const float m = lg == 1 ? mx : (lg == 2 ? my : mz);
     mo[kU + lg - 1] = f2d_exact(v0) + f2d_exact(m);
   }
@@ -257,6 +346,8 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     gather_tile_kernel(const float *__restrict__ v, int64_t np, const int64_t *__restrict__ off, int64_t n_cells,
                        double *__restrict__ mom, double *__restrict__ m6, int64_t n_chunks) {
   extern __shared__ __align__(128) float slot_buf[];
+  float *scratch_all = slot_buf + kSlots * kSlotFloats;
+  __shared__ __align__(16) float zeros[4];
   __shared__ __align__(8) uint64_t full_bar[kSlots], empty_bar[kSlots];
   __shared__ SlotMeta meta[kSlots];
   __shared__ int task_ctr[kSlots];
@@ -271,6 +362,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
       task_ctr[s] = 0;
     }
     failed = 0;
+    zeros[0] = zeros[1] = zeros[2] = zeros[3] = 0.f;
     fence_barrier_init();
   }
   __syncthreads();
@@ -420,6 +512,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     // ---------------- consumers ----------------
     bool ok = true;
     const int g = lane / kTileG;
+    float *scratch = scratch_all + (warp - 1) * kScratchFloats;
     for (int64_t sub = 0;; ++sub) {
       const int s = (int)(sub % kSlots);
       if (!mbar_wait_bounded(&full_bar[s], (uint32_t)((sub / kSlots) & 1))) {
@@ -443,11 +536,11 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         const int64_t a = M.offs[rc];
         const int n = valid ? (int)(M.offs[rc + 1] - a) : 0;
         if (M.big) {
-          reduce_cells<false, kLite>(valid, n, v + a, v + np + a, v + 2 * np + a, c, mom, m6, lane);
+          reduce_cells<false, kLite>(valid, n, v + a, v + np + a, v + 2 * np + a, c, mom, m6, scratch, zeros, lane);
         } else {
           const int64_t rel = a - M.pa;
           reduce_cells<true, kLite>(valid, n, bx + M.lead[0] + rel, bx + kCapF + M.lead[1] + rel,
-                             bx + 2 * kCapF + M.lead[2] + rel, c, mom, m6, lane);
+                             bx + 2 * kCapF + M.lead[2] + rel, c, mom, m6, scratch, zeros, lane);
         }
       }
       __syncwarp();

@@ -387,7 +387,7 @@ void launch_surrogate_tail(const float *tpred, const double *mom, const double *
   compact_kernel<<<(unsigned)blocks, 256, 0, st>>>(flags, n, list, count);
   double rtol = p.pivot_rtol;
   if (prec == FP_PREC_FP32_MOMENTS && rtol < FP_FP32_PIVOT_FLOOR) rtol = FP_FP32_PIVOT_FLOOR;
-  SolveParams prm{p.eps2_hat, rtol, p.min_particles};
+  SolveParams prm{p.eps2_hat, rtol, p.min_particles, prec == FP_PREC_FP32_MOMENTS ? FP_FP32_MIN_REGULAR : 0};
   fallback_kernel<<<(unsigned)(mlp_sm_count() * 4), 128, 0, st>>>(list, count, mom, tau, prm, coeffs, flags);
 }
 

@@ -161,6 +161,9 @@ def test_edge_cases(prec):
     near = _near_threshold(mp, prec)
     np.testing.assert_array_equal(gf[~near], fl[~near])
     assert fl[0] & api.FLAG_FEW and fl[25] & api.FLAG_SINGULAR and fl[26] & api.FLAG_NONFINITE
+    # a four-particle cell is singular whatever its velocities (oracle pin);
+    # both modes flag it, the FP32-moment mode without a solve
+    assert fl[4] & api.FLAG_SINGULAR and gf[4] & api.FLAG_SINGULAR
     ok = (fl == 0) & (gf == 0) & (cond <= 1e8)
     err = np.linalg.norm(gy - y, axis=1) / np.linalg.norm(y, axis=1)
     assert err[ok].max() <= TOL[prec]

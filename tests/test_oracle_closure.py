@@ -252,3 +252,24 @@ def test_degenerate_cells_fall_back_to_linear_drift():
     lin = np.array([-2.0, 0, 0, -2.0, 0, -2.0, 0, 0, 0])
     for c in range(5):
         np.testing.assert_array_equal(Y[c], lin)
+
+
+def test_four_particle_cells_are_singular():
+    """Brute force over random cells: with four particles the 9x9 system is
+    singular whatever the velocities (the smallest pivot ratio is at the
+    rounding level), with five it is generically regular.  The FP32-moment
+    GPU mode relies on this to flag four-particle cells without a solve."""
+    rng = np.random.default_rng(11)
+    for n, want_singular in ((4, True), (5, False)):
+        ratios = []
+        for _ in range(200):
+            v = rng.standard_normal((3, n)) * rng.uniform(0.3, 3) + rng.uniform(-5, 5, (3, 1))
+            m = O.moments(v, np.array([0, n]))
+            for e2 in (0.0, 1e-3, 1e-1):
+                _, fl, _, mp = O.closure(m, np.array([rng.uniform(0.5, 2.0)]), eps2_hat=e2, want_cond=True)
+                ratios.append(mp[0])
+        ratios = np.array(ratios)
+        if want_singular:
+            assert ratios.max() < 1e-12
+        else:
+            assert np.median(ratios) > 1e-3 and (ratios < 1e-12).mean() < 0.01
