@@ -395,11 +395,9 @@ def run_ours(args):
     lin[:, [0, 3, 5]] = -1.0
     rel_lin = ((lin - t_ex).norm(dim=1) / t_ex.norm(dim=1))[ok].float().cpu()
     # energy residual of the surrogate drift (exact closure: 0)
-    f = S.raw_features_t(imom)
+    ax = S.aux_moments(imom, itau)  # u^_ij, b^_i, s4^
     mult = torch.tensor([1, 2, 2, 1, 2, 1], dtype=torch.float64, device=dev)
-    b_hat = torch.stack([f[:, 6] + f[:, 9] + f[:, 11], f[:, 7] + f[:, 12] + f[:, 14], f[:, 8] + f[:, 13] + f[:, 15]], 1)
-    s4 = f[:, 16] + f[:, 19] + f[:, 21]
-    e = 1 + ((t_s[:, :6] * f[:, :6] * mult).sum(1) + (t_s[:, 6:] * b_hat).sum(1) - prm.eps2_hat * s4) / 3
+    e = 1 + ((t_s[:, :6] * ax[:, :6] * mult).sum(1) + (t_s[:, 6:] * ax[:, 6:9]).sum(1) - prm.eps2_hat * ax[:, 9]) / 3
     reps = 8
     big_mom = imom.repeat(reps, 1).contiguous()
     big_tau = itau.repeat(reps).contiguous()
@@ -527,7 +525,7 @@ def run_ours(args):
     trs = S.Surrogate.load(WEIGHTS, device=dev)
     tr = S.Trainer(trs, batch=8192)
     ts = S.TrainingSet(P.training_cells(16384, seed=55), eps2_hat=prm.eps2_hat)
-    xt = S.standardized_inputs(trs, ts.f[:8192]).contiguous()
+    xt = ts.inputs(trs)[:8192].contiguous()
     tt, at = ts.t[:8192].contiguous(), ts.aux[:8192].contiguous()
     t_train = float(np.median(timed(lambda: tr.step(xt, tt, at, 1.0 / 8192), 10, 3)))
 

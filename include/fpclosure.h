@@ -281,6 +281,27 @@ typedef struct {
 int64_t fp_mlp_param_count(void);
 int64_t fp_mlp_param_offset(int which, int layer);
 
+/* fp_surrogate_training_rows: what training of the learned closure reads for
+ * every cell (Sec. 4, Phases 1-2: the network is fit to coefficients of the
+ * exact closure), computed by the arithmetic of the inference kernels so that
+ * training and inference see the same inputs:
+ *   raw_out     [n_cells][32] FP32 unstandardised network inputs, zero padded:
+ *               lite_inputs = 0: the 25 normalised moments of `moments`, as
+ *               fp_surrogate_features forms them before standardising;
+ *               lite_inputs = 1: the 16 LITE inputs of `lite` and tau, as
+ *               fp_surrogate_lite_features forms them
+ *   target_out  [n_cells][16] FP32 dimensionless targets (tau C, tau sqrt(theta) G)
+ *               of the coefficients `coeffs` [n_cells][9], zero padded
+ *   aux_out     [n_cells][16] FP32 the loss's auxiliary moments (u^_ij (6),
+ *               b^_i = u^_ikk (3), s4^ = w^_kk, zeros) of `moments`
+ * moments [n_cells][FP_NMOM] is read unless only raw_out of LITE inputs is
+ * wanted; lite [n_cells][FP_NLITE] only for lite_inputs = 1; coeffs only for
+ * target_out.  Any output may be NULL; outputs 16-byte aligned.  Device
+ * pointers owned by the caller; no workspace; FP_ERR_ARG on a bad argument. */
+int fp_surrogate_training_rows(const double *moments, const double *lite, const double *coeffs, const double *tau,
+                               int64_t n_cells, int lite_inputs, float *raw_out, float *target_out, float *aux_out,
+                               fp_stream_t stream);
+
 /* Workspace of fp_closure_surrogate for n_cells cells. */
 size_t fp_surrogate_workspace_bytes(int64_t n_cells);
 

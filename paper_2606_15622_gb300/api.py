@@ -100,6 +100,7 @@ SIGNATURES = {
     "fp_mlp_param_offset": (_i64, [_i32, _i32]),
     "fp_surrogate_workspace_bytes": (_sz, [_i64]),
     "fp_surrogate_features": (_i32, [ctypes.POINTER(FpMlp), _vp, _i64, _vp, ctypes.POINTER(Params), _vp, _vp, _vp]),
+    "fp_surrogate_training_rows": (_i32, [_vp, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp]),
     "fp_mlp_forward": (_i32, [ctypes.POINTER(FpMlp), _vp, _i64, _i32, _vp, _vp, _vp, _vp]),
     "fp_closure_surrogate": (_i32, [ctypes.POINTER(FpMlp), _vp, _i64, _vp, ctypes.POINTER(Params), _i32, _vp, _vp,
                                     _vp, _sz, _vp]),
@@ -463,6 +464,28 @@ def fp_moments_lite(v, offsets, out=None, stream=None):
     rc = lib().fp_moments_lite(_ptr(v), _vdtype(v), n_p, _ptr(offsets), n_cells, _ptr(out), _stream(stream))
     _check(rc, "fp_moments_lite")
     return out
+
+
+def fp_surrogate_training_rows(moments, tau, coeffs=None, lite=None, lite_inputs=False, raw=True, targets=True,
+                               aux=True, stream=None):
+    """(raw [n, 32], targets [n, 16], aux [n, 16]) FP32 rows for training the
+    learned closure, from the library's kernels (None for outputs not asked
+    for): the unstandardised inputs as the inference kernels form them (full
+    set from `moments`, or LITE set from `lite` and tau), the dimensionless
+    targets of `coeffs`, the loss's auxiliary moments of `moments`."""
+    n = tau.numel()
+    dev = tau.device
+    r = torch.empty((n, 32), dtype=torch.float32, device=dev) if raw else None
+    t = torch.empty((n, 16), dtype=torch.float32, device=dev) if targets else None
+    x = torch.empty((n, 16), dtype=torch.float32, device=dev) if aux else None
+    _need_cuda(moments, tau, coeffs, lite, r, t, x)
+    _want_cells(n, None, tau, moments, coeffs)
+    if lite is not None:
+        _want_cells(n, None, None, lite, None, None, stride=NLITE)
+    rc = lib().fp_surrogate_training_rows(_ptr(moments), _ptr(lite), _ptr(coeffs), _ptr(tau), n,
+                                          1 if lite_inputs else 0, _ptr(r), _ptr(t), _ptr(x), _stream(stream))
+    _check(rc, "fp_surrogate_training_rows")
+    return r, t, x
 
 
 def fp_sort_by_cell(cell_of, n_cells, v=None, v_sorted=None, perm_out=None, offsets_out=None, workspace=None,

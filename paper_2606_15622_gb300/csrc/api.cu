@@ -19,6 +19,8 @@ void launch_velocity(const void *v, void *v_out, int v_dtype, int64_t np, const 
 void launch_adjoint(const void *v, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, const double *tau,
                     double eps2_hat, const double *mom, const double *coeffs, const int32_t *flags, const double *lu,
                     const double *gY, const double *gm_in, double *gm_out, void *gv, cudaStream_t st);
+void launch_training_rows(const double *mom, const double *lite, const double *coeffs, const double *tau, int64_t n,
+                          int lite_inputs, float *raw, float *targ, float *aux, cudaStream_t st);
 void launch_features(const fp_mlp &net, const double *mom, const double *tau, int64_t n, int min_particles,
                      double margin, void *x, int32_t *flags, cudaStream_t st);
 int launch_mlp_forward(const fp_mlp &net, const void *x, int64_t n, int standardized_out, float *out, void *h_save,
@@ -314,6 +316,25 @@ int fp_surrogate_features(const fp_mlp *net, const double *moments, int64_t n_ce
   fpc::launch_features(*net, moments, tau, n_cells, prm.min_particles, prm.surr_range_margin, x_out, flags_out,
                        (cudaStream_t)stream);
   return check_launch("features");
+}
+
+int fp_surrogate_training_rows(const double *moments, const double *lite, const double *coeffs, const double *tau,
+                               int64_t n_cells, int lite_inputs, float *raw_out, float *target_out, float *aux_out,
+                               fp_stream_t stream) {
+  g_err[0] = 0;
+  if (n_cells < 0) return fail(FP_ERR_ARG, "negative size");
+  if (lite_inputs != 0 && lite_inputs != 1) return fail(FP_ERR_ARG, "lite_inputs %d", lite_inputs);
+  if (n_cells == 0) return FP_OK;
+  const bool need_mom = target_out || aux_out || (raw_out && !lite_inputs);
+  if (!tau) return fail(FP_ERR_ARG, "null tau");
+  if (need_mom && !moments) return fail(FP_ERR_ARG, "null moments");
+  if (raw_out && lite_inputs && !lite) return fail(FP_ERR_ARG, "null lite vectors");
+  if (target_out && !coeffs) return fail(FP_ERR_ARG, "null coefficients");
+  if (((uintptr_t)raw_out | (uintptr_t)target_out | (uintptr_t)aux_out) % 16)
+    return fail(FP_ERR_ARG, "outputs not 16-byte aligned");
+  fpc::launch_training_rows(need_mom ? moments : nullptr, lite, coeffs, tau, n_cells, lite_inputs, raw_out, target_out,
+                            aux_out, (cudaStream_t)stream);
+  return check_launch("training rows");
 }
 
 int fp_mlp_forward(const fp_mlp *net, const void *x, int64_t n, int standardized_out, float *out, void *h_save,

@@ -92,6 +92,69 @@ __global__ void __launch_bounds__(256) features_kernel(MlpDev net, const double 
   flags[c] = fl;
 }
 
+// What training reads for each cell, by the arithmetic of the inference
+// kernels: the unstandardised inputs (the full set from moment vectors, the
+// LITE set from LITE vectors and tau), the dimensionless targets
+// (tau C, tau sqrt(theta) G) of the exact coefficients, and the loss's
+// auxiliary normalised moments (u^_ij, b^_i = u^_ikk, s4^ = w^_kk) of the full
+// features.  Rows are zero padded to 32 / 16 / 16 floats.
+__global__ void __launch_bounds__(256) training_rows_kernel(const double *__restrict__ mom,
+                                                            const double *__restrict__ lite,
+                                                            const double *__restrict__ coeffs,
+                                                            const double *__restrict__ tau, int64_t n, int lite_inputs,
+                                                            float *__restrict__ raw, float *__restrict__ targ,
+                                                            float *__restrict__ aux) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  float f[kNFeat];
+  if (mom) cell_features(mom + c * FP_NMOM, f);
+  if (raw) {
+    float r[kIn];
+#pragma unroll
+    for (int q = 0; q < kIn; ++q) r[q] = 0.f;
+    if (lite_inputs) {
+      float g[16];
+      lite_raw_features(lite + c * FP_NLITE, tau[c], g);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) r[q] = g[q];
+    } else {
+#pragma unroll
+      for (int q = 0; q < kNFeat; ++q) r[q] = f[q];
+    }
+    float4 *dst = reinterpret_cast<float4 *>(raw + c * kIn);
+#pragma unroll
+    for (int q = 0; q < kIn / 4; ++q) dst[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+  }
+  if (targ) {
+    const double tc = tau[c];
+    const double gs = tc * sqrt(mom[c * FP_NMOM + kTheta]);
+    float t[kOut];
+#pragma unroll
+    for (int a = 0; a < kOut; ++a) t[a] = 0.f;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) t[a] = d2f_rn(coeffs[c * 9 + a] * tc);
+#pragma unroll
+    for (int a = 6; a < 9; ++a) t[a] = d2f_rn(coeffs[c * 9 + a] * gs);
+    float4 *dst = reinterpret_cast<float4 *>(targ + c * kOut);
+#pragma unroll
+    for (int q = 0; q < kOut / 4; ++q) dst[q] = make_float4(t[4 * q], t[4 * q + 1], t[4 * q + 2], t[4 * q + 3]);
+  }
+  if (aux) {
+    float x[kOut];
+#pragma unroll
+    for (int a = 0; a < kOut; ++a) x[a] = 0.f;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) x[a] = f[a];
+    x[6] = f[6 + 0] + f[6 + 3] + f[6 + 5];
+    x[7] = f[6 + 1] + f[6 + 6] + f[6 + 8];
+    x[8] = f[6 + 2] + f[6 + 7] + f[6 + 9];
+    x[9] = f[16] + f[19] + f[21];
+    float4 *dst = reinterpret_cast<float4 *>(aux + c * kOut);
+#pragma unroll
+    for (int q = 0; q < kOut / 4; ++q) dst[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // fused forward
 // ---------------------------------------------------------------------------
@@ -335,6 +398,12 @@ void launch_features(const fp_mlp &net, const double *mom, const double *tau, in
   const int64_t blocks = (n + 255) / 256;
   features_kernel<<<(unsigned)blocks, 256, 0, st>>>(make_mlp_dev(net), mom, tau, n, min_particles, (float)margin,
                                                      reinterpret_cast<__nv_bfloat16 *>(x), flags);
+}
+
+void launch_training_rows(const double *mom, const double *lite, const double *coeffs, const double *tau, int64_t n,
+                          int lite_inputs, float *raw, float *targ, float *aux, cudaStream_t st) {
+  const int64_t blocks = (n + 255) / 256;
+  training_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(mom, lite, coeffs, tau, n, lite_inputs, raw, targ, aux);
 }
 
 int launch_mlp_forward_tc_dropout(const MlpDev &net, const __nv_bfloat16 *x, int64_t n, int standardized_out,

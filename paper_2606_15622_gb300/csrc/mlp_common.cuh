@@ -48,4 +48,28 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// The 16 raw inputs of one cell from its LITE vector and tau, in FP32 (the
+// entries narrowed on the integer pipe: d2f_rn).
+__device__ __forceinline__ void lite_raw_features(const double *__restrict__ m, double tau, float (&f)[16]) {
+  const float th = d2f_rn(m[4]);
+  const float u00 = d2f_rn(m[5]), u01 = d2f_rn(m[6]), u02 = d2f_rn(m[7]), u11 = d2f_rn(m[8]), u12 = d2f_rn(m[9]),
+              u22 = d2f_rn(m[10]);
+  f[0] = d2f_rn(m[0]);
+  f[1] = th;
+  f[2] = d2f_rn(m[1]);
+  f[3] = d2f_rn(m[2]);
+  f[4] = d2f_rn(m[3]);
+  f[5] = u00 - th;
+  f[6] = u01;
+  f[7] = u02;
+  f[8] = u11 - th;
+  f[9] = u12;
+  f[10] = u22 - th;
+  f[11] = 0.5f * d2f_rn(m[11]);
+  f[12] = 0.5f * d2f_rn(m[12]);
+  f[13] = 0.5f * d2f_rn(m[13]);
+  f[14] = fmaf(u00, fmaf(u11, u22, -u12 * u12), fmaf(-u01, fmaf(u01, u22, -u12 * u02), u02 * fmaf(u01, u12, -u11 * u02)));
+  f[15] = 1.f / d2f_rn(tau);
+}
+
 }  // namespace fpc

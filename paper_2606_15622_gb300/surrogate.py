@@ -283,54 +283,36 @@ class Surrogate:
 # ---------------------------------------------------------------------------
 # training data and training
 # ---------------------------------------------------------------------------
-def raw_features_t(mom):
-    """[n, 25] normalised moments (u/theta, u3/theta^1.5, w/theta^2, z/theta^2.5)."""
-    th = mom[:, 4:5]
-    return torch.cat([mom[:, 5:11] / th, mom[:, 11:21] / th ** 1.5, mom[:, 21:27] / th ** 2,
-                      mom[:, 27:30] / th ** 2.5], dim=1)
-
-
 def dimensionless(coeffs, mom, tau):
-    th = mom[:, 4]
-    return torch.cat([coeffs[:, :6] * tau[:, None], coeffs[:, 6:] * (tau * th.sqrt())[:, None]], dim=1)
+    """Dimensionless coefficients (tau C, tau sqrt(theta) G) [n, 9] of `coeffs`,
+    from the library's kernel (FP32 values, returned as float64)."""
+    _, t, _ = api.fp_surrogate_training_rows(mom, tau, coeffs=coeffs, raw=False, aux=False)
+    return t[:, :NOUT].double()
 
 
-def lite_raw_features_t(lite, tau):
-    """[n, 16] LITE network inputs rho = N, T = theta, U, Pi = u - theta I,
-    q = b / 2, DM2 = det u, nu = 1 / tau (FP64)."""
-    th = lite[:, 4:5]
-    u = lite[:, 5:11]
-    pi = u.clone()
-    pi[:, [0, 3, 5]] -= th
-    U3 = torch.stack([torch.stack([u[:, 0], u[:, 1], u[:, 2]], 1), torch.stack([u[:, 1], u[:, 3], u[:, 4]], 1),
-                      torch.stack([u[:, 2], u[:, 4], u[:, 5]], 1)], 1)
-    det = torch.linalg.det(U3)[:, None]
-    return torch.cat([lite[:, 0:1], th, lite[:, 1:4], pi, 0.5 * lite[:, 11:14], det, (1.0 / tau)[:, None]], dim=1)
-
-
-def aux_from_features(f):
-    """(u_hat (6), b_hat (3), s4_hat, 0 x 6) per row, FP32 [n, 16]."""
-    b = torch.stack([f[:, 6] + f[:, 9] + f[:, 11], f[:, 7] + f[:, 12] + f[:, 14], f[:, 8] + f[:, 13] + f[:, 15]],
-                    dim=1)
-    s4 = (f[:, 16] + f[:, 19] + f[:, 21])[:, None]
-    out = torch.zeros((f.shape[0], 16), dtype=torch.float32, device=f.device)
-    out[:, :6] = f[:, :6]
-    out[:, 6:9] = b
-    out[:, 9:10] = s4
-    return out
+def aux_moments(mom, tau):
+    """(u^_ij (6), b^_i (3), s4^) [n, 10] normalised moments of the full
+    moment vectors, from the library's kernel (FP32, returned as float64)."""
+    _, _, x = api.fp_surrogate_training_rows(mom, tau, raw=False, targets=False)
+    return x[:, :10].double()
 
 
 class TrainingSet:
-    """Cells labelled by the exact FP64 GPU closure: raw inputs of the
-    chosen set, targets, aux moments (always from the full moment vector:
-    the energy term of the loss needs s4); cells the exact closure flags,
-    and coefficients beyond 1e6 in magnitude (dimensionless), are dropped.
-    LITE inputs come from fp_moments_lite, the kernel that serves them."""
+    """Cells labelled by the exact FP64 GPU closure.  Everything the training
+    reads comes from the library's kernels (fp_surrogate_training_rows): the
+    unstandardised inputs of the chosen set (statistics for the scalers),
+    the dimensionless targets, and the aux moments (always from the full
+    moment vector: the energy term of the loss needs s4).  The network's
+    inputs themselves are made by the inference kernels (fp_surrogate_features
+    / fp_surrogate_lite_features) once the scalers are set (`inputs`), so
+    training and inference see the same BF16 inputs.  Cells the exact closure
+    flags, and coefficients beyond 1e6 in magnitude (dimensionless), are
+    dropped."""
 
     def __init__(self, pop, eps2_hat=1e-3, device="cuda", chunk=262144, features="full"):
         dev = torch.device(device)
         prm = api.default_params(eps2_hat=eps2_hat)
-        feats, targs, auxs = [], [], []
+        raws, targs, auxs, srcs, taus = [], [], [], [], []
         n_cells = pop.n_cells
         for c0 in range(0, n_cells, chunk):
             c1 = min(n_cells, c0 + chunk)
@@ -339,22 +321,41 @@ class TrainingSet:
             off = torch.from_numpy(pop.offsets[c0:c1 + 1] - a).to(dev)
             tau = torch.from_numpy(pop.tau[c0:c1]).to(dev)
             mom, y, fl = api.fp_closure_exact(v, off, tau, params=prm, prec="fp64")
-            t = dimensionless(y, mom, tau)
-            f_full = raw_features_t(mom)
-            f = f_full if features == "full" else lite_raw_features_t(api.fp_moments_lite(v, off), tau)
-            keep = ((fl == 0) & torch.isfinite(t).all(1) & (t.abs() <= 1e6).all(1) & torch.isfinite(f).all(1)
-                    & torch.isfinite(f_full).all(1))
-            feats.append(f[keep].float())
-            targs.append(t[keep].float())
-            auxs.append(aux_from_features(f_full[keep].float()))
-        self.f = torch.cat(feats)
+            lite = api.fp_moments_lite(v, off) if features != "full" else None
+            r, t, x = api.fp_surrogate_training_rows(mom, tau, coeffs=y, lite=lite, lite_inputs=features != "full")
+            rfull = r if features == "full" else api.fp_surrogate_training_rows(mom, tau, aux=False, targets=False)[0]
+            keep = ((fl == 0) & torch.isfinite(t).all(1) & (t.abs() <= 1e6).all(1) & torch.isfinite(r).all(1)
+                    & torch.isfinite(rfull).all(1))
+            nf = FEATURE_SETS[features][1]
+            raws.append(r[keep, :nf])
+            targs.append(t[keep, :NOUT])
+            auxs.append(x[keep])
+            srcs.append((mom if features == "full" else lite)[keep])
+            taus.append(tau[keep])
+        self.f = torch.cat(raws)
         self.t = torch.cat(targs)
         self.aux = torch.cat(auxs)
+        self.src = torch.cat(srcs)  # moment (or LITE) vectors of the kept cells
+        self.tau = torch.cat(taus)
         self.features = features
         self.eps2_hat = eps2_hat
 
     def __len__(self):
         return self.f.shape[0]
+
+    def inputs(self, s: "Surrogate"):
+        """The BF16 standardised inputs [n, 32] made by the inference kernel
+        with s's scalers."""
+        n = len(self)
+        x = torch.empty((n, IN), dtype=torch.bfloat16, device=self.f.device)
+        step = 1 << 20
+        for c0 in range(0, n, step):
+            c1 = min(n, c0 + step)
+            if self.features == "full":
+                s.features(self.src[c0:c1], self.tau[c0:c1], x_out=x[c0:c1])
+            else:
+                s.lite_features(self.src[c0:c1], self.tau[c0:c1], x_out=x[c0:c1])
+        return x
 
 
 def fit_scalers(s: Surrogate, ts: TrainingSet):
@@ -377,14 +378,6 @@ def fit_scalers(s: Surrogate, ts: TrainingSet):
     s.y_mu[NOUT:] = 0
     s.y_sigma[NOUT:] = 1
     s._net = None
-
-
-def standardized_inputs(s: Surrogate, f):
-    """BF16 standardised features [n, 32] (the layout the forward reads)."""
-    nf = s.nfeat
-    x = torch.zeros((f.shape[0], IN), dtype=torch.float32, device=f.device)
-    x[:, :nf] = (f - s.x_mu[:nf]) / s.x_sigma[:nf]
-    return x.to(torch.bfloat16)
 
 
 class Trainer:
@@ -430,7 +423,7 @@ class Trainer:
 
     def fit(self, ts: TrainingSet, epochs=10, seed=0, log=None, lr_decay=0.85):
         s = self.s
-        x_all = standardized_inputs(s, ts.f)
+        x_all = ts.inputs(s)
         n = len(ts)
         gen = torch.Generator(device="cpu").manual_seed(seed)
         hist = []

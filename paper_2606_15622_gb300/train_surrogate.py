@@ -52,6 +52,8 @@ def build_training_set(n_cells, seed, eps2_hat, chunk=250_000, log=print, featur
     out.f = torch.cat([p.f for p in parts])
     out.t = torch.cat([p.t for p in parts])
     out.aux = torch.cat([p.aux for p in parts])
+    out.src = torch.cat([p.src for p in parts])
+    out.tau = torch.cat([p.tau for p in parts])
     return out
 
 

@@ -207,7 +207,7 @@ def test_lite_training_beats_linear_closure():
     hist = tr.fit(ts, epochs=6, seed=1)
     assert hist[-1] < 0.5 * hist[0]
     tt = S.TrainingSet(P.training_cells(4000, seed=202), eps2_hat=1e-3, features="lite")
-    pred = s.forward(S.standardized_inputs(s, tt.f), standardized=False)[:, :9]
+    pred = s.forward(tt.inputs(s), standardized=False)[:, :9]
     torch.cuda.synchronize()
     err_net = ((pred - tt.t).norm(dim=1) / tt.t.norm(dim=1)).median().item()
     lin = torch.zeros_like(tt.t)
