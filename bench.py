@@ -49,8 +49,8 @@ NCU_DRAM_BYTES = {"velocity_update": 289.74e6, "gather_fp32": 159.85e6, "solve_f
                   "gather_lite": 152.62e6}
 ORACLE_BLOCK = 4096            # cells per block of the CPU oracle's timing
 E2E_CHUNKS = 8                 # chunks of the host-resident step (copy / compute overlap)
-WEIGHTS = os.path.join(ROOT, "paper_2606_15622_gb300", "weights", "surrogate_couette_cavity.fpw")
-WEIGHTS_LITE = os.path.join(ROOT, "paper_2606_15622_gb300", "weights", "surrogate_lite_couette_cavity.fpw")
+WEIGHTS = os.path.join(ROOT, "paper_2606_15622_gb300", "weights", "surrogate_full.fpw")
+WEIGHTS_LITE = os.path.join(ROOT, "paper_2606_15622_gb300", "weights", "surrogate_lite.fpw")
 
 # algorithmic work per unit of each kernel
 GATHER_BYTES_PER_PARTICLE = 12          # three FP32 components read once
@@ -376,6 +376,21 @@ def run_ours(args):
     t64 = float(np.median(timed(lambda: api.fp_closure_exact(v64, off, tau, params=prm, prec="fp64",
                                                              moments_out=mom, coeffs_out=coeffs, flags_out=flags,
                                                              stream=stream), 5, 2)))
+    # ---- error of the learned closure on these cells against the exact FP64 closure --
+    mom64, y64, fl64 = torch.empty_like(mom), torch.empty_like(coeffs), torch.empty_like(flags)
+    api.fp_closure_exact(v64, off, tau, params=prm, prec="fp64", moments_out=mom64, coeffs_out=y64, flags_out=fl64,
+                         stream=stream)
+    torch.cuda.synchronize()
+    sur_err = S.error_report(sur, mom64, tau, y64, fl64, prm.eps2_hat, params=prm)
+    c_exact()   # as deployed in the step: the learned closure on the FP32-moment gather's moments
+    c_surrogate()
+    torch.cuda.synchronize()
+    t_ex64 = S.dimensionless(y64, mom64, tau)
+    ok64 = fl64 == 0
+    rel_dep = ((S.dimensionless(coeffs_s, mom64, tau) - t_ex64).norm(dim=1) / t_ex64.norm(dim=1))[ok64].float().cpu()
+    sur_err["rel_err_closure_as_deployed_fp32_moments"] = {
+        "median": round(float(rel_dep.median()), 7), "p95": round(float(torch.quantile(rel_dep, 0.95)), 7),
+        "p99": round(float(torch.quantile(rel_dep, 0.99)), 7), "max": round(float(rel_dep.max()), 7)}
     c_exact()
     torch.cuda.synchronize()
 
@@ -443,6 +458,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         t_l = S.dimensionless(ly, imom, itau)
         rel_l = ((t_l - t_ex).norm(dim=1) / t_ex.norm(dim=1))[ok].float().cpu()
+        lite_err = S.error_report(sl, mom64, tau, y64, fl64, prm.eps2_hat, params=prm,
+                                  lite=api.fp_moments_lite(v64, off))
         # the coefficient-sensitivity probe of the cylinder study: 50 dropout passes at rate 0.2
         sens_ws = torch.empty(int(api.lib().fp_surrogate_sensitivity_workspace_bytes(n_cells)), dtype=torch.uint8,
                               device=dev)
@@ -460,6 +477,7 @@ def run_ours(args):
                     "held_out_rel_err_vs_exact": {"median": q(rel_l, 0.5), "p95": q(rel_l, 0.95),
                                                   "max": round(float(rel_l.max()), 6)},
                     "full_input_network_rel_err": {"median": q(rel, 0.5), "p95": q(rel, 0.95)},
+                    "error_vs_exact_fp64_cylinder": lite_err,
                     "note": "LITE moment pass (N, U, theta, u_ij, heat flux) + network on the 16 low-order "
                             "inputs; no exact fallback (flagged cells take the linear drift)"}
 
@@ -588,6 +606,7 @@ def run_ours(args):
                                       "fallback_rate": round(step_fallback_rate, 5),
                                       "range_flag_rate": round(step_range_rate, 5),
                                       "energy_flag_rate": round(step_energy_rate, 5),
+                                      "error_vs_exact_fp64": sur_err,
                                       "note": "flags of the step's learned closure: cells outside the training "
                                               "box (range) or with a large energy residual are recomputed by the "
                                               "exact closure"},

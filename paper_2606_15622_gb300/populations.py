@@ -362,10 +362,43 @@ def integer_cells(counts, lo=-3, hi=3, tau=1.0, seed: int = 0) -> Population:
     return from_counts("integer", counts, draw, tu)
 
 
-def training_cells(n_cells: int, seed: int) -> Population:
+def concat(pops, name="concat") -> Population:
+    """The cells of several populations one after another."""
+    counts = np.concatenate([p.counts for p in pops])
+    offs = np.zeros(len(counts) + 1, dtype=np.int64)
+    np.cumsum(counts, out=offs[1:])
+    v = np.ascontiguousarray(np.concatenate([p.v64 for p in pops], axis=1))
+    return Population(name, v, offs, np.concatenate([p.tau for p in pops]))
+
+
+def _cylinder_cells(n_cells: int, seed: int) -> Population:
+    """n_cells cells drawn at random from cylinder-like populations of fresh
+    seeds (the Mach-10 flow's free stream, shock layer, wall and wake cells
+    in their proportions)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts, left, k = [], n_cells, 0
+    while left > 0:
+        cyl = cylinder(seed=1000003 * (seed + 1) + k)
+        take = min(left, cyl.n_cells // 2)
+        parts.append(cyl.subset(np.sort(rng.choice(cyl.n_cells, take, replace=False))))
+        left -= take
+        k += 1
+    return concat(parts) if len(parts) > 1 else parts[0]
+
+
+def training_cells(n_cells: int, seed: int, cylinder_fraction: float = 0.0) -> Population:
     """Cells drawn from the Couette-like and cavity-like distributions (half
-    each): Maxwellian cells with 100 particles, and Grad-13 / bimodal cells
-    with Poisson(50) particles clipped to [8, 400] and theta in [1, 3]."""
+    each of the remainder): Maxwellian cells with 100 particles, and Grad-13 /
+    bimodal cells with Poisson(50) particles clipped to [8, 400] and theta in
+    [1, 3]; with cylinder_fraction > 0, that fraction of the cells comes from
+    cylinder-like populations of fresh seeds."""
+    n_cyl = int(round(cylinder_fraction * n_cells))
+    if n_cyl > 0:
+        rest = training_cells(n_cells - n_cyl, seed) if n_cells > n_cyl else None
+        cyl = _cylinder_cells(n_cyl, seed)
+        out = concat([rest, cyl]) if rest is not None else cyl
+        out.name = f"training_{n_cells}_cyl{cylinder_fraction:g}"
+        return out
     n_a = n_cells // 2
     n_b = n_cells - n_a
     rng = np.random.Generator(np.random.PCG64(seed))

@@ -297,6 +297,64 @@ def aux_moments(mom, tau):
     return x[:, :10].double()
 
 
+def error_report(s: "Surrogate", mom, tau, y_exact, flags_exact, eps2_hat, params=None, lite=None):
+    """Error of the learned closure against the exact closure's coefficients on
+    the same cells (dimensionless, ||dY|| / ||Y|| per cell, over the cells the
+    exact closure does not flag):
+      network   the network's prediction for every such cell (before fallback)
+      closure   the learned closure's output (after its fallback: cells it
+                flags are re-solved exactly, or take the linear drift on LITE
+                inputs)
+    plus |e| of the energy residual e = 1 + (sum C^_ij u^_ij + sum G^_i b^_i -
+    eps^2 s4^) / 3 of both (0 for the exact closure), the flag rates, and the
+    linear drift's error for scale.  `lite` selects LITE inputs."""
+    p = params if params is not None else api.default_params(eps2_hat=eps2_hat)
+    if lite is not None:
+        x, fl_in = s.lite_features(lite, tau, params=p)
+        y_s, fl_s = s.closure_lite(lite, tau, params=p)
+        fb = (fl_s & api.FALLBACK_FLAGS) != 0
+    else:
+        x, fl_in = s.features(mom, tau, params=p)
+        y_s, fl_s = s.closure(mom, tau, params=p)
+        fb = (fl_s & api.FLAG_FALLBACK) != 0
+    t_net = s.forward(x, standardized=False)[:, :NOUT].double()
+    t_ex = dimensionless(y_exact, mom, tau)
+    t_cl = dimensionless(y_s, mom, tau)
+    ax = aux_moments(mom, tau)
+    ok = (flags_exact == 0) & torch.isfinite(t_ex).all(1)
+    mult = torch.tensor([1, 2, 2, 1, 2, 1], dtype=torch.float64, device=t_ex.device)
+
+    def energy(t):
+        return 1 + ((t[:, :6] * ax[:, :6] * mult).sum(1) + (t[:, 6:] * ax[:, 6:9]).sum(1) - eps2_hat * ax[:, 9]) / 3
+
+    def stats(x):
+        x = x[torch.isfinite(x)].float().cpu()
+        if x.numel() == 0:
+            return None
+        return {"median": float(x.median()), "p95": float(torch.quantile(x, 0.95)),
+                "p99": float(torch.quantile(x, 0.99)), "max": float(x.max())}
+
+    nrm = t_ex.norm(dim=1)
+    rel_net = ((t_net - t_ex).norm(dim=1) / nrm)[ok]
+    rel_cl = ((t_cl - t_ex).norm(dim=1) / nrm)[ok]
+    lin = torch.zeros_like(t_ex)
+    lin[:, [0, 3, 5]] = -1.0
+    rel_lin = ((lin - t_ex).norm(dim=1) / nrm)[ok]
+    kept = ok & ~fb
+    return {
+        "cells": int(ok.numel()), "cells_compared": int(ok.sum()), "inputs": s.features_set,
+        "fallback_rate": float(fb.double().mean()),
+        "range_flag_rate": float(((fl_s & api.FLAG_RANGE) != 0).double().mean()),
+        "energy_flag_rate": float(((fl_s & api.FLAG_ENERGY) != 0).double().mean()),
+        "rel_err_network_before_fallback": stats(rel_net),
+        "rel_err_closure_after_fallback": stats(rel_cl),
+        "rel_err_network_on_kept_cells": stats(((t_cl - t_ex).norm(dim=1) / nrm)[kept]),
+        "energy_residual_abs_network": stats(energy(t_net)[ok].abs()),
+        "energy_residual_abs_closure": stats(energy(t_cl)[ok].abs()),
+        "rel_err_linear_closure": stats(rel_lin),
+    }
+
+
 class TrainingSet:
     """Cells labelled by the exact FP64 GPU closure.  Everything the training
     reads comes from the library's kernels (fp_surrogate_training_rows): the

@@ -21,7 +21,7 @@ from paper_2606_15622_gb300 import surrogate as S
 pytestmark = pytest.mark.gpu
 
 WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2606_15622_gb300",
-                       "weights", "surrogate_couette_cavity.fpw")
+                       "weights", "surrogate_full.fpw")
 
 
 def _reference(pop, v, prec, sur, dt, seed, step):

@@ -266,7 +266,7 @@ def test_collision_steps_full_size_cylinder():
     assert torch.equal(perm, perm_r) and torch.equal(y, yr) and torch.equal(fl, flr) and torch.equal(v_out, vr)
     # learned closure on LITE inputs
     s = S.Surrogate.load(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
-                                      "paper_2606_15622_gb300", "weights", "surrogate_lite_couette_cavity.fpw"))
+                                      "paper_2606_15622_gb300", "weights", "surrogate_lite.fpw"))
     v_out, perm, off, y, fl = api.fp_collision_step(cd, vd, pop.n_cells, tau, 0.1, net_lite=s.net(), seed=3, step=9)
     lr = api.fp_moments_lite(vs, off_r)
     yr, flr = s.closure_lite(lr, tau)

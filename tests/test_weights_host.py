@@ -13,8 +13,8 @@ from paper_2606_15622_gb300 import api
 from paper_2606_15622_gb300 import surrogate as S
 
 W = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2606_15622_gb300", "weights")
-FULL = os.path.join(W, "surrogate_couette_cavity.fpw")
-LITE = os.path.join(W, "surrogate_lite_couette_cavity.fpw")
+FULL = os.path.join(W, "surrogate_full.fpw")
+LITE = os.path.join(W, "surrogate_lite.fpw")
 
 
 def _tensors(s):
