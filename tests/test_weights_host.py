@@ -51,15 +51,17 @@ def test_round_trip_is_exact(tmp_path):
 
 
 def test_version_one_reads_as_full_inputs(tmp_path):
-    # the shipped full-input file predates the input-set field
-    assert _version(FULL) == 1 and _version(LITE) == 2
+    # a version-1 file (written before the input-set field existed) is the
+    # full-input network: make one from the shipped version-2 file
+    assert _version(FULL) == 2 and _version(LITE) == 2
     s = S.Surrogate.load(FULL, device="cpu")
     assert s.features_set == "full"
     raw = open(FULL, "rb").read()
     ver, *rest = struct.unpack("<IIIIIdQ", raw[4:40])
-    v2 = raw[:4] + struct.pack("<IIIIIdQ", 2, *rest) + struct.pack("<I", S.FEATURE_SETS["full"][0]) + raw[40:]
-    p = str(tmp_path / "v2.fpw")
-    open(p, "wb").write(v2)
+    assert struct.unpack("<I", raw[40:44])[0] == S.FEATURE_SETS["full"][0]
+    v1 = raw[:4] + struct.pack("<IIIIIdQ", 1, *rest) + raw[44:]
+    p = str(tmp_path / "v1.fpw")
+    open(p, "wb").write(v1)
     r = S.Surrogate.load(p, device="cpu")
     assert r.features_set == "full"
     for a, b in zip(_tensors(s), _tensors(r)):
