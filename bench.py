@@ -382,6 +382,7 @@ def run_ours(args):
                          stream=stream)
     torch.cuda.synchronize()
     sur_err = S.error_report(sur, mom64, tau, y64, fl64, prm.eps2_hat, params=prm)
+    reset_v()   # M^0, the particles of the FP64 reference above
     c_exact()   # as deployed in the step: the learned closure on the FP32-moment gather's moments
     c_surrogate()
     torch.cuda.synchronize()

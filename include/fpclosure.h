@@ -302,7 +302,8 @@ int fp_surrogate_training_rows(const double *moments, const double *lite, const 
                                int64_t n_cells, int lite_inputs, float *raw_out, float *target_out, float *aux_out,
                                fp_stream_t stream);
 
-/* Workspace of fp_closure_surrogate for n_cells cells. */
+/* Workspace of fp_closure_surrogate for n_cells cells: the list of cells for
+ * the exact fallback (4 bytes a cell) and its count. */
 size_t fp_surrogate_workspace_bytes(int64_t n_cells);
 
 /* Features of every cell: x_out [n_cells][32] BF16, and flags_out with
@@ -321,7 +322,9 @@ int fp_mlp_forward(const fp_mlp *net, const void *x, int64_t n, int standardized
                    float *z_save, fp_stream_t stream);
 
 /* The surrogate closure: features, network, coefficients C = t / tau,
- * G = t / (tau sqrt(theta)); a cell is recomputed by the exact FP64 closure
+ * G = t / (tau sqrt(theta)), all in one tcgen05 kernel (the inputs are formed
+ * from the moment rows inside it, the predictions never leave it), followed
+ * by the exact closure on the cells it lists; a cell is recomputed by the exact FP64 closure
  * from its moments (FP_FLAG_FALLBACK) when it fails the exact closure's
  * preconditions, a raw feature leaves the training box (FP_FLAG_RANGE),
  * the prediction is not finite, or the energy residual
@@ -436,15 +439,17 @@ int fp_velocity_update_lite(void *v, void *v_out, int v_dtype, int64_t n_particl
                             const fp_params *p, const void *xi, uint64_t seed, uint64_t step, double *alpha_out,
                             int32_t *flags, fp_stream_t stream);
 
+/* Workspace of fp_closure_surrogate_lite: 0 bytes (the call is one fused
+ * kernel); kept so that callers size every call the same way. */
 size_t fp_surrogate_lite_workspace_bytes(int64_t n_cells);
 
 /* fp_closure_surrogate_lite: the learned closure on the LITE inputs:
- * features, the network (tcgen05), and coefficients C = t_C / tau,
+ * features, the network and coefficients in one tcgen05 kernel, C = t_C / tau,
  * G = t_G / (tau sqrt(theta)).  There are no high-order moments to fall back
  * on: cells flagged FP_FLAG_FEW, FP_FLAG_SINGULAR or FP_FLAG_NONFINITE (also
  * for a non-finite prediction) take the linear drift C = -I/tau, G = 0;
- * FP_FLAG_RANGE is reported and the prediction kept.  ws >=
- * fp_surrogate_lite_workspace_bytes(n_cells), 256-byte aligned. */
+ * FP_FLAG_RANGE is reported and the prediction kept.  ws and ws_bytes are
+ * not read (ws may be NULL). */
 int fp_closure_surrogate_lite(const fp_mlp *net, const double *lite, int64_t n_cells, const double *tau,
                               const fp_params *p, double *coeffs_out, int32_t *flags_out, void *ws, size_t ws_bytes,
                               fp_stream_t stream);

@@ -25,15 +25,15 @@ void launch_features(const fp_mlp &net, const double *mom, const double *tau, in
                      double margin, void *x, int32_t *flags, cudaStream_t st);
 int launch_mlp_forward(const fp_mlp &net, const void *x, int64_t n, int standardized_out, float *out, void *h_save,
                        float *z_save, cudaStream_t st);
-void launch_surrogate_tail(const float *tpred, const double *mom, const double *tau, int64_t n, double eps2_hat,
-                           double energy_tol, const fp_params &p, int prec, double *coeffs, int32_t *flags,
-                           int32_t *list, uint32_t *count, cudaStream_t st);
+int launch_closure_surrogate(const fp_mlp &net, const double *mom, const double *tau, int64_t n, double eps2_hat,
+                             const fp_params &p, int prec, double *coeffs, int32_t *flags, int32_t *list,
+                             uint32_t *count, cudaStream_t st);
+int launch_closure_surrogate_lite(const fp_mlp &net, const double *lite, const double *tau, int64_t n,
+                                  const fp_params &p, double *coeffs, int32_t *flags, cudaStream_t st);
 void launch_gather_lite(const void *v, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, double *lite,
                         cudaStream_t st);
 void launch_lite_features(const fp_mlp &net, const double *lite, const double *tau, int64_t n, int min_particles,
                           double margin, void *x, int32_t *flags, cudaStream_t st);
-void launch_lite_epilogue(const float *tpred, const double *lite, const double *tau, int64_t n, double *coeffs,
-                          int32_t *flags, cudaStream_t st);
 int launch_mlp_forward_dropout(const fp_mlp &net, const void *x, int64_t n, float *out, double rate, uint64_t seed,
                                uint32_t pass, cudaStream_t st);
 void launch_sens_accumulate(const float *tpred, int64_t n, int k, double *mean, double *m2, cudaStream_t st);
@@ -99,14 +99,10 @@ int check_net(const fp_mlp *net) {
     return fail(FP_ERR_ARG, "null scaler");
   return FP_OK;
 }
-size_t surrogate_ws_parts(int64_t n, size_t *off_t, size_t *off_list, size_t *off_count) {
-  const size_t x = align_up((size_t)n * 32 * 2);
-  const size_t t = align_up((size_t)n * 16 * 4);
-  const size_t l = align_up((size_t)n * 4);
-  *off_t = x;
-  *off_list = x + t;
-  *off_count = x + t + l;
-  return x + t + l + 256;
+// fallback list [n] int32, then its count
+size_t surrogate_ws_parts(int64_t n, size_t *off_count) {
+  *off_count = align_up((size_t)n * 4);
+  return *off_count + 256;
 }
 }  // namespace
 
@@ -298,8 +294,8 @@ int64_t fp_mlp_param_offset(int which, int layer) {
 
 size_t fp_surrogate_workspace_bytes(int64_t n_cells) {
   if (n_cells <= 0) return 0;
-  size_t a, b, c;
-  return surrogate_ws_parts(n_cells, &a, &b, &c);
+  size_t c;
+  return surrogate_ws_parts(n_cells, &c);
 }
 
 int fp_surrogate_features(const fp_mlp *net, const double *moments, int64_t n_cells, const double *tau,
@@ -359,8 +355,8 @@ int fp_closure_surrogate(const fp_mlp *net, const double *moments, int64_t n_cel
   if (n_cells == 0) return FP_OK;
   if (prec != FP_PREC_FP64 && prec != FP_PREC_FP32_MOMENTS) return fail(FP_ERR_ARG, "prec %d", prec);
   if (!moments || !tau || !coeffs_out || !flags_out) return fail(FP_ERR_ARG, "null array pointer");
-  size_t off_t, off_list, off_count;
-  const size_t need = surrogate_ws_parts(n_cells, &off_t, &off_list, &off_count);
+  size_t off_count;
+  const size_t need = surrogate_ws_parts(n_cells, &off_count);
   if (!ws || ws_bytes < need) return fail(FP_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", need, ws_bytes);
   if ((uintptr_t)ws % kAlign) return fail(FP_ERR_ARG, "workspace not 256-byte aligned");
   fp_params prm;
@@ -368,16 +364,10 @@ int fp_closure_surrogate(const fp_mlp *net, const double *moments, int64_t n_cel
   if (p) prm = *p;
   if (prm.min_particles < 1) prm.min_particles = 1;
   char *w = (char *)ws;
-  cudaStream_t st = (cudaStream_t)stream;
-  fpc::launch_features(*net, moments, tau, n_cells, prm.min_particles, prm.surr_range_margin, w, flags_out, st);
-  if (int rc = check_launch("features")) return rc;
-  if (fpc::launch_mlp_forward(*net, w, n_cells, 0, (float *)(w + off_t), nullptr, nullptr, st))
+  if (fpc::launch_closure_surrogate(*net, moments, tau, n_cells, net->eps2_hat, prm, prec, coeffs_out, flags_out,
+                                    (int32_t *)w, (uint32_t *)(w + off_count), (cudaStream_t)stream))
     return fail(FP_ERR_CUDA, "could not raise the shared-memory limit of the MLP kernel");
-  if (int rc = check_launch("mlp_forward")) return rc;
-  fpc::launch_surrogate_tail((const float *)(w + off_t), moments, tau, n_cells, net->eps2_hat, prm.surr_energy_tol,
-                             prm, prec, coeffs_out, flags_out, (int32_t *)(w + off_list), (uint32_t *)(w + off_count),
-                             st);
-  return check_launch("surrogate tail");
+  return check_launch("closure_surrogate");
 }
 
 int fp_surrogate_loss(const float *out, const float *t_true, const float *aux, const float *y_mu,
@@ -473,32 +463,25 @@ int fp_surrogate_lite_features(const fp_mlp *net, const double *lite, int64_t n_
 }
 
 size_t fp_surrogate_lite_workspace_bytes(int64_t n_cells) {
-  if (n_cells < 0) return 0;
-  return align_up((size_t)n_cells * 32 * 2) + align_up((size_t)n_cells * 16 * 4);
+  (void)n_cells;
+  return 0;  // the fused kernel needs none
 }
 
 int fp_closure_surrogate_lite(const fp_mlp *net, const double *lite, int64_t n_cells, const double *tau,
                               const fp_params *p, double *coeffs_out, int32_t *flags_out, void *ws, size_t ws_bytes,
                               fp_stream_t stream) {
   g_err[0] = 0;
+  (void)ws;
+  (void)ws_bytes;
   if (int rc = check_net(net)) return rc;
   if (n_cells < 0) return fail(FP_ERR_ARG, "negative size");
   if (n_cells == 0) return FP_OK;
   if (!lite || !tau || !coeffs_out || !flags_out) return fail(FP_ERR_ARG, "null array pointer");
-  const size_t need = fp_surrogate_lite_workspace_bytes(n_cells);
-  if (!ws || ws_bytes < need) return fail(FP_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", need, ws_bytes);
-  if ((uintptr_t)ws % kAlign) return fail(FP_ERR_ARG, "workspace not 256-byte aligned");
   fp_params prm;
   fp_default_params(&prm);
   if (p) prm = *p;
-  const cudaStream_t st = (cudaStream_t)stream;
-  char *w = (char *)ws;
-  void *x = w;
-  float *tpred = (float *)(w + align_up((size_t)n_cells * 32 * 2));
-  fpc::launch_lite_features(*net, lite, tau, n_cells, prm.min_particles, prm.surr_range_margin, x, flags_out, st);
-  if (fpc::launch_mlp_forward(*net, x, n_cells, 0, tpred, nullptr, nullptr, st))
+  if (fpc::launch_closure_surrogate_lite(*net, lite, tau, n_cells, prm, coeffs_out, flags_out, (cudaStream_t)stream))
     return fail(FP_ERR_CUDA, "could not raise the shared-memory limit of the MLP kernel");
-  fpc::launch_lite_epilogue(tpred, lite, tau, n_cells, coeffs_out, flags_out, st);
   return check_launch("surrogate_lite");
 }
 
@@ -541,7 +524,7 @@ int fp_sort_by_cell(const int32_t *cell_of, int64_t n_particles, int64_t n_cells
 
 namespace {
 struct StepLayout {
-  size_t sort, vs, mom, m6, sur, total;
+  size_t sort, vs, mom, m6, total;
 };
 StepLayout step_layout(int64_t n_particles, int64_t n_cells, int v_dtype, int lite) {
   StepLayout L{};
@@ -552,8 +535,6 @@ StepLayout step_layout(int64_t n_particles, int64_t n_cells, int v_dtype, int li
   o += align_up((size_t)n_cells * (lite ? FP_NLITE : FP_NMOM) * 8);
   L.m6 = o;
   if (!lite) o += align_up((size_t)n_cells * 8);
-  L.sur = o;
-  if (lite) o += align_up(fp_surrogate_lite_workspace_bytes(n_cells));
   L.total = o;
   return L;
 }
@@ -604,15 +585,9 @@ int fp_collision_step(const int32_t *cell_of, const void *v, int v_dtype, int64_
       fpc::launch_velocity(vs, v_out, v_dtype, n_particles, cell_offsets_out, n_cells, mom, m6, coeffs_out, tau, dt,
                            prm.eps2_hat, nullptr, seed, step, prm.particle_offset, nullptr, flags_out, st);
     } else {
-      char *sw = w + L.sur;
-      void *x = sw;
-      float *tpred = (float *)(sw + align_up((size_t)n_cells * 32 * 2));
       fpc::launch_gather_lite(vs, v_dtype, n_particles, cell_offsets_out, n_cells, mom, st);
-      fpc::launch_lite_features(*net_lite, mom, tau, n_cells, prm.min_particles, prm.surr_range_margin, x, flags_out,
-                                st);
-      if (fpc::launch_mlp_forward(*net_lite, x, n_cells, 0, tpred, nullptr, nullptr, st))
+      if (fpc::launch_closure_surrogate_lite(*net_lite, mom, tau, n_cells, prm, coeffs_out, flags_out, st))
         return fail(FP_ERR_CUDA, "could not raise the shared-memory limit of the MLP kernel");
-      fpc::launch_lite_epilogue(tpred, mom, tau, n_cells, coeffs_out, flags_out, st);
       fpc::launch_velocity_lite(vs, v_out, v_dtype, n_particles, cell_offsets_out, n_cells, mom, coeffs_out, tau, dt,
                                 prm.eps2_hat, nullptr, seed, step, prm.particle_offset, nullptr, flags_out, st);
     }

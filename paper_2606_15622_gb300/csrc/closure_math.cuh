@@ -39,11 +39,13 @@ struct SolveParams {
 //   heat rows (i):     sum_l C_il b_l + 2 sum_kl C_kl u_ikl + G_i (s4 - 9 theta^2)
 //                      + 2 sum_k G_k (w_ki - 3 theta u_ki)
 //                      = -(4/(3 tau)) b_i + eps^2 (3 z_i - 3 theta b_i - 2 u_ik b_k)
-// Every entry is written as its own closed expression (a copy where a single
-// moment is the coefficient): on this GPU each FP64 instruction is expensive,
-// and accumulating into zeroed entries would cost an FP64 add per term.
-__device__ __forceinline__ void assemble(const double (&m)[FP_NMOM], double tau, double eps2_hat,
-                                         double (&a)[9][10]) {
+// Every nonzero entry is handed to emit(row, col, value) as its own closed
+// expression (a copy where a single moment is the coefficient): on this GPU
+// each FP64 instruction is expensive, and accumulating into zeroed entries
+// would cost an FP64 add per term.  Row and column are compile-time constants
+// once the loops unroll; entries never emitted are zero.
+template <class Emit>
+__device__ __forceinline__ void assemble_emit(const double (&m)[FP_NMOM], double tau, double eps2_hat, Emit &&emit) {
   double u[3][3], w[3][3], b[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -61,10 +63,6 @@ __device__ __forceinline__ void assemble(const double (&m)[FP_NMOM], double tau,
   const double inv_tau = 1.0 / tau;
   const double c_u = -2.0 * inv_tau, c_w = 2.0 * eps2;  // stress right-hand side
   const double th3 = 3.0 * theta;
-#pragma unroll
-  for (int r = 0; r < 9; ++r)
-#pragma unroll
-    for (int col = 0; col < 10; ++col) a[r][col] = 0.0;
   // stress rows
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -74,20 +72,20 @@ __device__ __forceinline__ void assemble(const double (&m)[FP_NMOM], double tau,
       if (i == j) {
         // 2 sum_k C_ik u_ki + 2 G_i b_i
 #pragma unroll
-        for (int k = 0; k < 3; ++k) a[row][sym2(i, k)] = 2.0 * u[k][i];
-        a[row][6 + i] = 2.0 * b[i];
+        for (int k = 0; k < 3; ++k) emit(row, sym2(i, k), 2.0 * u[k][i]);
+        emit(row, 6 + i, 2.0 * b[i]);
       } else {
         // C_ii u_ij + C_jj u_ij + C_ij (u_ii + u_jj) + C_it u_tj + C_jt u_ti
         const int t = 3 - i - j;
-        a[row][sym2(i, i)] = u[i][j];
-        a[row][sym2(j, j)] = u[i][j];
-        a[row][sym2(i, j)] = u[i][i] + u[j][j];
-        a[row][sym2(i, t)] = u[t][j];
-        a[row][sym2(j, t)] = u[t][i];
-        a[row][6 + i] = b[j];
-        a[row][6 + j] = b[i];
+        emit(row, sym2(i, i), u[i][j]);
+        emit(row, sym2(j, j), u[i][j]);
+        emit(row, sym2(i, j), u[i][i] + u[j][j]);
+        emit(row, sym2(i, t), u[t][j]);
+        emit(row, sym2(j, t), u[t][i]);
+        emit(row, 6 + i, b[j]);
+        emit(row, 6 + j, b[i]);
       }
-      a[row][9] = c_u * u[i][j] + c_w * w[i][j];
+      emit(row, 9, c_u * u[i][j] + c_w * w[i][j]);
     }
   // heat-flux rows
 #pragma unroll
@@ -109,16 +107,25 @@ __device__ __forceinline__ void assemble(const double (&m)[FP_NMOM], double tau,
           has_b = true;
         }
         const double f = p == q ? 2.0 : 4.0;
-        a[row][sym2(p, q)] = has_b ? fma(f, u3, bterm) : f * u3;
+        emit(row, sym2(p, q), has_b ? fma(f, u3, bterm) : f * u3);
       }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       const double gk = 2.0 * fma(-th3, u[k][i], w[k][i]);
-      a[row][6 + k] = k == i ? (s4 - 9.0 * theta * theta) + gk : gk;
+      emit(row, 6 + k, k == i ? (s4 - 9.0 * theta * theta) + gk : gk);
     }
     const double ub = u[i][0] * b[0] + u[i][1] * b[1] + u[i][2] * b[2];
-    a[row][9] = -(4.0 / 3.0) * inv_tau * b[i] + eps2 * (3.0 * m[kZ + i] - th3 * b[i] - 2.0 * ub);
+    emit(row, 9, -(4.0 / 3.0) * inv_tau * b[i] + eps2 * (3.0 * m[kZ + i] - th3 * b[i] - 2.0 * ub));
   }
+}
+
+__device__ __forceinline__ void assemble(const double (&m)[FP_NMOM], double tau, double eps2_hat,
+                                         double (&a)[9][10]) {
+#pragma unroll
+  for (int r = 0; r < 9; ++r)
+#pragma unroll
+    for (int col = 0; col < 10; ++col) a[r][col] = 0.0;
+  assemble_emit(m, tau, eps2_hat, [&](int row, int col, double v) { a[row][col] = v; });
 }
 
 // One elimination step for column K (a template so every index is static and
@@ -280,6 +287,113 @@ __device__ __forceinline__ int closure_cell(const double *__restrict__ mc, doubl
 #pragma unroll
         for (int j = 0; j < 9; ++j) lu[32 * (i * 9 + j)] = i == j ? rinv[i] : a[i][j];
       lu[32 * 81] = __longlong_as_double((long long)perm);
+    }
+  }
+  if (fl) {
+    const double c0 = (finite_d(tc) && tc > 0.0) ? -1.0 / tc : 0.0;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) y[q] = 0.0;
+    y[0] = c0;
+    y[3] = c0;
+    y[5] = c0;
+  }
+  return fl;
+}
+
+// The closure of one cell by a group of 16 lanes (a half warp; all 32 lanes
+// of the warp call this together, each half with its own cell, r = lane % 16).
+// Lane r < 9 of the group holds row r of [A | r]: the pivot search is a
+// max-reduction over the group, the swapped rows and the pivot row travel by
+// shuffles, and each lane eliminates its own row; the back substitution
+// broadcasts each y_k from lane k.  Every entry sees the operations of
+// closure_cell in the same order (the same emitted expressions, multipliers
+// a_iK * (1 / a_KK), fma updates, the sum over j ascending), so coefficients
+// and flags are identical; what changes is the length of the dependent chain
+// (FP64 instructions have a latency of about 64 cycles on this GPU, a
+// division about 550), roughly halved, which is what a short fallback list
+// waits for.  The division by each candidate pivot runs beside the pivot
+// search.  The solve runs even for a flagged cell (the warp must stay
+// converged for the shuffles) and its result is then discarded; valid =
+// false makes the group a passenger: no loads, results meaningless.
+__device__ __forceinline__ int closure_cell_group16(const double *__restrict__ mc, double tc, const SolveParams &prm,
+                                                    bool valid, int r, double (&y)[9]) {
+  constexpr unsigned kAll = 0xffffffffu;
+  double m[FP_NMOM];
+#pragma unroll
+  for (int k = 0; k < FP_NMOM; ++k) m[k] = valid ? mc[k] : 1.0;
+  int fl = 0;
+  bool fin = finite_d(tc) && tc > 0.0;
+#pragma unroll
+  for (int k = 0; k < FP_NMOM; ++k) fin = fin && finite_d(m[k]);
+  if (!fin) fl |= FP_FLAG_NONFINITE;
+  if (m[kN] < (double)prm.min_particles) fl |= FP_FLAG_FEW;
+  if (!(m[kTheta] > 0.0)) fl |= FP_FLAG_SINGULAR;
+  if (!fl && m[kN] < (double)prm.min_regular) fl |= FP_FLAG_SINGULAR;
+
+  double row[10];
+#pragma unroll
+  for (int col = 0; col < 10; ++col) row[col] = 0.0;
+  assemble_emit(m, tc, prm.eps2_hat, [&](int rr, int col, double v) {
+    if (rr == r) row[col] = v;
+  });
+  // max |A| over the group (rows 9.. are zero)
+  uint64_t amax = 0;
+#pragma unroll
+  for (int j = 0; j < 9; ++j) amax = max(amax, abs_bits(row[j]));
+#pragma unroll
+  for (int o = 8; o >= 1; o >>= 1) amax = max(amax, (uint64_t)__shfl_xor_sync(kAll, (unsigned long long)amax, o, 16));
+  const double amax_d = __longlong_as_double((long long)amax);
+  int sfl = 0;
+  if (!(amax_d > 0.0) || !finite_d(amax_d)) sfl = FP_FLAG_SINGULAR;
+  const uint64_t thr = abs_bits(prm.pivot_rtol * amax_d);
+  double rinv[9];
+#pragma unroll
+  for (int K = 0; K < 9; ++K) {
+    const double inv_own = 1.0 / row[K];  // this lane's candidate reciprocal, beside the search
+    // pivot: the largest |a_iK| over rows i >= K, the first such row on ties
+    // (key 0 for lanes that are not candidates)
+    const bool cand = r >= K && r < 9;
+    uint64_t key = cand ? ((abs_bits(row[K]) << 1) | 1ull) : 0ull;
+    int idx = r;
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) {
+      const uint64_t k2 = __shfl_xor_sync(kAll, (unsigned long long)key, o, 16);
+      const int i2 = __shfl_xor_sync(kAll, idx, o, 16);
+      if (k2 > key || (k2 == key && i2 < idx)) {
+        key = k2;
+        idx = i2;
+      }
+    }
+    const int bi = idx;
+    if (!((key >> 1) > thr)) sfl = FP_FLAG_SINGULAR;
+    // rows K and bi trade places; every lane reads the pivot row (old row bi)
+    const int src = r == K ? bi : (r == bi ? K : r);
+    double piv[10];
+#pragma unroll
+    for (int j = K; j < 10; ++j) {
+      piv[j] = __shfl_sync(kAll, row[j], bi, 16);
+      row[j] = __shfl_sync(kAll, row[j], src, 16);
+    }
+    rinv[K] = __shfl_sync(kAll, inv_own, bi, 16);
+    if (r > K && r < 9) {
+      const double l = row[K] * rinv[K];
+#pragma unroll
+      for (int j = K + 1; j < 10; ++j) row[j] = fma(-l, piv[j], row[j]);
+    }
+  }
+#pragma unroll
+  for (int k = 8; k >= 0; --k) {
+    double s = row[9];
+#pragma unroll
+    for (int j = k + 1; j < 9; ++j) s = fma(-row[j], y[j], s);
+    y[k] = __shfl_sync(kAll, s * rinv[k], k, 16);
+  }
+  if (!fl) {
+    fl = sfl;
+    if (!fl) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q)
+        if (!finite_d(y[q])) fl |= FP_FLAG_NONFINITE;
     }
   }
   if (fl) {

@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(256) lite_features_kernel(MlpDev net, const do
 #pragma unroll
   for (int k = 0; k < FP_NLITE; ++k) fin = fin && finite_d(m[k]);
   if (!fin) fl |= FP_FLAG_NONFINITE;
-  if (d2f_rn(m[0]) < (float)min_particles) fl |= FP_FLAG_FEW;  // N is a whole number
+  if (narrow(m[0]) < (float)min_particles) fl |= FP_FLAG_FEW;  // N is a whole number
   if (!positive_d(m[4])) fl |= FP_FLAG_SINGULAR;
   float f[16];
   lite_raw_features(m, tau[c], f);
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(256) lite_features_kernel(MlpDev net, const do
         const float sg = net.x_sigma[q];
         const float lo = net.x_min[q] - margin * sg, hi = net.x_max[q] + margin * sg;
         if (!(f[q] >= lo && f[q] <= hi)) fl |= FP_FLAG_RANGE;
-        xs[h] = (f[q] - net.x_mu[q]) / sg;
+        xs[h] = standardise(f[q], net.x_mu[q], 1.f / sg);
       }
     }
     packed[k / 2] = pack_bf16(xs[0], xs[1]);
@@ -198,45 +198,6 @@ __global__ void __launch_bounds__(256) lite_features_kernel(MlpDev net, const do
 #pragma unroll
   for (int q = 0; q < kIn / 8; ++q)
     dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
-  flags[c] = fl;
-}
-
-// Network outputs (dimensionless tau C, tau sqrt(theta) G) -> coefficients;
-// degenerate cells and non-finite predictions take the linear drift.
-__global__ void __launch_bounds__(256) lite_epilogue_kernel(const float *__restrict__ tpred,
-                                                            const double *__restrict__ lite,
-                                                            const double *__restrict__ tau, int64_t n,
-                                                            double *__restrict__ coeffs,
-                                                            int32_t *__restrict__ flags) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n) return;
-  int fl = flags[c];
-  double *y = coeffs + c * 9;
-  const double tc = tau[c];
-  bool fin = true;
-  float tp[kNOut];
-#pragma unroll
-  for (int a = 0; a < kNOut; ++a) {
-    tp[a] = tpred[c * kOut + a];
-    fin = fin && isfinite(tp[a]);
-  }
-  if (!fin) fl |= FP_FLAG_NONFINITE;
-  if (fl & (FP_FLAG_FEW | FP_FLAG_SINGULAR | FP_FLAG_NONFINITE)) {
-    const double c0 = (finite_d(tc) && positive_d(tc)) ? -1.0 / tc : 0.0;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) y[q] = 0.0;
-    y[0] = c0;
-    y[3] = c0;
-    y[5] = c0;
-  } else {
-    // the predictions carry FP32 (network) precision: scale in FP32, widen exactly
-    const float itc = 1.f / d2f_rn(tc);
-    const float ig = itc / sqrtf(d2f_rn(lite[c * FP_NLITE + 4]));
-#pragma unroll
-    for (int a = 0; a < 6; ++a) y[a] = f2d_exact(tp[a] * itc);
-#pragma unroll
-    for (int a = 6; a < 9; ++a) y[a] = f2d_exact(tp[a] * ig);
-  }
   flags[c] = fl;
 }
 
@@ -280,12 +241,6 @@ void launch_lite_features(const fp_mlp &net, const double *lite, const double *t
   const int64_t blocks = (n + 255) / 256;
   lite_features_kernel<<<(unsigned)blocks, 256, 0, st>>>(make_mlp_dev(net), lite, tau, n, min_particles,
                                                          (float)margin, reinterpret_cast<__nv_bfloat16 *>(x), flags);
-}
-
-void launch_lite_epilogue(const float *tpred, const double *lite, const double *tau, int64_t n, double *coeffs,
-                          int32_t *flags, cudaStream_t st) {
-  const int64_t blocks = (n + 255) / 256;
-  lite_epilogue_kernel<<<(unsigned)blocks, 256, 0, st>>>(tpred, lite, tau, n, coeffs, flags);
 }
 
 }  // namespace fpc

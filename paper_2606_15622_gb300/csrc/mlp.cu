@@ -1,6 +1,6 @@
-// mlp.cu -- the learned closure: features, the fused BF16 tensor-core MLP,
-// the surrogate epilogue with its range / energy checks, and the exact
-// per-cell fallback (sm_103a).
+// mlp.cu -- the learned closure's standalone input kernel, the training
+// forward pass, the exact per-cell fallback and the launchers of the fused
+// closure (whose kernel, with the inference pass, is in mlp_tc.cu) (sm_103a).
 //
 // Features: the 25 moments of w = c / sqrt(theta) (u/theta, u3/theta^1.5,
 // w/theta^2, z/theta^2.5), standardised, BF16, zero padded to 32.  The
@@ -37,20 +37,20 @@ constexpr size_t kMlpSmem =
 // ---------------------------------------------------------------------------
 // features
 // ---------------------------------------------------------------------------
-// (the moments are narrowed to FP32 on the integer pipe: d2f_rn)
+// (the moments narrowed to FP32 by `narrow`)
 __device__ __forceinline__ void cell_features(const double *__restrict__ m, float (&f)[kNFeat]) {
-  const float th = d2f_rn(m[kTheta]);
+  const float th = narrow(m[kTheta]);
   const float i1 = 1.f / th;
   const float ih = rsqrtf(th);
   const float i15 = i1 * ih, i2 = i1 * i1, i25 = i2 * ih;
 #pragma unroll
-  for (int a = 0; a < 6; ++a) f[a] = d2f_rn(m[kU2 + a]) * i1;
+  for (int a = 0; a < 6; ++a) f[a] = narrow(m[kU2 + a]) * i1;
 #pragma unroll
-  for (int a = 0; a < 10; ++a) f[6 + a] = d2f_rn(m[kU3 + a]) * i15;
+  for (int a = 0; a < 10; ++a) f[6 + a] = narrow(m[kU3 + a]) * i15;
 #pragma unroll
-  for (int a = 0; a < 6; ++a) f[16 + a] = d2f_rn(m[kW + a]) * i2;
+  for (int a = 0; a < 6; ++a) f[16 + a] = narrow(m[kW + a]) * i2;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) f[22 + a] = d2f_rn(m[kZ + a]) * i25;
+  for (int a = 0; a < 3; ++a) f[22 + a] = narrow(m[kZ + a]) * i25;
 }
 
 __global__ void __launch_bounds__(256) features_kernel(MlpDev net, const double *__restrict__ mom,
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(256) features_kernel(MlpDev net, const double 
 #pragma unroll
   for (int k = 0; k < FP_NMOM; ++k) fin = fin && finite_d(m[k]);
   if (!fin) fl |= FP_FLAG_NONFINITE;
-  if (d2f_rn(m[kN]) < (float)min_particles) fl |= FP_FLAG_FEW;  // N is a whole number
+  if (narrow(m[kN]) < (float)min_particles) fl |= FP_FLAG_FEW;  // N is a whole number
   if (!positive_d(m[kTheta])) fl |= FP_FLAG_SINGULAR;
   float f[kNFeat];
   cell_features(m, f);
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(256) features_kernel(MlpDev net, const double 
         const float sg = net.x_sigma[q];
         const float lo = net.x_min[q] - margin * sg, hi = net.x_max[q] + margin * sg;
         if (!(f[q] >= lo && f[q] <= hi)) fl |= FP_FLAG_RANGE;
-        xs[h] = (f[q] - net.x_mu[q]) / sg;
+        xs[h] = standardise(f[q], net.x_mu[q], 1.f / sg);
       }
     }
     packed[k / 2] = pack_bf16(xs[0], xs[1]);
@@ -283,72 +283,45 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
 }
 
 // ---------------------------------------------------------------------------
-// surrogate epilogue: dimensionless targets -> C, G; energy check
+// fallback: the exact closure on the cells the fused kernel listed
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) surrogate_epilogue_kernel(const float *__restrict__ tpred,
-                                                                 const double *__restrict__ mom,
-                                                                 const double *__restrict__ tau, int64_t n,
-                                                                 float eps2_hat, float energy_tol,
-                                                                 double *__restrict__ coeffs,
-                                                                 int32_t *__restrict__ flags) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n) return;
-  int fl = flags[c];
-  if (fl & (FP_FLAG_FEW | FP_FLAG_SINGULAR | FP_FLAG_NONFINITE)) return;  // the exact fallback decides
-  float tp[kNOut];
-  bool fin = true;
-#pragma unroll
-  for (int a = 0; a < kNOut; ++a) {
-    tp[a] = tpred[c * kOut + a];
-    fin = fin && isfinite(tp[a]);
-  }
-  float f[kNFeat];
-  cell_features(mom + c * FP_NMOM, f);
-  // e = 1 + (sum_ij C_hat_ij u_hat_ij + sum_i G_hat_i b_hat_i - eps2_hat s4_hat) / 3
-  const float cu = tp[0] * f[0] + 2.f * tp[1] * f[1] + 2.f * tp[2] * f[2] + tp[3] * f[3] + 2.f * tp[4] * f[4] +
-                   tp[5] * f[5];
-  const float b0 = f[6 + 0] + f[6 + 3] + f[6 + 5], b1 = f[6 + 1] + f[6 + 6] + f[6 + 8],
-              b2 = f[6 + 2] + f[6 + 7] + f[6 + 9];
-  const float s4 = f[16] + f[19] + f[21];
-  const float e = 1.f + (cu + tp[6] * b0 + tp[7] * b1 + tp[8] * b2 - eps2_hat * s4) * (1.f / 3.f);
-  if (!fin) fl |= FP_FLAG_NONFINITE;
-  if (!(fabsf(e) <= energy_tol)) fl |= FP_FLAG_ENERGY;
-  // the predictions carry FP32 (network) precision: scale in FP32, widen exactly
-  const float itc = 1.f / d2f_rn(tau[c]);
-  const float ig = itc / sqrtf(d2f_rn(mom[c * FP_NMOM + kTheta]));
-  double *y = coeffs + c * 9;
-#pragma unroll
-  for (int a = 0; a < 6; ++a) y[a] = f2d_exact(tp[a] * itc);
-#pragma unroll
-  for (int a = 6; a < 9; ++a) y[a] = f2d_exact(tp[a] * ig);
-  flags[c] = fl;
-}
+// A short list (the usual case: a few hundred cells) is latency-bound: each
+// cell goes to a half warp (closure_cell_group16), and consecutive entries go
+// to consecutive blocks so that they spread over every SM.  A long list (an
+// untrained or out-of-distribution network) is throughput-bound: one thread
+// per cell (closure_cell).  Both give the same coefficients and flags.
+constexpr int kFallbackThreads = 128;
 
-// ---------------------------------------------------------------------------
-// fallback: compact the flagged cells, solve them exactly
-// ---------------------------------------------------------------------------
-constexpr int kFallbackMask = FP_FLAG_FEW | FP_FLAG_SINGULAR | FP_FLAG_NONFINITE | FP_FLAG_RANGE | FP_FLAG_ENERGY;
-
-__global__ void __launch_bounds__(256) compact_kernel(const int32_t *__restrict__ flags, int64_t n,
-                                                      int32_t *__restrict__ list, uint32_t *__restrict__ count) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool pick = c < n && (flags[c] & kFallbackMask);
-  const unsigned m = __ballot_sync(0xffffffffu, pick);
-  if (!m) return;
-  const int lane = threadIdx.x & 31;
-  uint32_t base = 0;
-  if (lane == 0) base = atomicAdd(count, (uint32_t)__popc(m));
-  base = __shfl_sync(0xffffffffu, base, 0);
-  if (pick) list[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)c;
-}
-
-__global__ void __launch_bounds__(128) fallback_kernel(const int32_t *__restrict__ list,
-                                                       const uint32_t *__restrict__ count,
-                                                       const double *__restrict__ mom, const double *__restrict__ tau,
-                                                       SolveParams prm, double *__restrict__ coeffs,
-                                                       int32_t *__restrict__ flags) {
+__global__ void __launch_bounds__(kFallbackThreads) fallback_kernel(const int32_t *__restrict__ list,
+                                                                    const uint32_t *__restrict__ count,
+                                                                    const double *__restrict__ mom,
+                                                                    const double *__restrict__ tau, SolveParams prm,
+                                                                    double *__restrict__ coeffs,
+                                                                    int32_t *__restrict__ flags) {
   const uint32_t cnt = *count;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+  const uint32_t groups = gridDim.x * (kFallbackThreads / 16);  // half warps in the grid
+  if (cnt <= 2 * groups) {
+    const int r = threadIdx.x & 15;
+    // a warp runs only while its first half holds a cell (the solve is
+    // FP64-bound: idle warps must not compete for the pipe)
+    const uint32_t first = (threadIdx.x >> 5) * 2 * gridDim.x + blockIdx.x;
+    for (uint32_t base = 0; base + first < cnt; base += groups) {  // uniform over the warp
+      const uint32_t i = base + (threadIdx.x >> 4) * gridDim.x + blockIdx.x;
+      const bool valid = i < cnt;
+      const int64_t c = valid ? list[i] : 0;
+      double y[9];
+      const int fe = closure_cell_group16(mom + c * FP_NMOM, valid ? tau[c] : 1.0, prm, valid, r, y);
+      if (valid) {
+        double *yc = coeffs + c * 9;
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+          if (q == r) yc[q] = y[q];
+        if (r == 0) flags[c] = fe | (flags[c] & (FP_FLAG_RANGE | FP_FLAG_ENERGY)) | FP_FLAG_FALLBACK;
+      }
+    }
+    return;
+  }
+  for (uint32_t i = blockIdx.x * kFallbackThreads + threadIdx.x; i < cnt; i += gridDim.x * kFallbackThreads) {
     const int64_t c = list[i];
     double y[9];
     const int fe = closure_cell(mom + c * FP_NMOM, tau[c], prm, y);
@@ -446,18 +419,32 @@ int launch_mlp_forward(const fp_mlp &net, const void *x, int64_t n, int standard
   return 0;
 }
 
-void launch_surrogate_tail(const float *tpred, const double *mom, const double *tau, int64_t n, double eps2_hat,
-                           double energy_tol, const fp_params &p, int prec, double *coeffs, int32_t *flags,
-                           int32_t *list, uint32_t *count, cudaStream_t st) {
-  const int64_t blocks = (n + 255) / 256;
-  surrogate_epilogue_kernel<<<(unsigned)blocks, 256, 0, st>>>(tpred, mom, tau, n, (float)eps2_hat,
-                                                               (float)energy_tol, coeffs, flags);
+int launch_closure_surrogate_tc(const MlpDev &net, const FusedIO &io, int64_t n, int lite, cudaStream_t st);
+
+// The learned closure on full inputs: one fused kernel (inputs, network,
+// coefficients, checks, fallback list), then the exact closure on the listed
+// cells.  Returns -1 if the shared-memory limit could not be raised.
+int launch_closure_surrogate(const fp_mlp &net, const double *mom, const double *tau, int64_t n, double eps2_hat,
+                             const fp_params &p, int prec, double *coeffs, int32_t *flags, int32_t *list,
+                             uint32_t *count, cudaStream_t st) {
+  const FusedIO io{mom, tau, p.min_particles, (float)p.surr_range_margin, (float)eps2_hat, (float)p.surr_energy_tol,
+                   coeffs, flags, list, count};
   cudaMemsetAsync(count, 0, sizeof(uint32_t), st);
-  compact_kernel<<<(unsigned)blocks, 256, 0, st>>>(flags, n, list, count);
+  if (launch_closure_surrogate_tc(make_mlp_dev(net), io, n, 0, st)) return -1;
   double rtol = p.pivot_rtol;
   if (prec == FP_PREC_FP32_MOMENTS && rtol < FP_FP32_PIVOT_FLOOR) rtol = FP_FP32_PIVOT_FLOOR;
   SolveParams prm{p.eps2_hat, rtol, p.min_particles, prec == FP_PREC_FP32_MOMENTS ? FP_FP32_MIN_REGULAR : 0};
-  fallback_kernel<<<(unsigned)(mlp_sm_count() * 4), 128, 0, st>>>(list, count, mom, tau, prm, coeffs, flags);
+  // two blocks per SM: the occupancy the one-thread-per-cell path allows
+  fallback_kernel<<<(unsigned)(mlp_sm_count() * 2), kFallbackThreads, 0, st>>>(list, count, mom, tau, prm, coeffs,
+                                                                              flags);
+  return 0;
+}
+
+// The learned closure on LITE inputs: one fused kernel, no fallback list.
+int launch_closure_surrogate_lite(const fp_mlp &net, const double *lite, const double *tau, int64_t n,
+                                  const fp_params &p, double *coeffs, int32_t *flags, cudaStream_t st) {
+  const FusedIO io{lite, tau, p.min_particles, (float)p.surr_range_margin, 0.f, 0.f, coeffs, flags, nullptr, nullptr};
+  return launch_closure_surrogate_tc(make_mlp_dev(net), io, n, 1, st);
 }
 
 }  // namespace fpc

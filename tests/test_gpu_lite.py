@@ -220,9 +220,12 @@ def test_lite_argument_errors():
     s, _ = _lite_surrogate()
     lite = torch.zeros((4, L.NLITE), dtype=torch.float64, device="cuda")
     tau = torch.ones(4, dtype=torch.float64, device="cuda")
-    ws = torch.empty(16, dtype=torch.uint8, device="cuda")
+    # the fused closure needs no workspace: an empty one is accepted
+    assert api.lib().fp_surrogate_lite_workspace_bytes(4) == 0
+    s.closure_lite(lite, tau, workspace=torch.empty(0, dtype=torch.uint8, device="cuda"))
+    # a full-input network refuses LITE vectors
     with pytest.raises(api.FPError):
-        s.closure_lite(lite, tau, workspace=ws)
+        S.Surrogate(eps2_hat=1e-3, seed=1).closure_lite(lite, tau)
     with pytest.raises(api.FPError):
         api.fp_moments_lite(torch.zeros((3, 4), dtype=torch.float16, device="cuda"),
                             torch.tensor([0, 4], dtype=torch.int64, device="cuda"))
