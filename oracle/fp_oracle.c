@@ -291,17 +291,27 @@ static double inv_normal_cdf(double u) {
   return x;
 }
 
-/* The noise variates of particle p at a given step: Philox4x32-10 with key
- * (seed_lo, seed_hi) on counter (p_lo, p_hi, step_lo, step_hi); words 0..2
- * give uniforms u = (floor(w / 2^9) + 1/2) 2^-23 in (0, 1) (exact in FP32 as
- * well) and xi_k = Phi^-1(u_k), the inverse standard normal distribution
- * function.  Evaluated here in FP64. */
+/* The noise variates of particle p at a given step.  The variates of a step
+ * are one stream of 32-bit words: word j is word (j mod 4) of the
+ * Philox4x32-10 block with key (seed_lo, seed_hi) on counter
+ * (floor(j/4)_lo, floor(j/4)_hi, step_lo, step_hi), and particle p takes words
+ * 3p, 3p + 1, 3p + 2 (four consecutive particles use three whole blocks).
+ * A word w gives the uniform u = (floor(w / 2^9) + 1/2) 2^-23 in (0, 1)
+ * (exact in FP32 as well) and xi = Phi^-1(u), the inverse standard normal
+ * distribution function.  Evaluated here in FP64. */
 static void particle_normals(uint64_t seed, uint64_t step, uint64_t p, double xi[3]) {
-  uint32_t ctr[4] = {(uint32_t)p, (uint32_t)(p >> 32), (uint32_t)step, (uint32_t)(step >> 32)};
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint64_t have = ~(uint64_t)0;  /* the block whose words w holds */
   uint32_t w[4];
-  oracle_philox4x32_10(ctr, key, w);
-  for (int i = 0; i < 3; ++i) xi[i] = inv_normal_cdf(((double)(w[i] >> 9) + 0.5) * (1.0 / 8388608.0));
+  for (int i = 0; i < 3; ++i) {
+    const uint64_t j = 3 * p + (uint64_t)i, blk = j >> 2;
+    if (blk != have) {
+      uint32_t ctr[4] = {(uint32_t)blk, (uint32_t)(blk >> 32), (uint32_t)step, (uint32_t)(step >> 32)};
+      oracle_philox4x32_10(ctr, key, w);
+      have = blk;
+    }
+    xi[i] = inv_normal_cdf(((double)(w[j & 3] >> 9) + 0.5) * (1.0 / 8388608.0));
+  }
 }
 
 int oracle_normals(int64_t n, int64_t first_index, uint64_t seed, uint64_t step, double *xi) {

@@ -84,22 +84,76 @@ __device__ __forceinline__ float normal_quantile(uint32_t w) {
   return x * p;
 }
 
-// Three standard normals for particle p at `step`: the quantiles of Philox
-// words 0..2 on the counter (p, step).
-__device__ __forceinline__ void philox_normals(const PhiloxKeys &key, uint64_t step, uint64_t p, float &x0,
-                                               float &x1, float &x2) {
-  const uint4 w = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)(p >> 32), (uint32_t)step, (uint32_t)(step >> 32)),
-                                key);
-  x0 = normal_quantile(w.x);
-  x1 = normal_quantile(w.y);
-  x2 = normal_quantile(w.z);
+// Two normals at once: the same arithmetic as normal_quantile on a pair of
+// words, with the polynomial's multiply-adds packed two to an instruction
+// (each lane of fma.rn.f32x2 rounds as fmaf does, so the results are
+// identical).
+__device__ __forceinline__ float2 normal_quantile2(uint32_t wa, uint32_t wb) {
+  const int ma = (int)((wa >> 9) << 1) + 1 - (1 << 23), mb = (int)((wb >> 9) << 1) + 1 - (1 << 23);
+  const float2 x = make_float2((float)ma * 1.1920928955078125e-07f, (float)mb * 1.1920928955078125e-07f);
+  const float2 t = __ffma2_rn(make_float2(-x.x, -x.y), x, make_float2(1.0f, 1.0f));
+  float la, lb;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(la) : "f"(t.x));
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lb) : "f"(t.y));
+  const float2 v = __fadd2_rn(make_float2(la, lb), make_float2(4.0f, 4.0f));
+  constexpr float kP[10] = {3.862574705e-10f, 4.549878529e-10f, -5.210529963e-08f, -4.056917646e-07f,
+                            2.225996695e-06f, 6.797097012e-05f, 4.802460899e-04f, -3.469289979e-03f,
+                            -2.392821312e-01f, 2.217919827e+00f};
+  float2 p = make_float2(kP[0], kP[0]);
+#pragma unroll
+  for (int i = 1; i < 10; ++i) p = __ffma2_rn(p, v, make_float2(kP[i], kP[i]));
+  if (__builtin_expect(t.x < 0.00390625f, 0)) p.x = quantile_q(sqrtf(-la) - 3.75f);
+  if (__builtin_expect(t.y < 0.00390625f, 0)) p.y = quantile_q(sqrtf(-lb) - 3.75f);
+  return __fmul2_rn(x, p);
+}
+
+// The noise of a step is one stream of Philox words: word j is word j % 4
+// of the block on counter (j / 4, step); particle g (global index) takes
+// words 3g .. 3g + 2, so the quad of particles 4Q .. 4Q + 3 takes exactly the
+// blocks 3Q .. 3Q + 2.  Its twelve normals, particle u's component k at 3u + k.
+__device__ __forceinline__ void quad_normals(const PhiloxKeys &key, uint64_t step, uint64_t Q, float (&z)[12]) {
+  uint32_t w[12];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const uint64_t blk = 3 * Q + (uint64_t)k;
+    const uint4 r = philox4x32_10(
+        make_uint4((uint32_t)blk, (uint32_t)(blk >> 32), (uint32_t)step, (uint32_t)(step >> 32)), key);
+    w[4 * k] = r.x;
+    w[4 * k + 1] = r.y;
+    w[4 * k + 2] = r.z;
+    w[4 * k + 3] = r.w;
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const float2 q = normal_quantile2(w[2 * k], w[2 * k + 1]);
+    z[2 * k] = q.x;
+    z[2 * k + 1] = q.y;
+  }
+}
+
+// four consecutive values (16-byte aligned address) in and out
+__device__ __forceinline__ void load4(const float *p, float (&x)[4]) {
+  const float4 a = *reinterpret_cast<const float4 *>(p);
+  x[0] = a.x, x[1] = a.y, x[2] = a.z, x[3] = a.w;
+}
+__device__ __forceinline__ void load4(const double *p, double (&x)[4]) {
+  const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+  x[0] = a.x, x[1] = a.y, x[2] = b.x, x[3] = b.y;
+}
+__device__ __forceinline__ void store4(float *p, const float (&x)[4]) {
+  *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
+}
+__device__ __forceinline__ void store4(double *p, const double (&x)[4]) {
+  reinterpret_cast<double2 *>(p)[0] = make_double2(x[0], x[1]);
+  reinterpret_cast<double2 *>(p)[1] = make_double2(x[2], x[3]);
 }
 
 struct VelParams {
   double dt, eps2_hat;
   uint64_t step;
-  uint64_t particle_offset;  // Philox counter of particle i: particle_offset + i
+  uint64_t particle_offset;  // global index of particle i (its Philox words): particle_offset + i
   PhiloxKeys key;
+  int vec;  // 16-byte loads and stores of whole quads (aligned arrays, n_p and particle_offset multiples of 4)
 };
 
 template <typename T>
@@ -149,12 +203,41 @@ __device__ __forceinline__ void cell_drift_averages(const T (&vals)[kVConst], co
        T(2) * e2 * (gz - T(3) * th * gb);
 }
 
+// The first cell c in [0, n] with off[c] >= t (off nondecreasing, off[n] >=
+// t), found by the 16 lanes of the calling half warp together: each round
+// probes 16 evenly spaced offsets and keeps the interval where the answer
+// lies, so 2^17 cells take five dependent loads.
+__device__ __forceinline__ int64_t lower_bound16(const int64_t *__restrict__ off, int64_t n, int64_t t, int lane) {
+  const int h = lane & 15;
+  const unsigned hmask = 0xffffu << (lane & 16);
+  int64_t lo = 0, hi = n;  // the answer lies in [lo, hi]
+  while (hi - lo > 15) {
+    const int64_t step = (hi - lo + 15) / 16;
+    const int64_t c = min(lo + step * h, hi);
+    const unsigned b = (__ballot_sync(hmask, off[c] >= t) >> (lane & 16)) & 0xffffu;
+    if (b == 0) {
+      lo = min(lo + step * 15, hi) + 1;
+    } else {
+      const int f = __ffs(b) - 1;
+      if (f == 0) {
+        hi = lo;
+      } else {
+        hi = min(lo + step * f, hi);
+        lo = lo + step * (f - 1) + 1;
+      }
+    }
+  }
+  const int64_t c = min(lo + h, hi);
+  const unsigned b = (__ballot_sync(hmask, off[c] >= t) >> (lane & 16)) & 0xffffu;
+  return lo + (__ffs(b) - 1);
+}
+
 // With kOnePass the cell averages <N.N> and <M'.N> come from the moments (and
 // m6 = <|c|^6>) in closed form, so the particles are read once.  With kLite
 // the moment vectors are LITE vectors (FP_NLITE: U, theta, b_i stored
 // directly), and the averages come from a pass over the particles.
 template <typename VT, bool kOnePass, bool kLite = false>
-__global__ void __launch_bounds__(32 * kVWarps, sizeof(VT) == 4 ? 4 : 2) velocity_kernel(const VT *v, VT *vout, int64_t np,
+__global__ void __launch_bounds__(32 * kVWarps, sizeof(VT) == 4 ? 3 : 2) velocity_kernel(const VT *v, VT *vout, int64_t np,
                                                                 const int64_t *__restrict__ off, int64_t n_cells,
                                                                 const double *__restrict__ mom,
                                                                 const double *__restrict__ m6,
@@ -175,10 +258,27 @@ __global__ void __launch_bounds__(32 * kVWarps, sizeof(VT) == 4 ? 4 : 2) velocit
   VT *wx = vout, *wy = vout + np, *wz = vout + 2 * np;
   T(*tab)[kVConst] = table[wib];
 
-  for (int64_t base = warp * kVCells; base < n_cells; base += nwarps * kVCells) {
+  // ---- this warp's share: an equal slice [tA, tB) of the particles.  It
+  //      owns the cells that start in it (those write alpha and the flags);
+  //      with kOnePass it also takes the tail of the cell that straddles tA
+  //      (alpha comes from the moments, so a cell may be shared), otherwise
+  //      the slice is widened to whole cells. ----
+  const int64_t base0 = off[0], total = off[n_cells] - base0;
+  auto slice = [&](int64_t k) {  // base0 + floor(total k / nwarps), exactly
+    return base0 + (total / nwarps) * k + (total % nwarps) * k / nwarps;
+  };
+  const int64_t tA = slice(warp), tB = slice(warp + 1);
+  const int64_t Lx = lower_bound16(off, n_cells, lane < 16 ? tA : tB, lane);
+  const int64_t La = __shfl_sync(0xffffffffu, Lx, 0);
+  const int64_t cb = warp + 1 == nwarps ? n_cells : __shfl_sync(0xffffffffu, Lx, 16);
+  const int64_t ca = kOnePass && La > 0 && La <= n_cells && off[La] > tA ? La - 1 : La;
+  const int64_t Pa = kOnePass ? tA : off[La], Pb = kOnePass ? tB : off[cb];
+
+  for (int64_t base = ca; base < cb; base += kVCells) {
     const int64_t c = base + g;
-    const bool valid = c < n_cells;
-    const int64_t cc = valid ? c : n_cells;
+    const bool valid = c < cb;
+    const bool owned = valid && c >= La;
+    const int64_t cc = valid ? c : cb;
     const int64_t a0 = off[cc];
     const int64_t e = valid ? off[c + 1] : a0;
     const int fl = valid ? flags[c] : FP_FLAG_FEW;
@@ -268,11 +368,13 @@ __global__ void __launch_bounds__(32 * kVWarps, sizeof(VT) == 4 ? 4 : 2) velocit
     }
     // the warp's contiguous particle range and the inner boundaries,
     // relative to its first particle
-    const int64_t o0 = __shfl_sync(0xffffffffu, a0, 0);
-    const int i1 = (int)(__shfl_sync(0xffffffffu, a0, 8) - o0);
-    const int i2 = (int)(__shfl_sync(0xffffffffu, a0, 16) - o0);
-    const int i3 = (int)(__shfl_sync(0xffffffffu, a0, 24) - o0);
-    const int i4 = (int)(__shfl_sync(0xffffffffu, e, 24) - o0);
+    // (clipped to the warp's slice [Pa, Pb))
+    const int64_t o0 = max(__shfl_sync(0xffffffffu, a0, 0), Pa);
+    const int64_t oe = min(__shfl_sync(0xffffffffu, e, 24), Pb);
+    const int i4 = (int)max(oe - o0, (int64_t)0);
+    const int i1 = (int)min(max(__shfl_sync(0xffffffffu, a0, 8) - o0, (int64_t)0), (int64_t)i4);
+    const int i2 = (int)min(max(__shfl_sync(0xffffffffu, a0, 16) - o0, (int64_t)0), (int64_t)i4);
+    const int i3 = (int)min(max(__shfl_sync(0xffffffffu, a0, 24) - o0, (int64_t)0), (int64_t)i4);
     const VT *px = vx + o0, *py = vy + o0, *pz = vz + o0;
     VT *ox = wx + o0, *oy = wy + o0, *oz = wz + o0;
     __syncwarp();
@@ -341,52 +443,85 @@ __global__ void __launch_bounds__(32 * kVWarps, sizeof(VT) == 4 ? 4 : 2) velocit
       __syncwarp();
       if (lg == 0) {
         tab[g][VIA] = T(1) / alpha;
-        if (valid) {
+        if (owned) {
           flags[c] = flo;
           if (alpha_out) alpha_out[c] = (double)alpha;
         }
       }
     }
     __syncwarp();
-    // ---- pass 2: the update (kVBatch particles per lane per round; the
-    //      loads go first, since the stores may alias later loads as far
-    //      as the compiler can tell) ----
-    for (int q0 = lane; q0 < i4; q0 += 32 * kVBatch) {
-      T mx[kVBatch], my[kVBatch], mz[kVBatch];
+    // ---- pass 2: the update.  Lane l takes the quads Qs + l, Qs + l + 32, ..
+    //      (quad Q = global particles 4Q .. 4Q + 3, the unit of the Philox
+    //      stream); the quads at the ends of the range are partly masked.
+    //      Loads go before stores, since the stores may alias later loads as
+    //      far as the compiler can tell. ----
+    const uint64_t g0 = prm.particle_offset + (uint64_t)o0;  // global index of the range's first particle
+    const uint64_t Qs = g0 >> 2, Qe = i4 > 0 ? (g0 + (uint64_t)i4 + 3) >> 2 : Qs;
+    for (uint64_t Q = Qs + (uint64_t)lane; Q < Qe; Q += 32) {
+      const int qb = (int)((int64_t)(Q << 2) - (int64_t)g0);  // range index of the quad's first particle
+      const bool whole = prm.vec && qb >= 0 && qb + 4 <= i4;
+      T mx[4], my[4], mz[4];
+      if (whole) {
+        load4(px + qb, mx);
+        load4(py + qb, my);
+        load4(pz + qb, mz);
+      } else {
 #pragma unroll
-      for (int u = 0; u < kVBatch; ++u) {
-        const int q = min(q0 + 32 * u, i4 - 1);
-        mx[u] = px[q];
-        my[u] = py[q];
-        mz[u] = pz[q];
+        for (int u = 0; u < 4; ++u) {
+          const int q = qb + u;
+          mx[u] = my[u] = mz[u] = T(0);
+          if ((unsigned)q < (unsigned)i4) {
+            mx[u] = px[q];
+            my[u] = py[q];
+            mz[u] = pz[q];
+          }
+        }
+      }
+      T z[12];
+      if (xi) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = qb + u;
+          const bool in = q >= 0 && q < i4;
+          const int64_t p = o0 + (in ? q : 0);
+          z[3 * u] = in ? xi[p] : T(0);
+          z[3 * u + 1] = in ? xi[np + p] : T(0);
+          z[3 * u + 2] = in ? xi[2 * np + p] : T(0);
+        }
+      } else {
+        float f[12];
+        quad_normals(prm.key, prm.step, Q, f);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) z[k] = f[k];
       }
 #pragma unroll
-      for (int u = 0; u < kVBatch; ++u) {
-        const int q = q0 + 32 * u;
-        if (q < i4) {
-          const int cl = (q >= i1) + (q >= i2) + (q >= i3);
-          T K[kVConst];
-          load_row(tab[cl], K);
-          const T m0 = mx[u] - K[VU0], m1 = my[u] - K[VU1], m2 = mz[u] - K[VU2];
-          T n0 = 0, n1 = 0, n2 = 0;
-          if (K[VLIN] == T(0)) drift(K, m0, m1, m2, n0, n1, n2);
-          const int64_t p = o0 + q;
-          T x0, x1, x2;
-          if (xi) {
-            x0 = xi[p];
-            x1 = xi[np + p];
-            x2 = xi[2 * np + p];
-          } else {
-            float f0, f1, f2;
-            philox_normals(prm.key, prm.step, prm.particle_offset + (uint64_t)p, f0, f1, f2);
-            x0 = f0;
-            x1 = f1;
-            x2 = f2;
+      for (int u = 0; u < 4; ++u) {
+        // (particles outside the range are computed on zeros and not stored)
+        const int q = qb + u;
+        const int cl = (q >= i1) + (q >= i2) + (q >= i3);
+        T K[kVConst];
+        load_row(tab[cl], K);
+        const T m0 = mx[u] - K[VU0], m1 = my[u] - K[VU1], m2 = mz[u] - K[VU2];
+        T n0 = 0, n1 = 0, n2 = 0;
+        if (K[VLIN] == T(0)) drift(K, m0, m1, m2, n0, n1, n2);
+        const T a = K[VA], df = K[VDRIFT], nz = K[VNOISE], ia = K[VIA];
+        mx[u] = (m0 * a + df * n0 + nz * z[3 * u]) * ia + K[VU0];
+        my[u] = (m1 * a + df * n1 + nz * z[3 * u + 1]) * ia + K[VU1];
+        mz[u] = (m2 * a + df * n2 + nz * z[3 * u + 2]) * ia + K[VU2];
+      }
+      if (whole) {
+        store4(ox + qb, mx);
+        store4(oy + qb, my);
+        store4(oz + qb, mz);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = qb + u;
+          if ((unsigned)q < (unsigned)i4) {
+            ox[q] = mx[u];
+            oy[q] = my[u];
+            oz[q] = mz[u];
           }
-          const T a = K[VA], df = K[VDRIFT], nz = K[VNOISE], ia = K[VIA];
-          ox[q] = (m0 * a + df * n0 + nz * x0) * ia + K[VU0];
-          oy[q] = (m1 * a + df * n1 + nz * x1) * ia + K[VU1];
-          oz[q] = (m2 * a + df * n2 + nz * x2) * ia + K[VU2];
         }
       }
     }
@@ -394,8 +529,223 @@ __global__ void __launch_bounds__(32 * kVWarps, sizeof(VT) == 4 ? 4 : 2) velocit
   }
 }
 
-static VelParams make_vel_params(double dt, double eps2_hat, uint64_t seed, uint64_t step, uint64_t poff) {
-  return VelParams{dt, eps2_hat, step, poff, philox_keys(seed)};
+// ---------------------------------------------------------------------------
+// One-pass update in chunks of 32 cells
+// ---------------------------------------------------------------------------
+// The constants of one cell (the table row of velocity_kernel) and alpha,
+// computed by one lane from the FP64 moments, coefficients, tau and <|c|^6>
+// (each entry narrowed once to T), with <N.N> and <M'.N> in closed form.
+// flo: the cell's flags with FP_FLAG_ALPHA where alpha^2 is not a positive
+// finite number (then alpha = 1).
+template <typename T>
+__device__ __forceinline__ void cell_constants(const double *__restrict__ mc, const double *__restrict__ yc,
+                                               double tc_d, double m6_d, int fl, int n, const VelParams &prm,
+                                               T (&vals)[kVConst], T &alpha, int &flo) {
+  const bool linear = (fl & (FP_FLAG_FEW | FP_FLAG_SINGULAR | FP_FLAG_NONFINITE)) != 0;
+  const T th = (T)mc[kTheta], tc = (T)tc_d;
+  T u3[10], y[9];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) u3[q] = (T)mc[kU3 + q];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) y[q] = (T)yc[q];
+  const T itau = T(1) / tc;
+  const T x = T(prm.dt) * itau;
+  T one_m_a, a;
+  if (sizeof(T) == 4) {
+    one_m_a = -expm1f((float)-x);
+    a = expf((float)-x);
+  } else {
+    one_m_a = -expm1(-(double)x);
+    a = exp(-(double)x);
+  }
+  // b_i = u_ikk from the third moments 111,112,113,122,123,133,222,223,233,333
+  const T v[kVConst] = {(T)mc[kU], (T)mc[kU + 1], (T)mc[kU + 2], th,
+                        u3[0] + u3[3] + u3[5], u3[1] + u3[6] + u3[8], u3[2] + u3[7] + u3[9],
+                        y[0] + itau, y[1], y[2], y[3] + itau, y[4], y[5] + itau,
+                        y[6], y[7], y[8],
+                        T(prm.eps2_hat) / (tc * th), a, one_m_a * tc, sqrt(th * one_m_a * (T(1) + a)),
+                        T(1), linear ? T(1) : T(0), one_m_a, tc};
+#pragma unroll
+  for (int q = 0; q < kVConst; ++q) vals[q] = v[q];
+  T u[6], w[6], z[3];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    u[q] = (T)mc[kU2 + q];
+    w[q] = (T)mc[kW + q];
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) z[q] = (T)mc[kZ + q];
+  T nn, mn;
+  cell_drift_averages<T>(vals, u, w, z, (T)m6_d, nn, mn);
+  flo = fl;
+  alpha = 1;
+  if (!linear && n > 0) {
+    const T alpha2 = T(1) + tc / (T(3) * th) * (tc * one_m_a * one_m_a * nn + T(2) * (a * one_m_a) * mn);
+    if (alpha2 > T(0) && alpha2 < T(INFINITY))
+      alpha = sqrt(alpha2);
+    else
+      flo |= FP_FLAG_ALPHA;
+  }
+  vals[VIA] = T(1) / alpha;
+}
+
+// One-pass velocity update (<|c|^6> given): every warp takes an equal slice
+// of the particles (the tail of a cell that straddles the slice's start
+// included; the cells that start in it are its own and write alpha and the
+// flags) and walks its cells 32 at a time: lane l builds the constants of
+// cell l of the chunk (table row in shared memory, alpha from the moments),
+// then the warp streams the chunk's particles in quads of four consecutive
+// ones (the unit of the Philox stream), finding each particle's cell among
+// the chunk's 33 offsets.  A chunk's setup latency is paid once for about
+// 32 cells' particles.
+template <typename VT>
+__global__ void __launch_bounds__(sizeof(VT) == 4 ? 256 : 128, sizeof(VT) == 4 ? 3 : 4)
+    velocity_chunk_kernel(const VT *v, VT *vout, int64_t np, const int64_t *__restrict__ off, int64_t n_cells,
+                          const double *__restrict__ mom, const double *__restrict__ m6,
+                          const double *__restrict__ coeffs, const double *__restrict__ tau, VelParams prm,
+                          const VT *__restrict__ xi, double *__restrict__ alpha_out, int32_t *__restrict__ flags) {
+  using T = VT;
+  constexpr int kW = sizeof(VT) == 4 ? 8 : 4;  // warps per block
+  __shared__ __align__(16) T table[kW][32][kVConst];
+  __shared__ int cofs[kW][33];  // the chunk's cell starts, relative to its first particle
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const VT *vx = v, *vy = v + np, *vz = v + 2 * np;
+  VT *wx = vout, *wy = vout + np, *wz = vout + 2 * np;
+  T(*tab)[kVConst] = table[wib];
+  int *co = cofs[wib];
+
+  // ---- the warp's slice [tA, tB) of the particles and its cells [ca, cb) ----
+  const int64_t base0 = off[0], total = off[n_cells] - base0;
+  auto slice = [&](int64_t k) {  // base0 + floor(total k / nwarps), exactly
+    return base0 + (total / nwarps) * k + (total % nwarps) * k / nwarps;
+  };
+  const int64_t tA = slice(warp), tB = slice(warp + 1);
+  const int64_t Lx = lower_bound16(off, n_cells, lane < 16 ? tA : tB, lane);
+  const int64_t La = __shfl_sync(0xffffffffu, Lx, 0);
+  const int64_t cb = warp + 1 == nwarps ? n_cells : __shfl_sync(0xffffffffu, Lx, 16);
+  const int64_t ca = La > 0 && off[La] > tA ? La - 1 : La;
+
+  for (int64_t cbase = ca; cbase < cb; cbase += 32) {
+    const int64_t c = cbase + lane;
+    const bool valid = c < cb;
+    const int64_t a0 = off[valid ? c : cb];
+    const int64_t a1 = valid ? off[c + 1] : a0;
+    // the chunk's particle range, clipped to the slice
+    const int64_t o0 = max(__shfl_sync(0xffffffffu, a0, 0), tA);
+    const int64_t oe = min(__shfl_sync(0xffffffffu, a1, 31), tB);
+    const int i4 = (int)max(oe - o0, (int64_t)0);
+    co[lane] = (int)min(max(a0 - o0, (int64_t)0), (int64_t)i4);
+    if (lane == 31) co[32] = i4;
+    // ---- lane's cell: constants and alpha ----
+    {
+      T vals[kVConst];
+      if (valid) {
+        T alpha;
+        int flo;
+        cell_constants<T>(mom + c * FP_NMOM, coeffs + c * 9, tau[c], m6[c], flags[c], (int)(a1 - a0), prm, vals,
+                          alpha, flo);
+        if (c >= La) {  // the cell starts in this slice: its outputs are this warp's
+          flags[c] = flo;
+          if (alpha_out) alpha_out[c] = (double)alpha;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < kVConst; ++q) vals[q] = T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < kVConst; ++q) tab[lane][q] = vals[q];
+    }
+    __syncwarp();
+    // ---- the chunk's particles, in quads ----
+    const uint64_t g0 = prm.particle_offset + (uint64_t)o0;  // global index of the chunk's first particle
+    const uint64_t Qs = g0 >> 2, Qe = i4 > 0 ? (g0 + (uint64_t)i4 + 3) >> 2 : Qs;
+    const VT *px = vx + o0, *py = vy + o0, *pz = vz + o0;
+    VT *ox = wx + o0, *oy = wy + o0, *oz = wz + o0;
+    for (uint64_t Q = Qs + (uint64_t)lane; Q < Qe; Q += 32) {
+      const int qb = (int)((int64_t)(Q << 2) - (int64_t)g0);  // chunk index of the quad's first particle
+      const bool whole = prm.vec && qb >= 0 && qb + 4 <= i4;
+      T mx[4], my[4], mz[4];
+      if (whole) {
+        load4(px + qb, mx);
+        load4(py + qb, my);
+        load4(pz + qb, mz);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = qb + u;
+          mx[u] = my[u] = mz[u] = T(0);
+          if ((unsigned)q < (unsigned)i4) {
+            mx[u] = px[q];
+            my[u] = py[q];
+            mz[u] = pz[q];
+          }
+        }
+      }
+      T z[12];
+      if (xi) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = qb + u;
+          const bool in = (unsigned)q < (unsigned)i4;
+          const int64_t p = o0 + (in ? q : 0);
+          z[3 * u] = in ? xi[p] : T(0);
+          z[3 * u + 1] = in ? xi[np + p] : T(0);
+          z[3 * u + 2] = in ? xi[2 * np + p] : T(0);
+        }
+      } else {
+        float f[12];
+        quad_normals(prm.key, prm.step, Q, f);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) z[k] = f[k];
+      }
+      // cell of the quad's first particle: the last cl with co[cl] <= max(qb, 0)
+      const int q0 = max(qb, 0);
+      int cl = 0;
+#pragma unroll
+      for (int st = 16; st >= 1; st >>= 1)
+        if (co[cl + st] <= q0) cl += st;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        // (particles outside the chunk are computed on zeros and not stored)
+        const int q = qb + u;
+        while (cl < 31 && co[cl + 1] <= q) ++cl;  // past a cell boundary (or empty cells)
+        T K[kVConst];
+        load_row(tab[cl], K);
+        const T m0 = mx[u] - K[VU0], m1 = my[u] - K[VU1], m2 = mz[u] - K[VU2];
+        T n0 = 0, n1 = 0, n2 = 0;
+        if (K[VLIN] == T(0)) drift(K, m0, m1, m2, n0, n1, n2);
+        const T a = K[VA], df = K[VDRIFT], nz = K[VNOISE], ia = K[VIA];
+        mx[u] = (m0 * a + df * n0 + nz * z[3 * u]) * ia + K[VU0];
+        my[u] = (m1 * a + df * n1 + nz * z[3 * u + 1]) * ia + K[VU1];
+        mz[u] = (m2 * a + df * n2 + nz * z[3 * u + 2]) * ia + K[VU2];
+      }
+      if (whole) {
+        store4(ox + qb, mx);
+        store4(oy + qb, my);
+        store4(oz + qb, mz);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = qb + u;
+          if ((unsigned)q < (unsigned)i4) {
+            ox[q] = mx[u];
+            oy[q] = my[u];
+            oz[q] = mz[u];
+          }
+        }
+      }
+    }
+    __syncwarp();  // the table and offsets are rewritten by the next chunk
+  }
+}
+
+static VelParams make_vel_params(double dt, double eps2_hat, uint64_t seed, uint64_t step, uint64_t poff,
+                                 const void *v, const void *v_out, int64_t np) {
+  const int vec = (uintptr_t)v % 16 == 0 && (uintptr_t)v_out % 16 == 0 && np % 4 == 0 && poff % 4 == 0;
+  return VelParams{dt, eps2_hat, step, poff, philox_keys(seed), vec};
 }
 
 static int vel_sm_count() {
@@ -409,32 +759,60 @@ static int vel_sm_count() {
   return n;
 }
 
+// A persistent grid: every warp takes an equal slice of the particles, so
+// the grid is what the SMs hold at once (fewer blocks for small problems).
+template <typename VT, bool kOnePass, bool kLite>
+static int64_t vel_blocks(int64_t n_cells) {
+  static int per_sm = 0;
+  if (!per_sm) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, velocity_kernel<VT, kOnePass, kLite>, 32 * kVWarps, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+  }
+  int64_t blocks = (int64_t)vel_sm_count() * per_sm;
+  const int64_t by_cells = (n_cells + kVWarps - 1) / kVWarps;  // about one cell per warp at least
+  if (blocks > by_cells) blocks = by_cells;
+  return blocks < 1 ? 1 : blocks;
+}
+
+template <typename VT>
+static int64_t vel_chunk_blocks(int64_t n_cells) {
+  constexpr int kW = sizeof(VT) == 4 ? 8 : 4;
+  static int per_sm = 0;
+  if (!per_sm) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, velocity_chunk_kernel<VT>, 32 * kW, 0) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+  }
+  int64_t blocks = (int64_t)vel_sm_count() * per_sm;
+  const int64_t by_cells = (n_cells + 4 * kW - 1) / (4 * kW);  // at least about four cells per warp
+  if (blocks > by_cells) blocks = by_cells;
+  return blocks < 1 ? 1 : blocks;
+}
+
 void launch_velocity(const void *v, void *v_out, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells,
                      const double *mom, const double *m6, const double *coeffs, const double *tau, double dt,
                      double eps2_hat, const void *xi, uint64_t seed, uint64_t step, uint64_t particle_offset,
                      double *alpha_out, int32_t *flags, cudaStream_t st) {
-  const VelParams prm = make_vel_params(dt, eps2_hat, seed, step, particle_offset);
+  const VelParams prm = make_vel_params(dt, eps2_hat, seed, step, particle_offset, v, v_out, np);
   const int threads = 32 * kVWarps;
-  const int64_t cells_per_block = kVWarps * kVCells;
-  int64_t blocks = (n_cells + cells_per_block - 1) / cells_per_block;
-  const int64_t cap = (int64_t)vel_sm_count() * 8;
-  if (blocks > cap) blocks = cap;
-  if (blocks < 1) blocks = 1;
 #define FP_VEL_LAUNCH(VT, ONE)                                                                                    \
-  velocity_kernel<VT, ONE><<<(unsigned)blocks, threads, 0, st>>>((const VT *)v, (VT *)v_out, np, off, n_cells, mom, \
-                                                                 m6, coeffs, tau, prm, (const VT *)xi, alpha_out,  \
-                                                                 flags)
-  if (v_dtype == FP_V_F32) {
-    if (m6)
-      FP_VEL_LAUNCH(float, true);
-    else
-      FP_VEL_LAUNCH(float, false);
-  } else {
-    if (m6)
-      FP_VEL_LAUNCH(double, true);
-    else
-      FP_VEL_LAUNCH(double, false);
-  }
+  velocity_kernel<VT, ONE><<<(unsigned)vel_blocks<VT, ONE, false>(n_cells), threads, 0, st>>>(                    \
+      (const VT *)v, (VT *)v_out, np, off, n_cells, mom, m6, coeffs, tau, prm, (const VT *)xi, alpha_out, flags)
+  // with <|c|^6> alpha comes from the moments: the chunked one-pass kernel
+  if (m6 && v_dtype == FP_V_F32)
+    velocity_chunk_kernel<float><<<(unsigned)vel_chunk_blocks<float>(n_cells), 256, 0, st>>>(
+        (const float *)v, (float *)v_out, np, off, n_cells, mom, m6, coeffs, tau, prm, (const float *)xi, alpha_out,
+        flags);
+  else if (m6)
+    velocity_chunk_kernel<double><<<(unsigned)vel_chunk_blocks<double>(n_cells), 128, 0, st>>>(
+        (const double *)v, (double *)v_out, np, off, n_cells, mom, m6, coeffs, tau, prm, (const double *)xi,
+        alpha_out, flags);
+  else if (v_dtype == FP_V_F32)
+    FP_VEL_LAUNCH(float, false);
+  else
+    FP_VEL_LAUNCH(double, false);
 #undef FP_VEL_LAUNCH
 }
 
@@ -444,19 +822,14 @@ void launch_velocity_lite(const void *v, void *v_out, int v_dtype, int64_t np, c
                           const double *lite, const double *coeffs, const double *tau, double dt, double eps2_hat,
                           const void *xi, uint64_t seed, uint64_t step, uint64_t particle_offset,
                           double *alpha_out, int32_t *flags, cudaStream_t st) {
-  const VelParams prm = make_vel_params(dt, eps2_hat, seed, step, particle_offset);
+  const VelParams prm = make_vel_params(dt, eps2_hat, seed, step, particle_offset, v, v_out, np);
   const int threads = 32 * kVWarps;
-  const int64_t cells_per_block = kVWarps * kVCells;
-  int64_t blocks = (n_cells + cells_per_block - 1) / cells_per_block;
-  const int64_t cap = (int64_t)vel_sm_count() * 8;
-  if (blocks > cap) blocks = cap;
-  if (blocks < 1) blocks = 1;
   if (v_dtype == FP_V_F32)
-    velocity_kernel<float, false, true><<<(unsigned)blocks, threads, 0, st>>>(
+    velocity_kernel<float, false, true><<<(unsigned)vel_blocks<float, false, true>(n_cells), threads, 0, st>>>(
         (const float *)v, (float *)v_out, np, off, n_cells, lite, nullptr, coeffs, tau, prm, (const float *)xi,
         alpha_out, flags);
   else
-    velocity_kernel<double, false, true><<<(unsigned)blocks, threads, 0, st>>>(
+    velocity_kernel<double, false, true><<<(unsigned)vel_blocks<double, false, true>(n_cells), threads, 0, st>>>(
         (const double *)v, (double *)v_out, np, off, n_cells, lite, nullptr, coeffs, tau, prm, (const double *)xi,
         alpha_out, flags);
 }

@@ -64,18 +64,26 @@ def test_philox_known_answers():
 
 
 def test_normals_are_the_inverse_distribution_of_the_philox_words():
-    """xi_k = Phi^-1(u_k), u_k = (floor(w_k / 2^9) + 1/2) 2^-23 from Philox
-    words 0..2 (the published known answers pin the words); Phi^-1 checked
-    against scipy's ndtri and against tabulated quantiles."""
+    """xi_k of particle p = Phi^-1(u), u = (floor(w / 2^9) + 1/2) 2^-23 of
+    word j = 3p + k of the step's Philox stream (word j % 4 of the block on
+    counter j // 4; the published known answers pin the blocks); Phi^-1
+    checked against scipy's ndtri and against tabulated quantiles.  Particles
+    1000..1007 span blocks 750..755, two of them split between blocks."""
     from scipy.special import ndtri
     seed, step = 0x0123456789ABCDEF, 0x1122334455667788
-    xi = O.normals(6, seed, step, first_index=1000)
-    for k in range(6):
+    xi = O.normals(8, seed, step, first_index=1000)
+    blocks = {}
+    for k in range(8):
         p = 1000 + k
-        w = O.philox4x32_10([p & 0xFFFFFFFF, p >> 32, step & 0xFFFFFFFF, step >> 32],
-                            [seed & 0xFFFFFFFF, seed >> 32])
-        u = (np.array([int(x) >> 9 for x in w[:3]], dtype=np.float64) + 0.5) * 2.0 ** -23
-        np.testing.assert_allclose(xi[:, k], ndtri(u), rtol=1e-12, atol=1e-13)
+        for i in range(3):
+            j = 3 * p + i
+            b = j // 4
+            if b not in blocks:
+                blocks[b] = O.philox4x32_10([b & 0xFFFFFFFF, b >> 32, step & 0xFFFFFFFF, step >> 32],
+                                            [seed & 0xFFFFFFFF, seed >> 32])
+            u = ((int(blocks[b][j % 4]) >> 9) + 0.5) * 2.0 ** -23
+            np.testing.assert_allclose(xi[i, k], ndtri(u), rtol=1e-12, atol=1e-13)
+    assert sorted(blocks) == list(range(750, 756))
     # the map through the oracle at tabulated points: Phi^-1(0.975) = 1.959963984540054,
     # Phi^-1(0.5) = 0, Phi(1) = 0.8413447460685429; the extreme uniforms
     for u, x in [(0.975, 1.959963984540054), (0.025, -1.959963984540054), (0.5, 0.0),

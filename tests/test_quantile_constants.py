@@ -52,14 +52,15 @@ def _kernel_quantile(w):
 
 
 def test_kernel_quantile_matches_the_oracle_inverse():
-    n, seed, step = 200_000, 4242, 9
-    ctr = np.zeros((n, 4), dtype=np.uint64)
-    p = np.arange(n, dtype=np.uint64)
-    ctr[:, 0], ctr[:, 1], ctr[:, 2], ctr[:, 3] = p & 0xFFFFFFFF, p >> 32, step, 0
-    words = OM.philox4x32_10(ctr, (seed & 0xFFFFFFFF, seed >> 32))
-    xi = O.normals(n, seed, step)  # [3, n], the oracle's FP64 quantiles of words 0..2
+    n, seed, step = 200_000, 4242, 9  # n particles: 3n words, 3n / 4 Philox blocks
+    nb = 3 * n // 4
+    ctr = np.zeros((nb, 4), dtype=np.uint64)
+    b = np.arange(nb, dtype=np.uint64)
+    ctr[:, 0], ctr[:, 1], ctr[:, 2], ctr[:, 3] = b & 0xFFFFFFFF, b >> 32, step, 0
+    words = OM.philox4x32_10(ctr, (seed & 0xFFFFFFFF, seed >> 32)).reshape(-1)  # the stream, word j of block j // 4
+    xi = O.normals(n, seed, step)  # [3, n], the oracle's FP64 quantiles of words 3p + k
     for k in range(3):
-        z = _kernel_quantile(words[:, k].astype(np.uint64))
+        z = _kernel_quantile(words[3 * np.arange(n) + k].astype(np.uint64))
         err = np.abs(z - xi[k])
         assert err.max() <= 1.0e-6, (k, err.max())
         assert (err / np.abs(xi[k])).max() <= 3.0e-7
