@@ -2,21 +2,25 @@
 // (paper Sec. 3.9-3.10: Eq. update_vel with N from Eq. update_N and the
 // energy factor alpha of Eq. update_alpha) for sm_103a.
 //
-// A warp takes four consecutive cells, whose particles are one contiguous
-// range, and walks that range with all 32 lanes (a lane's cell is found by
-// comparing its particle index with the three inner offsets):
-//   pass 1  <N.N> and <M'.N> per cell (four accumulator pairs per lane, one
-//           warp reduction) -> alpha;
-//   pass 2  M^{n+1} = (M' a + (1-a) tau N + sqrt(theta (1-a^2)) xi) / alpha + U,
-//           written in place or to a separate output array.
-// The per-cell constants (U, theta, b, C + I/tau, G, eps^2, a, (1-a) tau, the
-// noise amplitude, 1/alpha) are built once per cell by an 8-lane group from
-// the FP64 moments and coefficients -- one FP64 conversion per constant --
-// and kept in a shared-memory table read as float4.  FP32 velocities are
-// updated in FP32 arithmetic, FP64 velocities in FP64.
-// Noise: the caller's variates, or Philox4x32-10 keyed by the seed on the
-// counter (particle index, step), mapped to normals by the inverse normal
-// distribution function in FP32 (normal_quantile).
+//   M^{n+1} = (M' a + (1-a) tau N + sqrt(theta (1-a^2)) xi) / alpha + U,
+// written in place or to a separate output array.  FP32 velocities are
+// updated in FP32 arithmetic, FP64 velocities in FP64.  The per-cell
+// constants (U, theta, b, C + I/tau, G, eps^2, a, (1-a) tau, the noise
+// amplitude, 1/alpha) live in a shared-memory table read as float4.
+//
+// One pass (with <|c|^6>: velocity_chunk_kernel): alpha comes from the
+// moments in closed form.  Every warp of a persistent grid takes an equal
+// slice of the particles and walks its cells 32 at a time: each lane builds
+// one cell's constants and alpha, then the warp streams the chunk's
+// particles.  Two passes (velocity_kernel: no <|c|^6>, or LITE vectors): a
+// warp takes whole cells, four at a time (an 8-lane group per cell builds
+// its constants), sums <N.N> and <M'.N> over the particles, then updates.
+// Both stream particles in quads of four consecutive ones per lane, with
+// vector loads and stores where the arrays' alignment allows.
+// Noise: the caller's variates, or one Philox4x32-10 word stream per step
+// (keyed by the seed; particle g takes words 3g .. 3g + 2) mapped to normals
+// by the inverse normal distribution function in FP32 (normal_quantile).
+#include <climits>
 #include <cstdint>
 
 #include "fp_device.cuh"
@@ -42,45 +46,42 @@ enum { VU0 = 0, VU1, VU2, VTH, VB0, VB1, VB2, VC00, VC01, VC02, VC11, VC12, VC22
 // evaluates this FP32 arithmetic for all 2^23 words: |dz| <= 1.3e-6 and
 // |dz| / |z| <= 3.3e-7 with lg2.approx anywhere within its error bound.
 
-// P (degree 9, in lg + 4) and Q (degree 8, in sqrt(-lg) - 3.75) by Horner's rule
-__device__ __forceinline__ float quantile_p(float v) {
-  float p = 3.862574705e-10f;
-  p = fmaf(p, v, 4.549878529e-10f);
-  p = fmaf(p, v, -5.210529963e-08f);
-  p = fmaf(p, v, -4.056917646e-07f);
-  p = fmaf(p, v, 2.225996695e-06f);
-  p = fmaf(p, v, 6.797097012e-05f);
-  p = fmaf(p, v, 4.802460899e-04f);
-  p = fmaf(p, v, -3.469289979e-03f);
-  p = fmaf(p, v, -2.392821312e-01f);
-  p = fmaf(p, v, 2.217919827e+00f);
+// P (degree 9, in lg + 4) and Q (degree 8, in sqrt(-lg) - 3.75), leading
+// coefficient first, evaluated by Horner's rule
+__device__ constexpr float kQuantileP[10] = {3.862574705e-10f, 4.549878529e-10f, -5.210529963e-08f, -4.056917646e-07f,
+                                             2.225996695e-06f, 6.797097012e-05f, 4.802460899e-04f, -3.469289979e-03f,
+                                             -2.392821312e-01f, 2.217919827e+00f};
+__device__ constexpr float kQuantileQ[9] = {-6.398928963e-05f, -6.059690350e-05f, 6.303846603e-04f,
+                                            -1.477855956e-03f, 2.589873038e-03f, -4.353985656e-03f,
+                                            6.956293248e-03f, 1.181739330e+00f, 4.179551601e+00f};
+
+__device__ __forceinline__ float quantile_q(float v) {
+  float p = kQuantileQ[0];
+#pragma unroll
+  for (int i = 1; i < 9; ++i) p = fmaf(p, v, kQuantileQ[i]);
   return p;
 }
 
-__device__ __forceinline__ float quantile_q(float v) {
-  float p = -6.398928963e-05f;
-  p = fmaf(p, v, -6.059690350e-05f);
-  p = fmaf(p, v, 6.303846603e-04f);
-  p = fmaf(p, v, -1.477855956e-03f);
-  p = fmaf(p, v, 2.589873038e-03f);
-  p = fmaf(p, v, -4.353985656e-03f);
-  p = fmaf(p, v, 6.956293248e-03f);
-  p = fmaf(p, v, 1.181739330e+00f);
-  p = fmaf(p, v, 4.179551601e+00f);
-  return p;
+// x = (2k + 1 - 2^23) 2^-23 for k = w >> 9, from f = 1 + k 2^-23 (the bits
+// of k under the exponent of 1): x = 2 (f - 1.5) + 2^-23, every step exact
+__device__ __forceinline__ float quantile_x(uint32_t w) {
+  return fmaf(2.0f, __uint_as_float((w >> 9) | 0x3f800000u) - 1.5f, 1.1920928955078125e-07f);
 }
 
 __device__ __forceinline__ float normal_quantile(uint32_t w) {
-  const int m = (int)((w >> 9) << 1) + 1 - (1 << 23);
-  const float x = (float)m * 1.1920928955078125e-07f;  // times 2^-23, exact
-  const float t = fmaf(-x, x, 1.0f);                   // 1 - x^2 in [2^-22, 1]
+  const float x = quantile_x(w);
+  const float t = fmaf(-x, x, 1.0f);  // 1 - x^2 in [2^-22, 1]
   float lg;
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(t));
   float p;
-  if (__builtin_expect(t < 0.00390625f, 0))  // 2^-8: the tails, one word in 500
+  if (__builtin_expect(t < 0.00390625f, 0)) {  // 2^-8: the tails, one word in 500
     p = quantile_q(sqrtf(-lg) - 3.75f);
-  else
-    p = quantile_p(lg + 4.0f);
+  } else {
+    const float v = lg + 4.0f;
+    p = kQuantileP[0];
+#pragma unroll
+    for (int i = 1; i < 10; ++i) p = fmaf(p, v, kQuantileP[i]);
+  }
   return x * p;
 }
 
@@ -89,19 +90,19 @@ __device__ __forceinline__ float normal_quantile(uint32_t w) {
 // (each lane of fma.rn.f32x2 rounds as fmaf does, so the results are
 // identical).
 __device__ __forceinline__ float2 normal_quantile2(uint32_t wa, uint32_t wb) {
-  const int ma = (int)((wa >> 9) << 1) + 1 - (1 << 23), mb = (int)((wb >> 9) << 1) + 1 - (1 << 23);
-  const float2 x = make_float2((float)ma * 1.1920928955078125e-07f, (float)mb * 1.1920928955078125e-07f);
+  const float2 x = __ffma2_rn(make_float2(2.0f, 2.0f),
+                              __fadd2_rn(make_float2(__uint_as_float((wa >> 9) | 0x3f800000u),
+                                                     __uint_as_float((wb >> 9) | 0x3f800000u)),
+                                         make_float2(-1.5f, -1.5f)),
+                              make_float2(1.1920928955078125e-07f, 1.1920928955078125e-07f));
   const float2 t = __ffma2_rn(make_float2(-x.x, -x.y), x, make_float2(1.0f, 1.0f));
   float la, lb;
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(la) : "f"(t.x));
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lb) : "f"(t.y));
   const float2 v = __fadd2_rn(make_float2(la, lb), make_float2(4.0f, 4.0f));
-  constexpr float kP[10] = {3.862574705e-10f, 4.549878529e-10f, -5.210529963e-08f, -4.056917646e-07f,
-                            2.225996695e-06f, 6.797097012e-05f, 4.802460899e-04f, -3.469289979e-03f,
-                            -2.392821312e-01f, 2.217919827e+00f};
-  float2 p = make_float2(kP[0], kP[0]);
+  float2 p = make_float2(kQuantileP[0], kQuantileP[0]);
 #pragma unroll
-  for (int i = 1; i < 10; ++i) p = __ffma2_rn(p, v, make_float2(kP[i], kP[i]));
+  for (int i = 1; i < 10; ++i) p = __ffma2_rn(p, v, make_float2(kQuantileP[i], kQuantileP[i]));
   if (__builtin_expect(t.x < 0.00390625f, 0)) p.x = quantile_q(sqrtf(-la) - 3.75f);
   if (__builtin_expect(t.y < 0.00390625f, 0)) p.y = quantile_q(sqrtf(-lb) - 3.75f);
   return __fmul2_rn(x, p);
@@ -131,6 +132,13 @@ __device__ __forceinline__ void quad_normals(const PhiloxKeys &key, uint64_t ste
   }
 }
 
+// a quad of one component by its alignment class (2: one 16-byte access of
+// floats or two of doubles, 1: two 8-byte float pairs, 0: four scalars)
+template <typename T>
+__device__ __forceinline__ void load_comp(const T *p, int cls, T (&x)[4]);
+template <typename T>
+__device__ __forceinline__ void store_comp(T *p, int cls, const T (&x)[4]);
+
 // four consecutive values (16-byte aligned address) in and out
 __device__ __forceinline__ void load4(const float *p, float (&x)[4]) {
   const float4 a = *reinterpret_cast<const float4 *>(p);
@@ -148,12 +156,52 @@ __device__ __forceinline__ void store4(double *p, const double (&x)[4]) {
   reinterpret_cast<double2 *>(p)[1] = make_double2(x[2], x[3]);
 }
 
+template <>
+__device__ __forceinline__ void load_comp<float>(const float *p, int cls, float (&x)[4]) {
+  if (cls == 2) {
+    load4(p, x);
+  } else if (cls == 1) {
+    const float2 a = reinterpret_cast<const float2 *>(p)[0], b = reinterpret_cast<const float2 *>(p)[1];
+    x[0] = a.x, x[1] = a.y, x[2] = b.x, x[3] = b.y;
+  } else {
+    x[0] = p[0], x[1] = p[1], x[2] = p[2], x[3] = p[3];
+  }
+}
+template <>
+__device__ __forceinline__ void load_comp<double>(const double *p, int cls, double (&x)[4]) {
+  if (cls == 2)
+    load4(p, x);
+  else
+    x[0] = p[0], x[1] = p[1], x[2] = p[2], x[3] = p[3];
+}
+template <>
+__device__ __forceinline__ void store_comp<float>(float *p, int cls, const float (&x)[4]) {
+  if (cls == 2) {
+    store4(p, x);
+  } else if (cls == 1) {
+    reinterpret_cast<float2 *>(p)[0] = make_float2(x[0], x[1]);
+    reinterpret_cast<float2 *>(p)[1] = make_float2(x[2], x[3]);
+  } else {
+    p[0] = x[0], p[1] = x[1], p[2] = x[2], p[3] = x[3];
+  }
+}
+template <>
+__device__ __forceinline__ void store_comp<double>(double *p, int cls, const double (&x)[4]) {
+  if (cls == 2)
+    store4(p, x);
+  else
+    p[0] = x[0], p[1] = x[1], p[2] = x[2], p[3] = x[3];
+}
+
 struct VelParams {
   double dt, eps2_hat;
   uint64_t step;
   uint64_t particle_offset;  // global index of particle i (its Philox words): particle_offset + i
   PhiloxKeys key;
-  int vec;  // 16-byte loads and stores of whole quads (aligned arrays, n_p and particle_offset multiples of 4)
+  // vector loads and stores of whole quads, per component (bits 2d, 2d + 1):
+  // 2 = four values at once, 1 = two pairs, 0 = one at a time (the alignment
+  // of element 4Q - particle_offset of component d)
+  int vec;
 };
 
 template <typename T>
@@ -232,11 +280,12 @@ __device__ __forceinline__ int64_t lower_bound16(const int64_t *__restrict__ off
   return lo + (__ffs(b) - 1);
 }
 
-// With kOnePass the cell averages <N.N> and <M'.N> come from the moments (and
-// m6 = <|c|^6>) in closed form, so the particles are read once.  With kLite
-// the moment vectors are LITE vectors (FP_NLITE: U, theta, b_i stored
-// directly), and the averages come from a pass over the particles.
-template <typename VT, bool kOnePass, bool kLite = false>
+// The two-pass update: without <|c|^6> (or from LITE vectors, kLite: U,
+// theta and b_i stored directly, FP_NLITE per cell) the averages <N.N> and
+// <M'.N> of Eq. update_alpha come from a first pass over the particles, so
+// a warp takes whole cells: four at a time, the group of eight lanes of each
+// building its constants.
+template <typename VT, bool kLite = false>
 __global__ void __launch_bounds__(32 * kVWarps, sizeof(VT) == 4 ? 3 : 2) velocity_kernel(const VT *v, VT *vout, int64_t np,
                                                                 const int64_t *__restrict__ off, int64_t n_cells,
                                                                 const double *__restrict__ mom,
@@ -258,11 +307,8 @@ __global__ void __launch_bounds__(32 * kVWarps, sizeof(VT) == 4 ? 3 : 2) velocit
   VT *wx = vout, *wy = vout + np, *wz = vout + 2 * np;
   T(*tab)[kVConst] = table[wib];
 
-  // ---- this warp's share: an equal slice [tA, tB) of the particles.  It
-  //      owns the cells that start in it (those write alpha and the flags);
-  //      with kOnePass it also takes the tail of the cell that straddles tA
-  //      (alpha comes from the moments, so a cell may be shared), otherwise
-  //      the slice is widened to whole cells. ----
+  // ---- this warp's share: the cells that start in an equal slice
+  //      [tA, tB) of the particles ----
   const int64_t base0 = off[0], total = off[n_cells] - base0;
   auto slice = [&](int64_t k) {  // base0 + floor(total k / nwarps), exactly
     return base0 + (total / nwarps) * k + (total % nwarps) * k / nwarps;
@@ -271,13 +317,10 @@ __global__ void __launch_bounds__(32 * kVWarps, sizeof(VT) == 4 ? 3 : 2) velocit
   const int64_t Lx = lower_bound16(off, n_cells, lane < 16 ? tA : tB, lane);
   const int64_t La = __shfl_sync(0xffffffffu, Lx, 0);
   const int64_t cb = warp + 1 == nwarps ? n_cells : __shfl_sync(0xffffffffu, Lx, 16);
-  const int64_t ca = kOnePass && La > 0 && La <= n_cells && off[La] > tA ? La - 1 : La;
-  const int64_t Pa = kOnePass ? tA : off[La], Pb = kOnePass ? tB : off[cb];
 
-  for (int64_t base = ca; base < cb; base += kVCells) {
+  for (int64_t base = La; base < cb; base += kVCells) {
     const int64_t c = base + g;
     const bool valid = c < cb;
-    const bool owned = valid && c >= La;
     const int64_t cc = valid ? c : cb;
     const int64_t a0 = off[cc];
     const int64_t e = valid ? off[c + 1] : a0;
@@ -308,7 +351,6 @@ __global__ void __launch_bounds__(32 * kVWarps, sizeof(VT) == 4 ? 3 : 2) velocit
       return __shfl_sync(0xffffffffu, cv[slot / kVG], (lane & ~(kVG - 1)) + slot % kVG);
     };
     const bool linear = (fl & (FP_FLAG_FEW | FP_FLAG_SINGULAR | FP_FLAG_NONFINITE)) != 0;
-    T nn_mom = 0, mn_mom = 0;  // one-pass: <N.N>, <M'.N> from the moments
     {
       const T th = cst(3), tc = cst(23);
       const T itau = T(1) / tc;
@@ -333,55 +375,21 @@ __global__ void __launch_bounds__(32 * kVWarps, sizeof(VT) == 4 ? 3 : 2) velocit
 #pragma unroll
         for (int q = 0; q < kVConst; ++q) tab[g][q] = vals[q];
       }
-      if (kOnePass) {
-        // lane lg also converts u_ij (slots 0..5), w_ij (6..11), z_i (12..14)
-        // and <|c|^6> (15) as slots lg and lg + 8
-        T cw[2];
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int slot = lg + k * kVG;
-          double x = 0.0;
-          if (valid) {
-            if (slot < 6)
-              x = mom[c * FP_NMOM + kU2 + slot];
-            else if (slot < 12)
-              x = mom[c * FP_NMOM + kW + (slot - 6)];
-            else if (slot < 15)
-              x = mom[c * FP_NMOM + kZ + (slot - 12)];
-            else
-              x = m6[c];
-          }
-          cw[k] = (T)x;
-        }
-        auto cm = [&](int slot) -> T {
-          return __shfl_sync(0xffffffffu, cw[slot / kVG], (lane & ~(kVG - 1)) + slot % kVG);
-        };
-        T u[6], w[6];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-          u[q] = cm(q);
-          w[q] = cm(6 + q);
-        }
-        const T z[3] = {cm(12), cm(13), cm(14)}, m6c = cm(15);
-        cell_drift_averages<T>(vals, u, w, z, m6c, nn_mom, mn_mom);
-      }
     }
     // the warp's contiguous particle range and the inner boundaries,
     // relative to its first particle
-    // (clipped to the warp's slice [Pa, Pb))
-    const int64_t o0 = max(__shfl_sync(0xffffffffu, a0, 0), Pa);
-    const int64_t oe = min(__shfl_sync(0xffffffffu, e, 24), Pb);
-    const int i4 = (int)max(oe - o0, (int64_t)0);
-    const int i1 = (int)min(max(__shfl_sync(0xffffffffu, a0, 8) - o0, (int64_t)0), (int64_t)i4);
-    const int i2 = (int)min(max(__shfl_sync(0xffffffffu, a0, 16) - o0, (int64_t)0), (int64_t)i4);
-    const int i3 = (int)min(max(__shfl_sync(0xffffffffu, a0, 24) - o0, (int64_t)0), (int64_t)i4);
+    const int64_t o0 = __shfl_sync(0xffffffffu, a0, 0);
+    const int i1 = (int)(__shfl_sync(0xffffffffu, a0, 8) - o0);
+    const int i2 = (int)(__shfl_sync(0xffffffffu, a0, 16) - o0);
+    const int i3 = (int)(__shfl_sync(0xffffffffu, a0, 24) - o0);
+    const int i4 = (int)(__shfl_sync(0xffffffffu, e, 24) - o0);
     const VT *px = vx + o0, *py = vy + o0, *pz = vz + o0;
     VT *ox = wx + o0, *oy = wy + o0, *oz = wz + o0;
     __syncwarp();
     // ---- pass 1: <N.N>, <M'.N> per cell ----
     const unsigned nonlin = __ballot_sync(0xffffffffu, !linear && n > 0 && lg == 0);
     T s_nn[kVCells] = {}, s_mn[kVCells] = {};
-    if (!kOnePass && nonlin) {
+    if (nonlin) {
       // kVBatch particles per lane per round, all loads issued first
       for (int q0 = lane; q0 < i4; q0 += 32 * kVBatch) {
         T mx[kVBatch], my[kVBatch], mz[kVBatch];
@@ -433,7 +441,7 @@ __global__ void __launch_bounds__(32 * kVWarps, sizeof(VT) == 4 ? 3 : 2) velocit
       if (valid && !linear && n > 0) {
         const T inv_n = T(1) / T(n);
         const T th = tab[g][VTH], tc = tab[g][VTAU], a = tab[g][VA], om = tab[g][VOMA];
-        const T nn_avg = kOnePass ? nn_mom : snn * inv_n, mn_avg = kOnePass ? mn_mom : smn * inv_n;
+        const T nn_avg = snn * inv_n, mn_avg = smn * inv_n;
         const T alpha2 = T(1) + tc / (T(3) * th) * (tc * om * om * nn_avg + T(2) * (a * om) * mn_avg);
         if (alpha2 > T(0) && alpha2 < T(INFINITY))
           alpha = sqrt(alpha2);
@@ -443,7 +451,7 @@ __global__ void __launch_bounds__(32 * kVWarps, sizeof(VT) == 4 ? 3 : 2) velocit
       __syncwarp();
       if (lg == 0) {
         tab[g][VIA] = T(1) / alpha;
-        if (owned) {
+        if (valid) {
           flags[c] = flo;
           if (alpha_out) alpha_out[c] = (double)alpha;
         }
@@ -459,12 +467,12 @@ __global__ void __launch_bounds__(32 * kVWarps, sizeof(VT) == 4 ? 3 : 2) velocit
     const uint64_t Qs = g0 >> 2, Qe = i4 > 0 ? (g0 + (uint64_t)i4 + 3) >> 2 : Qs;
     for (uint64_t Q = Qs + (uint64_t)lane; Q < Qe; Q += 32) {
       const int qb = (int)((int64_t)(Q << 2) - (int64_t)g0);  // range index of the quad's first particle
-      const bool whole = prm.vec && qb >= 0 && qb + 4 <= i4;
+      const bool whole = qb >= 0 && qb + 4 <= i4;
       T mx[4], my[4], mz[4];
       if (whole) {
-        load4(px + qb, mx);
-        load4(py + qb, my);
-        load4(pz + qb, mz);
+        load_comp(px + qb, prm.vec & 3, mx);
+        load_comp(py + qb, (prm.vec >> 2) & 3, my);
+        load_comp(pz + qb, (prm.vec >> 4) & 3, mz);
       } else {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -510,9 +518,9 @@ __global__ void __launch_bounds__(32 * kVWarps, sizeof(VT) == 4 ? 3 : 2) velocit
         mz[u] = (m2 * a + df * n2 + nz * z[3 * u + 2]) * ia + K[VU2];
       }
       if (whole) {
-        store4(ox + qb, mx);
-        store4(oy + qb, my);
-        store4(oz + qb, mz);
+        store_comp(ox + qb, prm.vec & 3, mx);
+        store_comp(oy + qb, (prm.vec >> 2) & 3, my);
+        store_comp(oz + qb, (prm.vec >> 4) & 3, mz);
       } else {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -666,12 +674,12 @@ __global__ void __launch_bounds__(sizeof(VT) == 4 ? 256 : 128, sizeof(VT) == 4 ?
     VT *ox = wx + o0, *oy = wy + o0, *oz = wz + o0;
     for (uint64_t Q = Qs + (uint64_t)lane; Q < Qe; Q += 32) {
       const int qb = (int)((int64_t)(Q << 2) - (int64_t)g0);  // chunk index of the quad's first particle
-      const bool whole = prm.vec && qb >= 0 && qb + 4 <= i4;
+      const bool whole = qb >= 0 && qb + 4 <= i4;
       T mx[4], my[4], mz[4];
       if (whole) {
-        load4(px + qb, mx);
-        load4(py + qb, my);
-        load4(pz + qb, mz);
+        load_comp(px + qb, prm.vec & 3, mx);
+        load_comp(py + qb, (prm.vec >> 2) & 3, my);
+        load_comp(pz + qb, (prm.vec >> 4) & 3, mz);
       } else {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -707,13 +715,18 @@ __global__ void __launch_bounds__(sizeof(VT) == 4 ? 256 : 128, sizeof(VT) == 4 ?
 #pragma unroll
       for (int st = 16; st >= 1; st >>= 1)
         if (co[cl + st] <= q0) cl += st;
+      T K[kVConst];
+      load_row(tab[cl], K);
+      int next = cl < 31 ? co[cl + 1] : INT_MAX;  // where the next cell starts
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         // (particles outside the chunk are computed on zeros and not stored)
         const int q = qb + u;
-        while (cl < 31 && co[cl + 1] <= q) ++cl;  // past a cell boundary (or empty cells)
-        T K[kVConst];
-        load_row(tab[cl], K);
+        if (q >= next) {  // past a cell boundary (and any empty cells): the quad's rare case
+          while (cl < 31 && co[cl + 1] <= q) ++cl;
+          load_row(tab[cl], K);
+          next = cl < 31 ? co[cl + 1] : INT_MAX;
+        }
         const T m0 = mx[u] - K[VU0], m1 = my[u] - K[VU1], m2 = mz[u] - K[VU2];
         T n0 = 0, n1 = 0, n2 = 0;
         if (K[VLIN] == T(0)) drift(K, m0, m1, m2, n0, n1, n2);
@@ -723,9 +736,9 @@ __global__ void __launch_bounds__(sizeof(VT) == 4 ? 256 : 128, sizeof(VT) == 4 ?
         mz[u] = (m2 * a + df * n2 + nz * z[3 * u + 2]) * ia + K[VU2];
       }
       if (whole) {
-        store4(ox + qb, mx);
-        store4(oy + qb, my);
-        store4(oz + qb, mz);
+        store_comp(ox + qb, prm.vec & 3, mx);
+        store_comp(oy + qb, (prm.vec >> 2) & 3, my);
+        store_comp(oz + qb, (prm.vec >> 4) & 3, mz);
       } else {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -743,8 +756,19 @@ __global__ void __launch_bounds__(sizeof(VT) == 4 ? 256 : 128, sizeof(VT) == 4 ?
 }
 
 static VelParams make_vel_params(double dt, double eps2_hat, uint64_t seed, uint64_t step, uint64_t poff,
-                                 const void *v, const void *v_out, int64_t np) {
-  const int vec = (uintptr_t)v % 16 == 0 && (uintptr_t)v_out % 16 == 0 && np % 4 == 0 && poff % 4 == 0;
+                                 const void *v, const void *v_out, int64_t np, int v_dtype) {
+  int vec = 0;
+  if ((uintptr_t)v % 16 == 0 && (uintptr_t)v_out % 16 == 0) {
+    for (int d = 0; d < 3; ++d) {
+      const int e = (int)((((int64_t)d * np - (int64_t)(poff % 4)) % 4 + 4) % 4);  // element alignment
+      int cls = 0;
+      if (v_dtype == FP_V_F32)
+        cls = e == 0 ? 2 : (e == 2 ? 1 : 0);
+      else
+        cls = e % 2 == 0 ? 2 : 0;  // two 16-byte pairs cover a quad of doubles
+      vec |= cls << (2 * d);
+    }
+  }
   return VelParams{dt, eps2_hat, step, poff, philox_keys(seed), vec};
 }
 
@@ -761,11 +785,11 @@ static int vel_sm_count() {
 
 // A persistent grid: every warp takes an equal slice of the particles, so
 // the grid is what the SMs hold at once (fewer blocks for small problems).
-template <typename VT, bool kOnePass, bool kLite>
+template <typename VT, bool kLite>
 static int64_t vel_blocks(int64_t n_cells) {
   static int per_sm = 0;
   if (!per_sm) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, velocity_kernel<VT, kOnePass, kLite>, 32 * kVWarps, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, velocity_kernel<VT, kLite>, 32 * kVWarps, 0) !=
             cudaSuccess ||
         per_sm < 1)
       per_sm = 1;
@@ -795,10 +819,10 @@ void launch_velocity(const void *v, void *v_out, int v_dtype, int64_t np, const 
                      const double *mom, const double *m6, const double *coeffs, const double *tau, double dt,
                      double eps2_hat, const void *xi, uint64_t seed, uint64_t step, uint64_t particle_offset,
                      double *alpha_out, int32_t *flags, cudaStream_t st) {
-  const VelParams prm = make_vel_params(dt, eps2_hat, seed, step, particle_offset, v, v_out, np);
+  const VelParams prm = make_vel_params(dt, eps2_hat, seed, step, particle_offset, v, v_out, np, v_dtype);
   const int threads = 32 * kVWarps;
-#define FP_VEL_LAUNCH(VT, ONE)                                                                                    \
-  velocity_kernel<VT, ONE><<<(unsigned)vel_blocks<VT, ONE, false>(n_cells), threads, 0, st>>>(                    \
+#define FP_VEL_LAUNCH(VT)                                                                                         \
+  velocity_kernel<VT><<<(unsigned)vel_blocks<VT, false>(n_cells), threads, 0, st>>>(                              \
       (const VT *)v, (VT *)v_out, np, off, n_cells, mom, m6, coeffs, tau, prm, (const VT *)xi, alpha_out, flags)
   // with <|c|^6> alpha comes from the moments: the chunked one-pass kernel
   if (m6 && v_dtype == FP_V_F32)
@@ -810,9 +834,9 @@ void launch_velocity(const void *v, void *v_out, int v_dtype, int64_t np, const 
         (const double *)v, (double *)v_out, np, off, n_cells, mom, m6, coeffs, tau, prm, (const double *)xi,
         alpha_out, flags);
   else if (v_dtype == FP_V_F32)
-    FP_VEL_LAUNCH(float, false);
+    FP_VEL_LAUNCH(float);
   else
-    FP_VEL_LAUNCH(double, false);
+    FP_VEL_LAUNCH(double);
 #undef FP_VEL_LAUNCH
 }
 
@@ -822,14 +846,14 @@ void launch_velocity_lite(const void *v, void *v_out, int v_dtype, int64_t np, c
                           const double *lite, const double *coeffs, const double *tau, double dt, double eps2_hat,
                           const void *xi, uint64_t seed, uint64_t step, uint64_t particle_offset,
                           double *alpha_out, int32_t *flags, cudaStream_t st) {
-  const VelParams prm = make_vel_params(dt, eps2_hat, seed, step, particle_offset, v, v_out, np);
+  const VelParams prm = make_vel_params(dt, eps2_hat, seed, step, particle_offset, v, v_out, np, v_dtype);
   const int threads = 32 * kVWarps;
   if (v_dtype == FP_V_F32)
-    velocity_kernel<float, false, true><<<(unsigned)vel_blocks<float, false, true>(n_cells), threads, 0, st>>>(
+    velocity_kernel<float, true><<<(unsigned)vel_blocks<float, true>(n_cells), threads, 0, st>>>(
         (const float *)v, (float *)v_out, np, off, n_cells, lite, nullptr, coeffs, tau, prm, (const float *)xi,
         alpha_out, flags);
   else
-    velocity_kernel<double, false, true><<<(unsigned)vel_blocks<double, false, true>(n_cells), threads, 0, st>>>(
+    velocity_kernel<double, true><<<(unsigned)vel_blocks<double, true>(n_cells), threads, 0, st>>>(
         (const double *)v, (double *)v_out, np, off, n_cells, lite, nullptr, coeffs, tau, prm, (const double *)xi,
         alpha_out, flags);
 }

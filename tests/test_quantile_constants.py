@@ -20,12 +20,12 @@ SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), 
 
 
 def _horner_coefficients(name):
-    """Coefficients of the Horner chain `name`, constant term first."""
+    """Coefficients of the Horner array `name` (leading first in the
+    source), constant term first."""
     src = open(SRC).read()
-    body = re.search(r"float " + name + r"\(float v\) \{(.*?)\n\}", src, re.S).group(1)
-    lead = re.search(r"float p = ([-+0-9.e]+)f;", body).group(1)
-    rest = re.findall(r"p = fmaf\(p, v, ([-+0-9.e]+)f\);", body)
-    return [np.float32(c) for c in reversed([lead] + rest)]
+    body = re.search(r"constexpr float " + name + r"\[\d+\] = \{(.*?)\};", src, re.S).group(1)
+    coef = re.findall(r"([-+0-9.e]+)f", body)
+    return [np.float32(c) for c in reversed(coef)]
 
 
 def _f32(a):
@@ -40,7 +40,7 @@ def _horner32(coef, v):
 
 
 def _kernel_quantile(w):
-    P, Q = _horner_coefficients("quantile_p"), _horner_coefficients("quantile_q")
+    P, Q = _horner_coefficients("kQuantileP"), _horner_coefficients("kQuantileQ")
     assert len(P) == 10 and len(Q) == 9
     m = ((w >> 9).astype(np.int64) << 1) + 1 - (1 << 23)
     x = m * 2.0 ** -23
