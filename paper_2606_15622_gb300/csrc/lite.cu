@@ -3,8 +3,8 @@
 // computed from it, and the learned closure on those inputs.
 //
 // LITE moment vector (FP_NLITE = 14 per cell): N, U (3), theta, u_ij (6, sym
-// order 11,12,13,22,23,33), b_i = <c_i |c|^2> (3).  Its gather accumulates
-// 9 central sums a particle (the full moment vector needs 26).
+// order 11,12,13,22,23,33), b_i = <c_i |c|^2> (3).  Its one-pass tiled gather
+// accumulates 12 sums a particle (the full moment vector needs 29).
 //
 // Network inputs (16, then zero padding to 32): rho, T, U (3), Pi (6), q (3),
 // DM2, nu, read as  rho = N (the cell's particle count: proportional to the
