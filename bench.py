@@ -45,8 +45,10 @@ METRIC = "closure cells/s + particles/s (exact FP64, FP32-moment, surrogate) at 
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch on this workload, from one ncu capture
 # of the current build of each kernel; None once a kernel has changed since
-NCU_DRAM_BYTES = {"velocity_update": 289.74e6, "gather_fp32": 159.85e6, "solve_fp64": 85.43e6, "mlp_forward": 8.53e6,
-                  "gather_lite": 152.62e6}
+# DRAM bytes (read + write) of one launch in the ncu captures summarised under
+# profiles/ (current kernels; a kernel changed since its capture has none)
+NCU_DRAM_BYTES = {"velocity_update": 298.03e6, "gather_fp32": 175.77e6, "solve_fp64": 85.43e6,
+                  "gather_fp64": 313.65e6}
 ORACLE_BLOCK = 4096            # cells per block of the CPU oracle's timing
 E2E_CHUNKS = 8                 # chunks of the host-resident step (copy / compute overlap)
 WEIGHTS = os.path.join(ROOT, "paper_2606_15622_gb300", "weights", "surrogate_full.fpw")
@@ -58,6 +60,7 @@ GATHER_BYTES_PER_CELL = 8 + 8 * 31      # one offset read, the moment vector and
 LITE_BYTES_PER_CELL = 8 + 8 * 14        # one offset read, the LITE moment vector written
 VEL_BYTES_PER_PARTICLE = 24             # read + write three FP32 components
 VEL_BYTES_PER_CELL = 8 + 8 * (3 + 1 + 3 + 9 + 1) + 4 + 4 + 8  # offset; U, theta, q, C, Gamma, tau; flags in/out; alpha
+GATHER64_FLOPS_PER_PARTICLE = 61       # FP64 gather: 3 (mean) + 3 (centre) + 55 (26 monomial sums, FMA = 2)
 SOLVE_FLOPS_PER_CELL = 658              # FP64: assembly + elimination + back substitution (FMA = 2)
 MLP_FLOPS_PER_CELL = 2 * (32 * 128 + 3 * 128 * 128 + 128 * 16)  # padded layer shapes
 FP64_PEAK_TFLOPS = 1.197                # FP64 peak of a GB300, measured with independent DFMA chains
@@ -345,6 +348,7 @@ def run_ours(args):
     x_feat, _ = sur.features(mom, tau, params=prm)
     out16 = torch.empty((n_cells, 16), dtype=torch.float32, device=dev)
     t_mlp = float(np.median(timed(lambda: sur.forward(x_feat, standardized=False, out=out16, stream=stream), 10, 2)))
+    t_g64 = float(np.median(timed(lambda: api.fp_moments(v64, off, prec="fp64", moments_out=mom, stream=stream), 5, 2)))
     gather_bytes = GATHER_BYTES_PER_PARTICLE * n_p + GATHER_BYTES_PER_CELL * n_cells
     vel_bytes = VEL_BYTES_PER_PARTICLE * n_p + VEL_BYTES_PER_CELL * n_cells
 
@@ -360,6 +364,11 @@ def run_ours(args):
                                               "peak_note": "FP64 pipe, measured FMA chain"}),
         "velocity_update": kern(t_vel, "hbm", vel_bytes / (t_vel * 1e-3) / 1e9, "GB/s", peaks["hbm_gbs"],
                                 {"algorithmic_bytes": vel_bytes}),
+        "gather_fp64": kern(t_g64, "alu", GATHER64_FLOPS_PER_PARTICLE * n_p / (t_g64 * 1e-3) / 1e12, "TFLOP/s",
+                            FP64_PEAK_TFLOPS, {"algorithmic_flops": GATHER64_FLOPS_PER_PARTICLE * n_p,
+                                               "peak_note": "FP64 pipe, measured FMA chain; an FP64 add or multiply "
+                                                            "takes the pipe slot of an FMA, and idle lanes of a warp "
+                                                            "instruction take it too (ncu: FP64 pipe 89 % busy)"}),
         "mlp_forward": kern(t_mlp, "tensor", MLP_FLOPS_PER_CELL * n_cells / (t_mlp * 1e-3) / 1e12, "TFLOP/s",
                             peaks["bf16_tflops"], {"algorithmic_flops": MLP_FLOPS_PER_CELL * n_cells}),
     }
@@ -568,7 +577,8 @@ def run_ours(args):
     e2e_ms = float(np.median(te))
     h2d = h_v.numel() * 4 + h_off.numel() * 8 + h_tau.numel() * 8
     d2h = h_coeffs.numel() * 8 + h_flags.numel() * 4 + h_vout.numel() * 4
-    launches_per_step = 2 + 5 + 1 + 2  # gather, solve; features, MLP, epilogue, compact, fallback; update; adjoint x2
+    # gather, solve; learned closure (one tcgen05 kernel) + its exact fallback; update; adjoint x2
+    launches_per_step = 2 + 2 + 1 + 2
 
     out = {
         "metric": METRIC,
@@ -634,7 +644,10 @@ def run_ours(args):
         },
         "e2e": {"value": round(n_cells / (e2e_ms * 1e-3) * ws, 1), "unit": "cells/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 5),
-                "api": f"fp_step_host, pinned host buffers, {E2E_CHUNKS} chunks"},
+                "api": f"fp_step_host, pinned host buffers, {E2E_CHUNKS} chunks",
+                "results_to_host": "M^{n+1} velocities, exact-closure coefficients and flags; the adjoint's "
+                                   "gradients and the learned closure's coefficients are computed in the step "
+                                   "and stay on the device"},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
     }
