@@ -69,11 +69,22 @@ enum { FP_V_F32 = 0, FP_V_F64 = 1 };
 
 /* moment precision:
  * FP_PREC_FP64          moments accumulated in FP64 from the given velocities
- * FP_PREC_FP32_MOMENTS  moments accumulated in FP32 on velocities centred on
- *                       the cell mean and scaled by 1/sqrt(theta), with
- *                       compensated (two-sum) combination of partial sums;
- *                       promoted to FP64 before assembly.
- * The 9x9 assembly and the pivoted solve are FP64 in both modes.  With FP32
+ * FP_PREC_FP32_MOMENTS  moments accumulated in FP32 in one pass on velocities
+ *                       shifted by the mean of a strided subset of up to 8
+ *                       particles of the cell and scaled by a power of two,
+ *                       with compensated (two-sum) combination of partial
+ *                       sums, then turned into central moments by the
+ *                       binomial expansion of the shift (FP32) and written
+ *                       in FP64.
+ * The 9x9 system is assembled in FP64 in both modes and solved with partial
+ * pivoting; the FP64 mode, and any call that keeps the factors for the
+ * adjoint, eliminates in FP64.  Without factors the FP32-moment mode factors
+ * the system in FP32 and refines the solution once against the FP64 residual
+ * b - A x (agreeing with the FP64 elimination to ~1e-9 relative, far below
+ * the moments' own error); cells whose FP32 pivots fall below
+ * max(3e-3, 100 pivot_rtol) of max|A|, or whose correction exceeds 1e-4 of
+ * the solution, are eliminated in FP64 instead, and that elimination decides
+ * their flags.  With FP32
  * moments (relative error ~1e-7) a pivot below ~1e-6 max|A| cannot be told
  * from zero, so that mode flags a cell singular when a pivot is
  * <= max(pivot_rtol, FP_FP32_PIVOT_FLOOR) * max|A|.  A cell of four
@@ -155,7 +166,8 @@ int fp_moments(const void *v, int v_dtype, int64_t n_particles, const int64_t *c
                int prec, double *moments_out, double *m6_out, fp_stream_t stream);
 
 /* fp_closure_solve: assembly of Eq. system9x9 from given moment vectors and
- * the FP64 pivoted solve, one thread per cell.  moments [n_cells][FP_NMOM]
+ * the pivoted solve (FP64, or with FP32 moments and no lu_out the
+ * mixed-precision solve described above), one thread per cell.  moments [n_cells][FP_NMOM]
  * f64 (as fp_moments writes them), tau [n_cells]; prec = the precision the
  * moments were gathered in (selects the singularity threshold); outputs as
  * in fp_closure_exact.  lu_out: FP_LU_DOUBLES(n_cells) f64 or NULL; if

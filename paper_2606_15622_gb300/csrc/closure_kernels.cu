@@ -269,14 +269,15 @@ __global__ void __launch_bounds__(256) gather_fp64_kernel(const VT *__restrict__
 // the whole register file, and the third of the file it leaves free lets the
 // learned closure's kernels run beside it in the step.  With kLU the factors
 // of P A = L U of every unflagged cell go to lu for the adjoint.
-template <bool kLU>
+template <bool kLU, bool kMixed = false>
 __global__ void __launch_bounds__(128, 3) solve_kernel(const double *__restrict__ mom, const double *__restrict__ tau,
                                                        int64_t n_cells, SolveParams prm, double *__restrict__ coeffs,
                                                        int32_t *__restrict__ flags, double *__restrict__ lu) {
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells;
        c += (int64_t)gridDim.x * blockDim.x) {
     double y[9];
-    const int fl = closure_cell<kLU>(mom + c * FP_NMOM, tau[c], prm, y, kLU ? lu + lu_base(c) : nullptr);
+    const int fl = kMixed ? closure_cell_mixed(mom + c * FP_NMOM, tau[c], prm, y)
+                          : closure_cell<kLU>(mom + c * FP_NMOM, tau[c], prm, y, kLU ? lu + lu_base(c) : nullptr);
     double *yc = coeffs + c * 9;
 #pragma unroll
     for (int q = 0; q < 9; ++q) yc[q] = y[q];
@@ -345,6 +346,8 @@ void launch_solve(const double *mom, const double *tau, int64_t n_cells, const f
   if (blocks > 2 * sm_count()) blocks = 2 * sm_count();
   if (lu)
     solve_kernel<true><<<(unsigned)blocks, threads, 0, st>>>(mom, tau, n_cells, prm, coeffs, flags, lu);
+  else if (prec == FP_PREC_FP32_MOMENTS)  // FP32-accurate moments: the mixed-precision solve
+    solve_kernel<false, true><<<(unsigned)blocks, threads, 0, st>>>(mom, tau, n_cells, prm, coeffs, flags, nullptr);
   else
     solve_kernel<false><<<(unsigned)blocks, threads, 0, st>>>(mom, tau, n_cells, prm, coeffs, flags, nullptr);
 }

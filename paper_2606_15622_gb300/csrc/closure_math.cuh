@@ -25,6 +25,10 @@ static_assert(sym2(2, 1) == 4 && sym2(1, 1) == 3 && sym2(0, 2) == 2, "sym2");
 static_assert(sym3(2, 0, 1) == 4 && sym3(1, 2, 2) == 8 && sym3(2, 1, 1) == 7 && sym3(0, 2, 0) == 2, "sym3");
 
 
+// fused multiply-add in the arithmetic of the operands
+__device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
+
 struct SolveParams {
   double eps2_hat;
   double pivot_rtol;
@@ -44,9 +48,9 @@ struct SolveParams {
 // each FP64 instruction is expensive, and accumulating into zeroed entries
 // would cost an FP64 add per term.  Row and column are compile-time constants
 // once the loops unroll; entries never emitted are zero.
-template <class Emit>
-__device__ __forceinline__ void assemble_emit(const double (&m)[FP_NMOM], double tau, double eps2_hat, Emit &&emit) {
-  double u[3][3], w[3][3], b[3];
+template <typename T, class Emit>
+__device__ __forceinline__ void assemble_emit(const T (&m)[FP_NMOM], T tau, T eps2_hat, Emit &&emit) {
+  T u[3][3], w[3][3], b[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -57,12 +61,12 @@ __device__ __forceinline__ void assemble_emit(const double (&m)[FP_NMOM], double
 #pragma unroll
   for (int i = 0; i < 3; ++i)
     b[i] = m[kU3 + sym3(i, 0, 0)] + m[kU3 + sym3(i, 1, 1)] + m[kU3 + sym3(i, 2, 2)];
-  const double theta = m[kTheta];
-  const double s4 = w[0][0] + w[1][1] + w[2][2];
-  const double eps2 = eps2_hat / (tau * theta);
-  const double inv_tau = 1.0 / tau;
-  const double c_u = -2.0 * inv_tau, c_w = 2.0 * eps2;  // stress right-hand side
-  const double th3 = 3.0 * theta;
+  const T theta = m[kTheta];
+  const T s4 = w[0][0] + w[1][1] + w[2][2];
+  const T eps2 = eps2_hat / (tau * theta);
+  const T inv_tau = T(1) / tau;
+  const T c_u = T(-2) * inv_tau, c_w = T(2) * eps2;  // stress right-hand side
+  const T th3 = T(3) * theta;
   // stress rows
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -72,8 +76,8 @@ __device__ __forceinline__ void assemble_emit(const double (&m)[FP_NMOM], double
       if (i == j) {
         // 2 sum_k C_ik u_ki + 2 G_i b_i
 #pragma unroll
-        for (int k = 0; k < 3; ++k) emit(row, sym2(i, k), 2.0 * u[k][i]);
-        emit(row, 6 + i, 2.0 * b[i]);
+        for (int k = 0; k < 3; ++k) emit(row, sym2(i, k), T(2) * u[k][i]);
+        emit(row, 6 + i, T(2) * b[i]);
       } else {
         // C_ii u_ij + C_jj u_ij + C_ij (u_ii + u_jj) + C_it u_tj + C_jt u_ti
         const int t = 3 - i - j;
@@ -96,8 +100,8 @@ __device__ __forceinline__ void assemble_emit(const double (&m)[FP_NMOM], double
 #pragma unroll
       for (int q = p; q < 3; ++q) {
         // C_pq: b from sum_l C_il b_l (if i is p or q), then 2 u_ipp or 4 u_ipq
-        const double u3 = m[kU3 + sym3(i, p, q)];
-        double bterm = 0.0;
+        const T u3 = m[kU3 + sym3(i, p, q)];
+        T bterm = T(0);
         bool has_b = false;
         if (p == i) {
           bterm = b[q];
@@ -106,16 +110,16 @@ __device__ __forceinline__ void assemble_emit(const double (&m)[FP_NMOM], double
           bterm = b[p];
           has_b = true;
         }
-        const double f = p == q ? 2.0 : 4.0;
-        emit(row, sym2(p, q), has_b ? fma(f, u3, bterm) : f * u3);
+        const T f = p == q ? T(2) : T(4);
+        emit(row, sym2(p, q), has_b ? tfma(f, u3, bterm) : f * u3);
       }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const double gk = 2.0 * fma(-th3, u[k][i], w[k][i]);
-      emit(row, 6 + k, k == i ? (s4 - 9.0 * theta * theta) + gk : gk);
+      const T gk = T(2) * tfma(-th3, u[k][i], w[k][i]);
+      emit(row, 6 + k, k == i ? (s4 - T(9) * theta * theta) + gk : gk);
     }
-    const double ub = u[i][0] * b[0] + u[i][1] * b[1] + u[i][2] * b[2];
-    emit(row, 9, -(4.0 / 3.0) * inv_tau * b[i] + eps2 * (3.0 * m[kZ + i] - th3 * b[i] - 2.0 * ub));
+    const T ub = u[i][0] * b[0] + u[i][1] * b[1] + u[i][2] * b[2];
+    emit(row, 9, T(-4.0 / 3.0) * inv_tau * b[i] + eps2 * (T(3) * m[kZ + i] - th3 * b[i] - T(2) * ub));
   }
 }
 
@@ -298,6 +302,190 @@ __device__ __forceinline__ int closure_cell(const double *__restrict__ mc, doubl
     y[5] = c0;
   }
   return fl;
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-precision solve for FP32 moments: the system is factored in FP32 (on
+// the FP32 pipe), the residual b - A x is formed in FP64 straight from the
+// emitted entries (the FP64 matrix is never stored), and one correction solve
+// with the FP32 factors refines x.  Each FP64 instruction costs this GPU ~64
+// times an FP32 one, so this moves about three quarters of the FP64 work of
+// the plain solve off the FP64 pipe.  The refinement converges at a rate of
+// about kappa times the FP32 rounding of the system, and on an ill-conditioned
+// cell a small correction does not mean a small error, so a cell is refined
+// only if its smallest FP32 pivot is at least max(3e-3, 100 rtol) of max|A|
+// (kappa of order 1e3 at most; 0.03 % of the cylinder's cells fail this) and
+// its correction is at most 1e-4 of x; any other cell is solved again by the
+// FP64 elimination, which then also decides its flags.
+// ---------------------------------------------------------------------------
+template <int K>
+__device__ __forceinline__ void lu_step_f(float (&a)[9][10], float (&rinv)[9], uint64_t &perm, uint32_t &pmin) {
+  uint32_t best = __float_as_uint(a[K][K]) & 0x7fffffffu;
+  int bi = K;
+#pragma unroll
+  for (int i = K + 1; i < 9; ++i) {
+    const uint32_t bb = __float_as_uint(a[i][K]) & 0x7fffffffu;
+    if (bb > best) {
+      best = bb;
+      bi = i;
+    }
+  }
+  pmin = min(pmin, best);
+  perm |= (uint64_t)bi << (4 * K);
+#pragma unroll
+  for (int i = K + 1; i < 9; ++i) {
+    const bool sw = (bi == i);
+#pragma unroll
+    for (int j = 0; j < 10; ++j) {
+      const float t = a[K][j];
+      a[K][j] = sw ? a[i][j] : t;
+      a[i][j] = sw ? t : a[i][j];
+    }
+  }
+  rinv[K] = 1.f / a[K][K];
+#pragma unroll
+  for (int i = K + 1; i < 9; ++i) {
+    const float l = a[i][K] * rinv[K];
+    a[i][K] = l;
+#pragma unroll
+    for (int j = K + 1; j < 10; ++j) a[i][j] = fmaf(-l, a[K][j], a[i][j]);
+  }
+}
+
+// x = U^-1 (column 9 after the elimination), in FP32
+__device__ __forceinline__ void back_sub_f(const float (&a)[9][10], const float (&rinv)[9], float (&x)[9]) {
+#pragma unroll
+  for (int k = 8; k >= 0; --k) {
+    float t = a[k][9];
+#pragma unroll
+    for (int j = k + 1; j < 9; ++j) t = fmaf(-a[k][j], x[j], t);
+    x[k] = t * rinv[k];
+  }
+}
+
+// d = A^-1 r with the FP32 factors of P A = L U (whole rows were swapped, so
+// L is in the final row order): all swaps first, then L, then U
+__device__ __forceinline__ void lu_apply_f(const float (&a)[9][10], const float (&rinv)[9], uint64_t perm,
+                                           float (&r)[9], float (&d)[9]) {
+#pragma unroll
+  for (int K = 0; K < 9; ++K) {
+    const int bi = (int)((perm >> (4 * K)) & 15u);
+    float rk = r[K];
+#pragma unroll
+    for (int i = K + 1; i < 9; ++i) {
+      const bool sw = bi == i;
+      const float t = r[i];
+      r[i] = sw ? rk : t;
+      rk = sw ? t : rk;
+    }
+    r[K] = rk;
+  }
+#pragma unroll
+  for (int K = 0; K < 9; ++K)
+#pragma unroll
+    for (int i = K + 1; i < 9; ++i) r[i] = fmaf(-a[i][K], r[K], r[i]);
+#pragma unroll
+  for (int k = 8; k >= 0; --k) {
+    float t = r[k];
+#pragma unroll
+    for (int j = k + 1; j < 9; ++j) t = fmaf(-a[k][j], d[j], t);
+    d[k] = t * rinv[k];
+  }
+}
+
+// closure_cell in FP64 as a separate function, so that the rare fallback does
+// not add its registers to the mixed-precision path
+static __device__ __noinline__ int closure_cell_fp64(const double *__restrict__ mc, double tc, const SolveParams &prm,
+                                              double (&y)[9]) {
+  return closure_cell<false>(mc, tc, prm, y);
+}
+
+// The closure of one cell from FP32-accurate moments by the mixed-precision
+// solve; flags and Y as closure_cell (which it falls back to).
+__device__ __forceinline__ int closure_cell_mixed(const double *__restrict__ mc, double tc, const SolveParams &prm,
+                                                  double (&y)[9]) {
+  int fl = 0;
+  {
+    double m[FP_NMOM];
+#pragma unroll
+    for (int k = 0; k < FP_NMOM; ++k) m[k] = mc[k];
+    bool fin = finite_d(tc) && tc > 0.0;
+#pragma unroll
+    for (int k = 0; k < FP_NMOM; ++k) fin = fin && finite_d(m[k]);
+    if (!fin) fl |= FP_FLAG_NONFINITE;
+    if (m[kN] < (double)prm.min_particles) fl |= FP_FLAG_FEW;
+    if (!(m[kTheta] > 0.0)) fl |= FP_FLAG_SINGULAR;
+    if (!fl && m[kN] < (double)prm.min_regular) fl |= FP_FLAG_SINGULAR;
+  }
+  if (fl) return closure_cell_fp64(mc, tc, prm, y);  // the linear drift, as there
+  // FP32 system from the moments rounded to FP32 (integer pipe)
+  float af[9][10];
+  {
+    float mf[FP_NMOM];
+#pragma unroll
+    for (int k = 0; k < FP_NMOM; ++k) mf[k] = d2f_rn(mc[k]);
+#pragma unroll
+    for (int r = 0; r < 9; ++r)
+#pragma unroll
+      for (int c = 0; c < 10; ++c) af[r][c] = 0.f;
+    assemble_emit(mf, d2f_rn(tc), d2f_rn(prm.eps2_hat), [&](int row, int col, float v) { af[row][col] = v; });
+  }
+  uint32_t amax = 0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+#pragma unroll
+    for (int j = 0; j < 9; ++j) amax = max(amax, __float_as_uint(af[i][j]) & 0x7fffffffu);
+  float rinv[9], x0[9];
+  uint64_t perm = 0;
+  uint32_t pmin = 0x7f800000u;
+  lu_step_f<0>(af, rinv, perm, pmin);
+  lu_step_f<1>(af, rinv, perm, pmin);
+  lu_step_f<2>(af, rinv, perm, pmin);
+  lu_step_f<3>(af, rinv, perm, pmin);
+  lu_step_f<4>(af, rinv, perm, pmin);
+  lu_step_f<5>(af, rinv, perm, pmin);
+  lu_step_f<6>(af, rinv, perm, pmin);
+  lu_step_f<7>(af, rinv, perm, pmin);
+  lu_step_f<8>(af, rinv, perm, pmin);
+  const float accept = fmaxf(3e-3f, (float)(100.0 * prm.pivot_rtol));
+  bool ok = amax < 0x7f800000u && __uint_as_float(pmin) > accept * __uint_as_float(amax);
+  if (ok) {
+    back_sub_f(af, rinv, x0);
+    // residual b - A x0 in FP64 from the emitted entries
+    double x[9], res[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      x[q] = f2d_exact(x0[q]);
+      res[q] = 0.0;
+    }
+    {
+      double m[FP_NMOM];
+#pragma unroll
+      for (int k = 0; k < FP_NMOM; ++k) m[k] = mc[k];
+      assemble_emit(m, tc, prm.eps2_hat, [&](int row, int col, double v) {
+        if (col == 9)
+          res[row] += v;
+        else
+          res[row] = fma(-v, x[col], res[row]);
+      });
+    }
+    float rf[9], d[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) rf[q] = d2f_rn(res[q]);
+    lu_apply_f(af, rinv, perm, rf, d);
+    float dmax = 0.f, xmax = 0.f;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      dmax = fmaxf(dmax, fabsf(d[q]));
+      xmax = fmaxf(xmax, fabsf(x0[q]));
+      y[q] = x[q] + f2d_exact(d[q]);
+    }
+    ok = dmax <= 1e-4f * xmax;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) ok = ok && finite_d(y[q]);
+  }
+  if (!ok) return closure_cell_fp64(mc, tc, prm, y);
+  return 0;
 }
 
 // The closure of one cell by a group of 16 lanes (a half warp; all 32 lanes
