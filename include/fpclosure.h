@@ -69,13 +69,16 @@ enum { FP_V_F32 = 0, FP_V_F64 = 1 };
 
 /* moment precision:
  * FP_PREC_FP64          moments accumulated in FP64 from the given velocities
- * FP_PREC_FP32_MOMENTS  moments accumulated in FP32 in one pass on velocities
- *                       shifted by the mean of a strided subset of up to 8
- *                       particles of the cell and scaled by a power of two,
- *                       with compensated (two-sum) combination of partial
- *                       sums, then turned into central moments by the
- *                       binomial expansion of the shift (FP32) and written
- *                       in FP64.
+ * FP_PREC_FP32_MOMENTS  moments accumulated in FP32 with compensated
+ *                       (two-sum) combination of partial sums and written in
+ *                       FP64.  FP32 velocities in 16-byte aligned arrays take
+ *                       one pass: velocities shifted by the mean of a
+ *                       strided subset of up to 8 particles of the cell and
+ *                       scaled by a power of two, the shifted sums turned
+ *                       into central moments by the binomial expansion of
+ *                       the shift (FP32); other inputs take two passes
+ *                       (the cell mean, then sums centred on it and scaled
+ *                       by a power of two ~1/sqrt(theta)).
  * The 9x9 system is assembled in FP64 in both modes and solved with partial
  * pivoting; the FP64 mode, and any call that keeps the factors for the
  * adjoint, eliminates in FP64.  Without factors the FP32-moment mode factors
