@@ -57,7 +57,7 @@ int64_t mlp_param_offset(int which, int layer);
 void launch_wait_timeout(uint64_t limit_ns, int32_t *status, uint64_t *waited_ns, cudaStream_t st);
 int64_t mlp_param_count();
 size_t mlp_backward_ws(int64_t n);
-void launch_mlp_backward(const fp_mlp &net, const void *x, const void *h_save, const float *z_save,
+int launch_mlp_backward(const fp_mlp &net, const void *x, const void *h_save, const float *z_save,
                          const void *dout_bf, const float *dout, int64_t n, float *grads, void *ws, cudaStream_t st);
 void launch_loss(const float *out, const float *t_true, const float *aux, const float *y_mu, const float *y_sigma,
                  int64_t n, const float *w, float lam_d, float lam_e, float eps2_hat, float scale, float *dout,
@@ -397,7 +397,8 @@ int fp_mlp_backward(const fp_mlp *net, const void *x, const void *h_save, const 
   const size_t need = fpc::mlp_backward_ws(n);
   if (!ws || ws_bytes < need) return fail(FP_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", need, ws_bytes);
   if ((uintptr_t)ws % kAlign) return fail(FP_ERR_ARG, "workspace not 256-byte aligned");
-  fpc::launch_mlp_backward(*net, x, h_save, z_save, dout_bf16, dout, n, grads, ws, (cudaStream_t)stream);
+  if (fpc::launch_mlp_backward(*net, x, h_save, z_save, dout_bf16, dout, n, grads, ws, (cudaStream_t)stream))
+    return fail(FP_ERR_CUDA, "mlp_backward: shared-memory limit could not be raised");
   return check_launch("mlp_backward");
 }
 

@@ -1,6 +1,6 @@
 // mlp_train.cu -- training kernels of the surrogate: the loss and its
-// gradient, the backward pass (BF16 tensor-core GEMMs with FP32
-// accumulation) and Adam, for sm_103a.
+// gradient and Adam, for sm_103a (the backward pass on the tensor cores is
+// in mlp_train_tc.cu).
 //
 // Loss per cell (dimensionless targets t, prediction t' = mu + sigma o):
 //   sum_a w_a (o_a - (t_a - mu_a) / sigma_a)^2              coefficient MSE
@@ -121,127 +121,6 @@ __global__ void __launch_bounds__(256) loss_kernel(const float *__restrict__ out
   }
 }
 
-// ---------------------------------------------------------------------------
-// generic BF16 GEMM (mma.sync m16n8k16, FP32 accumulation)
-//   C(m, n) = sum_k A(m, k) B(k, n),  A(m,k) = A[m sam + k sak], B(k,n) = B[k sbk + n sbn]
-// EPI 0: FP32 partial for K-split blockIdx.z at outf + z M ldo
-// EPI 1: BF16 C(m, n) silu'(Z(m, n)) at outb (the next layer's dZ)
-// ---------------------------------------------------------------------------
-constexpr int kGT = 64, kGK = 32, kGS = kGK + 8;
-
-template <int EPI>
-__global__ void __launch_bounds__(128) gemm_kernel(int M, int N, int K, int k_chunk, const __nv_bfloat16 *__restrict__ A,
-                                                   int64_t sam, int64_t sak, const __nv_bfloat16 *__restrict__ B,
-                                                   int64_t sbk, int64_t sbn, float *__restrict__ outf,
-                                                   __nv_bfloat16 *__restrict__ outb, int64_t ldo,
-                                                   const float *__restrict__ Z, int64_t ldz) {
-  __shared__ __align__(16) __nv_bfloat16 As[kGT][kGS], Bs[kGT][kGS];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  const int m0 = blockIdx.y * kGT, n0 = blockIdx.x * kGT;
-  const int kbeg = blockIdx.z * k_chunk;
-  const int kend = min(K, kbeg + k_chunk);
-  const int wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
-  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
-  for (int kk = kbeg; kk < kend; kk += kGK) {
-    for (int e = tid; e < kGT * kGK; e += 128) {
-      int m, k;
-      if (sak == 1) {
-        m = e / kGK;
-        k = e % kGK;
-      } else {
-        k = e / kGT;
-        m = e % kGT;
-      }
-      As[m][k] = (m0 + m < M && kk + k < kend) ? A[(int64_t)(m0 + m) * sam + (int64_t)(kk + k) * sak] : zero;
-      int n2, k2;
-      if (sbn == 1) {
-        k2 = e / kGT;
-        n2 = e % kGT;
-      } else {
-        n2 = e / kGK;
-        k2 = e % kGK;
-      }
-      Bs[n2][k2] = (n0 + n2 < N && kk + k2 < kend) ? B[(int64_t)(kk + k2) * sbk + (int64_t)(n0 + n2) * sbn] : zero;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int ks = 0; ks < kGK; ks += 16) {
-      uint32_t a[2][4], b[4][2];
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        const int r = wm + mt * 16 + g;
-        a[mt][0] = *reinterpret_cast<const uint32_t *>(&As[r][ks + 2 * t]);
-        a[mt][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][ks + 2 * t]);
-        a[mt][2] = *reinterpret_cast<const uint32_t *>(&As[r][ks + 8 + 2 * t]);
-        a[mt][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][ks + 8 + 2 * t]);
-      }
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int cidx = wn + nt * 8 + g;
-        b[nt][0] = *reinterpret_cast<const uint32_t *>(&Bs[cidx][ks + 2 * t]);
-        b[nt][1] = *reinterpret_cast<const uint32_t *>(&Bs[cidx][ks + 8 + 2 * t]);
-      }
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b[nt][0], b[nt][1]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int m = m0 + wm + mt * 16 + g + 8 * h;
-        const int n = n0 + wn + nt * 8 + 2 * t;
-        if (m >= M) continue;
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          if (n + q >= N) continue;
-          const float v = acc[mt][nt][2 * h + q];
-          if (EPI == 0)
-            outf[(int64_t)blockIdx.z * M * ldo + (int64_t)m * ldo + n + q] = v;
-          else
-            outb[(int64_t)m * ldo + n + q] = __float2bfloat16_rn(v * silu_grad(Z[(int64_t)m * ldz + n + q]));
-        }
-      }
-}
-
-// out[i] = sum_z part[z][i] over nz partial products of size cnt
-__global__ void reduce_parts_kernel(const float *__restrict__ part, int nz, int64_t cnt, float *__restrict__ out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= cnt) return;
-  float s = 0.f;
-  for (int z = 0; z < nz; ++z) s += part[z * cnt + i];
-  out[i] = s;
-}
-
-// column sums of an [n][cols] matrix (FP32 accumulation)
-template <typename T>
-__global__ void colsum_kernel(const T *__restrict__ a, int64_t n, int cols, float *__restrict__ out) {
-  const int cidx = blockIdx.x;
-  float s = 0.f;
-  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) s += (float)a[r * cols + cidx];
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  __shared__ float ws[32];
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float tot = 0.f;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += ws[i];
-    out[cidx] = tot;
-  }
-}
-
 __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ gr, float *__restrict__ m,
                             float *__restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float bc1,
                             float bc2, __nv_bfloat16 *__restrict__ shadow) {
@@ -270,71 +149,18 @@ int64_t mlp_param_offset(int which, int layer) {
 }
 int64_t mlp_param_count() { return mlp_param_offset(1, 4) + kOut; }
 
-constexpr int kMaxSplit = 64;
+size_t mlp_backward_tc_ws(int64_t n);
+int launch_mlp_backward_tc(const MlpDev &net, const void *x, const void *h_save, const float *z_save,
+                           const void *dout_bf, const float *dout, int64_t n, float *grads, void *ws,
+                           cudaStream_t st);
+MlpDev make_mlp_dev(const fp_mlp &m);
 
-size_t mlp_backward_ws(int64_t n) {
-  const size_t dz = (size_t)2 * n * kHid * sizeof(__nv_bfloat16);
-  const size_t parts = (size_t)kMaxSplit * kHid * kHid * sizeof(float);
-  return ((dz + 255) / 256) * 256 + parts;
-}
+size_t mlp_backward_ws(int64_t n) { return mlp_backward_tc_ws(n); }
 
-static void gemm(int epi, int M, int N, int K, const __nv_bfloat16 *A, int64_t sam, int64_t sak,
-                 const __nv_bfloat16 *B, int64_t sbk, int64_t sbn, float *outf, __nv_bfloat16 *outb, int64_t ldo,
-                 const float *Z, int64_t ldz, int nsplit, cudaStream_t st) {
-  int k_chunk = (K + nsplit - 1) / nsplit;
-  k_chunk = ((k_chunk + kGK - 1) / kGK) * kGK;
-  nsplit = (K + k_chunk - 1) / k_chunk;
-  if (nsplit < 1) nsplit = 1;
-  dim3 grid((N + kGT - 1) / kGT, (M + kGT - 1) / kGT, nsplit);
-  if (epi == 0)
-    gemm_kernel<0><<<grid, 128, 0, st>>>(M, N, K, k_chunk, A, sam, sak, B, sbk, sbn, outf, outb, ldo, Z, ldz);
-  else
-    gemm_kernel<1><<<grid, 128, 0, st>>>(M, N, K, k_chunk, A, sam, sak, B, sbk, sbn, outf, outb, ldo, Z, ldz);
-}
-
-// dW = dZ^T H (K = n split over the batch), reduced into grads
-static void weight_grad(const __nv_bfloat16 *dZ, int dcols, const __nv_bfloat16 *H, int hcols, int64_t n,
-                        float *parts, float *gW, cudaStream_t st) {
-  int nsplit = (int)((n + 255) / 256);
-  if (nsplit > kMaxSplit) nsplit = kMaxSplit;
-  if (nsplit < 1) nsplit = 1;
-  int k_chunk = (int)((n + nsplit - 1) / nsplit);
-  k_chunk = ((k_chunk + kGK - 1) / kGK) * kGK;
-  nsplit = (int)((n + k_chunk - 1) / k_chunk);
-  gemm(0, dcols, hcols, (int)n, dZ, 1, dcols, H, hcols, 1, parts, nullptr, hcols, nullptr, 0, nsplit, st);
-  const int64_t cnt = (int64_t)dcols * hcols;
-  reduce_parts_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(parts, nsplit, cnt, gW);
-}
-
-void launch_mlp_backward(const fp_mlp &net, const void *x, const void *h_save, const float *z_save,
-                         const void *dout_bf, const float *dout, int64_t n, float *grads, void *ws, cudaStream_t st) {
-  const __nv_bfloat16 *X = reinterpret_cast<const __nv_bfloat16 *>(x);
-  const __nv_bfloat16 *Hs = reinterpret_cast<const __nv_bfloat16 *>(h_save);
-  const __nv_bfloat16 *dO = reinterpret_cast<const __nv_bfloat16 *>(dout_bf);
-  __nv_bfloat16 *dz0 = reinterpret_cast<__nv_bfloat16 *>(ws);
-  __nv_bfloat16 *dz1 = dz0 + (size_t)n * kHid;
-  const size_t dz_bytes = (((size_t)2 * n * kHid * sizeof(__nv_bfloat16)) + 255) / 256 * 256;
-  float *parts = reinterpret_cast<float *>(reinterpret_cast<char *>(ws) + dz_bytes);
-  auto Hp = [&](int l) { return Hs + (size_t)(l - 1) * n * kHid; };     // H_l, l = 1..4
-  auto Zp = [&](int l) { return z_save + (size_t)(l - 1) * n * kHid; };  // Z_l, l = 1..4
-  auto Wb = [&](int l) { return reinterpret_cast<const __nv_bfloat16 *>(net.W[l - 1]); };
-  // layer 5
-  weight_grad(dO, kOut, Hp(4), kHid, n, parts, grads + mlp_param_offset(0, 4), st);
-  colsum_kernel<float><<<kOut, 256, 0, st>>>(dout, n, kOut, grads + mlp_param_offset(1, 4));
-  gemm(1, (int)n, kHid, kOut, dO, kOut, 1, Wb(5), kHid, 1, nullptr, dz0, kHid, Zp(4), kHid, 1, st);
-  // layers 4..2: dz holds dZ_l
-  __nv_bfloat16 *cur = dz0, *nxt = dz1;
-  for (int l = 4; l >= 2; --l) {
-    weight_grad(cur, kHid, Hp(l - 1), kHid, n, parts, grads + mlp_param_offset(0, l - 1), st);
-    colsum_kernel<__nv_bfloat16><<<kHid, 256, 0, st>>>(cur, n, kHid, grads + mlp_param_offset(1, l - 1));
-    gemm(1, (int)n, kHid, kHid, cur, kHid, 1, Wb(l), kHid, 1, nullptr, nxt, kHid, Zp(l - 1), kHid, 1, st);
-    __nv_bfloat16 *tmp = cur;
-    cur = nxt;
-    nxt = tmp;
-  }
-  // layer 1
-  weight_grad(cur, kHid, X, kIn, n, parts, grads + mlp_param_offset(0, 0), st);
-  colsum_kernel<__nv_bfloat16><<<kHid, 256, 0, st>>>(cur, n, kHid, grads + mlp_param_offset(1, 0));
+// the backward pass on the tensor cores (mlp_train_tc.cu); -1 if it could not be launched
+int launch_mlp_backward(const fp_mlp &net, const void *x, const void *h_save, const float *z_save,
+                        const void *dout_bf, const float *dout, int64_t n, float *grads, void *ws, cudaStream_t st) {
+  return launch_mlp_backward_tc(make_mlp_dev(net), x, h_save, z_save, dout_bf, dout, n, grads, ws, st);
 }
 
 void launch_loss(const float *out, const float *t_true, const float *aux, const float *y_mu, const float *y_sigma,

@@ -1,0 +1,333 @@
+// mlp_train_tc.cu -- backward pass of the network for training, on the
+// fifth-generation tensor cores of sm_103a (tcgen05, BF16 x BF16 -> FP32).
+//
+// One CTA per 128-row tile of the batch, one thread per row (= TMEM lane).
+// Going down the layers l = 5 .. 1 with dZ_5 = dout:
+//   weight gradient  dW_l = dZ_l^T H_(l-1)   (M = out, N = in, K = the
+//                    tile's 128 rows; layer 5 as dW_5^T = H_4^T dZ_5 so that
+//                    M = 128; layer 1 with H_0 = X, N = 32)
+//   data gradient    dA_(l-1) = dZ_l W_l    (M = 128 rows, N = in, K = out)
+//   next dZ          dZ_(l-1) = dA_(l-1) silu'(Z_(l-1)), rounded to BF16
+//   bias gradient    db_l = column sums of dZ_l (BF16 values, FP32 sums;
+//                    db_5 from the FP32 dout)
+// Every operand is K-major in the no-swizzle core-matrix layout (as the
+// inference kernel's): W_l^T is staged transposed once per CTA, dZ_l is
+// written by the epilogue both row-major (the A operand of the data
+// gradient) and transposed (the A operand of the weight gradient), and
+// H_(l-1) is staged transposed from the forward's saved activations.  The
+// weight gradient and the data gradient of a layer are issued together into
+// two 128-column TMEM accumulators and committed to one mbarrier.  Each tile
+// writes its complete gradient (the flat parameter layout) to its own slot
+// of the workspace, and a second kernel sums the slots in a fixed order, so
+// the result does not depend on scheduling.
+// The one thread that waits on the mbarrier does so with a bound; a wait
+// that runs out fills the tile's slot with NaN (the caller sees non-finite
+// gradients) and the CTA waits once more, bounded, for the batch it gave up
+// on before releasing its tensor memory.
+#include <cstdint>
+#include <cuda_bf16.h>
+
+#include "fp_device.cuh"
+#include "mlp_common.cuh"
+#include "tc_common.cuh"
+
+namespace fpc {
+
+int64_t mlp_param_offset(int which, int layer);
+int64_t mlp_param_count();
+
+namespace {
+
+constexpr int kBR = 128;               // rows per tile = TMEM lanes = threads
+constexpr uint32_t kBTmemCols = 256;   // data gradient [0, 128), weight gradient [128, 256)
+
+// shared-memory carve-up (bytes from a 1024-byte aligned base)
+constexpr uint32_t kBOffWT = 0;                                // W2^T, W3^T, W4^T: 3 x [128 in][128 out]
+constexpr uint32_t kBOffWT5 = kBOffWT + 3 * kHid * kHid * 2;   // W5^T: [128 in][16 out]
+constexpr uint32_t kBOffDZ = kBOffWT5 + kHid * kOut * 2;       // dZ: [128 rows][K = out]
+constexpr uint32_t kBOffDZT = kBOffDZ + kBR * kHid * 2;        // dZ^T: [out][K = 128 rows]
+constexpr uint32_t kBOffHT = kBOffDZT + kHid * kBR * 2;        // H^T: [in][K = 128 rows]
+constexpr uint32_t kBOffBar = kBOffHT + kHid * kBR * 2;         // one mbarrier
+constexpr uint32_t kBOffSlot = kBOffBar + 8;                   // TMEM address, verdict
+constexpr uint32_t kBSmemUsed = kBOffSlot + 16;
+constexpr size_t kBSmem = kBSmemUsed + 1024;
+static_assert(kBSmem <= 227 * 1024, "shared memory");
+
+// element (row r, column k) of a K-major operand with K columns
+__device__ __forceinline__ uint32_t cm_elem(int r, int k, int K) { return cm_off(r, k >> 3, K) + (uint32_t)(k & 7) * 2; }
+
+// the flat parameter layout W1 | b1 | W2 | b2 | ... | W5 | b5 (as mlp_param_offset)
+__host__ __device__ constexpr int64_t poff(int which, int layer) {
+  int64_t off = 0;
+  for (int l = 0; l < layer; ++l)
+    off += (l == 0 ? kHid * kIn : (l == 4 ? kOut * kHid : kHid * kHid)) + (l == 4 ? kOut : kHid);
+  return which == 0 ? off : off + (layer == 0 ? kHid * kIn : (layer == 4 ? kOut * kHid : kHid * kHid));
+}
+
+// row t's values at columns i0 .. i0 + 7 (packed BF16 pairs) stored
+// transposed: element (i0 + j, t) of a K-major operand with K = 128 rows
+__device__ __forceinline__ void st_col8(unsigned char *base, int i0, int t, uint4 q) {
+  const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    *reinterpret_cast<uint16_t *>(base + cm_elem(i0 + 2 * j, t, kBR)) = (uint16_t)(w4[j] & 0xffffu);
+    *reinterpret_cast<uint16_t *>(base + cm_elem(i0 + 2 * j + 1, t, kBR)) = (uint16_t)(w4[j] >> 16);
+  }
+}
+
+// a row of NV x 8 BF16 values loaded with 16-byte loads (all issued first)
+// and stored transposed (zeros past the batch)
+template <int NV>
+__device__ __forceinline__ void stage_row_t(unsigned char *base, const __nv_bfloat16 *row, bool live, int t) {
+  uint4 q[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) q[v] = live ? reinterpret_cast<const uint4 *>(row)[v] : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) st_col8(base, 8 * v, t, q[v]);
+}
+
+// 16 accumulator columns of this thread's lane, as floats
+__device__ __forceinline__ void ld_cols16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  tc_ld16(taddr, r);
+  tc_wait16(r);
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kBR, 1)
+    mlp_backward_tc_kernel(MlpDev net, const __nv_bfloat16 *__restrict__ x, const __nv_bfloat16 *__restrict__ h_save,
+                           const float *__restrict__ z_save, const __nv_bfloat16 *__restrict__ dout_bf,
+                           const float *__restrict__ dout, int64_t n, int64_t n_params, float *__restrict__ parts) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kBOffBar);
+  volatile uint32_t *slot = reinterpret_cast<volatile uint32_t *>(sm + kBOffSlot);
+  unsigned char *DZ = sm + kBOffDZ, *DZT = sm + kBOffDZT, *HT = sm + kBOffHT;
+  const int t = threadIdx.x, warp = t >> 5;
+  const int64_t row0 = (int64_t)blockIdx.x * kBR, r = row0 + t;
+  const bool live = r < n;
+  float *part = parts + (int64_t)blockIdx.x * n_params;
+  const size_t plane = (size_t)n * kHid;  // one layer of h_save / z_save
+
+  // W_l^T (l = 2..4) and W_5^T, transposed into the B layout once
+  for (int l = 0; l < 3; ++l) {
+    const __nv_bfloat16 *W = net.W[1 + l];  // [out][in]
+    unsigned char *WT = sm + kBOffWT + (uint32_t)l * kHid * kHid * 2;
+    for (int e = t; e < kHid * kHid / 8; e += kBR) {  // 8 consecutive inputs of output o
+      const int o = e / (kHid / 8), i0 = 8 * (e % (kHid / 8));
+      const uint4 q = reinterpret_cast<const uint4 *>(W)[e];
+      const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        *reinterpret_cast<uint16_t *>(WT + cm_elem(i0 + 2 * j, o, kHid)) = (uint16_t)(w4[j] & 0xffffu);
+        *reinterpret_cast<uint16_t *>(WT + cm_elem(i0 + 2 * j + 1, o, kHid)) = (uint16_t)(w4[j] >> 16);
+      }
+    }
+  }
+  for (int e = t; e < kOut * kHid; e += kBR) {
+    const int o = e / kHid, i = e % kHid;
+    *reinterpret_cast<__nv_bfloat16 *>(sm + kBOffWT5 + cm_elem(i, o, kOut)) = net.W[4][e];
+  }
+  // layer 5 operands: dout (A of dA_4, K = 16), dout^T (B of dW_5^T), H_4^T
+  // (A of dW_5^T); rows past the batch are zero
+  stage_rows_async(DZ, dout_bf + row0 * kOut, kBR, kOut, n - row0, t, kBR);
+  {
+    stage_row_t<kOut / 8>(DZT, dout_bf + r * kOut, live, t);
+    stage_row_t<kHid / 8>(HT, h_save + 3 * plane + r * kHid, live, t);
+  }
+  // db_5: column sums of the FP32 dout over the tile's rows
+  if (t < kOut) {
+    float s = 0.f;
+    for (int q = 0; q < kBR && row0 + q < n; ++q) s += dout[(row0 + q) * kOut + t];
+    part[poff(1, 4) + t] = s;
+  }
+  if (t == 0) {
+    mbar_init(bar, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32((const void *)slot)),
+                 "r"(kBTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  cp_async_wait();
+  fence_proxy_async_smem();  // operands written through the generic proxy, read by the MMA
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = slot[0];
+  const uint32_t d_a = tmem, d_w = tmem + (uint32_t)kHid;
+  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+  const uint32_t dz_addr = smem_u32(DZ), dzt_addr = smem_u32(DZT), ht_addr = smem_u32(HT);
+  uint32_t phase = 0;
+  bool failed = false;
+
+  // the leader waits for the layer's commit; everybody learns the verdict
+  auto wait_layer = [&]() -> bool {
+    if (t == 0) slot[1] = mma_wait(bar, phase) ? 1u : 0u;
+    phase ^= 1u;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    return slot[1] != 0u;
+  };
+  // after the operands of the next MMAs were written by this CTA's threads
+  auto operands_ready = [&]() {
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  };
+
+  // ---- layer 5: dW_5^T = H_4^T dout (N = 16), dA_4 = dout W_5 (K = 16) ----
+  if (t == 0) {
+    for (int s = 0; s < kBR / 16; ++s)
+      tc_mma(d_w, smem_desc(ht_addr + 256 * s, 128, kBR * 16), smem_desc(dzt_addr + 256 * s, 128, kBR * 16),
+             idesc_bf16(kBR, kOut), s > 0 ? 1u : 0u);
+    tc_mma(d_a, smem_desc(dz_addr, 128, kOut * 16), smem_desc(smem_u32(sm + kBOffWT5), 128, kOut * 16),
+           idesc_bf16(kBR, kHid), 0u);
+    tc_commit(bar);
+  }
+  // layers l = 5 .. 1: epilogue of layer l's MMAs, then the MMAs of layer l - 1
+#pragma unroll 1
+  for (int l = 5; l >= 1; --l) {
+    if (!wait_layer()) {
+      failed = true;
+      break;
+    }
+    // weight gradient of layer l: lane t holds row t of dW_l (out t), or for
+    // layer 5 row t of dW_5^T (in t)
+    if (l == 5) {
+      float v[16];
+      ld_cols16(d_w + lane_off, v);
+      float *g = part + poff(0, 4);  // W5 [16][128]
+#pragma unroll
+      for (int o = 0; o < kOut; ++o) g[o * kHid + t] = v[o];
+    } else {
+      const int in = l == 1 ? kIn : kHid;
+      float4 *g = reinterpret_cast<float4 *>(part + poff(0, l - 1) + (int64_t)t * in);
+      for (int c = 0; c < in / 16; ++c) {
+        float v[16];
+        ld_cols16(d_w + lane_off + (uint32_t)(16 * c), v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) g[4 * c + q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      }
+    }
+    if (l == 1) break;
+    // dZ_(l-1) = dA_(l-1) silu'(Z_(l-1)) -> DZ (row t) and DZT (column t)
+    {
+      const float4 *z4 = reinterpret_cast<const float4 *>(z_save + (size_t)(l - 2) * plane + r * kHid);
+      float4 zc[4], zn[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) zc[q] = live ? z4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+      for (int c = 0; c < kHid / 16; ++c) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          zn[q] = live && c + 1 < kHid / 16 ? z4[4 * (c + 1) + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float v[16];
+        ld_cols16(d_a + lane_off + (uint32_t)(16 * c), v);
+        const float zz[16] = {zc[0].x, zc[0].y, zc[0].z, zc[0].w, zc[1].x, zc[1].y, zc[1].z, zc[1].w,
+                              zc[2].x, zc[2].y, zc[2].z, zc[2].w, zc[3].x, zc[3].y, zc[3].z, zc[3].w};
+        uint32_t pk[8];
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+          const float g0 = live ? v[j] * silu_grad(zz[j]) : 0.f, g1 = live ? v[j + 1] * silu_grad(zz[j + 1]) : 0.f;
+          pk[j / 2] = pack_bf16(g0, g1);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) zc[q] = zn[q];
+        const uint4 lo = make_uint4(pk[0], pk[1], pk[2], pk[3]), hi = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        *reinterpret_cast<uint4 *>(DZ + cm_off(t, 2 * c, kHid)) = lo;
+        *reinterpret_cast<uint4 *>(DZ + cm_off(t, 2 * c + 1, kHid)) = hi;
+        st_col8(DZT, 16 * c, t, lo);
+        st_col8(DZT, 16 * c + 8, t, hi);
+      }
+    }
+    // H_(l-2)^T for the weight gradient of layer l - 1 (X^T for layer 1)
+    if (l - 1 == 1)
+      stage_row_t<kIn / 8>(HT, x + r * kIn, live, t);
+    else
+      stage_row_t<kHid / 8>(HT, h_save + (size_t)(l - 3) * plane + r * kHid, live, t);
+    operands_ready();
+    // MMAs of layer l - 1: dW_(l-1) = dZ^T H^T^T, dA_(l-2) = dZ W_(l-1)
+    if (t == 0) {
+      const int nw = l - 1 == 1 ? kIn : kHid;
+      for (int s = 0; s < kBR / 16; ++s)
+        tc_mma(d_w, smem_desc(dzt_addr + 256 * s, 128, kBR * 16), smem_desc(ht_addr + 256 * s, 128, kBR * 16),
+               idesc_bf16(kBR, nw), s > 0 ? 1u : 0u);
+      if (l - 1 >= 2) {
+        const uint32_t wt = smem_u32(sm + kBOffWT + (uint32_t)(l - 3) * kHid * kHid * 2);  // W_(l-1)^T
+        for (int s = 0; s < kHid / 16; ++s)
+          tc_mma(d_a, smem_desc(dz_addr + 256 * s, 128, kHid * 16), smem_desc(wt + 256 * s, 128, kHid * 16),
+                 idesc_bf16(kBR, kHid), s > 0 ? 1u : 0u);
+      }
+      tc_commit(bar);
+    }
+    // db_(l-1): column t of dZ_(l-1) summed over the tile's rows (row t of DZT)
+    {
+      float s = 0.f;
+#pragma unroll
+      for (int k8 = 0; k8 < kBR / 8; ++k8) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(DZT + cm_off(t, k8, kBR));
+        const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          s += __uint_as_float(w4[e] << 16) + __uint_as_float(w4[e] & 0xffff0000u);
+      }
+      part[poff(1, l - 2) + t] = s;
+    }
+  }
+  if (failed) {
+    // the tile's gradient is unusable: NaN in its whole slot
+    for (int64_t i = t; i < n_params; i += kBR) part[i] = __int_as_float(0x7fc00000);
+    if (t == 0) (void)mbar_wait_bounded(bar, phase ^ 1u, 200000000ull);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(slot[0]), "r"(kBTmemCols) : "memory");
+}
+
+__global__ void sum_tiles_kernel(const float *__restrict__ parts, int ntiles, int64_t cnt, float *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cnt) return;
+  float s = 0.f;
+  for (int z = 0; z < ntiles; ++z) s += parts[z * cnt + i];
+  out[i] = s;
+}
+
+size_t mlp_backward_tc_ws(int64_t n) {
+  const int64_t tiles = (n + kBR - 1) / kBR;
+  return (size_t)tiles * (size_t)mlp_param_count() * sizeof(float);
+}
+
+// Returns -1 if the shared-memory limit could not be raised.
+int launch_mlp_backward_tc(const MlpDev &net, const void *x, const void *h_save, const float *z_save,
+                           const void *dout_bf, const float *dout, int64_t n, float *grads, void *ws,
+                           cudaStream_t st) {
+  static int attr_done[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr_done[dev]) {
+    if (cudaFuncSetAttribute(mlp_backward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBSmem) !=
+        cudaSuccess)
+      return -1;
+    attr_done[dev] = 1;
+  }
+  const int64_t tiles = (n + kBR - 1) / kBR;
+  const int64_t np = mlp_param_count();
+  float *parts = reinterpret_cast<float *>(ws);
+  mlp_backward_tc_kernel<<<(unsigned)tiles, kBR, kBSmem, st>>>(
+      net, reinterpret_cast<const __nv_bfloat16 *>(x), reinterpret_cast<const __nv_bfloat16 *>(h_save), z_save,
+      reinterpret_cast<const __nv_bfloat16 *>(dout_bf), dout, n, np, parts);
+  sum_tiles_kernel<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(parts, (int)tiles, np, grads);
+  return 0;
+}
+
+}  // namespace fpc
