@@ -1,21 +1,13 @@
-// mlp.cu -- the learned closure's standalone input kernel, the training
-// forward pass, the exact per-cell fallback and the launchers of the fused
-// closure (whose kernel, with the inference pass, is in mlp_tc.cu) (sm_103a).
+// mlp.cu -- the learned closure's standalone input kernels (features and
+// training rows), the exact per-cell fallback and the launchers of the
+// network's passes (the kernels of the inference pass and of the fused
+// closure are in mlp_tc.cu, those of training in mlp_train_tc.cu) (sm_103a).
 //
 // Features: the 25 moments of w = c / sqrt(theta) (u/theta, u3/theta^1.5,
 // w/theta^2, z/theta^2.5), standardised, BF16, zero padded to 32.  The
 // network maps them to the standardised dimensionless coefficients
 // (tau C, tau sqrt(theta) G); the cubic-FP system of Eq. system9x9 is
 // invariant under c -> c/sqrt(theta), so those depend on the features alone.
-//
-// Fused forward for training (the inference pass is the tcgen05 kernel of
-// mlp_tc.cu): one CTA of 8 warps holds all five weight matrices in shared
-// memory (~120 KB, loaded once) and streams 128-row tiles; each warp owns 16
-// rows for the whole network, so a layer's activations go from the FP32
-// accumulators through bias + SiLU to BF16 in the warp's own rows of the
-// activation tile -- and, with the pre-activations, out to the buffers the
-// backward pass reads -- and feed the next layer with no block barrier.  The
-// MMAs are mma.sync m16n8k16 (BF16 x BF16 -> FP32).
 #include <cstdint>
 #include <cuda_bf16.h>
 
@@ -24,15 +16,6 @@
 #include "mlp_common.cuh"
 
 namespace fpc {
-
-constexpr int kWS1 = kIn + 8;    // smem row stride (bf16) of W1
-constexpr int kWSH = kHid + 8;   // smem row stride of W2..W5 and of the activation tile
-constexpr int kRows = 128;       // rows per CTA tile
-constexpr int kMlpWarps = 8;
-constexpr int kMlpThreads = 32 * kMlpWarps;
-constexpr size_t kMlpSmem =
-    (size_t)(kHid * kWS1 + 3 * kHid * kWSH + kOut * kWSH + kRows * kWSH) * sizeof(__nv_bfloat16) +
-    (size_t)(4 * kHid + kOut) * sizeof(float);
 
 // ---------------------------------------------------------------------------
 // features
@@ -156,133 +139,6 @@ __global__ void __launch_bounds__(256) training_rows_kernel(const double *__rest
 }
 
 // ---------------------------------------------------------------------------
-// fused forward
-// ---------------------------------------------------------------------------
-// One layer for the warp's 16 rows: acc[NT][4] = act[rows][0:K] . W^T
-template <int K, int NT, int WS>
-__device__ __forceinline__ void warp_layer(const __nv_bfloat16 *__restrict__ act, const __nv_bfloat16 *__restrict__ W,
-                                           float (&acc)[NT][4], int r0, int lane) {
-  const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-  for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-#pragma unroll
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    const uint32_t a0 = *reinterpret_cast<const uint32_t *>(act + (r0 + g) * kWSH + k0 + 2 * t);
-    const uint32_t a1 = *reinterpret_cast<const uint32_t *>(act + (r0 + g + 8) * kWSH + k0 + 2 * t);
-    const uint32_t a2 = *reinterpret_cast<const uint32_t *>(act + (r0 + g) * kWSH + k0 + 8 + 2 * t);
-    const uint32_t a3 = *reinterpret_cast<const uint32_t *>(act + (r0 + g + 8) * kWSH + k0 + 8 + 2 * t);
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-      const __nv_bfloat16 *wr = W + (nt * 8 + g) * WS + k0 + 2 * t;
-      const uint32_t b0 = *reinterpret_cast<const uint32_t *>(wr);
-      const uint32_t b1 = *reinterpret_cast<const uint32_t *>(wr + 8);
-      mma_bf16(acc[nt], a0, a1, a2, a3, b0, b1);
-    }
-  }
-}
-
-template <bool kSave>
-__global__ void __launch_bounds__(kMlpThreads, 1)
-    mlp_forward_kernel(MlpDev net, const __nv_bfloat16 *__restrict__ x, int64_t n, int standardized_out,
-                       float *__restrict__ out, __nv_bfloat16 *__restrict__ h_save, float *__restrict__ z_save) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __nv_bfloat16 *W1 = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
-  __nv_bfloat16 *WH = W1 + kHid * kWS1;          // W2, W3, W4
-  __nv_bfloat16 *W5 = WH + 3 * kHid * kWSH;
-  __nv_bfloat16 *act = W5 + kOut * kWSH;
-  float *bias = reinterpret_cast<float *>(act + kRows * kWSH);  // b1..b4 [4][128], b5 [16]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-
-  // weights and biases into shared memory (once per CTA)
-  for (int i = tid; i < kHid * kIn / 2; i += kMlpThreads) {
-    const int r = (2 * i) / kIn, cidx = (2 * i) % kIn;
-    *reinterpret_cast<uint32_t *>(W1 + r * kWS1 + cidx) = *reinterpret_cast<const uint32_t *>(net.W[0] + 2 * i);
-  }
-  for (int l = 0; l < 3; ++l)
-    for (int i = tid; i < kHid * kHid / 2; i += kMlpThreads) {
-      const int r = (2 * i) / kHid, cidx = (2 * i) % kHid;
-      *reinterpret_cast<uint32_t *>(WH + l * kHid * kWSH + r * kWSH + cidx) =
-          *reinterpret_cast<const uint32_t *>(net.W[1 + l] + 2 * i);
-    }
-  for (int i = tid; i < kOut * kHid / 2; i += kMlpThreads) {
-    const int r = (2 * i) / kHid, cidx = (2 * i) % kHid;
-    *reinterpret_cast<uint32_t *>(W5 + r * kWSH + cidx) = *reinterpret_cast<const uint32_t *>(net.W[4] + 2 * i);
-  }
-  for (int i = tid; i < 4 * kHid + kOut; i += kMlpThreads) bias[i] = i < 4 * kHid ? net.b[i / kHid][i % kHid] : net.b[4][i - 4 * kHid];
-  __syncthreads();
-
-  const int g = lane >> 2, t = lane & 3;
-  const int r0 = warp * 16;
-  const int64_t n_tiles = (n + kRows - 1) / kRows;
-  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const int64_t row0 = tile * kRows + r0;  // first global row of this warp
-    // input rows -> act[:, 0:32]; 16 rows x 64 B = 64 x 16 B, two per lane
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int e = lane + 32 * q;  // 0..63
-      const int rr = e >> 2, part = e & 3;
-      uint4 val = make_uint4(0u, 0u, 0u, 0u);
-      if (row0 + rr < n) val = *reinterpret_cast<const uint4 *>(x + (row0 + rr) * kIn + part * 8);
-      *reinterpret_cast<uint4 *>(act + (r0 + rr) * kWSH + part * 8) = val;
-    }
-    __syncwarp();
-    // hidden layers
-#pragma unroll 1
-    for (int l = 0; l < 4; ++l) {
-      float acc[kHid / 8][4];
-      if (l == 0)
-        warp_layer<kIn, kHid / 8, kWS1>(act, W1, acc, r0, lane);
-      else
-        warp_layer<kHid, kHid / 8, kWSH>(act, WH + (l - 1) * kHid * kWSH, acc, r0, lane);
-      __syncwarp();
-      const float *bl = bias + l * kHid;
-#pragma unroll
-      for (int nt = 0; nt < kHid / 8; ++nt) {
-        const int col = nt * 8 + 2 * t;
-        const float z0 = acc[nt][0] + bl[col], z1 = acc[nt][1] + bl[col + 1];
-        const float z2 = acc[nt][2] + bl[col], z3 = acc[nt][3] + bl[col + 1];
-        const uint32_t h01 = pack_bf16(silu(z0), silu(z1)), h23 = pack_bf16(silu(z2), silu(z3));
-        *reinterpret_cast<uint32_t *>(act + (r0 + g) * kWSH + col) = h01;
-        *reinterpret_cast<uint32_t *>(act + (r0 + g + 8) * kWSH + col) = h23;
-        if (kSave) {
-          const int64_t ra = row0 + g, rb = row0 + g + 8;
-          const size_t plane = (size_t)n * kHid * l;
-          if (ra < n) {
-            *reinterpret_cast<float2 *>(z_save + plane + ra * kHid + col) = make_float2(z0, z1);
-            *reinterpret_cast<uint32_t *>(h_save + plane + ra * kHid + col) = h01;
-          }
-          if (rb < n) {
-            *reinterpret_cast<float2 *>(z_save + plane + rb * kHid + col) = make_float2(z2, z3);
-            *reinterpret_cast<uint32_t *>(h_save + plane + rb * kHid + col) = h23;
-          }
-        }
-      }
-      __syncwarp();
-    }
-    // output layer (16 columns, 9 used)
-    float acc[kOut / 8][4];
-    warp_layer<kHid, kOut / 8, kWSH>(act, W5, acc, r0, lane);
-    const float *b5 = bias + 4 * kHid;
-#pragma unroll
-    for (int nt = 0; nt < kOut / 8; ++nt) {
-      const int col = nt * 8 + 2 * t;
-      float o[4] = {acc[nt][0] + b5[col], acc[nt][1] + b5[col + 1], acc[nt][2] + b5[col], acc[nt][3] + b5[col + 1]};
-      if (!standardized_out) {
-        const float m0 = net.y_mu[col], m1 = net.y_mu[col + 1], s0 = net.y_sigma[col], s1 = net.y_sigma[col + 1];
-        o[0] = fmaf(o[0], s0, m0);
-        o[1] = fmaf(o[1], s1, m1);
-        o[2] = fmaf(o[2], s0, m0);
-        o[3] = fmaf(o[3], s1, m1);
-      }
-      const int64_t ra = row0 + g, rb = row0 + g + 8;
-      if (ra < n) *reinterpret_cast<float2 *>(out + ra * kOut + col) = make_float2(o[0], o[1]);
-      if (rb < n) *reinterpret_cast<float2 *>(out + rb * kOut + col) = make_float2(o[2], o[3]);
-    }
-    __syncwarp();
-  }
-}
-
-// ---------------------------------------------------------------------------
 // fallback: the exact closure on the cells the fused kernel listed
 // ---------------------------------------------------------------------------
 // A short list (the usual case: a few hundred cells) is latency-bound: each
@@ -346,8 +202,6 @@ static int mlp_sm_count() {
   return n;
 }
 
-static int g_mlp_attr_done[64];
-
 int launch_mlp_forward_tc(const MlpDev &net, const __nv_bfloat16 *x, int64_t n, int standardized_out, float *out,
                           cudaStream_t st);
 
@@ -395,28 +249,17 @@ int launch_mlp_forward_dropout(const fp_mlp &net, const void *x, int64_t n, floa
                                        st);
 }
 
+int launch_mlp_forward_train_tc(const MlpDev &net, const void *x, int64_t n, int standardized_out, float *out,
+                                void *h_save, float *z_save, cudaStream_t st);
+
 int launch_mlp_forward(const fp_mlp &net, const void *x, int64_t n, int standardized_out, float *out, void *h_save,
                        float *z_save, cudaStream_t st) {
   const MlpDev d = make_mlp_dev(net);
   const __nv_bfloat16 *xb = reinterpret_cast<const __nv_bfloat16 *>(x);
-  // inference: the tcgen05 kernel; training (activations saved for the
-  // backward pass): the mma.sync kernel, whose warps own their rows end to end
+  // inference: the persistent tcgen05 kernel; training (activations saved
+  // for the backward pass): the tile-per-CTA tcgen05 kernel of mlp_train_tc.cu
   if (h_save == nullptr || z_save == nullptr) return launch_mlp_forward_tc(d, xb, n, standardized_out, out, st);
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !g_mlp_attr_done[dev]) {
-    if (cudaFuncSetAttribute(mlp_forward_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMlpSmem) !=
-        cudaSuccess)
-      return -1;
-    g_mlp_attr_done[dev] = 1;
-  }
-  const int64_t n_tiles = (n + kRows - 1) / kRows;
-  int64_t grid = mlp_sm_count();
-  if (grid > n_tiles) grid = n_tiles;
-  if (grid < 1) grid = 1;
-  mlp_forward_kernel<true><<<(unsigned)grid, kMlpThreads, kMlpSmem, st>>>(
-      d, xb, n, standardized_out, out, reinterpret_cast<__nv_bfloat16 *>(h_save), z_save);
-  return 0;
+  return launch_mlp_forward_train_tc(d, xb, n, standardized_out, out, h_save, z_save, st);
 }
 
 int launch_closure_surrogate_tc(const MlpDev &net, const FusedIO &io, int64_t n, int lite, cudaStream_t st);

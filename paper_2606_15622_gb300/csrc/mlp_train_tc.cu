@@ -294,6 +294,175 @@ __global__ void __launch_bounds__(kBR, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(slot[0]), "r"(kBTmemCols) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// training forward: the network on a 128-row tile per CTA, one thread per
+// row, saving every hidden layer's pre-activations Z (FP32) and activations
+// H = SiLU(Z) (BF16, the exponential form the backward pass differentiates)
+// ---------------------------------------------------------------------------
+namespace {
+constexpr uint32_t kFOffW1 = 0;                               // W1 [128 out][K = 32 in]
+constexpr uint32_t kFOffWH = kFOffW1 + kHid * kIn * 2;        // W2..W4 [128][K = 128]
+constexpr uint32_t kFOffW5 = kFOffWH + 3 * kHid * kHid * 2;   // W5 [16][K = 128]
+constexpr uint32_t kFOffA = kFOffW5 + kOut * kHid * 2;        // activations [128 rows][K = 128]
+constexpr uint32_t kFOffX = kFOffA + kBR * kHid * 2;          // inputs [128 rows][K = 32]
+constexpr uint32_t kFOffBias = kFOffX + kBR * kIn * 2;        // b1..b4 (4 x 128), b5, y_mu, y_sigma (3 x 16)
+constexpr uint32_t kFOffBar = kFOffBias + (4 * kHid + 3 * kOut) * 4;
+constexpr uint32_t kFOffSlot = kFOffBar + 8;
+constexpr uint32_t kFSmemUsed = kFOffSlot + 16;
+constexpr size_t kFSmem = kFSmemUsed + 1024;
+constexpr uint32_t kFTmemCols = 128;
+static_assert(kFSmem <= 227 * 1024, "shared memory");
+static_assert(kFOffBar % 8 == 0, "mbarrier alignment");
+}  // namespace
+
+__global__ void __launch_bounds__(kBR, 1)
+    mlp_forward_train_tc_kernel(MlpDev net, const __nv_bfloat16 *__restrict__ x, int64_t n, int standardized_out,
+                                float *__restrict__ out, __nv_bfloat16 *__restrict__ h_save,
+                                float *__restrict__ z_save) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kFOffBar);
+  volatile uint32_t *slot = reinterpret_cast<volatile uint32_t *>(sm + kFOffSlot);
+  float *bias = reinterpret_cast<float *>(sm + kFOffBias);
+  unsigned char *A = sm + kFOffA, *X = sm + kFOffX;
+  const int t = threadIdx.x, warp = t >> 5;
+  const int64_t row0 = (int64_t)blockIdx.x * kBR, r = row0 + t;
+  const bool live = r < n;
+  const size_t plane = (size_t)n * kHid;
+
+  stage_rows_async(sm + kFOffW1, net.W[0], kHid, kIn, kHid, t, kBR);
+  for (int l = 0; l < 3; ++l)
+    stage_rows_async(sm + kFOffWH + (uint32_t)l * kHid * kHid * 2, net.W[1 + l], kHid, kHid, kHid, t, kBR);
+  stage_rows_async(sm + kFOffW5, net.W[4], kOut, kHid, kOut, t, kBR);
+  stage_rows_async(X, x + row0 * kIn, kBR, kIn, n - row0, t, kBR);
+  for (int i = t; i < 4 * kHid + 3 * kOut; i += kBR)
+    bias[i] = i < 4 * kHid ? net.b[i / kHid][i % kHid]
+                           : (i < 4 * kHid + kOut ? net.b[4][i - 4 * kHid]
+                                                  : (i < 4 * kHid + 2 * kOut ? net.y_mu[i - 4 * kHid - kOut]
+                                                                             : net.y_sigma[i - 4 * kHid - 2 * kOut]));
+  if (t == 0) {
+    mbar_init(bar, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32((const void *)slot)),
+                 "r"(kFTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  cp_async_wait();
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = slot[0];
+  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+  const uint32_t a_addr = smem_u32(A), x_addr = smem_u32(X);
+  uint32_t phase = 0;
+  bool failed = false;
+  auto wait_layer = [&]() -> bool {
+    if (t == 0) slot[1] = mma_wait(bar, phase) ? 1u : 0u;
+    phase ^= 1u;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    return slot[1] != 0u;
+  };
+
+  // layer 1
+  if (t == 0) {
+    for (int s = 0; s < kIn / 16; ++s)
+      tc_mma(tmem, smem_desc(x_addr + 256 * s, 128, kIn * 16), smem_desc(smem_u32(sm + kFOffW1) + 256 * s, 128, kIn * 16),
+             idesc_bf16(kBR, kHid), s > 0 ? 1u : 0u);
+    tc_commit(bar);
+  }
+#pragma unroll 1
+  for (int l = 0; l < 4; ++l) {
+    if (!wait_layer()) {
+      failed = true;
+      break;
+    }
+    // z = acc + b, H = SiLU(z): saved, and the next layer's A operand
+    const float *bl = bias + l * kHid;
+    float4 *zs = reinterpret_cast<float4 *>(z_save + (size_t)l * plane + r * kHid);
+    uint4 *hs = reinterpret_cast<uint4 *>(h_save + (size_t)l * plane + r * kHid);
+#pragma unroll 1
+    for (int c = 0; c < kHid / 16; ++c) {
+      float v[16];
+      ld_cols16(tmem + lane_off + (uint32_t)(16 * c), v);
+      uint32_t pk[8];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] += bl[16 * c + j];
+#pragma unroll
+      for (int j = 0; j < 16; j += 2) pk[j / 2] = pack_bf16(silu(v[j]), silu(v[j + 1]));
+      const uint4 lo = make_uint4(pk[0], pk[1], pk[2], pk[3]), hi = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+      *reinterpret_cast<uint4 *>(A + cm_off(t, 2 * c, kHid)) = lo;
+      *reinterpret_cast<uint4 *>(A + cm_off(t, 2 * c + 1, kHid)) = hi;
+      if (live) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) zs[4 * c + q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        hs[2 * c] = lo;
+        hs[2 * c + 1] = hi;
+      }
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (t == 0) {
+      const int n_next = l == 3 ? kOut : kHid;
+      const uint32_t w = l == 3 ? smem_u32(sm + kFOffW5) : smem_u32(sm + kFOffWH + (uint32_t)l * kHid * kHid * 2);
+      for (int s = 0; s < kHid / 16; ++s)
+        tc_mma(tmem, smem_desc(a_addr + 256 * s, 128, kHid * 16), smem_desc(w + 256 * s, 128, kHid * 16),
+               idesc_bf16(kBR, n_next), s > 0 ? 1u : 0u);
+      tc_commit(bar);
+    }
+  }
+  if (!failed && !wait_layer()) failed = true;
+  if (!failed) {
+    float v[16];
+    ld_cols16(tmem + lane_off, v);
+    const float *b5 = bias + 4 * kHid, *ymu = b5 + kOut, *ysg = ymu + kOut;
+#pragma unroll
+    for (int j = 0; j < kOut; ++j) {
+      v[j] += b5[j];
+      if (!standardized_out) v[j] = fmaf(ysg[j], v[j], ymu[j]);
+    }
+    if (live) {
+      float4 *o4 = reinterpret_cast<float4 *>(out + r * kOut);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) o4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
+  } else if (live) {
+    for (int j = 0; j < kOut; ++j) out[r * kOut + j] = __int_as_float(0x7fc00000);
+    if (t == 0) (void)mbar_wait_bounded(bar, phase ^ 1u, 200000000ull);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(slot[0]), "r"(kFTmemCols) : "memory");
+}
+
+// Returns -1 if the shared-memory limit could not be raised.
+int launch_mlp_forward_train_tc(const MlpDev &net, const void *x, int64_t n, int standardized_out, float *out,
+                                void *h_save, float *z_save, cudaStream_t st) {
+  static int attr_done[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr_done[dev]) {
+    if (cudaFuncSetAttribute(mlp_forward_train_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kFSmem) != cudaSuccess)
+      return -1;
+    attr_done[dev] = 1;
+  }
+  const int64_t tiles = (n + kBR - 1) / kBR;
+  mlp_forward_train_tc_kernel<<<(unsigned)tiles, kBR, kFSmem, st>>>(
+      net, reinterpret_cast<const __nv_bfloat16 *>(x), n, standardized_out, out,
+      reinterpret_cast<__nv_bfloat16 *>(h_save), z_save);
+  return 0;
+}
+
 __global__ void sum_tiles_kernel(const float *__restrict__ parts, int ntiles, int64_t cnt, float *__restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= cnt) return;
