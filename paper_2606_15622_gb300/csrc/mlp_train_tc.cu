@@ -1,7 +1,8 @@
 // mlp_train_tc.cu -- backward pass of the network for training, on the
 // fifth-generation tensor cores of sm_103a (tcgen05, BF16 x BF16 -> FP32).
 //
-// One CTA per 128-row tile of the batch, one thread per row (= TMEM lane).
+// One CTA per 128-row tile of the batch, two threads per row (= TMEM lane),
+// each with half of the row's columns.
 // Going down the layers l = 5 .. 1 with dZ_5 = dout:
 //   weight gradient  dW_l = dZ_l^T H_(l-1)   (M = out, N = in, K = the
 //                    tile's 128 rows; layer 5 as dW_5^T = H_4^T dZ_5 so that
@@ -38,7 +39,8 @@ int64_t mlp_param_count();
 
 namespace {
 
-constexpr int kBR = 128;               // rows per tile = TMEM lanes = threads
+constexpr int kBR = 128;               // rows per tile = TMEM lanes
+constexpr int kBT = 2 * kBR;           // threads: two per row, each with half of the row's columns
 constexpr uint32_t kBTmemCols = 256;   // data gradient [0, 128), weight gradient [128, 256)
 
 // shared-memory carve-up (bytes from a 1024-byte aligned base)
@@ -75,15 +77,16 @@ __device__ __forceinline__ void st_col8(unsigned char *base, int i0, int t, uint
   }
 }
 
-// a row of NV x 8 BF16 values loaded with 16-byte loads (all issued first)
-// and stored transposed (zeros past the batch)
+// values 8 v0 .. 8 (v0 + NV) - 1 of a BF16 row, loaded with 16-byte loads
+// (all issued first) and stored transposed (zeros past the batch)
 template <int NV>
-__device__ __forceinline__ void stage_row_t(unsigned char *base, const __nv_bfloat16 *row, bool live, int t) {
+__device__ __forceinline__ void stage_row_t(unsigned char *base, const __nv_bfloat16 *row, bool live, int t, int v0) {
   uint4 q[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) q[v] = live ? reinterpret_cast<const uint4 *>(row)[v] : make_uint4(0u, 0u, 0u, 0u);
+  for (int v = 0; v < NV; ++v)
+    q[v] = live ? reinterpret_cast<const uint4 *>(row)[v0 + v] : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-  for (int v = 0; v < NV; ++v) st_col8(base, 8 * v, t, q[v]);
+  for (int v = 0; v < NV; ++v) st_col8(base, 8 * (v0 + v), t, q[v]);
 }
 
 // 16 accumulator columns of this thread's lane, as floats
@@ -97,7 +100,7 @@ __device__ __forceinline__ void ld_cols16(uint32_t taddr, float (&v)[16]) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(kBR, 1)
+__global__ void __launch_bounds__(kBT, 1)
     mlp_backward_tc_kernel(MlpDev net, const __nv_bfloat16 *__restrict__ x, const __nv_bfloat16 *__restrict__ h_save,
                            const float *__restrict__ z_save, const __nv_bfloat16 *__restrict__ dout_bf,
                            const float *__restrict__ dout, int64_t n, int64_t n_params, float *__restrict__ parts) {
@@ -106,7 +109,7 @@ __global__ void __launch_bounds__(kBR, 1)
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kBOffBar);
   volatile uint32_t *slot = reinterpret_cast<volatile uint32_t *>(sm + kBOffSlot);
   unsigned char *DZ = sm + kBOffDZ, *DZT = sm + kBOffDZT, *HT = sm + kBOffHT;
-  const int t = threadIdx.x, warp = t >> 5;
+  const int tid = threadIdx.x, t = tid & (kBR - 1), h = tid >> 7, warp = tid >> 5;
   const int64_t row0 = (int64_t)blockIdx.x * kBR, r = row0 + t;
   const bool live = r < n;
   float *part = parts + (int64_t)blockIdx.x * n_params;
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(kBR, 1)
   for (int l = 0; l < 3; ++l) {
     const __nv_bfloat16 *W = net.W[1 + l];  // [out][in]
     unsigned char *WT = sm + kBOffWT + (uint32_t)l * kHid * kHid * 2;
-    for (int e = t; e < kHid * kHid / 8; e += kBR) {  // 8 consecutive inputs of output o
+    for (int e = tid; e < kHid * kHid / 8; e += kBT) {  // 8 consecutive inputs of output o
       const int o = e / (kHid / 8), i0 = 8 * (e % (kHid / 8));
       const uint4 q = reinterpret_cast<const uint4 *>(W)[e];
       const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
@@ -127,24 +130,22 @@ __global__ void __launch_bounds__(kBR, 1)
       }
     }
   }
-  for (int e = t; e < kOut * kHid; e += kBR) {
+  for (int e = tid; e < kOut * kHid; e += kBT) {
     const int o = e / kHid, i = e % kHid;
     *reinterpret_cast<__nv_bfloat16 *>(sm + kBOffWT5 + cm_elem(i, o, kOut)) = net.W[4][e];
   }
   // layer 5 operands: dout (A of dA_4, K = 16), dout^T (B of dW_5^T), H_4^T
   // (A of dW_5^T); rows past the batch are zero
-  stage_rows_async(DZ, dout_bf + row0 * kOut, kBR, kOut, n - row0, t, kBR);
-  {
-    stage_row_t<kOut / 8>(DZT, dout_bf + r * kOut, live, t);
-    stage_row_t<kHid / 8>(HT, h_save + 3 * plane + r * kHid, live, t);
-  }
+  stage_rows_async(DZ, dout_bf + row0 * kOut, kBR, kOut, n - row0, tid, kBT);
+  if (h == 0) stage_row_t<kOut / 8>(DZT, dout_bf + r * kOut, live, t, 0);
+  stage_row_t<kHid / 16>(HT, h_save + 3 * plane + r * kHid, live, t, h * (kHid / 16));
   // db_5: column sums of the FP32 dout over the tile's rows
-  if (t < kOut) {
+  if (tid < kOut) {
     float s = 0.f;
-    for (int q = 0; q < kBR && row0 + q < n; ++q) s += dout[(row0 + q) * kOut + t];
-    part[poff(1, 4) + t] = s;
+    for (int q = 0; q < kBR && row0 + q < n; ++q) s += dout[(row0 + q) * kOut + tid];
+    part[poff(1, 4) + tid] = s;
   }
-  if (t == 0) {
+  if (tid == 0) {
     mbar_init(bar, 1);
     fence_barrier_init();
   }
@@ -161,14 +162,14 @@ __global__ void __launch_bounds__(kBR, 1)
   tc_fence_after();
   const uint32_t tmem = slot[0];
   const uint32_t d_a = tmem, d_w = tmem + (uint32_t)kHid;
-  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+  const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;  // warps w and w + 4 share lanes
   const uint32_t dz_addr = smem_u32(DZ), dzt_addr = smem_u32(DZT), ht_addr = smem_u32(HT);
   uint32_t phase = 0;
   bool failed = false;
 
   // the leader waits for the layer's commit; everybody learns the verdict
   auto wait_layer = [&]() -> bool {
-    if (t == 0) slot[1] = mma_wait(bar, phase) ? 1u : 0u;
+    if (tid == 0) slot[1] = mma_wait(bar, phase) ? 1u : 0u;
     phase ^= 1u;
     tc_fence_before();
     __syncthreads();
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(kBR, 1)
   };
 
   // ---- layer 5: dW_5^T = H_4^T dout (N = 16), dA_4 = dout W_5 (K = 16) ----
-  if (t == 0) {
+  if (tid == 0) {
     for (int s = 0; s < kBR / 16; ++s)
       tc_mma(d_w, smem_desc(ht_addr + 256 * s, 128, kBR * 16), smem_desc(dzt_addr + 256 * s, 128, kBR * 16),
              idesc_bf16(kBR, kOut), s > 0 ? 1u : 0u);
@@ -202,15 +203,17 @@ __global__ void __launch_bounds__(kBR, 1)
     // weight gradient of layer l: lane t holds row t of dW_l (out t), or for
     // layer 5 row t of dW_5^T (in t)
     if (l == 5) {
+      if (h == 0) {
       float v[16];
       ld_cols16(d_w + lane_off, v);
       float *g = part + poff(0, 4);  // W5 [16][128]
 #pragma unroll
       for (int o = 0; o < kOut; ++o) g[o * kHid + t] = v[o];
+      }
     } else {
       const int in = l == 1 ? kIn : kHid;
       float4 *g = reinterpret_cast<float4 *>(part + poff(0, l - 1) + (int64_t)t * in);
-      for (int c = 0; c < in / 16; ++c) {
+      for (int c = h * (in / 32); c < (h + 1) * (in / 32); ++c) {
         float v[16];
         ld_cols16(d_w + lane_off + (uint32_t)(16 * c), v);
 #pragma unroll
@@ -222,13 +225,14 @@ __global__ void __launch_bounds__(kBR, 1)
     {
       const float4 *z4 = reinterpret_cast<const float4 *>(z_save + (size_t)(l - 2) * plane + r * kHid);
       float4 zc[4], zn[4];
+      const int c0 = h * (kHid / 32), c1 = c0 + kHid / 32;  // this thread's 16-column chunks
 #pragma unroll
-      for (int q = 0; q < 4; ++q) zc[q] = live ? z4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int q = 0; q < 4; ++q) zc[q] = live ? z4[4 * c0 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 1
-      for (int c = 0; c < kHid / 16; ++c) {
+      for (int c = c0; c < c1; ++c) {
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-          zn[q] = live && c + 1 < kHid / 16 ? z4[4 * (c + 1) + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+          zn[q] = live && c + 1 < c1 ? z4[4 * (c + 1) + q] : make_float4(0.f, 0.f, 0.f, 0.f);
         float v[16];
         ld_cols16(d_a + lane_off + (uint32_t)(16 * c), v);
         const float zz[16] = {zc[0].x, zc[0].y, zc[0].z, zc[0].w, zc[1].x, zc[1].y, zc[1].z, zc[1].w,
@@ -250,12 +254,12 @@ __global__ void __launch_bounds__(kBR, 1)
     }
     // H_(l-2)^T for the weight gradient of layer l - 1 (X^T for layer 1)
     if (l - 1 == 1)
-      stage_row_t<kIn / 8>(HT, x + r * kIn, live, t);
+      stage_row_t<kIn / 16>(HT, x + r * kIn, live, t, h * (kIn / 16));
     else
-      stage_row_t<kHid / 8>(HT, h_save + (size_t)(l - 3) * plane + r * kHid, live, t);
+      stage_row_t<kHid / 16>(HT, h_save + (size_t)(l - 3) * plane + r * kHid, live, t, h * (kHid / 16));
     operands_ready();
     // MMAs of layer l - 1: dW_(l-1) = dZ^T H^T^T, dA_(l-2) = dZ W_(l-1)
-    if (t == 0) {
+    if (tid == 0) {
       const int nw = l - 1 == 1 ? kIn : kHid;
       for (int s = 0; s < kBR / 16; ++s)
         tc_mma(d_w, smem_desc(dzt_addr + 256 * s, 128, kBR * 16), smem_desc(ht_addr + 256 * s, 128, kBR * 16),
@@ -269,7 +273,7 @@ __global__ void __launch_bounds__(kBR, 1)
       tc_commit(bar);
     }
     // db_(l-1): column t of dZ_(l-1) summed over the tile's rows (row t of DZT)
-    {
+    if (h == 0) {
       float s = 0.f;
 #pragma unroll
       for (int k8 = 0; k8 < kBR / 8; ++k8) {
@@ -284,8 +288,8 @@ __global__ void __launch_bounds__(kBR, 1)
   }
   if (failed) {
     // the tile's gradient is unusable: NaN in its whole slot
-    for (int64_t i = t; i < n_params; i += kBR) part[i] = __int_as_float(0x7fc00000);
-    if (t == 0) (void)mbar_wait_bounded(bar, phase ^ 1u, 200000000ull);
+    for (int64_t i = tid; i < n_params; i += kBT) part[i] = __int_as_float(0x7fc00000);
+    if (tid == 0) (void)mbar_wait_bounded(bar, phase ^ 1u, 200000000ull);
   }
   tc_fence_before();
   __syncthreads();
@@ -295,8 +299,8 @@ __global__ void __launch_bounds__(kBR, 1)
 }
 
 // ---------------------------------------------------------------------------
-// training forward: the network on a 128-row tile per CTA, one thread per
-// row, saving every hidden layer's pre-activations Z (FP32) and activations
+// training forward: the network on a 128-row tile per CTA, two threads per
+// row (half of its columns each), saving every hidden layer's pre-activations Z (FP32) and activations
 // H = SiLU(Z) (BF16, the exponential form the backward pass differentiates)
 // ---------------------------------------------------------------------------
 namespace {
@@ -315,7 +319,7 @@ static_assert(kFSmem <= 227 * 1024, "shared memory");
 static_assert(kFOffBar % 8 == 0, "mbarrier alignment");
 }  // namespace
 
-__global__ void __launch_bounds__(kBR, 1)
+__global__ void __launch_bounds__(kBT, 1)
     mlp_forward_train_tc_kernel(MlpDev net, const __nv_bfloat16 *__restrict__ x, int64_t n, int standardized_out,
                                 float *__restrict__ out, __nv_bfloat16 *__restrict__ h_save,
                                 float *__restrict__ z_save) {
@@ -325,22 +329,26 @@ __global__ void __launch_bounds__(kBR, 1)
   volatile uint32_t *slot = reinterpret_cast<volatile uint32_t *>(sm + kFOffSlot);
   float *bias = reinterpret_cast<float *>(sm + kFOffBias);
   unsigned char *A = sm + kFOffA, *X = sm + kFOffX;
-  const int t = threadIdx.x, warp = t >> 5;
+  const int tid = threadIdx.x, t = tid & (kBR - 1), h = tid >> 7, warp = tid >> 5;
   const int64_t row0 = (int64_t)blockIdx.x * kBR, r = row0 + t;
   const bool live = r < n;
   const size_t plane = (size_t)n * kHid;
 
-  stage_rows_async(sm + kFOffW1, net.W[0], kHid, kIn, kHid, t, kBR);
+  stage_rows_async(sm + kFOffW1, net.W[0], kHid, kIn, kHid, tid, kBT);
   for (int l = 0; l < 3; ++l)
-    stage_rows_async(sm + kFOffWH + (uint32_t)l * kHid * kHid * 2, net.W[1 + l], kHid, kHid, kHid, t, kBR);
-  stage_rows_async(sm + kFOffW5, net.W[4], kOut, kHid, kOut, t, kBR);
-  stage_rows_async(X, x + row0 * kIn, kBR, kIn, n - row0, t, kBR);
-  for (int i = t; i < 4 * kHid + 3 * kOut; i += kBR)
-    bias[i] = i < 4 * kHid ? net.b[i / kHid][i % kHid]
-                           : (i < 4 * kHid + kOut ? net.b[4][i - 4 * kHid]
-                                                  : (i < 4 * kHid + 2 * kOut ? net.y_mu[i - 4 * kHid - kOut]
-                                                                             : net.y_sigma[i - 4 * kHid - 2 * kOut]));
-  if (t == 0) {
+    stage_rows_async(sm + kFOffWH + (uint32_t)l * kHid * kHid * 2, net.W[1 + l], kHid, kHid, kHid, tid, kBT);
+  stage_rows_async(sm + kFOffW5, net.W[4], kOut, kHid, kOut, tid, kBT);
+  stage_rows_async(X, x + row0 * kIn, kBR, kIn, n - row0, tid, kBT);
+  if (tid < kHid) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) bias[l * kHid + tid] = net.b[l][tid];
+  } else if (tid < kHid + kOut) {
+    const int j = tid - kHid;
+    bias[4 * kHid + j] = net.b[4][j];
+    bias[4 * kHid + kOut + j] = net.y_mu[j];
+    bias[4 * kHid + 2 * kOut + j] = net.y_sigma[j];
+  }
+  if (tid == 0) {
     mbar_init(bar, 1);
     fence_barrier_init();
   }
@@ -356,12 +364,12 @@ __global__ void __launch_bounds__(kBR, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = slot[0];
-  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+  const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;  // warps w and w + 4 share lanes
   const uint32_t a_addr = smem_u32(A), x_addr = smem_u32(X);
   uint32_t phase = 0;
   bool failed = false;
   auto wait_layer = [&]() -> bool {
-    if (t == 0) slot[1] = mma_wait(bar, phase) ? 1u : 0u;
+    if (tid == 0) slot[1] = mma_wait(bar, phase) ? 1u : 0u;
     phase ^= 1u;
     tc_fence_before();
     __syncthreads();
@@ -370,7 +378,7 @@ __global__ void __launch_bounds__(kBR, 1)
   };
 
   // layer 1
-  if (t == 0) {
+  if (tid == 0) {
     for (int s = 0; s < kIn / 16; ++s)
       tc_mma(tmem, smem_desc(x_addr + 256 * s, 128, kIn * 16), smem_desc(smem_u32(sm + kFOffW1) + 256 * s, 128, kIn * 16),
              idesc_bf16(kBR, kHid), s > 0 ? 1u : 0u);
@@ -387,7 +395,7 @@ __global__ void __launch_bounds__(kBR, 1)
     float4 *zs = reinterpret_cast<float4 *>(z_save + (size_t)l * plane + r * kHid);
     uint4 *hs = reinterpret_cast<uint4 *>(h_save + (size_t)l * plane + r * kHid);
 #pragma unroll 1
-    for (int c = 0; c < kHid / 16; ++c) {
+    for (int c = h * (kHid / 32); c < (h + 1) * (kHid / 32); ++c) {  // this thread's half of the columns
       float v[16];
       ld_cols16(tmem + lane_off + (uint32_t)(16 * c), v);
       uint32_t pk[8];
@@ -409,7 +417,7 @@ __global__ void __launch_bounds__(kBR, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (t == 0) {
+    if (tid == 0) {
       const int n_next = l == 3 ? kOut : kHid;
       const uint32_t w = l == 3 ? smem_u32(sm + kFOffW5) : smem_u32(sm + kFOffWH + (uint32_t)l * kHid * kHid * 2);
       for (int s = 0; s < kHid / 16; ++s)
@@ -419,7 +427,7 @@ __global__ void __launch_bounds__(kBR, 1)
     }
   }
   if (!failed && !wait_layer()) failed = true;
-  if (!failed) {
+  if (!failed && h == 0) {
     float v[16];
     ld_cols16(tmem + lane_off, v);
     const float *b5 = bias + 4 * kHid, *ymu = b5 + kOut, *ysg = ymu + kOut;
@@ -433,9 +441,10 @@ __global__ void __launch_bounds__(kBR, 1)
 #pragma unroll
       for (int q = 0; q < 4; ++q) o4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     }
-  } else if (live) {
-    for (int j = 0; j < kOut; ++j) out[r * kOut + j] = __int_as_float(0x7fc00000);
-    if (t == 0) (void)mbar_wait_bounded(bar, phase ^ 1u, 200000000ull);
+  } else if (failed) {
+    if (live && h == 0)
+      for (int j = 0; j < kOut; ++j) out[r * kOut + j] = __int_as_float(0x7fc00000);
+    if (tid == 0) (void)mbar_wait_bounded(bar, phase ^ 1u, 200000000ull);
   }
   tc_fence_before();
   __syncthreads();
@@ -457,7 +466,7 @@ int launch_mlp_forward_train_tc(const MlpDev &net, const void *x, int64_t n, int
     attr_done[dev] = 1;
   }
   const int64_t tiles = (n + kBR - 1) / kBR;
-  mlp_forward_train_tc_kernel<<<(unsigned)tiles, kBR, kFSmem, st>>>(
+  mlp_forward_train_tc_kernel<<<(unsigned)tiles, kBT, kFSmem, st>>>(
       net, reinterpret_cast<const __nv_bfloat16 *>(x), n, standardized_out, out,
       reinterpret_cast<__nv_bfloat16 *>(h_save), z_save);
   return 0;
@@ -492,7 +501,7 @@ int launch_mlp_backward_tc(const MlpDev &net, const void *x, const void *h_save,
   const int64_t tiles = (n + kBR - 1) / kBR;
   const int64_t np = mlp_param_count();
   float *parts = reinterpret_cast<float *>(ws);
-  mlp_backward_tc_kernel<<<(unsigned)tiles, kBR, kBSmem, st>>>(
+  mlp_backward_tc_kernel<<<(unsigned)tiles, kBT, kBSmem, st>>>(
       net, reinterpret_cast<const __nv_bfloat16 *>(x), reinterpret_cast<const __nv_bfloat16 *>(h_save), z_save,
       reinterpret_cast<const __nv_bfloat16 *>(dout_bf), dout, n, np, parts);
   sum_tiles_kernel<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(parts, (int)tiles, np, grads);
