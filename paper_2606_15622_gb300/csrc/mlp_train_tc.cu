@@ -66,14 +66,42 @@ __host__ __device__ constexpr int64_t poff(int which, int layer) {
   return which == 0 ? off : off + (layer == 0 ? kHid * kIn : (layer == 4 ? kOut * kHid : kHid * kHid));
 }
 
-// row t's values at columns i0 .. i0 + 7 (packed BF16 pairs) stored
-// transposed: element (i0 + j, t) of a K-major operand with K = 128 rows
-__device__ __forceinline__ void st_col8(unsigned char *base, int i0, int t, uint4 q) {
-  const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+// w rotated left by r (0 .. N - 1) places, with selects (no local memory)
+template <int N>
+__device__ __forceinline__ void rotate_words(uint32_t (&w)[N], int r) {
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    *reinterpret_cast<uint16_t *>(base + cm_elem(i0 + 2 * j, t, kBR)) = (uint16_t)(w4[j] & 0xffffu);
-    *reinterpret_cast<uint16_t *>(base + cm_elem(i0 + 2 * j + 1, t, kBR)) = (uint16_t)(w4[j] >> 16);
+  for (int b = 1; b < N; b <<= 1) {
+    uint32_t u[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) u[k] = (r & b) ? w[(k + b) % N] : w[k];
+#pragma unroll
+    for (int k = 0; k < N; ++k) w[k] = u[k];
+  }
+}
+
+// row t's values at columns i0 .. i0 + 7 (packed BF16 pairs, i0 a multiple
+// of 8) stored transposed: element (i0 + j, t) of a K-major operand with
+// K = 128 rows.  Elements (i, t) and (i, t ^ 1) share a 32-bit word, so lanes
+// t and t ^ 1 swap their values and each writes four whole words (the even
+// lane the even columns); the start is rotated by the lane's 8-row group so
+// that the 32 stores of one instruction fall in 32 different banks.  Called
+// by all lanes of a warp, with t = the row = a multiple of 32 plus the lane.
+__device__ __forceinline__ void st_col8(unsigned char *base, int i0, int t, uint4 q) {
+  const uint32_t mine[4] = {q.x, q.y, q.z, q.w};
+  const bool odd = t & 1;
+  uint32_t w[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t nb = __shfl_xor_sync(0xffffffffu, mine[k], 1);
+    // word of column i0 + 2k + odd: low half row t & ~1, high half row t | 1
+    w[k] = odd ? __byte_perm(nb, mine[k], 0x7632) : __byte_perm(mine[k], nb, 0x5410);
+  }
+  const int g = (t >> 3) & 3;
+  rotate_words(w, g);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int i = i0 + 2 * ((k + g) & 3) + (odd ? 1 : 0);
+    *reinterpret_cast<uint32_t *>(base + cm_elem(i, t & ~1, kBR)) = w[k];
   }
 }
 
@@ -115,19 +143,29 @@ __global__ void __launch_bounds__(kBT, 1)
   float *part = parts + (int64_t)blockIdx.x * n_params;
   const size_t plane = (size_t)n * kHid;  // one layer of h_save / z_save
 
-  // W_l^T (l = 2..4) and W_5^T, transposed into the B layout once
+  // W_l^T (l = 2..4) and W_5^T, transposed into the B layout once.  Element
+  // (i, o) and (i, o + 1) share a 32-bit word: a thread takes inputs
+  // 8 ib .. 8 ib + 7 of an output pair and writes eight words, starting at an
+  // input rotated by its block, so that a warp's 32 stores (four output pairs
+  // by eight input blocks) fall in 32 different banks
   for (int l = 0; l < 3; ++l) {
-    const __nv_bfloat16 *W = net.W[1 + l];  // [out][in]
+    const uint4 *W = reinterpret_cast<const uint4 *>(net.W[1 + l]);  // [out][in], 8 inputs a vector
     unsigned char *WT = sm + kBOffWT + (uint32_t)l * kHid * kHid * 2;
-    for (int e = tid; e < kHid * kHid / 8; e += kBT) {  // 8 consecutive inputs of output o
-      const int o = e / (kHid / 8), i0 = 8 * (e % (kHid / 8));
-      const uint4 q = reinterpret_cast<const uint4 *>(W)[e];
-      const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+    for (int e = tid; e < (kHid / 2) * (kHid / 8); e += kBT) {
+      const int lane = e & 31, grp = e >> 5, jb = lane >> 2;
+      const int o = 2 * (4 * (grp % 16) + (lane & 3)), ib = 8 * (grp / 16) + jb;
+      const uint4 qa = W[o * (kHid / 8) + ib], qb = W[(o + 1) * (kHid / 8) + ib];
+      const uint32_t a4[4] = {qa.x, qa.y, qa.z, qa.w}, b4[4] = {qb.x, qb.y, qb.z, qb.w};
+      uint32_t w[8];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        *reinterpret_cast<uint16_t *>(WT + cm_elem(i0 + 2 * j, o, kHid)) = (uint16_t)(w4[j] & 0xffffu);
-        *reinterpret_cast<uint16_t *>(WT + cm_elem(i0 + 2 * j + 1, o, kHid)) = (uint16_t)(w4[j] >> 16);
+      for (int k = 0; k < 4; ++k) {
+        w[2 * k] = __byte_perm(a4[k], b4[k], 0x5410);
+        w[2 * k + 1] = __byte_perm(a4[k], b4[k], 0x7632);
       }
+      rotate_words(w, jb);
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        *reinterpret_cast<uint32_t *>(WT + cm_elem(8 * ib + ((k + jb) & 7), o, kHid)) = w[k];
     }
   }
   for (int e = tid; e < kOut * kHid; e += kBT) {
