@@ -330,9 +330,12 @@ int fp_surrogate_features(const fp_mlp *net, const double *moments, int64_t n_ce
 
 /* The fused network on n rows of BF16 features x [n][32]:
  * out [n][16] FP32 -- standardised outputs when standardized_out != 0, else
- * y_mu + y_sigma * output.  For training, h_save ([4][n][128] BF16, the
- * hidden activations) and z_save ([4][n][128] FP32, their pre-activations)
- * are written when both are non-NULL.  No workspace. */
+ * y_mu + y_sigma * output.  For training, h_save (4 x n x 128 BF16, the
+ * hidden activations) and z_save (4 x n x 128 FP32, their pre-activations)
+ * are written when both are non-NULL, column-block-major so that the rows of
+ * a warp are written and read back contiguously: columns 8k .. 8k + 7 of
+ * row r of layer l at h_save + ((l * 16 + k) * n + r) * 8, columns
+ * 4k .. 4k + 3 at z_save + ((l * 32 + k) * n + r) * 4.  No workspace. */
 int fp_mlp_forward(const fp_mlp *net, const void *x, int64_t n, int standardized_out, float *out, void *h_save,
                    float *z_save, fp_stream_t stream);
 

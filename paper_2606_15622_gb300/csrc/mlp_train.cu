@@ -28,22 +28,39 @@ struct LossParams {
   float lam_d, lam_e, eps2_hat, scale;  // scale multiplies the gradient (1 / batch)
 };
 
-__global__ void __launch_bounds__(256) loss_kernel(const float *__restrict__ out, const float *__restrict__ t_true,
-                                                   const float *__restrict__ aux, const float *__restrict__ y_mu,
-                                                   const float *__restrict__ y_sigma, int64_t n, LossParams prm,
-                                                   float *__restrict__ dout, __nv_bfloat16 *__restrict__ dout_bf,
-                                                   float *__restrict__ loss_sum) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// A warp takes 32 consecutive rows: their out, aux and t_true rows are
+// copied into shared memory with coalesced loads (rows of 16 padded to 17
+// floats, so that the lanes' row reads fall in different banks), each lane
+// computes its row, and dout goes back the same way.
+constexpr int kLossWarps = 2;
+constexpr int kLS = kOut + 1;  // padded row stride (floats)
+
+__global__ void __launch_bounds__(32 * kLossWarps)
+    loss_kernel(const float *__restrict__ out, const float *__restrict__ t_true, const float *__restrict__ aux,
+                const float *__restrict__ y_mu, const float *__restrict__ y_sigma, int64_t n, LossParams prm,
+                float *__restrict__ dout, __nv_bfloat16 *__restrict__ dout_bf, float *__restrict__ loss_sum) {
+  __shared__ float s_o[kLossWarps][32 * kLS], s_a[kLossWarps][32 * kLS], s_t[kLossWarps][32 * kNOut];
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  const int64_t row0 = ((int64_t)blockIdx.x * kLossWarps + wq) * 32, r = row0 + lane;
+  const int nr = (int)(n - row0 < 32 ? (n - row0 > 0 ? n - row0 : 0) : 32);  // rows of this warp
+  float *so = s_o[wq], *sa = s_a[wq], *sT = s_t[wq];
+  for (int i = lane; i < nr * kOut; i += 32) {
+    so[(i / kOut) * kLS + i % kOut] = out[row0 * kOut + i];
+    sa[(i / kOut) * kLS + i % kOut] = aux[row0 * 16 + i];
+  }
+  for (int i = lane; i < nr * kNOut; i += 32) sT[i] = t_true[row0 * kNOut + i];
+  __syncwarp();
   float lsum = 0.f;
   if (r < n) {
+    const float *orow = so + lane * kLS, *trow = sT + lane * kNOut;
     float o[kNOut], d[kNOut], gr[kNOut];
 #pragma unroll
     for (int a = 0; a < kNOut; ++a) {
-      o[a] = out[r * kOut + a];
+      o[a] = orow[a];
       const float tp = y_mu[a] + y_sigma[a] * o[a];
-      d[a] = tp - t_true[r * kNOut + a];
+      d[a] = tp - trow[a];
     }
-    const float *x = aux + r * 16;  // u_hat (6), b_hat (3), s4_hat
+    const float *x = sa + lane * kLS;  // u_hat (6), b_hat (3), s4_hat
     const float U[3][3] = {{x[0], x[1], x[2]}, {x[1], x[3], x[4]}, {x[2], x[4], x[5]}};
     const float b[3] = {x[6], x[7], x[8]};
     const float s4 = x[9];
@@ -95,18 +112,21 @@ __global__ void __launch_bounds__(256) loss_kernel(const float *__restrict__ out
     float mse = 0.f;
 #pragma unroll
     for (int a = 0; a < kNOut; ++a) {
-      const float z = (t_true[r * kNOut + a] - y_mu[a]) / y_sigma[a];
+      const float z = (trow[a] - y_mu[a]) / y_sigma[a];
       const float df = o[a] - z;
       mse += prm.w[a] * df * df;
       gr[a] = 2.f * prm.w[a] * df + y_sigma[a] * (prm.lam_d * gq[a] + prm.lam_e * 2.f * e * de[a]);
     }
     lsum = mse + prm.lam_d * q + prm.lam_e * e * e;
+    float *drow = so + lane * kLS;  // this lane's out row is no longer needed
 #pragma unroll
-    for (int a = 0; a < kOut; ++a) {
-      const float v = a < kNOut ? gr[a] * prm.scale : 0.f;
-      dout[r * kOut + a] = v;
-      dout_bf[r * kOut + a] = __float2bfloat16_rn(v);
-    }
+    for (int a = 0; a < kOut; ++a) drow[a] = a < kNOut ? gr[a] * prm.scale : 0.f;
+  }
+  __syncwarp();
+  for (int i = lane; i < nr * kOut; i += 32) {
+    const float v = so[(i / kOut) * kLS + i % kOut];
+    dout[row0 * kOut + i] = v;
+    dout_bf[row0 * kOut + i] = __float2bfloat16_rn(v);
   }
   // block sum of the loss
 #pragma unroll
@@ -172,7 +192,7 @@ void launch_loss(const float *out, const float *t_true, const float *aux, const 
   prm.lam_e = lam_e;
   prm.eps2_hat = eps2_hat;
   prm.scale = scale;
-  loss_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, t_true, aux, y_mu, y_sigma, n, prm, dout,
+  loss_kernel<<<(unsigned)((n + 32 * kLossWarps - 1) / (32 * kLossWarps)), 32 * kLossWarps, 0, st>>>(out, t_true, aux, y_mu, y_sigma, n, prm, dout,
                                                             reinterpret_cast<__nv_bfloat16 *>(dout_bf), loss_sum);
 }
 

@@ -141,7 +141,6 @@ __global__ void __launch_bounds__(kBT, 1)
   const int64_t row0 = (int64_t)blockIdx.x * kBR, r = row0 + t;
   const bool live = r < n;
   float *part = parts + (int64_t)blockIdx.x * n_params;
-  const size_t plane = (size_t)n * kHid;  // one layer of h_save / z_save
 
   // W_l^T (l = 2..4) and W_5^T, transposed into the B layout once.  Element
   // (i, o) and (i, o + 1) share a 32-bit word: a thread takes inputs
@@ -176,7 +175,14 @@ __global__ void __launch_bounds__(kBT, 1)
   // (A of dW_5^T); rows past the batch are zero
   stage_rows_async(DZ, dout_bf + row0 * kOut, kBR, kOut, n - row0, tid, kBT);
   if (h == 0) stage_row_t<kOut / 8>(DZT, dout_bf + r * kOut, live, t, 0);
-  stage_row_t<kHid / 16>(HT, h_save + 3 * plane + r * kHid, live, t, h * (kHid / 16));
+  {
+    const uint4 *h4 = reinterpret_cast<const uint4 *>(h_save) + ((size_t)3 * (kHid / 8) + h * (kHid / 16)) * n + r;
+    uint4 q[kHid / 16];
+#pragma unroll
+    for (int v = 0; v < kHid / 16; ++v) q[v] = live ? h4[(size_t)v * n] : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+    for (int v = 0; v < kHid / 16; ++v) st_col8(HT, 8 * (h * (kHid / 16) + v), t, q[v]);
+  }
   // db_5: column sums of the FP32 dout over the tile's rows
   if (tid < kOut) {
     float s = 0.f;
@@ -234,6 +240,23 @@ __global__ void __launch_bounds__(kBT, 1)
   // layers l = 5 .. 1: epilogue of layer l's MMAs, then the MMAs of layer l - 1
 #pragma unroll 1
   for (int l = 5; l >= 1; --l) {
+    // this thread's half row of Z_(l-1) and of H_(l-2) (X for layer 1),
+    // loaded while the layer's MMAs run
+    float4 zr[kHid / 8];
+    uint4 hr[kHid / 16];
+    if (l >= 2) {
+      const float4 *z4 = reinterpret_cast<const float4 *>(z_save) + ((size_t)(l - 2) * (kHid / 4) + h * (kHid / 8)) * n + r;
+#pragma unroll
+      for (int q = 0; q < kHid / 8; ++q) zr[q] = live ? z4[(size_t)q * n] : make_float4(0.f, 0.f, 0.f, 0.f);
+      // X rows are row-major, the saved H column-block-major
+      const uint4 *h4 = l - 1 == 1 ? reinterpret_cast<const uint4 *>(x + r * kIn) + h * (kIn / 16)
+                                   : reinterpret_cast<const uint4 *>(h_save) +
+                                         ((size_t)(l - 3) * (kHid / 8) + h * (kHid / 16)) * n + r;
+      const int nh = l - 1 == 1 ? kIn / 16 : kHid / 16;
+      const size_t hstride = l - 1 == 1 ? 1 : (size_t)n;
+#pragma unroll
+      for (int v = 0; v < kHid / 16; ++v) hr[v] = live && v < nh ? h4[v * hstride] : make_uint4(0u, 0u, 0u, 0u);
+    }
     if (!wait_layer()) {
       failed = true;
       break;
@@ -249,40 +272,37 @@ __global__ void __launch_bounds__(kBT, 1)
       for (int o = 0; o < kOut; ++o) g[o * kHid + t] = v[o];
       }
     } else {
+      // kept in blocks of four inputs ([in / 4][out][4], coalesced; the
+      // tile sum restores the flat layout)
       const int in = l == 1 ? kIn : kHid;
-      float4 *g = reinterpret_cast<float4 *>(part + poff(0, l - 1) + (int64_t)t * in);
+      float4 *g = reinterpret_cast<float4 *>(part + poff(0, l - 1)) + t;
       for (int c = h * (in / 32); c < (h + 1) * (in / 32); ++c) {
         float v[16];
         ld_cols16(d_w + lane_off + (uint32_t)(16 * c), v);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) g[4 * c + q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        for (int q = 0; q < 4; ++q)
+          g[(4 * c + q) * kHid] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
       }
     }
     if (l == 1) break;
     // dZ_(l-1) = dA_(l-1) silu'(Z_(l-1)) -> DZ (row t) and DZT (column t)
     {
-      const float4 *z4 = reinterpret_cast<const float4 *>(z_save + (size_t)(l - 2) * plane + r * kHid);
-      float4 zc[4], zn[4];
-      const int c0 = h * (kHid / 32), c1 = c0 + kHid / 32;  // this thread's 16-column chunks
+      const int c0 = h * (kHid / 32);  // this thread's 16-column chunks c0 .. c0 + 3
 #pragma unroll
-      for (int q = 0; q < 4; ++q) zc[q] = live ? z4[4 * c0 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 1
-      for (int c = c0; c < c1; ++c) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          zn[q] = live && c + 1 < c1 ? z4[4 * (c + 1) + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int cc = 0; cc < kHid / 32; ++cc) {
+        const int c = c0 + cc;
         float v[16];
         ld_cols16(d_a + lane_off + (uint32_t)(16 * c), v);
-        const float zz[16] = {zc[0].x, zc[0].y, zc[0].z, zc[0].w, zc[1].x, zc[1].y, zc[1].z, zc[1].w,
-                              zc[2].x, zc[2].y, zc[2].z, zc[2].w, zc[3].x, zc[3].y, zc[3].z, zc[3].w};
+        const float zz[16] = {zr[4 * cc].x,     zr[4 * cc].y,     zr[4 * cc].z,     zr[4 * cc].w,
+                              zr[4 * cc + 1].x, zr[4 * cc + 1].y, zr[4 * cc + 1].z, zr[4 * cc + 1].w,
+                              zr[4 * cc + 2].x, zr[4 * cc + 2].y, zr[4 * cc + 2].z, zr[4 * cc + 2].w,
+                              zr[4 * cc + 3].x, zr[4 * cc + 3].y, zr[4 * cc + 3].z, zr[4 * cc + 3].w};
         uint32_t pk[8];
 #pragma unroll
         for (int j = 0; j < 16; j += 2) {
           const float g0 = live ? v[j] * silu_grad(zz[j]) : 0.f, g1 = live ? v[j + 1] * silu_grad(zz[j + 1]) : 0.f;
           pk[j / 2] = pack_bf16(g0, g1);
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) zc[q] = zn[q];
         const uint4 lo = make_uint4(pk[0], pk[1], pk[2], pk[3]), hi = make_uint4(pk[4], pk[5], pk[6], pk[7]);
         *reinterpret_cast<uint4 *>(DZ + cm_off(t, 2 * c, kHid)) = lo;
         *reinterpret_cast<uint4 *>(DZ + cm_off(t, 2 * c + 1, kHid)) = hi;
@@ -291,10 +311,13 @@ __global__ void __launch_bounds__(kBT, 1)
       }
     }
     // H_(l-2)^T for the weight gradient of layer l - 1 (X^T for layer 1)
-    if (l - 1 == 1)
-      stage_row_t<kIn / 16>(HT, x + r * kIn, live, t, h * (kIn / 16));
-    else
-      stage_row_t<kHid / 16>(HT, h_save + (size_t)(l - 3) * plane + r * kHid, live, t, h * (kHid / 16));
+    if (l - 1 == 1) {
+#pragma unroll
+      for (int v = 0; v < kIn / 16; ++v) st_col8(HT, 8 * (h * (kIn / 16) + v), t, hr[v]);
+    } else {
+#pragma unroll
+      for (int v = 0; v < kHid / 16; ++v) st_col8(HT, 8 * (h * (kHid / 16) + v), t, hr[v]);
+    }
     operands_ready();
     // MMAs of layer l - 1: dW_(l-1) = dZ^T H^T^T, dA_(l-2) = dZ W_(l-1)
     if (tid == 0) {
@@ -370,7 +393,6 @@ __global__ void __launch_bounds__(kBT, 1)
   const int tid = threadIdx.x, t = tid & (kBR - 1), h = tid >> 7, warp = tid >> 5;
   const int64_t row0 = (int64_t)blockIdx.x * kBR, r = row0 + t;
   const bool live = r < n;
-  const size_t plane = (size_t)n * kHid;
 
   stage_rows_async(sm + kFOffW1, net.W[0], kHid, kIn, kHid, tid, kBT);
   for (int l = 0; l < 3; ++l)
@@ -430,8 +452,10 @@ __global__ void __launch_bounds__(kBT, 1)
     }
     // z = acc + b, H = SiLU(z): saved, and the next layer's A operand
     const float *bl = bias + l * kHid;
-    float4 *zs = reinterpret_cast<float4 *>(z_save + (size_t)l * plane + r * kHid);
-    uint4 *hs = reinterpret_cast<uint4 *>(h_save + (size_t)l * plane + r * kHid);
+    // saved column-block-major (Z in blocks of four columns, H of eight), so
+    // that the 32 rows of a warp write 512 contiguous bytes
+    float4 *zs = reinterpret_cast<float4 *>(z_save) + (size_t)l * (kHid / 4) * n + r;
+    uint4 *hs = reinterpret_cast<uint4 *>(h_save) + (size_t)l * (kHid / 8) * n + r;
 #pragma unroll 1
     for (int c = h * (kHid / 32); c < (h + 1) * (kHid / 32); ++c) {  // this thread's half of the columns
       float v[16];
@@ -446,9 +470,10 @@ __global__ void __launch_bounds__(kBT, 1)
       *reinterpret_cast<uint4 *>(A + cm_off(t, 2 * c + 1, kHid)) = hi;
       if (live) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) zs[4 * c + q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        hs[2 * c] = lo;
-        hs[2 * c + 1] = hi;
+        for (int q = 0; q < 4; ++q)
+          zs[(size_t)(4 * c + q) * n] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        hs[(size_t)(2 * c) * n] = lo;
+        hs[(size_t)(2 * c + 1) * n] = hi;
       }
     }
     fence_proxy_async_smem();
@@ -513,9 +538,29 @@ int launch_mlp_forward_train_tc(const MlpDev &net, const void *x, int64_t n, int
 __global__ void sum_tiles_kernel(const float *__restrict__ parts, int ntiles, int64_t cnt, float *__restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= cnt) return;
+  // tile order (the result does not depend on scheduling), loads eight at a time
   float s = 0.f;
-  for (int z = 0; z < ntiles; ++z) s += parts[z * cnt + i];
-  out[i] = s;
+  int z = 0;
+  for (; z + 8 <= ntiles; z += 8) {
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = parts[(int64_t)(z + k) * cnt + i];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += v[k];
+  }
+  for (; z < ntiles; ++z) s += parts[(int64_t)z * cnt + i];
+  // the hidden layers' weight gradients are kept in blocks of four inputs
+  // ([in / 4][out][4]); everything else is in the flat layout
+  int64_t dst = i;
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    const int64_t off = poff(0, l), in = l == 0 ? kIn : kHid;
+    if (i >= off && i < off + kHid * in) {
+      const int64_t loc = i - off;
+      dst = off + ((loc >> 2) % kHid) * in + 4 * (loc / (4 * kHid)) + (loc & 3);
+    }
+  }
+  out[dst] = s;
 }
 
 size_t mlp_backward_tc_ws(int64_t n) {

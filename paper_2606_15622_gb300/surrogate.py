@@ -56,6 +56,13 @@ def param_offset(which: int, layer: int) -> int:
     return int(_lib().fp_mlp_param_offset(which, layer))
 
 
+def saved_rows(a):
+    """A saved-activation buffer of fp_mlp_forward ([4][128 / b][n][b]: b = 8
+    for H, 4 for Z) as [4][n][128]."""
+    d, kb, n, b = a.shape
+    return a.permute(0, 2, 1, 3).reshape(d, n, kb * b)
+
+
 def _p(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
@@ -150,9 +157,9 @@ class Surrogate:
         n = x.shape[0]
         o = out if out is not None else torch.empty((n, OUT), dtype=torch.float32, device=self.device)
         h = z = None
-        if save:
-            h = torch.empty((DEPTH, n, HID), dtype=torch.bfloat16, device=self.device)
-            z = torch.empty((DEPTH, n, HID), dtype=torch.float32, device=self.device)
+        if save:  # column-block-major (see saved_rows)
+            h = torch.empty((DEPTH, HID // 8, n, 8), dtype=torch.bfloat16, device=self.device)
+            z = torch.empty((DEPTH, HID // 4, n, 4), dtype=torch.float32, device=self.device)
         api._need_cuda(x, o)
         api._want(x, "x", torch.bfloat16, n * IN)
         api._want(o, "out", torch.float32, n * OUT)

@@ -53,16 +53,17 @@ def test_forward_matches_reference(n):
 
 @pytest.mark.parametrize("n", [1, 128, 129, 255, 256, 40000])
 def test_tensor_core_inference_matches_training_forward(n):
-    """The inference pass (tcgen05, accumulators in tensor memory) and the
-    training pass (mma.sync) round at the same points; they differ only by
-    FP32 accumulation order.  Sizes cover one row, exact and ragged 128-row
-    tiles, both groups of a CTA and many tiles per CTA."""
+    """The inference pass (persistent tcgen05 kernel, two tile groups a CTA)
+    and the training pass (a 128-row tile a CTA, saving the activations)
+    round at the same points; they differ only by FP32 accumulation order.
+    Sizes cover one row, exact and ragged 128-row tiles, both groups of a CTA
+    and many tiles per CTA."""
     s, prm = _surrogate_with_random_params(seed=8)
     x = torch.from_numpy(_inputs(n, 100 + n)).cuda().to(torch.bfloat16)
     o_tc = s.forward(x, standardized=True)
-    o_mma = s.forward(x, standardized=True, save=True)[0]
+    o_tr = s.forward(x, standardized=True, save=True)[0]
     torch.cuda.synchronize()
-    a, b = o_tc.cpu().numpy(), o_mma.cpu().numpy()
+    a, b = o_tc.cpu().numpy(), o_tr.cpu().numpy()
     assert np.isfinite(a).all()
     err = np.abs(a - b)
     assert err.max() <= 2e-2 * np.abs(b).max()
@@ -86,6 +87,15 @@ def test_forward_saves_activations_and_unstandardizes():
     np.testing.assert_allclose((o_inf * s.y_sigma + s.y_mu).cpu().numpy()[:, :9], o_raw.cpu().numpy()[:, :9],
                                rtol=1e-6, atol=1e-6)
     # saved activations are SiLU of the saved pre-activations, rounded to BF16
+    h, z = S.saved_rows(h), S.saved_rows(z)
+    assert h.shape == z.shape == (4, 300, 128)
+    # in the documented layout: every layer's pre-activations against the
+    # oracle's (BF16 operands, FP32 results)
+    _, (hs_ref, zs_ref) = M.forward(prm, x.float().cpu().numpy().astype(np.float64), bf16=True, keep=True)
+    for l in range(4):
+        zr = zs_ref[l]
+        err = np.abs(z[l].cpu().numpy() - zr)
+        assert np.all(err <= 2.0 ** -6 * np.abs(zr) + 2.0 ** -6 * np.sqrt((zr ** 2).mean(0, keepdims=True))), l
     np.testing.assert_allclose(h.float().cpu().numpy(), M.bf16_round(M.silu(z.cpu().numpy())), rtol=1e-2, atol=1e-3)
 
 
