@@ -1,8 +1,8 @@
 // mlp_train_tc.cu -- backward pass of the network for training, on the
 // fifth-generation tensor cores of sm_103a (tcgen05, BF16 x BF16 -> FP32).
 //
-// One CTA per 128-row tile of the batch, two threads per row (= TMEM lane),
-// each with half of the row's columns.
+// One CTA per 128-row tile of the batch, four threads per row (= TMEM lane),
+// each with a quarter of the row's columns.
 // Going down the layers l = 5 .. 1 with dZ_5 = dout:
 //   weight gradient  dW_l = dZ_l^T H_(l-1)   (M = out, N = in, K = the
 //                    tile's 128 rows; layer 5 as dW_5^T = H_4^T dZ_5 so that
@@ -40,7 +40,12 @@ int64_t mlp_param_count();
 namespace {
 
 constexpr int kBR = 128;               // rows per tile = TMEM lanes
-constexpr int kBT = 2 * kBR;           // threads: two per row, each with half of the row's columns
+constexpr int kPart = 4;               // threads per row, each with a quarter of the row's columns
+constexpr int kBT = kPart * kBR;
+constexpr int kZB = kHid / 4 / kPart;  // a thread's 4-column blocks of Z
+constexpr int kHB = kHid / 8 / kPart;  // a thread's 8-column blocks of H
+constexpr int kXB = kIn / 8 / kPart;   // a thread's 8-column blocks of X
+static_assert(kZB % 4 == 0 && kXB >= 1, "a thread's columns are whole 16-column chunks");
 constexpr uint32_t kBTmemCols = 256;   // data gradient [0, 128), weight gradient [128, 256)
 
 // shared-memory carve-up (bytes from a 1024-byte aligned base)
@@ -51,7 +56,8 @@ constexpr uint32_t kBOffDZT = kBOffDZ + kBR * kHid * 2;        // dZ^T: [out][K 
 constexpr uint32_t kBOffHT = kBOffDZT + kHid * kBR * 2;        // H^T: [in][K = 128 rows]
 constexpr uint32_t kBOffBar = kBOffHT + kHid * kBR * 2;         // one mbarrier
 constexpr uint32_t kBOffSlot = kBOffBar + 8;                   // TMEM address, verdict
-constexpr uint32_t kBSmemUsed = kBOffSlot + 16;
+constexpr uint32_t kBOffRed = kBOffSlot + 16;                  // db_5 partial sums: [16 row groups][16]
+constexpr uint32_t kBSmemUsed = kBOffRed + kBT * 4;
 constexpr size_t kBSmem = kBSmemUsed + 1024;
 static_assert(kBSmem <= 227 * 1024, "shared memory");
 
@@ -137,7 +143,7 @@ __global__ void __launch_bounds__(kBT, 1)
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kBOffBar);
   volatile uint32_t *slot = reinterpret_cast<volatile uint32_t *>(sm + kBOffSlot);
   unsigned char *DZ = sm + kBOffDZ, *DZT = sm + kBOffDZT, *HT = sm + kBOffHT;
-  const int tid = threadIdx.x, t = tid & (kBR - 1), h = tid >> 7, warp = tid >> 5;
+  const int tid = threadIdx.x, t = tid & (kBR - 1), qd = tid >> 7, warp = tid >> 5;  // row t, part qd
   const int64_t row0 = (int64_t)blockIdx.x * kBR, r = row0 + t;
   const bool live = r < n;
   float *part = parts + (int64_t)blockIdx.x * n_params;
@@ -147,9 +153,11 @@ __global__ void __launch_bounds__(kBT, 1)
   // 8 ib .. 8 ib + 7 of an output pair and writes eight words, starting at an
   // input rotated by its block, so that a warp's 32 stores (four output pairs
   // by eight input blocks) fall in 32 different banks
+#pragma unroll
   for (int l = 0; l < 3; ++l) {
     const uint4 *W = reinterpret_cast<const uint4 *>(net.W[1 + l]);  // [out][in], 8 inputs a vector
     unsigned char *WT = sm + kBOffWT + (uint32_t)l * kHid * kHid * 2;
+#pragma unroll 1
     for (int e = tid; e < (kHid / 2) * (kHid / 8); e += kBT) {
       const int lane = e & 31, grp = e >> 5, jb = lane >> 2;
       const int o = 2 * (4 * (grp % 16) + (lane & 3)), ib = 8 * (grp / 16) + jb;
@@ -174,20 +182,30 @@ __global__ void __launch_bounds__(kBT, 1)
   // layer 5 operands: dout (A of dA_4, K = 16), dout^T (B of dW_5^T), H_4^T
   // (A of dW_5^T); rows past the batch are zero
   stage_rows_async(DZ, dout_bf + row0 * kOut, kBR, kOut, n - row0, tid, kBT);
-  if (h == 0) stage_row_t<kOut / 8>(DZT, dout_bf + r * kOut, live, t, 0);
+  if (qd == 0) stage_row_t<kOut / 8>(DZT, dout_bf + r * kOut, live, t, 0);
   {
-    const uint4 *h4 = reinterpret_cast<const uint4 *>(h_save) + ((size_t)3 * (kHid / 8) + h * (kHid / 16)) * n + r;
-    uint4 q[kHid / 16];
+    const uint4 *h4 = reinterpret_cast<const uint4 *>(h_save) + ((size_t)3 * (kHid / 8) + qd * kHB) * n + r;
+    uint4 q[kHB];
 #pragma unroll
-    for (int v = 0; v < kHid / 16; ++v) q[v] = live ? h4[(size_t)v * n] : make_uint4(0u, 0u, 0u, 0u);
+    for (int v = 0; v < kHB; ++v) q[v] = live ? h4[(size_t)v * n] : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-    for (int v = 0; v < kHid / 16; ++v) st_col8(HT, 8 * (h * (kHid / 16) + v), t, q[v]);
+    for (int v = 0; v < kHB; ++v) st_col8(HT, 8 * (qd * kHB + v), t, q[v]);
   }
-  // db_5: column sums of the FP32 dout over the tile's rows
-  if (tid < kOut) {
+  // db_5, first half: column tid % 16 of the FP32 dout summed over rows
+  // tid / 16 + G k, G = kBT / 16 row groups (coalesced loads, all issued at once)
+  {
+    constexpr int G = kBT / kOut;
+    static_assert(kBR % G == 0, "db_5 row groups");
+    float d[kBR / G];
+#pragma unroll
+    for (int k = 0; k < kBR / G; ++k) {
+      const int64_t q = (tid >> 4) + G * k;
+      d[k] = row0 + q < n ? dout[(row0 + q) * kOut + (tid & 15)] : 0.f;
+    }
     float s = 0.f;
-    for (int q = 0; q < kBR && row0 + q < n; ++q) s += dout[(row0 + q) * kOut + tid];
-    part[poff(1, 4) + tid] = s;
+#pragma unroll
+    for (int k = 0; k < kBR / G; ++k) s += d[k];
+    reinterpret_cast<float *>(sm + kBOffRed)[tid] = s;
   }
   if (tid == 0) {
     mbar_init(bar, 1);
@@ -206,7 +224,7 @@ __global__ void __launch_bounds__(kBT, 1)
   tc_fence_after();
   const uint32_t tmem = slot[0];
   const uint32_t d_a = tmem, d_w = tmem + (uint32_t)kHid;
-  const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;  // warps w and w + 4 share lanes
+  const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;  // warps w, w + 4, w + 8, w + 12 share lanes
   const uint32_t dz_addr = smem_u32(DZ), dzt_addr = smem_u32(DZT), ht_addr = smem_u32(HT);
   uint32_t phase = 0;
   bool failed = false;
@@ -240,22 +258,21 @@ __global__ void __launch_bounds__(kBT, 1)
   // layers l = 5 .. 1: epilogue of layer l's MMAs, then the MMAs of layer l - 1
 #pragma unroll 1
   for (int l = 5; l >= 1; --l) {
-    // this thread's half row of Z_(l-1) and of H_(l-2) (X for layer 1),
+    // this thread's part of row t of Z_(l-1) and of H_(l-2) (X for layer 1),
     // loaded while the layer's MMAs run
-    float4 zr[kHid / 8];
-    uint4 hr[kHid / 16];
+    float4 zr[kZB];
+    uint4 hr[kHB];
     if (l >= 2) {
-      const float4 *z4 = reinterpret_cast<const float4 *>(z_save) + ((size_t)(l - 2) * (kHid / 4) + h * (kHid / 8)) * n + r;
+      const float4 *z4 = reinterpret_cast<const float4 *>(z_save) + ((size_t)(l - 2) * (kHid / 4) + qd * kZB) * n + r;
 #pragma unroll
-      for (int q = 0; q < kHid / 8; ++q) zr[q] = live ? z4[(size_t)q * n] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int q = 0; q < kZB; ++q) zr[q] = live ? z4[(size_t)q * n] : make_float4(0.f, 0.f, 0.f, 0.f);
       // X rows are row-major, the saved H column-block-major
-      const uint4 *h4 = l - 1 == 1 ? reinterpret_cast<const uint4 *>(x + r * kIn) + h * (kIn / 16)
-                                   : reinterpret_cast<const uint4 *>(h_save) +
-                                         ((size_t)(l - 3) * (kHid / 8) + h * (kHid / 16)) * n + r;
-      const int nh = l - 1 == 1 ? kIn / 16 : kHid / 16;
+      const uint4 *h4 = l - 1 == 1 ? reinterpret_cast<const uint4 *>(x + r * kIn) + qd * kXB
+                                   : reinterpret_cast<const uint4 *>(h_save) + ((size_t)(l - 3) * (kHid / 8) + qd * kHB) * n + r;
+      const int nh = l - 1 == 1 ? kXB : kHB;
       const size_t hstride = l - 1 == 1 ? 1 : (size_t)n;
 #pragma unroll
-      for (int v = 0; v < kHid / 16; ++v) hr[v] = live && v < nh ? h4[v * hstride] : make_uint4(0u, 0u, 0u, 0u);
+      for (int v = 0; v < kHB; ++v) hr[v] = live && v < nh ? h4[v * hstride] : make_uint4(0u, 0u, 0u, 0u);
     }
     if (!wait_layer()) {
       failed = true;
@@ -264,7 +281,15 @@ __global__ void __launch_bounds__(kBT, 1)
     // weight gradient of layer l: lane t holds row t of dW_l (out t), or for
     // layer 5 row t of dW_5^T (in t)
     if (l == 5) {
-      if (h == 0) {
+      // db_5, second half: the 16 row groups in order
+      if (tid < kOut) {
+        const float *red = reinterpret_cast<const float *>(sm + kBOffRed);
+        float s = 0.f;
+#pragma unroll
+        for (int g = 0; g < kBT / kOut; ++g) s += red[g * kOut + tid];
+        part[poff(1, 4) + tid] = s;
+      }
+      if (qd == 0) {
       float v[16];
       ld_cols16(d_w + lane_off, v);
       float *g = part + poff(0, 4);  // W5 [16][128]
@@ -276,7 +301,8 @@ __global__ void __launch_bounds__(kBT, 1)
       // tile sum restores the flat layout)
       const int in = l == 1 ? kIn : kHid;
       float4 *g = reinterpret_cast<float4 *>(part + poff(0, l - 1)) + t;
-      for (int c = h * (in / 32); c < (h + 1) * (in / 32); ++c) {
+      const int nch = in / 16;  // 16-column chunks, split over the row's threads
+      for (int c = qd * nch / kPart; c < (qd + 1) * nch / kPart; ++c) {
         float v[16];
         ld_cols16(d_w + lane_off + (uint32_t)(16 * c), v);
 #pragma unroll
@@ -287,9 +313,9 @@ __global__ void __launch_bounds__(kBT, 1)
     if (l == 1) break;
     // dZ_(l-1) = dA_(l-1) silu'(Z_(l-1)) -> DZ (row t) and DZT (column t)
     {
-      const int c0 = h * (kHid / 32);  // this thread's 16-column chunks c0 .. c0 + 3
+      const int c0 = qd * (kZB / 4);  // this thread's 16-column chunks
 #pragma unroll
-      for (int cc = 0; cc < kHid / 32; ++cc) {
+      for (int cc = 0; cc < kZB / 4; ++cc) {
         const int c = c0 + cc;
         float v[16];
         ld_cols16(d_a + lane_off + (uint32_t)(16 * c), v);
@@ -313,10 +339,10 @@ __global__ void __launch_bounds__(kBT, 1)
     // H_(l-2)^T for the weight gradient of layer l - 1 (X^T for layer 1)
     if (l - 1 == 1) {
 #pragma unroll
-      for (int v = 0; v < kIn / 16; ++v) st_col8(HT, 8 * (h * (kIn / 16) + v), t, hr[v]);
+      for (int v = 0; v < kXB; ++v) st_col8(HT, 8 * (qd * kXB + v), t, hr[v]);
     } else {
 #pragma unroll
-      for (int v = 0; v < kHid / 16; ++v) st_col8(HT, 8 * (h * (kHid / 16) + v), t, hr[v]);
+      for (int v = 0; v < kHB; ++v) st_col8(HT, 8 * (qd * kHB + v), t, hr[v]);
     }
     operands_ready();
     // MMAs of layer l - 1: dW_(l-1) = dZ^T H^T^T, dA_(l-2) = dZ W_(l-1)
@@ -334,7 +360,7 @@ __global__ void __launch_bounds__(kBT, 1)
       tc_commit(bar);
     }
     // db_(l-1): column t of dZ_(l-1) summed over the tile's rows (row t of DZT)
-    if (h == 0) {
+    if (qd == 0) {
       float s = 0.f;
 #pragma unroll
       for (int k8 = 0; k8 < kBR / 8; ++k8) {
@@ -360,8 +386,9 @@ __global__ void __launch_bounds__(kBT, 1)
 }
 
 // ---------------------------------------------------------------------------
-// training forward: the network on a 128-row tile per CTA, two threads per
-// row (half of its columns each), saving every hidden layer's pre-activations Z (FP32) and activations
+// training forward: the network on a 128-row tile per CTA, four threads per
+// row (a quarter of its columns each; the warps w, w + 4, w + 8, w + 12 share
+// TMEM lanes), saving every hidden layer's pre-activations Z (FP32) and activations
 // H = SiLU(Z) (BF16, the exponential form the backward pass differentiates)
 // ---------------------------------------------------------------------------
 namespace {
@@ -376,11 +403,12 @@ constexpr uint32_t kFOffSlot = kFOffBar + 8;
 constexpr uint32_t kFSmemUsed = kFOffSlot + 16;
 constexpr size_t kFSmem = kFSmemUsed + 1024;
 constexpr uint32_t kFTmemCols = 128;
+constexpr int kFT = 4 * kBR;  // threads: four per row, each with a quarter of the row's columns
 static_assert(kFSmem <= 227 * 1024, "shared memory");
 static_assert(kFOffBar % 8 == 0, "mbarrier alignment");
 }  // namespace
 
-__global__ void __launch_bounds__(kBT, 1)
+__global__ void __launch_bounds__(kFT, 1)
     mlp_forward_train_tc_kernel(MlpDev net, const __nv_bfloat16 *__restrict__ x, int64_t n, int standardized_out,
                                 float *__restrict__ out, __nv_bfloat16 *__restrict__ h_save,
                                 float *__restrict__ z_save) {
@@ -390,15 +418,15 @@ __global__ void __launch_bounds__(kBT, 1)
   volatile uint32_t *slot = reinterpret_cast<volatile uint32_t *>(sm + kFOffSlot);
   float *bias = reinterpret_cast<float *>(sm + kFOffBias);
   unsigned char *A = sm + kFOffA, *X = sm + kFOffX;
-  const int tid = threadIdx.x, t = tid & (kBR - 1), h = tid >> 7, warp = tid >> 5;
+  const int tid = threadIdx.x, t = tid & (kBR - 1), qd = tid >> 7, warp = tid >> 5;
   const int64_t row0 = (int64_t)blockIdx.x * kBR, r = row0 + t;
   const bool live = r < n;
 
-  stage_rows_async(sm + kFOffW1, net.W[0], kHid, kIn, kHid, tid, kBT);
+  stage_rows_async(sm + kFOffW1, net.W[0], kHid, kIn, kHid, tid, kFT);
   for (int l = 0; l < 3; ++l)
-    stage_rows_async(sm + kFOffWH + (uint32_t)l * kHid * kHid * 2, net.W[1 + l], kHid, kHid, kHid, tid, kBT);
-  stage_rows_async(sm + kFOffW5, net.W[4], kOut, kHid, kOut, tid, kBT);
-  stage_rows_async(X, x + row0 * kIn, kBR, kIn, n - row0, tid, kBT);
+    stage_rows_async(sm + kFOffWH + (uint32_t)l * kHid * kHid * 2, net.W[1 + l], kHid, kHid, kHid, tid, kFT);
+  stage_rows_async(sm + kFOffW5, net.W[4], kOut, kHid, kOut, tid, kFT);
+  stage_rows_async(X, x + row0 * kIn, kBR, kIn, n - row0, tid, kFT);
   if (tid < kHid) {
 #pragma unroll
     for (int l = 0; l < 4; ++l) bias[l * kHid + tid] = net.b[l][tid];
@@ -424,7 +452,7 @@ __global__ void __launch_bounds__(kBT, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = slot[0];
-  const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;  // warps w and w + 4 share lanes
+  const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;  // warps w, w + 4, w + 8, w + 12 share lanes
   const uint32_t a_addr = smem_u32(A), x_addr = smem_u32(X);
   uint32_t phase = 0;
   bool failed = false;
@@ -457,7 +485,7 @@ __global__ void __launch_bounds__(kBT, 1)
     float4 *zs = reinterpret_cast<float4 *>(z_save) + (size_t)l * (kHid / 4) * n + r;
     uint4 *hs = reinterpret_cast<uint4 *>(h_save) + (size_t)l * (kHid / 8) * n + r;
 #pragma unroll 1
-    for (int c = h * (kHid / 32); c < (h + 1) * (kHid / 32); ++c) {  // this thread's half of the columns
+    for (int c = qd * (kHid / 64); c < (qd + 1) * (kHid / 64); ++c) {  // this thread's quarter of the columns
       float v[16];
       ld_cols16(tmem + lane_off + (uint32_t)(16 * c), v);
       uint32_t pk[8];
@@ -490,7 +518,7 @@ __global__ void __launch_bounds__(kBT, 1)
     }
   }
   if (!failed && !wait_layer()) failed = true;
-  if (!failed && h == 0) {
+  if (!failed && qd == 0) {
     float v[16];
     ld_cols16(tmem + lane_off, v);
     const float *b5 = bias + 4 * kHid, *ymu = b5 + kOut, *ysg = ymu + kOut;
@@ -505,7 +533,7 @@ __global__ void __launch_bounds__(kBT, 1)
       for (int q = 0; q < 4; ++q) o4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     }
   } else if (failed) {
-    if (live && h == 0)
+    if (live && qd == 0)
       for (int j = 0; j < kOut; ++j) out[r * kOut + j] = __int_as_float(0x7fc00000);
     if (tid == 0) (void)mbar_wait_bounded(bar, phase ^ 1u, 200000000ull);
   }
@@ -529,7 +557,7 @@ int launch_mlp_forward_train_tc(const MlpDev &net, const void *x, int64_t n, int
     attr_done[dev] = 1;
   }
   const int64_t tiles = (n + kBR - 1) / kBR;
-  mlp_forward_train_tc_kernel<<<(unsigned)tiles, kBT, kFSmem, st>>>(
+  mlp_forward_train_tc_kernel<<<(unsigned)tiles, kFT, kFSmem, st>>>(
       net, reinterpret_cast<const __nv_bfloat16 *>(x), n, standardized_out, out,
       reinterpret_cast<__nv_bfloat16 *>(h_save), z_save);
   return 0;
