@@ -313,6 +313,13 @@ def run_ours(args):
             fns["lite"] = lambda: (api.fp_moments_lite(vb[cur[0]], off, out=lite, stream=stream),
                                    sl.closure_lite(lite, tau, params=prm, coeffs_out=coeffs_s, flags_out=flags_s,
                                                    stream=stream))
+        if args.only == "train":
+            trs = S.Surrogate.load(WEIGHTS, device=dev)
+            tr = S.Trainer(trs, batch=8192)
+            ts = S.TrainingSet(P.training_cells(16384, seed=55), eps2_hat=prm.eps2_hat)
+            xt = ts.inputs(trs)[:8192].contiguous()
+            tt, at = ts.t[:8192].contiguous(), ts.aux[:8192].contiguous()
+            fns["train"] = lambda: tr.step(xt, tt, at, 1.0 / 8192)
         for _ in range(args.steps):
             fns[args.only]()
         torch.cuda.synchronize()
@@ -899,7 +906,7 @@ def main():
                     help="host processes for the oracle's all-cores timing (default: every core)")
     ap.add_argument("--only", default=None,
                     choices=["gather", "gather64", "solve", "exact_closure", "surrogate_closure", "adjoint",
-                             "velocity_update", "step", "mlp", "gather_lite", "lite", "sort", "collision"],
+                             "velocity_update", "step", "mlp", "gather_lite", "lite", "sort", "collision", "train"],
                     help="profiling mode: launch one call --steps times, print no bench line")
     args = ap.parse_args()
     if args.warmup < 3:

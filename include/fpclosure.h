@@ -386,6 +386,30 @@ int fp_mlp_backward(const fp_mlp *net, const void *x, const void *h_save, const 
 int fp_adam_step(float *params, const float *grads, float *m, float *v, int64_t n_params, float lr, float beta1,
                  float beta2, float eps, int64_t t, void *shadow_bf16, fp_stream_t stream);
 
+/* One training step of the learned closure (Sec. 4, Phase 2) in four kernel
+ * launches: fp_mlp_forward (standardised outputs, activations saved) with the
+ * loss of fp_surrogate_loss fused into its last layer, then fp_mlp_backward
+ * with the Adam step of fp_adam_step fused into the sum of its per-tile
+ * gradients.  It computes what those four calls compute in sequence, with
+ * y_mu, y_sigma and eps2_hat taken from net (the loss's arithmetic is the
+ * same code; results agree to FP32 rounding of the fused kernels' order).
+ *   x [n][32] BF16 (16-byte aligned), t_true [n][9], aux [n][16] (as for
+ *   fp_surrogate_loss); w [9] host array; scale multiplies dL/dout;
+ *   params [n_params] FP32 (the flat layout, n_params = fp_mlp_param_count()),
+ *   m, v: Adam moments; params, m, v updated in place; shadow_bf16 [n_params]
+ *   BF16 copy of params written when non-NULL (net->W must point into it
+ *   for the next step to see the update); t >= 1 the Adam step number;
+ *   grads [n_params] FP32: the gradient (written); loss_sum [1] FP32 += sum
+ *   of the row losses (non-finite, with non-finite gradients, if a tensor-core
+ *   wait timed out);
+ *   ws >= fp_surrogate_train_step_workspace_bytes(n), 256-byte aligned. */
+size_t fp_surrogate_train_step_workspace_bytes(int64_t n);
+int fp_surrogate_train_step(const fp_mlp *net, const void *x, const float *t_true, const float *aux, int64_t n,
+                            const float *w, float lam_drift, float lam_energy, float scale, float *params,
+                            float *grads, float *m, float *v, int64_t n_params, float lr, float beta1, float beta2,
+                            float eps, int64_t t, void *shadow_bf16, float *loss_sum, void *ws, size_t ws_bytes,
+                            fp_stream_t stream);
+
 /* fp_closure_exact_static: fp_closure_exact for callers that cannot allocate
  * device memory.  (The paper has no counterpart; this is a deployment
  * convenience of this library.)

@@ -110,6 +110,11 @@ SIGNATURES = {
     "fp_mlp_backward": (_i32, [ctypes.POINTER(FpMlp), _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _sz, _vp]),
     "fp_adam_step": (_i32, [_vp, _vp, _vp, _vp, _i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                             ctypes.c_float, _i64, _vp, _vp]),
+    "fp_surrogate_train_step_workspace_bytes": (_sz, [_i64]),
+    "fp_surrogate_train_step": (_i32, [ctypes.POINTER(FpMlp), _vp, _vp, _vp, _i64, _vp, ctypes.c_float,
+                                       ctypes.c_float, ctypes.c_float, _vp, _vp, _vp, _vp, _i64, ctypes.c_float,
+                                       ctypes.c_float, ctypes.c_float, ctypes.c_float, _i64, _vp, _vp, _vp, _sz,
+                                       _vp]),
     "fp_closure_exact_static": (_i32, [_vp, _i32, _i64, _vp, _i64, _vp, ctypes.POINTER(Params), _i32, _vp, _vp,
                                        _vp]),
     "fp_closure_exact_static_error": (ctypes.c_char_p, []),

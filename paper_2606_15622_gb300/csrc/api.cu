@@ -6,6 +6,7 @@
 #include <cstring>
 
 #include "fp_device.cuh"
+#include "train_math.cuh"
 
 namespace fpc {
 void launch_gather(const void *v, int v_dtype, int64_t np, const int64_t *off, int64_t n_cells, int prec,
@@ -64,6 +65,10 @@ void launch_loss(const float *out, const float *t_true, const float *aux, const 
                  void *dout_bf, float *loss_sum, cudaStream_t st);
 void launch_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2, float eps,
                  float bc1, float bc2, void *shadow, cudaStream_t st);
+size_t train_step_ws(int64_t n);
+int launch_train_step(const fp_mlp &net, const void *x, const float *t_true, const float *aux, int64_t n,
+                      const float *w, float lam_d, float lam_e, float scale, float *grads, const AdamParams &adam,
+                      float *loss_sum, void *ws, cudaStream_t st);
 }  // namespace fpc
 
 
@@ -412,6 +417,35 @@ int fp_adam_step(float *params, const float *grads, float *m, float *v, int64_t 
   const float bc2 = (float)(1.0 - pow((double)beta2, (double)t));
   fpc::launch_adam(params, grads, m, v, n_params, lr, beta1, beta2, eps, bc1, bc2, shadow_bf16, (cudaStream_t)stream);
   return check_launch("adam");
+}
+
+size_t fp_surrogate_train_step_workspace_bytes(int64_t n) { return n > 0 ? fpc::train_step_ws(n) : 0; }
+
+int fp_surrogate_train_step(const fp_mlp *net, const void *x, const float *t_true, const float *aux, int64_t n,
+                            const float *w, float lam_drift, float lam_energy, float scale, float *params,
+                            float *grads, float *m, float *v, int64_t n_params, float lr, float beta1, float beta2,
+                            float eps, int64_t t, void *shadow_bf16, float *loss_sum, void *ws, size_t ws_bytes,
+                            fp_stream_t stream) {
+  g_err[0] = 0;
+  if (int rc = check_net(net)) return rc;
+  if (n < 0 || t < 1) return fail(FP_ERR_ARG, "n < 0 or t < 1");
+  if (n_params != fpc::mlp_param_count())
+    return fail(FP_ERR_ARG, "n_params %lld is not fp_mlp_param_count()", (long long)n_params);
+  if (n == 0) return FP_OK;
+  if (!x || !t_true || !aux || !w || !params || !grads || !m || !v || !loss_sum)
+    return fail(FP_ERR_ARG, "null array pointer");
+  if ((uintptr_t)x % 16) return fail(FP_ERR_ARG, "misaligned x");
+  const size_t need = fpc::train_step_ws(n);
+  if (!ws || ws_bytes < need) return fail(FP_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", need, ws_bytes);
+  if ((uintptr_t)ws % kAlign) return fail(FP_ERR_ARG, "workspace not 256-byte aligned");
+  const float bc1 = (float)(1.0 - pow((double)beta1, (double)t));
+  const float bc2 = (float)(1.0 - pow((double)beta2, (double)t));
+  const fpc::AdamParams adam{params, m, v, reinterpret_cast<__nv_bfloat16 *>(shadow_bf16), lr, beta1, beta2, eps,
+                             bc1, bc2};
+  if (fpc::launch_train_step(*net, x, t_true, aux, n, w, lam_drift, lam_energy, scale, grads, adam, loss_sum, ws,
+                             (cudaStream_t)stream))
+    return fail(FP_ERR_CUDA, "train_step: shared-memory limit could not be raised");
+  return check_launch("train_step");
 }
 
 int fp_diagnostics(const double *moments, const double *m6, const double *rho, int64_t n_cells, double theta_inf,

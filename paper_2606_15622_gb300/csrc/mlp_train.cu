@@ -1,33 +1,19 @@
 // mlp_train.cu -- training kernels of the surrogate: the loss and its
-// gradient and Adam, for sm_103a (the backward pass on the tensor cores is
-// in mlp_train_tc.cu).
-//
-// Loss per cell (dimensionless targets t, prediction t' = mu + sigma o):
-//   sum_a w_a (o_a - (t_a - mu_a) / sigma_a)^2              coefficient MSE
-//   + lam_d [tr(D u D) + 2 g.D b + |g|^2 (s4 - 9)]          induced drift
-//   + lam_e e^2                                              energy residual
-// with (D, g) = t' - t split into the symmetric C block and the G block and
-// u, b, s4 the cell's normalised moments: tr(D u D) + ... is the mean square
-// over the cell of the difference of the drifts of Eq. cubic_drift the two
-// coefficient sets induce (times tau^2 / theta), and
-// e = 1 + (sum_ij C'_ij u_ij + sum_i G'_i b_i - eps2_hat s4) / 3 the energy
-// residual (zero for the exact closure: the trace of its stress rows).
+// gradient (the per-row arithmetic is in train_math.cuh) and Adam, for sm_103a
+// (the training forward and the backward pass on the tensor cores are in
+// mlp_train_tc.cu).
 #include <cstdint>
 #include <cuda_bf16.h>
 
 #include "fp_device.cuh"
 #include "mlp_common.cuh"
+#include "train_math.cuh"
 
 namespace fpc {
 
 // ---------------------------------------------------------------------------
 // loss
 // ---------------------------------------------------------------------------
-struct LossParams {
-  float w[kNOut];
-  float lam_d, lam_e, eps2_hat, scale;  // scale multiplies the gradient (1 / batch)
-};
-
 // A warp takes 32 consecutive rows: their out, aux and t_true rows are
 // copied into shared memory with coalesced loads (rows of 16 padded to 17
 // floats, so that the lanes' row reads fall in different banks), each lane
@@ -53,71 +39,8 @@ __global__ void __launch_bounds__(32 * kLossWarps)
   float lsum = 0.f;
   if (r < n) {
     const float *orow = so + lane * kLS, *trow = sT + lane * kNOut;
-    float o[kNOut], d[kNOut], gr[kNOut];
-#pragma unroll
-    for (int a = 0; a < kNOut; ++a) {
-      o[a] = orow[a];
-      const float tp = y_mu[a] + y_sigma[a] * o[a];
-      d[a] = tp - trow[a];
-    }
-    const float *x = sa + lane * kLS;  // u_hat (6), b_hat (3), s4_hat
-    const float U[3][3] = {{x[0], x[1], x[2]}, {x[1], x[3], x[4]}, {x[2], x[4], x[5]}};
-    const float b[3] = {x[6], x[7], x[8]};
-    const float s4 = x[9];
-    const float D[3][3] = {{d[0], d[1], d[2]}, {d[1], d[3], d[4]}, {d[2], d[4], d[5]}};
-    const float g[3] = {d[6], d[7], d[8]};
-    // drift term and its gradient
-    float DU[3][3], Db[3];
-    float q = 0.f;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      Db[i] = D[i][0] * b[0] + D[i][1] * b[1] + D[i][2] * b[2];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) DU[i][j] = D[i][0] * U[0][j] + D[i][1] * U[1][j] + D[i][2] * U[2][j];
-    }
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-#pragma unroll
-      for (int j = 0; j < 3; ++j) q += DU[i][j] * D[j][i];
-      q += 2.f * g[i] * Db[i] + g[i] * g[i] * (s4 - 9.f);
-    }
-    float full[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) full[i][j] = 2.f * DU[i][j] + 2.f * g[i] * b[j];
-    const int si[6] = {0, 0, 0, 1, 1, 2}, sj[6] = {0, 1, 2, 1, 2, 2};
-    float gq[kNOut];
-#pragma unroll
-    for (int a = 0; a < 6; ++a) gq[a] = si[a] == sj[a] ? full[si[a]][sj[a]] : full[si[a]][sj[a]] + full[sj[a]][si[a]];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) gq[6 + i] = 2.f * Db[i] + 2.f * (s4 - 9.f) * g[i];
-    // energy residual of the prediction
-    const float mult[6] = {1.f, 2.f, 2.f, 1.f, 2.f, 1.f};
-    const float uh[6] = {x[0], x[1], x[2], x[3], x[4], x[5]};
-    float e = 1.f - prm.eps2_hat * s4 / 3.f;
-    float de[kNOut];
-#pragma unroll
-    for (int a = 0; a < 6; ++a) {
-      const float tp = y_mu[a] + y_sigma[a] * o[a];
-      de[a] = mult[a] * uh[a] / 3.f;
-      e += tp * de[a];
-    }
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const float tp = y_mu[6 + i] + y_sigma[6 + i] * o[6 + i];
-      de[6 + i] = b[i] / 3.f;
-      e += tp * de[6 + i];
-    }
-    float mse = 0.f;
-#pragma unroll
-    for (int a = 0; a < kNOut; ++a) {
-      const float z = (trow[a] - y_mu[a]) / y_sigma[a];
-      const float df = o[a] - z;
-      mse += prm.w[a] * df * df;
-      gr[a] = 2.f * prm.w[a] * df + y_sigma[a] * (prm.lam_d * gq[a] + prm.lam_e * 2.f * e * de[a]);
-    }
-    lsum = mse + prm.lam_d * q + prm.lam_e * e * e;
+    float gr[kNOut];
+    lsum = loss_row(orow, trow, sa + lane * kLS, y_mu, y_sigma, prm, gr);
     float *drow = so + lane * kLS;  // this lane's out row is no longer needed
 #pragma unroll
     for (int a = 0; a < kOut; ++a) drow[a] = a < kNOut ? gr[a] * prm.scale : 0.f;
@@ -141,19 +64,10 @@ __global__ void __launch_bounds__(32 * kLossWarps)
   }
 }
 
-__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ gr, float *__restrict__ m,
-                            float *__restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float bc1,
-                            float bc2, __nv_bfloat16 *__restrict__ shadow) {
+__global__ void adam_kernel(const float *__restrict__ gr, int64_t n, AdamParams a) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const float g = gr[i];
-  const float mi = b1 * m[i] + (1.f - b1) * g;
-  const float vi = b2 * v[i] + (1.f - b2) * g * g;
-  m[i] = mi;
-  v[i] = vi;
-  const float pi = p[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
-  p[i] = pi;
-  if (shadow) shadow[i] = __float2bfloat16_rn(pi);
+  adam_update(a, i, gr[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -173,6 +87,12 @@ size_t mlp_backward_tc_ws(int64_t n);
 int launch_mlp_backward_tc(const MlpDev &net, const void *x, const void *h_save, const float *z_save,
                            const void *dout_bf, const float *dout, int64_t n, float *grads, void *ws,
                            cudaStream_t st);
+int launch_mlp_backward_adam_tc(const MlpDev &net, const void *x, const void *h_save, const float *z_save,
+                                const void *dout_bf, const float *dout, int64_t n, float *grads, void *ws,
+                                const AdamParams *adam, cudaStream_t st);
+int launch_mlp_forward_loss_tc(const MlpDev &net, const void *x, int64_t n, int standardized_out, float *out,
+                               void *h_save, float *z_save, const float *t_true, const float *aux,
+                               const LossParams *lp, float *dout, void *dout_bf, float *loss_sum, cudaStream_t st);
 MlpDev make_mlp_dev(const fp_mlp &m);
 
 size_t mlp_backward_ws(int64_t n) { return mlp_backward_tc_ws(n); }
@@ -181,6 +101,48 @@ size_t mlp_backward_ws(int64_t n) { return mlp_backward_tc_ws(n); }
 int launch_mlp_backward(const fp_mlp &net, const void *x, const void *h_save, const float *z_save,
                         const void *dout_bf, const float *dout, int64_t n, float *grads, void *ws, cudaStream_t st) {
   return launch_mlp_backward_tc(make_mlp_dev(net), x, h_save, z_save, dout_bf, dout, n, grads, ws, st);
+}
+
+// ---------------------------------------------------------------------------
+// one training step: forward with the loss fused into its last layer, then
+// the backward pass with Adam fused into the tile sum (two kernels each)
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kTsAlign = 256;
+size_t ts_round(size_t b) { return (b + kTsAlign - 1) / kTsAlign * kTsAlign; }
+}  // namespace
+
+// workspace: h_save | z_save | dout | dout_bf | the backward's tile slots
+size_t train_step_ws(int64_t n) {
+  const size_t rows = (size_t)n;
+  return ts_round(rows * kDepth * kHid * 2) + ts_round(rows * kDepth * kHid * 4) + ts_round(rows * kOut * 4) +
+         ts_round(rows * kOut * 2) + ts_round(mlp_backward_tc_ws(n));
+}
+
+int launch_train_step(const fp_mlp &net, const void *x, const float *t_true, const float *aux, int64_t n,
+                      const float *w, float lam_d, float lam_e, float scale, float *grads, const AdamParams &adam,
+                      float *loss_sum, void *ws, cudaStream_t st) {
+  const size_t rows = (size_t)n;
+  char *c = reinterpret_cast<char *>(ws);
+  void *h_save = c;
+  c += ts_round(rows * kDepth * kHid * 2);
+  float *z_save = reinterpret_cast<float *>(c);
+  c += ts_round(rows * kDepth * kHid * 4);
+  float *dout = reinterpret_cast<float *>(c);
+  c += ts_round(rows * kOut * 4);
+  void *dout_bf = c;
+  c += ts_round(rows * kOut * 2);
+  LossParams prm;
+  for (int a = 0; a < kNOut; ++a) prm.w[a] = w[a];
+  prm.lam_d = lam_d;
+  prm.lam_e = lam_e;
+  prm.eps2_hat = (float)net.eps2_hat;
+  prm.scale = scale;
+  const MlpDev d = make_mlp_dev(net);
+  if (launch_mlp_forward_loss_tc(d, x, n, 1, nullptr, h_save, z_save, t_true, aux, &prm, dout, dout_bf, loss_sum,
+                                 st))
+    return -1;
+  return launch_mlp_backward_adam_tc(d, x, h_save, z_save, dout_bf, dout, n, grads, c, &adam, st);
 }
 
 void launch_loss(const float *out, const float *t_true, const float *aux, const float *y_mu, const float *y_sigma,
@@ -198,8 +160,8 @@ void launch_loss(const float *out, const float *t_true, const float *aux, const 
 
 void launch_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2, float eps,
                  float bc1, float bc2, void *shadow, cudaStream_t st) {
-  adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, bc1, bc2,
-                                                            reinterpret_cast<__nv_bfloat16 *>(shadow));
+  const AdamParams a{p, m, v, reinterpret_cast<__nv_bfloat16 *>(shadow), lr, b1, b2, eps, bc1, bc2};
+  adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, n, a);
 }
 
 }  // namespace fpc

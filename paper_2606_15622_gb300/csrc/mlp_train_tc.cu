@@ -31,6 +31,7 @@
 #include "fp_device.cuh"
 #include "mlp_common.cuh"
 #include "tc_common.cuh"
+#include "train_math.cuh"
 
 namespace fpc {
 
@@ -398,7 +399,10 @@ constexpr uint32_t kFOffW5 = kFOffWH + 3 * kHid * kHid * 2;   // W5 [16][K = 128
 constexpr uint32_t kFOffA = kFOffW5 + kOut * kHid * 2;        // activations [128 rows][K = 128]
 constexpr uint32_t kFOffX = kFOffA + kBR * kHid * 2;          // inputs [128 rows][K = 32]
 constexpr uint32_t kFOffBias = kFOffX + kBR * kIn * 2;        // b1..b4 (4 x 128), b5, y_mu, y_sigma (3 x 16)
-constexpr uint32_t kFOffBar = kFOffBias + (4 * kHid + 3 * kOut) * 4;
+constexpr uint32_t kFOffLT = kFOffBias + (4 * kHid + 3 * kOut) * 4;  // loss: the tile's targets [128][9]
+constexpr int kLA = 17;                                               // loss: padded aux row stride (floats)
+constexpr uint32_t kFOffLA = kFOffLT + kBR * kNOut * 4;              // loss: the tile's aux rows [128][17]
+constexpr uint32_t kFOffBar = kFOffLA + kBR * kLA * 4;
 constexpr uint32_t kFOffSlot = kFOffBar + 8;
 constexpr uint32_t kFSmemUsed = kFOffSlot + 16;
 constexpr size_t kFSmem = kFSmemUsed + 1024;
@@ -411,16 +415,25 @@ static_assert(kFOffBar % 8 == 0, "mbarrier alignment");
 __global__ void __launch_bounds__(kFT, 1)
     mlp_forward_train_tc_kernel(MlpDev net, const __nv_bfloat16 *__restrict__ x, int64_t n, int standardized_out,
                                 float *__restrict__ out, __nv_bfloat16 *__restrict__ h_save,
-                                float *__restrict__ z_save) {
+                                float *__restrict__ z_save, const float *__restrict__ t_true,
+                                const float *__restrict__ aux, LossParams prm, float *__restrict__ dout,
+                                __nv_bfloat16 *__restrict__ dout_bf, float *__restrict__ loss_sum) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kFOffBar);
   volatile uint32_t *slot = reinterpret_cast<volatile uint32_t *>(sm + kFOffSlot);
   float *bias = reinterpret_cast<float *>(sm + kFOffBias);
   unsigned char *A = sm + kFOffA, *X = sm + kFOffX;
+  float *sLT = reinterpret_cast<float *>(sm + kFOffLT), *sLA = reinterpret_cast<float *>(sm + kFOffLA);
   const int tid = threadIdx.x, t = tid & (kBR - 1), qd = tid >> 7, warp = tid >> 5;
   const int64_t row0 = (int64_t)blockIdx.x * kBR, r = row0 + t;
   const bool live = r < n;
+  const bool with_loss = t_true != nullptr;  // the loss of the standardised outputs, fused
+  if (with_loss) {  // the tile's targets and aux rows, coalesced
+    const int nr = (int)(n - row0 < kBR ? n - row0 : kBR);
+    for (int i = tid; i < nr * kNOut; i += kFT) sLT[i] = t_true[row0 * kNOut + i];
+    for (int i = tid; i < nr * 16; i += kFT) sLA[(i >> 4) * kLA + (i & 15)] = aux[row0 * 16 + i];
+  }
 
   stage_rows_async(sm + kFOffW1, net.W[0], kHid, kIn, kHid, tid, kFT);
   for (int l = 0; l < 3; ++l)
@@ -527,14 +540,45 @@ __global__ void __launch_bounds__(kFT, 1)
       v[j] += b5[j];
       if (!standardized_out) v[j] = fmaf(ysg[j], v[j], ymu[j]);
     }
-    if (live) {
+    if (live && out) {
       float4 *o4 = reinterpret_cast<float4 *>(out + r * kOut);
 #pragma unroll
       for (int q = 0; q < 4; ++q) o4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     }
+    if (with_loss) {
+      // the row's loss and scale * dL/dout (FP32 and BF16), the loss summed
+      // over the warp and added to loss_sum
+      float lrow = 0.f;
+      if (live) {
+        float gr[kNOut];
+        lrow = loss_row(v, sLT + t * kNOut, sLA + t * kLA, ymu, ysg, prm, gr);
+        float gs[kOut];
+#pragma unroll
+        for (int a = 0; a < kOut; ++a) gs[a] = a < kNOut ? gr[a] * prm.scale : 0.f;
+        float4 *d4 = reinterpret_cast<float4 *>(dout + r * kOut);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d4[q] = make_float4(gs[4 * q], gs[4 * q + 1], gs[4 * q + 2], gs[4 * q + 3]);
+        uint4 *b4 = reinterpret_cast<uint4 *>(dout_bf + r * kOut);
+        b4[0] = make_uint4(pack_bf16(gs[0], gs[1]), pack_bf16(gs[2], gs[3]), pack_bf16(gs[4], gs[5]),
+                           pack_bf16(gs[6], gs[7]));
+        b4[1] = make_uint4(pack_bf16(gs[8], gs[9]), pack_bf16(gs[10], gs[11]), pack_bf16(gs[12], gs[13]),
+                           pack_bf16(gs[14], gs[15]));
+      }
+#pragma unroll
+      for (int o2 = 16; o2 >= 1; o2 >>= 1) lrow += __shfl_xor_sync(0xffffffffu, lrow, o2);
+      if ((tid & 31) == 0) atomicAdd(loss_sum, lrow);
+    }
   } else if (failed) {
-    if (live && qd == 0)
-      for (int j = 0; j < kOut; ++j) out[r * kOut + j] = __int_as_float(0x7fc00000);
+    if (live && qd == 0) {
+      for (int j = 0; j < kOut; ++j) {
+        if (out) out[r * kOut + j] = __int_as_float(0x7fc00000);
+        if (with_loss) {
+          dout[r * kOut + j] = __int_as_float(0x7fc00000);
+          dout_bf[r * kOut + j] = __float2bfloat16_rn(__int_as_float(0x7fc00000));
+        }
+      }
+    }
+    if (with_loss && tid == 0) atomicAdd(loss_sum, __int_as_float(0x7fc00000));
     if (tid == 0) (void)mbar_wait_bounded(bar, phase ^ 1u, 200000000ull);
   }
   tc_fence_before();
@@ -545,8 +589,11 @@ __global__ void __launch_bounds__(kFT, 1)
 }
 
 // Returns -1 if the shared-memory limit could not be raised.
-int launch_mlp_forward_train_tc(const MlpDev &net, const void *x, int64_t n, int standardized_out, float *out,
-                                void *h_save, float *z_save, cudaStream_t st) {
+// With t_true non-null the loss (lp, over the standardised outputs) is fused
+// into the last layer: dout, dout_bf and loss_sum are written, out may be null.
+int launch_mlp_forward_loss_tc(const MlpDev &net, const void *x, int64_t n, int standardized_out, float *out,
+                               void *h_save, float *z_save, const float *t_true, const float *aux,
+                               const LossParams *lp, float *dout, void *dout_bf, float *loss_sum, cudaStream_t st) {
   static int attr_done[64];
   int dev = 0;
   cudaGetDevice(&dev);
@@ -557,13 +604,25 @@ int launch_mlp_forward_train_tc(const MlpDev &net, const void *x, int64_t n, int
     attr_done[dev] = 1;
   }
   const int64_t tiles = (n + kBR - 1) / kBR;
+  LossParams prm{};
+  if (lp) prm = *lp;
   mlp_forward_train_tc_kernel<<<(unsigned)tiles, kFT, kFSmem, st>>>(
       net, reinterpret_cast<const __nv_bfloat16 *>(x), n, standardized_out, out,
-      reinterpret_cast<__nv_bfloat16 *>(h_save), z_save);
+      reinterpret_cast<__nv_bfloat16 *>(h_save), z_save, t_true, aux, prm, dout,
+      reinterpret_cast<__nv_bfloat16 *>(dout_bf), loss_sum);
   return 0;
 }
 
-__global__ void sum_tiles_kernel(const float *__restrict__ parts, int ntiles, int64_t cnt, float *__restrict__ out) {
+int launch_mlp_forward_train_tc(const MlpDev &net, const void *x, int64_t n, int standardized_out, float *out,
+                                void *h_save, float *z_save, cudaStream_t st) {
+  return launch_mlp_forward_loss_tc(net, x, n, standardized_out, out, h_save, z_save, nullptr, nullptr, nullptr,
+                                    nullptr, nullptr, nullptr, st);
+}
+
+// The gradient summed over the tiles' slots into out (the flat layout); with
+// adam.p non-null the Adam step of that parameter follows.
+__global__ void sum_tiles_kernel(const float *__restrict__ parts, int ntiles, int64_t cnt, float *__restrict__ out,
+                                 AdamParams adam) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= cnt) return;
   // tile order (the result does not depend on scheduling), loads eight at a time
@@ -589,6 +648,7 @@ __global__ void sum_tiles_kernel(const float *__restrict__ parts, int ntiles, in
     }
   }
   out[dst] = s;
+  if (adam.p) adam_update(adam, dst, s);
 }
 
 size_t mlp_backward_tc_ws(int64_t n) {
@@ -597,9 +657,11 @@ size_t mlp_backward_tc_ws(int64_t n) {
 }
 
 // Returns -1 if the shared-memory limit could not be raised.
-int launch_mlp_backward_tc(const MlpDev &net, const void *x, const void *h_save, const float *z_save,
-                           const void *dout_bf, const float *dout, int64_t n, float *grads, void *ws,
-                           cudaStream_t st) {
+// With adam non-null, the Adam step of every parameter follows its gradient
+// in the tile sum.
+int launch_mlp_backward_adam_tc(const MlpDev &net, const void *x, const void *h_save, const float *z_save,
+                                const void *dout_bf, const float *dout, int64_t n, float *grads, void *ws,
+                                const AdamParams *adam, cudaStream_t st) {
   static int attr_done[64];
   int dev = 0;
   cudaGetDevice(&dev);
@@ -615,8 +677,16 @@ int launch_mlp_backward_tc(const MlpDev &net, const void *x, const void *h_save,
   mlp_backward_tc_kernel<<<(unsigned)tiles, kBT, kBSmem, st>>>(
       net, reinterpret_cast<const __nv_bfloat16 *>(x), reinterpret_cast<const __nv_bfloat16 *>(h_save), z_save,
       reinterpret_cast<const __nv_bfloat16 *>(dout_bf), dout, n, np, parts);
-  sum_tiles_kernel<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(parts, (int)tiles, np, grads);
+  AdamParams a{};
+  if (adam) a = *adam;
+  sum_tiles_kernel<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(parts, (int)tiles, np, grads, a);
   return 0;
+}
+
+int launch_mlp_backward_tc(const MlpDev &net, const void *x, const void *h_save, const float *z_save,
+                           const void *dout_bf, const float *dout, int64_t n, float *grads, void *ws,
+                           cudaStream_t st) {
+  return launch_mlp_backward_adam_tc(net, x, h_save, z_save, dout_bf, dout, n, grads, ws, nullptr, st);
 }
 
 }  // namespace fpc

@@ -449,8 +449,10 @@ class Trainer:
     """Adam on the loss of fp_surrogate_loss, every step in the library's
     kernels; returns the per-epoch mean losses."""
 
-    def __init__(self, s: Surrogate, batch=8192, lr=1e-3, w_gamma=2.0, lam_drift=0.1, lam_energy=1.0):
+    def __init__(self, s: Surrogate, batch=8192, lr=1e-3, w_gamma=2.0, lam_drift=0.1, lam_energy=1.0,
+                 fused=True):
         self.s = s
+        self.fused = fused  # one fp_surrogate_train_step call, else the four calls it fuses
         self.batch = batch
         self.lr = lr
         self.w = np.array([1.0] * 6 + [w_gamma] * 3, dtype=np.float32)  # Gamma block weighted up (q-weighting)
@@ -467,11 +469,27 @@ class Trainer:
         self.dout_bf = torch.empty((B, OUT), dtype=torch.bfloat16, device=dev)
         self.loss_acc = torch.zeros(1, dtype=torch.float32, device=dev)
         self.ws = torch.empty(int(_lib().fp_mlp_backward_workspace_bytes(B)), dtype=torch.uint8, device=dev)
+        self.ws_step = torch.empty(int(_lib().fp_surrogate_train_step_workspace_bytes(B)), dtype=torch.uint8,
+                                   device=dev)
+        self.wbuf = (ctypes.c_float * 9)(*self.w.tolist())
 
     def step(self, x, t, aux, scale):
         s = self.s
         L = _lib()
         n = x.shape[0]
+        if self.fused:
+            ws = self.ws_step
+            if n > self.batch:
+                ws = torch.empty(int(L.fp_surrogate_train_step_workspace_bytes(n)), dtype=torch.uint8,
+                                 device=s.device)
+            self.t += 1
+            rc = L.fp_surrogate_train_step(ctypes.byref(s.net()), _p(x), _p(t), _p(aux), n, self.wbuf,
+                                           self.lam_drift, self.lam_energy, scale, _p(s.params), _p(self.grads),
+                                           _p(self.m), _p(self.v), s.params.numel(), self.lr, 0.9, 0.999, 1e-8,
+                                           self.t, _p(s.shadow), _p(self.loss_acc), _p(ws), ws.numel(),
+                                           api._stream(None))
+            api._check(rc, "fp_surrogate_train_step")
+            return
         out, h, z = s.forward(x, standardized=True, save=True)
         wbuf = (ctypes.c_float * 9)(*self.w.tolist())
         rc = L.fp_surrogate_loss(_p(out), _p(t), _p(aux), _p(s.y_mu), _p(s.y_sigma), n, wbuf, self.lam_drift,

@@ -200,6 +200,52 @@ def test_adam_matches_reference():
     assert torch.equal(sh, P_.to(torch.bfloat16))
 
 
+def test_fused_training_step_matches_the_four_calls_and_the_oracle():
+    """fp_surrogate_train_step (the loss fused into the forward's last layer,
+    Adam into the gradient tile sum) against the four calls it fuses, its
+    loss against the oracle's, and its parameter update against the oracle's
+    Adam applied to its own gradient.  1000 rows: seven full 128-row tiles and
+    a ragged one."""
+    n = 1000
+    _, t_true, aux, y_mu, y_sigma, m = _loss_args(n, 5)
+    x = _inputs(n, 21)
+    dev = lambda a, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
+    xd, td, ad = dev(x, torch.bfloat16), dev(t_true), dev(aux)
+    trainers = []
+    for fused in (True, False):
+        s, prm = _surrogate_with_random_params(9)
+        s.y_mu.copy_(dev(y_mu))
+        s.y_sigma.copy_(dev(y_sigma))
+        s._net = None
+        trainers.append(S.Trainer(s, batch=n, fused=fused))
+    tf, tu = trainers
+    out = tf.s.forward(xd, standardized=True).cpu().numpy().astype(np.float64)
+    p0, m0, v0 = (a.cpu().numpy().astype(np.float64) for a in (tf.s.params, tf.m, tf.v))
+    for tr in trainers:
+        tr.step(xd, td, ad, 1.0 / n)
+    torch.cuda.synchronize()
+    # the same loss and gradient as the four calls (FP32 order of the fused kernels)
+    lf, lu = float(tf.loss_acc.item()), float(tu.loss_acc.item())
+    assert abs(lf - lu) <= 1e-5 * abs(lu)
+    gf, gu = tf.grads.cpu().numpy().astype(np.float64), tu.grads.cpu().numpy().astype(np.float64)
+    for l in range(5):
+        for which in (0, 1):
+            a, b = S.param_offset(which, l), (S.param_offset(1, l) if which == 0 else
+                                              (S.param_offset(0, l + 1) if l < 4 else S.param_count()))
+            assert np.linalg.norm(gf[a:b] - gu[a:b]) <= 1e-3 * np.linalg.norm(gu[a:b]) + 1e-12, (l, which)
+    # the loss against the oracle's, on the network's standardised outputs
+    ref = M.loss(out, t_true, m, y_mu[:9], y_sigma[:9], 1e-3, tf.w.astype(np.float64), tf.lam_drift,
+                 tf.lam_energy)
+    assert abs(lf / n - ref) <= 1e-4 * abs(ref)
+    # Adam on the step's own gradient
+    pr, mr, vr = M.adam_step(p0, gf, m0, v0, 1, lr=tf.lr)
+    np.testing.assert_allclose(tf.s.params.cpu().numpy(), pr, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(tf.m.cpu().numpy(), mr, rtol=1e-5, atol=1e-9)
+    # 1 - beta2 evaluated in FP32 is 1e-3 (1 - 1.3e-5)
+    np.testing.assert_allclose(tf.v.cpu().numpy(), vr, rtol=3e-5, atol=1e-12)
+    assert torch.equal(tf.s.shadow, tf.s.params.to(torch.bfloat16))
+
+
 def test_surrogate_fallback_is_exact_for_flagged_cells(cavity_pop):
     """An untrained network fails the energy check on essentially every cell;
     those cells must come back with the exact FP64 closure."""
