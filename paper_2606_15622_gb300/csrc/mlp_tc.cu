@@ -39,7 +39,7 @@
 // the exact closure to a list (one atomic per warp), so the inputs and the
 // predictions never travel through HBM.
 // Only the group's leader waits on the mbarrier, with a bound, and passes its
-// verdict to the group through shared memory at the next group barrier; a
+// outcome to the group through shared memory at the next group barrier; a
 // wait that runs out marks the group's remaining rows (NaN outputs, or
 // non-finite cells that the exact fallback or the linear drift serves), and
 // the CTA frees its tensor memory before returning.
@@ -70,7 +70,7 @@ constexpr uint32_t kOffX = kOffA + kTcGroups * kTcRows * kHid * 2;  // 2 x [128]
 constexpr uint32_t kOffBias = kOffX + kTcGroups * kTcRows * kIn * 2;
 constexpr uint32_t kNBias = 4 * kHid + 3 * kOut;               // b1..b4 / 2, b5, y_mu, y_sigma
 constexpr uint32_t kOffBar = kOffBias + kNBias * 4;            // 2 mbarriers
-constexpr uint32_t kOffTmemSlot = kOffBar + 8 * kTcGroups;       // TMEM address + two verdicts
+constexpr uint32_t kOffTmemSlot = kOffBar + 8 * kTcGroups;       // TMEM address + two outcomes
 constexpr uint32_t kOffScal = kOffTmemSlot + 16;               // [32] float4 input scalers (closure variants)
 constexpr uint32_t kOffFlags = kOffScal + 4 * kIn * 4;         // [2 groups][2 parities][128] part-1 input flags
 constexpr uint32_t kTcSmemUsed = kOffFlags + kTcGroups * 2 * kTcRows * 4;
@@ -487,11 +487,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t a_addr = smem_u32(A), x_addr = smem_u32(X);
   const uint32_t w1_addr = smem_u32(sm + kOffW1), wh_addr = smem_u32(sm + kOffWH), w5_addr = smem_u32(sm + kOffW5);
   const bool leader = gt == 0;
-  volatile uint32_t *group_ok = tmem_slot + 1 + g;  // the leader's verdict on the last wait
+  volatile uint32_t *group_ok = tmem_slot + 1 + g;  // the leader's outcome on the last wait
   uint32_t phase = 0;
   bool failed = false;
 
-  // the leader waits for the group's last commit; the group learns the verdict
+  // the leader waits for the group's last commit; the group learns the outcome
   auto wait_layer = [&]() -> bool {
     if (leader) *group_ok = mma_wait(&bar[g], phase) ? 1u : 0u;
     phase ^= 1u;

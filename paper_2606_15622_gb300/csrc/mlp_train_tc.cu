@@ -56,7 +56,7 @@ constexpr uint32_t kBOffDZ = kBOffWT5 + kHid * kOut * 2;       // dZ: [128 rows]
 constexpr uint32_t kBOffDZT = kBOffDZ + kBR * kHid * 2;        // dZ^T: [out][K = 128 rows]
 constexpr uint32_t kBOffHT = kBOffDZT + kHid * kBR * 2;        // H^T: [in][K = 128 rows]
 constexpr uint32_t kBOffBar = kBOffHT + kHid * kBR * 2;         // one mbarrier
-constexpr uint32_t kBOffSlot = kBOffBar + 8;                   // TMEM address, verdict
+constexpr uint32_t kBOffSlot = kBOffBar + 8;                   // TMEM address, outcome
 constexpr uint32_t kBOffRed = kBOffSlot + 16;                  // db_5 partial sums: [16 row groups][16]
 constexpr uint32_t kBSmemUsed = kBOffRed + kBT * 4;
 constexpr size_t kBSmem = kBSmemUsed + 1024;
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kBT, 1)
   uint32_t phase = 0;
   bool failed = false;
 
-  // the leader waits for the layer's commit; everybody learns the verdict
+  // the leader waits for the layer's commit; everybody learns the outcome
   auto wait_layer = [&]() -> bool {
     if (tid == 0) slot[1] = mma_wait(bar, phase) ? 1u : 0u;
     phase ^= 1u;

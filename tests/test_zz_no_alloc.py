@@ -77,7 +77,7 @@ def _check(pop, prec):
 def test_static_scratch_matches_workspace_path_and_oracle_on_two_calls(prec):
     _check(P.cavity(seed=12), prec)
     fs = _check(_edge_cells(), prec)
-    # the edge cells kept their own verdicts, not the first call's moments
+    # the edge cells kept their own flags, not the first call's moments
     assert fs[0] & api.FLAG_FEW and fs[1] & api.FLAG_FEW
     assert fs[25] & api.FLAG_SINGULAR and fs[26] & api.FLAG_NONFINITE
 
