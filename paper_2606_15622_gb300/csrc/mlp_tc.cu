@@ -429,17 +429,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   for (int l = 0; l < 3; ++l)
     stage_rows_async(sm + kOffWH + l * kHid * kHid * 2, net.W[1 + l], kHid, kHid, kHid, tid, kTcThreads);
   stage_rows_async(sm + kOffW5, net.W[4], kOut, kHid, kOut, tid, kTcThreads);
-  for (int i = tid; i < (int)kNBias; i += blockDim.x) {
-    float b;
-    if (i < 4 * kHid)
-      b = 0.5f * net.b[i / kHid][i % kHid];  // hidden biases halved (see silu_tanh)
-    else if (i < 4 * kHid + kOut)
-      b = net.b[4][i - 4 * kHid];
-    else if (i < 4 * kHid + 2 * kOut)
-      b = net.y_mu[i - 4 * kHid - kOut];
-    else
-      b = net.y_sigma[i - 4 * kHid - 2 * kOut];
-    bias[i] = b;
+  // (the parameter arrays indexed by constants only: no local-memory copy)
+  if (tid < kHid) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) bias[l * kHid + tid] = 0.5f * net.b[l][tid];  // hidden biases halved (see silu_tanh)
+  } else if (tid < kHid + kOut) {
+    const int j = tid - kHid;
+    bias[4 * kHid + j] = net.b[4][j];
+    bias[4 * kHid + kOut + j] = net.y_mu[j];
+    bias[4 * kHid + 2 * kOut + j] = net.y_sigma[j];
   }
   if (kSrc != kSrcX && tid < kIn) {
     // mu, 1 / sigma and the widened training box [x_min - m sigma, x_max + m sigma]
