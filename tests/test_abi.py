@@ -74,3 +74,40 @@ def test_binding_checks_tensor_arguments_before_the_abi():
     with pytest.raises(api.FPError, match="moments"):
         api._want_cells(4, moments=torch.zeros((4, api.NLITE), dtype=torch.float64))
     api._want_cells(4, moments=torch.zeros((4, api.NLITE), dtype=torch.float64), stride=api.NLITE)
+
+
+def test_train_step_refuses_bad_arguments_on_the_host():
+    """fp_surrogate_train_step validates its arguments before any launch (no
+    GPU needed): network shape, parameter count, step number, null arrays,
+    alignment and workspace size; an empty batch is a no-op."""
+    from paper_2606_15622_gb300 import api
+    L = api.lib()
+    net = api.FpMlp()
+    for l in range(5):
+        net.W[l] = 0x1000 * (l + 1)
+        net.b[l] = 0x10000 + 0x1000 * l
+    net.x_mu = net.x_sigma = net.y_mu = net.y_sigma = net.x_min = net.x_max = 0x20000
+    net.in_dim, net.hidden, net.depth, net.out_dim, net.eps2_hat = 32, 128, 4, 16, 1e-3
+    npar = int(L.fp_mlp_param_count())
+    w = (ctypes.c_float * 9)(*([1.0] * 9))
+    fake = 0x40000  # never dereferenced: every call below fails (or returns) before a launch
+    n = 1000
+    need = int(L.fp_surrogate_train_step_workspace_bytes(n))
+    assert need > 0 and int(L.fp_surrogate_train_step_workspace_bytes(0)) == 0
+
+    def call(n=n, npar=npar, t=1, x=fake, ws=fake, ws_bytes=need, net=net):
+        return L.fp_surrogate_train_step(ctypes.byref(net), x, fake, fake, n, w, 0.1, 1.0, 1.0 / max(n, 1), fake,
+                                         fake, fake, fake, npar, 1e-3, 0.9, 0.999, 1e-8, t, None, fake, ws,
+                                         ws_bytes, None)
+
+    assert call(npar=npar - 1) == api.FP_ERR_ARG
+    assert call(t=0) == api.FP_ERR_ARG
+    assert call(n=-1) == api.FP_ERR_ARG
+    assert call(n=0) == api.FP_OK
+    assert call(x=None) == api.FP_ERR_ARG
+    assert call(x=fake + 8) == api.FP_ERR_ARG           # x must be 16-byte aligned
+    assert call(ws_bytes=need - 1) == api.FP_ERR_WORKSPACE
+    assert call(ws=fake + 64) == api.FP_ERR_ARG         # workspace must be 256-byte aligned
+    bad = api.FpMlp.from_buffer_copy(net)
+    bad.hidden = 64
+    assert call(net=bad) == api.FP_ERR_UNSUPPORTED
