@@ -20,6 +20,126 @@
 
 namespace fpc {
 
+// gm += -(dF/dm)^T lambda for F(m, Y) = A(m) Y - r(m) (the assembly of
+// Eq. system9x9 differentiated by hand), with u, w, u3 adjoints kept per full
+// index and folded onto the symmetric moment slots at the end.  Every factor
+// that does not depend on the row's lambda is formed once per cell, so each
+// term costs one FMA on the (scarce) FP64 pipe.
+//   stress rows (ij): F = sum_k (C_ik u_kj + C_jk u_ki) + G_i b_j + G_j b_i
+//                         + (2 / tau) u_ij - 2 e2 w_ij
+//   heat rows (i):    F = sum_l C_il b_l + 2 sum_kl C_kl u_ikl + G_i (s4 - 9 th^2)
+//                         + 2 sum_k G_k (w_ki - 3 th u_ki) + (4 / (3 tau)) b_i
+//                         - e2 (3 z_i - 3 th b_i - 2 sum_k u_ik b_k)
+// with b_i = sum_k u_ikk, s4 = sum_k w_kk, e2 = eps2_hat / (tau th).
+__host__ __device__ __forceinline__ void assembly_vjp(const double (&m)[FP_NMOM], const double (&Y)[9],
+                                                      const double (&lam)[9], double tc, double eps2_hat,
+                                                      double (&gm)[FP_NMOM]) {
+  double C[3][3], G[3], u[3][3], w[3][3], b[3], z[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    G[i] = Y[6 + i];
+    z[i] = m[kZ + i];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      C[i][j] = Y[sym2(i, j)];
+      u[i][j] = m[kU2 + sym2(i, j)];
+      w[i][j] = m[kW + sym2(i, j)];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) b[i] = m[kU3 + sym3(i, 0, 0)] + m[kU3 + sym3(i, 1, 1)] + m[kU3 + sym3(i, 2, 2)];
+  const double th = m[kTheta];
+  const double e2 = eps2_hat / (tc * th);
+  const double itau = 1.0 / tc;
+  // per-cell factors of the row adjoints
+  const double itau2 = 2.0 * itau, me2x2 = -2.0 * e2, e2x2 = 2.0 * e2, mz = -3.0 * e2;
+  const double kb = fma(4.0 / 3.0, itau, 3.0 * e2 * th);  // heat row i on b_i
+  const double m18th = -18.0 * th, m6th = -6.0 * th, e2x3 = 3.0 * e2, th3 = 3.0 * th;
+  double G2[3], G6[3], eb2[3], P[3], E[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    G2[k] = 2.0 * G[k];
+    G6[k] = m6th * G[k];
+    eb2[k] = e2x2 * b[k];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    // heat row i on theta: -18 th G_i - 6 sum_k G_k u_ki + 3 e2 b_i;
+    // on e2: -(3 z_i - 3 th b_i - 2 sum_k u_ik b_k)
+    const double gu = fma(G[0], u[0][i], fma(G[1], u[1][i], G[2] * u[2][i]));
+    const double ubs = fma(u[i][0], b[0], fma(u[i][1], b[1], u[i][2] * b[2]));
+    P[i] = fma(m18th, G[i], fma(-6.0, gu, e2x3 * b[i]));
+    E[i] = fma(2.0, ubs, fma(th3, b[i], -3.0 * z[i]));
+  }
+  double ub[3][3] = {}, wb[3][3] = {}, u3b[10] = {}, zb[3], bb[3] = {};
+  double thb = 0.0, s4b = 0.0, e2b = 0.0, sw = 0.0;
+  // stress rows
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      const double f = -lam[sym2(i, j)];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        ub[k][j] = fma(f, C[i][k], ub[k][j]);
+        ub[k][i] = fma(f, C[j][k], ub[k][i]);
+      }
+      bb[j] = fma(f, G[i], bb[j]);
+      bb[i] = fma(f, G[j], bb[i]);
+      ub[i][j] = fma(f, itau2, ub[i][j]);
+      wb[i][j] = fma(f, me2x2, wb[i][j]);
+      sw = fma(f, w[i][j], sw);  // e2 adjoint: -2 sum f w_ij
+    }
+  // heat-flux rows
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const double f = -lam[6 + i], f2 = 2.0 * f, f4 = 4.0 * f, fe = e2x2 * f;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) bb[l] = fma(f, C[i][l], bb[l]);
+    // 2 sum_kl C_kl u_ikl: a slot with k != l collects (k, l) and (l, k)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      u3b[sym3(i, k, k)] = fma(f2, C[k][k], u3b[sym3(i, k, k)]);
+#pragma unroll
+      for (int l = k + 1; l < 3; ++l) u3b[sym3(i, k, l)] = fma(f4, C[k][l], u3b[sym3(i, k, l)]);
+    }
+    s4b = fma(f, G[i], s4b);
+    thb = fma(f, P[i], thb);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      wb[k][i] = fma(f, G2[k], wb[k][i]);
+      ub[k][i] = fma(f, G6[k], ub[k][i]);
+      ub[i][k] = fma(f, eb2[k], ub[i][k]);
+      bb[k] = fma(fe, u[i][k], bb[k]);
+    }
+    bb[i] = fma(f, kb, bb[i]);
+    zb[i] = f * mz;
+    e2b = fma(f, E[i], e2b);
+  }
+  // e2 = eps2_hat / (tau th);  b_i = sum_k u_ikk;  s4 = sum_k w_kk
+  e2b = fma(-2.0, sw, e2b);
+  thb = fma(e2b, -e2 / th, thb);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) u3b[sym3(i, k, k)] += bb[i];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) wb[k][k] += s4b;
+  // fold onto the moment slots
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      gm[kU2 + sym2(i, j)] += i != j ? ub[i][j] + ub[j][i] : ub[i][j];
+      gm[kW + sym2(i, j)] += i != j ? wb[i][j] + wb[j][i] : wb[i][j];
+    }
+#pragma unroll
+  for (int q = 0; q < 10; ++q) gm[kU3 + q] += u3b[q];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) gm[kZ + i] += zb[i];
+  gm[kTheta] += thb;
+}
+
 template <bool kLU>
 __device__ __forceinline__ void adjoint_cell(int64_t c, const double *__restrict__ mom,
                                              const double *__restrict__ coeffs, const int32_t *__restrict__ flags,
@@ -58,93 +178,7 @@ __device__ __forceinline__ void adjoint_cell(int64_t c, const double *__restrict
     double Y[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) Y[q] = coeffs[c * 9 + q];
-    double C[3][3], G[3], u[3][3], w[3][3], b[3], z[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      G[i] = Y[6 + i];
-      z[i] = m[kZ + i];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        C[i][j] = Y[sym2(i, j)];
-        u[i][j] = m[kU2 + sym2(i, j)];
-        w[i][j] = m[kW + sym2(i, j)];
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < 3; ++i) b[i] = m[kU3 + sym3(i, 0, 0)] + m[kU3 + sym3(i, 1, 1)] + m[kU3 + sym3(i, 2, 2)];
-    const double th = m[kTheta];
-    const double e2 = eps2_hat / (tc * th);
-    const double itau = 1.0 / tc;
-    // adjoints of the intermediates (full-index for the symmetric tensors)
-    double ub[3][3] = {}, wb[3][3] = {}, u3b[10] = {}, zb[3] = {}, bb[3] = {};
-    double thb = 0.0, s4b = 0.0, e2b = 0.0;
-    // stress rows: F_ij = sum_k (C_ik u_kj + C_jk u_ki) + G_i b_j + G_j b_i + (2/tau) u_ij - 2 e2 w_ij
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = i; j < 3; ++j) {
-        const double f = -lam[sym2(i, j)];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          ub[k][j] += f * C[i][k];
-          ub[k][i] += f * C[j][k];
-        }
-        bb[j] += f * G[i];
-        bb[i] += f * G[j];
-        ub[i][j] += f * 2.0 * itau;
-        wb[i][j] += f * (-2.0 * e2);
-        e2b += f * (-2.0 * w[i][j]);
-      }
-    // heat-flux rows: F_i = sum_l C_il b_l + 2 sum_kl C_kl u_ikl + G_i (s4 - 9 th^2)
-    //   + 2 sum_k G_k (w_ki - 3 th u_ki) + (4/(3 tau)) b_i - e2 (3 z_i - 3 th b_i - 2 sum_k u_ik b_k)
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const double f = -lam[6 + i];
-#pragma unroll
-      for (int l = 0; l < 3; ++l) bb[l] += f * C[i][l];
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int l = 0; l < 3; ++l) u3b[sym3(i, k, l)] += f * 2.0 * C[k][l];
-      s4b += f * G[i];
-      thb += f * (-18.0 * th * G[i]);
-      double ub_sum = 0.0;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        wb[k][i] += f * 2.0 * G[k];
-        ub[k][i] += f * (-6.0 * th * G[k]);
-        thb += f * (-6.0 * G[k] * u[k][i]);
-        ub[i][k] += f * (2.0 * e2 * b[k]);
-        bb[k] += f * (2.0 * e2 * u[i][k]);
-        ub_sum += u[i][k] * b[k];
-      }
-      bb[i] += f * (4.0 / 3.0) * itau;
-      zb[i] += f * (-3.0 * e2);
-      thb += f * (3.0 * e2 * b[i]);
-      bb[i] += f * (3.0 * e2 * th);
-      e2b += f * (-(3.0 * z[i] - 3.0 * th * b[i] - 2.0 * ub_sum));
-    }
-    // e2 = eps2_hat / (tau th);  b_i = sum_k u_ikk;  s4 = sum_k w_kk
-    thb += e2b * (-e2 / th);
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) u3b[sym3(i, k, k)] += bb[i];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) wb[k][k] += s4b;
-    // fold onto the moment slots
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = i; j < 3; ++j) {
-        gm[kU2 + sym2(i, j)] += ub[i][j] + (i != j ? ub[j][i] : 0.0);
-        gm[kW + sym2(i, j)] += wb[i][j] + (i != j ? wb[j][i] : 0.0);
-      }
-#pragma unroll
-    for (int s = 0; s < 10; ++s) gm[kU3 + s] += u3b[s];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) gm[kZ + i] += zb[i];
-    gm[kTheta] += thb;
+    assembly_vjp(m, Y, lam, tc, eps2_hat, gm);
   }
 #pragma unroll
   for (int k = 0; k < FP_NMOM; ++k) gm_out[c * FP_NMOM + k] = gm[k];
