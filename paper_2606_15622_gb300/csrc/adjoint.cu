@@ -30,7 +30,10 @@ namespace fpc {
 //   heat rows (i):    F = sum_l C_il b_l + 2 sum_kl C_kl u_ikl + G_i (s4 - 9 th^2)
 //                         + 2 sum_k G_k (w_ki - 3 th u_ki) + (4 / (3 tau)) b_i
 //                         - e2 (3 z_i - 3 th b_i - 2 sum_k u_ik b_k)
-// with b_i = sum_k u_ikk, s4 = sum_k w_kk, e2 = eps2_hat / (tau th).
+// with b_i = sum_k u_ikk, s4 = sum_k w_kk, e2 = eps2_hat / (tau th).  With
+// kAdd the results are added to gm, else they are stored in the 26 slots they
+// fill (the N and U slots are left as they are).
+template <bool kAdd>
 __host__ __device__ __forceinline__ void assembly_vjp(const double (&m)[FP_NMOM], const double (&Y)[9],
                                                       const double (&lam)[9], double tc, double eps2_hat,
                                                       double (&gm)[FP_NMOM]) {
@@ -49,8 +52,8 @@ __host__ __device__ __forceinline__ void assembly_vjp(const double (&m)[FP_NMOM]
 #pragma unroll
   for (int i = 0; i < 3; ++i) b[i] = m[kU3 + sym3(i, 0, 0)] + m[kU3 + sym3(i, 1, 1)] + m[kU3 + sym3(i, 2, 2)];
   const double th = m[kTheta];
-  const double e2 = eps2_hat / (tc * th);
-  const double itau = 1.0 / tc;
+  const double itau = 1.0 / tc, ith = 1.0 / th;
+  const double e2 = eps2_hat * itau * ith;
   // per-cell factors of the row adjoints
   const double itau2 = 2.0 * itau, me2x2 = -2.0 * e2, e2x2 = 2.0 * e2, mz = -3.0 * e2;
   const double kb = fma(4.0 / 3.0, itau, 3.0 * e2 * th);  // heat row i on b_i
@@ -118,7 +121,7 @@ __host__ __device__ __forceinline__ void assembly_vjp(const double (&m)[FP_NMOM]
   }
   // e2 = eps2_hat / (tau th);  b_i = sum_k u_ikk;  s4 = sum_k w_kk
   e2b = fma(-2.0, sw, e2b);
-  thb = fma(e2b, -e2 / th, thb);
+  thb = fma(e2b, -e2 * ith, thb);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -126,18 +129,24 @@ __host__ __device__ __forceinline__ void assembly_vjp(const double (&m)[FP_NMOM]
 #pragma unroll
   for (int k = 0; k < 3; ++k) wb[k][k] += s4b;
   // fold onto the moment slots
+  auto put = [&](int k, double v) {
+    if (kAdd)
+      gm[k] += v;
+    else
+      gm[k] = v;
+  };
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = i; j < 3; ++j) {
-      gm[kU2 + sym2(i, j)] += i != j ? ub[i][j] + ub[j][i] : ub[i][j];
-      gm[kW + sym2(i, j)] += i != j ? wb[i][j] + wb[j][i] : wb[i][j];
+      put(kU2 + sym2(i, j), i != j ? ub[i][j] + ub[j][i] : ub[i][j]);
+      put(kW + sym2(i, j), i != j ? wb[i][j] + wb[j][i] : wb[i][j]);
     }
 #pragma unroll
-  for (int q = 0; q < 10; ++q) gm[kU3 + q] += u3b[q];
+  for (int q = 0; q < 10; ++q) put(kU3 + q, u3b[q]);
 #pragma unroll
-  for (int i = 0; i < 3; ++i) gm[kZ + i] += zb[i];
-  gm[kTheta] += thb;
+  for (int i = 0; i < 3; ++i) put(kZ + i, zb[i]);
+  put(kTheta, thb);
 }
 
 template <bool kLU>
@@ -178,7 +187,10 @@ __device__ __forceinline__ void adjoint_cell(int64_t c, const double *__restrict
     double Y[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) Y[q] = coeffs[c * 9 + q];
-    assembly_vjp(m, Y, lam, tc, eps2_hat, gm);
+    if (gm_in)
+      assembly_vjp<true>(m, Y, lam, tc, eps2_hat, gm);
+    else
+      assembly_vjp<false>(m, Y, lam, tc, eps2_hat, gm);
   }
 #pragma unroll
   for (int k = 0; k < FP_NMOM; ++k) gm_out[c * FP_NMOM + k] = gm[k];
