@@ -402,7 +402,11 @@ int fp_adam_step(float *params, const float *grads, float *m, float *v, int64_t 
  *   grads [n_params] FP32: the gradient (written); loss_sum [1] FP32 += sum
  *   of the row losses (non-finite, with non-finite gradients, if a tensor-core
  *   wait timed out);
- *   ws >= fp_surrogate_train_step_workspace_bytes(n), 256-byte aligned. */
+ *   ws >= fp_surrogate_train_step_workspace_bytes(n), 256-byte aligned.
+ * All arrays are device memory owned by the caller except w.  Returns
+ * FP_ERR_ARG (n < 0, t < 1, n_params wrong, a null or misaligned pointer),
+ * FP_ERR_UNSUPPORTED (network shape), FP_ERR_WORKSPACE, or FP_ERR_CUDA (launch);
+ * every check precedes the first launch, and n = 0 launches nothing. */
 size_t fp_surrogate_train_step_workspace_bytes(int64_t n);
 int fp_surrogate_train_step(const fp_mlp *net, const void *x, const float *t_true, const float *aux, int64_t n,
                             const float *w, float lam_drift, float lam_energy, float scale, float *params,
